@@ -1,0 +1,175 @@
+/*
+ * bmlp.h - C ABI of the GB300 (sm_103a) Boolean Matrix Logic Programming
+ * library: bottom-up evaluation of linear dyadic recursive datalog
+ *
+ *     p(X,Y) <- r(X,Y).
+ *     p(X,Y) <- r(X,Z), p(Z,Y).
+ *
+ * as Boolean matrix algebra (paper: "Boolean Matrix Logic Programming on the
+ * GPU", Sec. 2-4). A relation over n constants is an n x n Boolean matrix R:
+ * R[i][j] = 1 iff r(c_i, c_j) holds (Sec. 3.2; constants are mapped to
+ * 0..n-1 by the caller). Boolean "+" is OR and the product is OR-of-ANDs
+ * (Sec. 2).
+ *
+ * Matrix formats (argument `fmt`):
+ *   BMLP_FMT_U8        n x n bytes, row-major, leading dimension n. Any
+ *                      nonzero input byte means 1; outputs are 0 or 1.
+ *   BMLP_FMT_PACKED64  n rows of ceil(n/64) uint64 words, row-major. Bit j of
+ *                      row i is bit (j % 64), least significant first, of word
+ *                      j / 64 (the bit code b_i of Sec. 3.2). Input bits at
+ *                      columns >= n are ignored; output padding bits are 0.
+ *
+ * Pointers: every matrix pointer may be device memory or host memory
+ * (pageable or pinned); the library detects which with
+ * cudaPointerGetAttributes and stages host buffers through its own device
+ * workspace. The caller owns all input and output buffers; the context owns
+ * its workspace. Inputs and outputs must not overlap.
+ *
+ * Streams: every call is ordered on `stream` (0 = legacy default stream).
+ * Calls with device outputs return once the work is enqueued and the fixpoint
+ * has been decided (see bmlp_options.loop); host outputs are complete on
+ * return.
+ *
+ * Errors: every entry point returns a bmlp_status; nothing is thrown across
+ * the ABI. bmlp_last_error() gives a message for the last failure on a
+ * context. A context may be used by one host thread at a time.
+ */
+#ifndef BMLP_H
+#define BMLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cudaStream_t; /* the CUDA runtime's stream handle */
+
+typedef enum bmlp_status {
+    BMLP_OK = 0,
+    BMLP_ERR_INVALID_ARG = 1,   /* null pointer with n > 0, n < 0, bad enum  */
+    BMLP_ERR_OOM = 2,           /* device workspace allocation failed        */
+    BMLP_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed         */
+    BMLP_ERR_TIMEOUT = 4,       /* a bounded in-kernel wait ran out           */
+    BMLP_ERR_NOT_CONVERGED = 5, /* fixpoint not reached within max_iters      */
+    BMLP_ERR_UNSUPPORTED = 6    /* size or variant outside what is built      */
+} bmlp_status;
+
+typedef enum bmlp_format {
+    BMLP_FMT_U8 = 0,
+    BMLP_FMT_PACKED64 = 1
+} bmlp_format;
+
+/* Which kernel family evaluates the fixpoint. Every variant returns the same
+ * bits; they differ only in speed. */
+typedef enum bmlp_variant {
+    BMLP_AUTO = 0,        /* library choice (learned dispatcher if trained)    */
+    BMLP_RMS_TC = 1,      /* repeated squaring, tcgen05 FP8 tensor-core product */
+    BMLP_RMS_PACKED = 2,  /* repeated squaring on uint64 row bitsets            */
+    BMLP_SMP_TC = 3,      /* frontier expansion, tensor-core frontier product   */
+    BMLP_SMP_PACKED = 4   /* frontier expansion on uint64 row bitsets           */
+} bmlp_variant;
+
+typedef enum bmlp_loop {
+    BMLP_LOOP_HOST = 0,   /* host loop: one product launch per iteration, the
+                             changed flag is read back after each             */
+    BMLP_LOOP_GRAPH = 1   /* device loop: the iteration runs inside a CUDA graph
+                             conditional WHILE node; no host round trip per
+                             iteration                                        */
+} bmlp_loop;
+
+typedef struct bmlp_options {
+    int32_t variant;     /* bmlp_variant                                       */
+    int32_t reflexive;   /* 0: R1+ (paths of >= 1 edge, Eq. 1); 1: I + R1+     */
+    int32_t max_iters;   /* iteration cap; 0 = the bound of Appendix C
+                            (ceil(log2 n) + 2 products for squaring, n + 1
+                            levels for frontier expansion)                     */
+    int32_t loop;        /* bmlp_loop                                          */
+    int32_t profile;     /* 1: time the product kernel with CUDA events        */
+    int32_t reserved;
+    uint64_t timeout_ns; /* bound of every in-kernel wait; 0 = 2 s             */
+} bmlp_options;
+
+/* Per-call statistics of the last call on a context. */
+typedef struct bmlp_stats {
+    int32_t iterations;        /* products (squaring) or levels (frontier)      */
+    int32_t variant;           /* variant that ran                              */
+    int32_t product_launches;  /* launches of the product kernel                */
+    int32_t launches;          /* all kernel launches of the call               */
+    int64_t n_pad;             /* padded matrix size used by the kernels        */
+    double product_ms;         /* summed device time of the product launches
+                                  (only with options.profile = 1)               */
+    double issued_ops;         /* Boolean multiply-adds issued x 2 (tensor core
+                                  path: 2 * M * N * K per tile actually run)    */
+} bmlp_stats;
+
+typedef struct bmlp_ctx bmlp_ctx;
+
+/* Create a context on CUDA device `device`. The context owns a grow-only
+ * device workspace and a few CUDA events. */
+bmlp_status bmlp_ctx_create(bmlp_ctx** ctx, int32_t device);
+
+/* Free the workspace and the context (synchronises the device first). */
+bmlp_status bmlp_ctx_destroy(bmlp_ctx* ctx);
+
+/* Message of the last failure on ctx (static storage inside ctx). */
+const char* bmlp_last_error(const bmlp_ctx* ctx);
+
+/* Fill *opts with the defaults (variant AUTO, host loop, no profiling). */
+void bmlp_default_options(bmlp_options* opts);
+
+/* Statistics of the last completed call on ctx. */
+bmlp_status bmlp_get_stats(const bmlp_ctx* ctx, bmlp_stats* out);
+
+/*
+ * bmlp_rms - all derivable groundings of r2 (BMLP-RMS, paper Sec. 3.3 Eq. 4,
+ * Algorithm 1; Def. 1 of Sec. 3.1 for the output):
+ *
+ *     out = R1+ = sum_{k>=1} R1^k        (out = I + R1+ if opts->reflexive)
+ *
+ * computed by the fixpoint R <- R + R.R started from R1 (same result as
+ * Algorithm 1's (I + R1)^(2^k) followed by one product with R1). R and out
+ * are n x n in format fmt. *iters_out (if not null) receives the number of
+ * products issued (ceil(log2 L) + 1, L the longest shortest path). n = 0 is
+ * a no-op that returns BMLP_OK.
+ * Variants: BMLP_RMS_TC, BMLP_RMS_PACKED, BMLP_SMP_PACKED (all n rows as
+ * frontiers), BMLP_AUTO.
+ */
+bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out,
+                     const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
+
+/*
+ * bmlp_smp - partially grounded queries r2(c, Y) (BMLP-SMP, paper Sec. 3.3
+ * Eq. 5, Algorithm 2):
+ *
+ *     out_q = v_q R1+     for every query row q = 0..nq-1
+ *
+ * v_q is row q of src_rows (nq rows of ceil(n/64) uint64 words, packed as
+ * above; several set bits = a union of constants). out_rows has the same
+ * layout. A source is in its own output row only if it lies on a cycle.
+ * R is n x n in format fmt. *iters_out receives the deepest frontier level.
+ * Variants: BMLP_SMP_PACKED, BMLP_SMP_TC, BMLP_AUTO.
+ */
+bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
+                     const uint64_t* src_rows, int64_t nq, uint64_t* out_rows,
+                     const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
+
+/*
+ * bmlp_compose - the general binary linear recursion of paper Sec. 3.4
+ * (Thm. 1):
+ *
+ *     p(X,Y) <- r1(X,Y).
+ *     p(X,Y) <- r2(X,Z), p(Z,Y).        out = (I + R2+) R1
+ *
+ * R1, R2 and out are n x n in format fmt over one shared constant index.
+ * *iters_out receives the products of the R2 closure. Variants: BMLP_RMS_TC
+ * (closure and final product on tensor cores), BMLP_RMS_PACKED, BMLP_AUTO.
+ */
+bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt,
+                         void* out, const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMLP_H */

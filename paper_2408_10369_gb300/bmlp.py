@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in ``include/bmlp.h`` (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_build/libbmlp.so``; there
+is no Python or CPU implementation of any step. If the library cannot be
+loaded, every call raises ``RuntimeError``.
+
+Arrays may be ``torch.Tensor`` (device or host memory) or ``numpy.ndarray``
+(host memory); their data pointers are passed through unchanged. The CUDA
+stream is the caller's ``stream`` argument, else torch's current stream for
+the context's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bmlp.h")
+
+BMLP_OK = 0
+BMLP_ERR_INVALID_ARG = 1
+BMLP_ERR_OOM = 2
+BMLP_ERR_CUDA = 3
+BMLP_ERR_TIMEOUT = 4
+BMLP_ERR_NOT_CONVERGED = 5
+BMLP_ERR_UNSUPPORTED = 6
+
+BMLP_FMT_U8 = 0
+BMLP_FMT_PACKED64 = 1
+
+BMLP_AUTO = 0
+BMLP_RMS_TC = 1
+BMLP_RMS_PACKED = 2
+BMLP_SMP_TC = 3
+BMLP_SMP_PACKED = 4
+
+BMLP_LOOP_HOST = 0
+BMLP_LOOP_GRAPH = 1
+
+VARIANTS = {"auto": BMLP_AUTO, "rms_tc": BMLP_RMS_TC, "rms_packed": BMLP_RMS_PACKED,
+            "smp_tc": BMLP_SMP_TC, "smp_packed": BMLP_SMP_PACKED}
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_CONVERGED", 6: "UNSUPPORTED"}
+
+
+class bmlp_options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("reflexive", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("loop", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("timeout_ns", ctypes.c_uint64)]
+
+
+class bmlp_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("variant", ctypes.c_int32), ("product_launches", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("n_pad", ctypes.c_int64), ("product_ms", ctypes.c_double),
+                ("issued_ops", ctypes.c_double)]
+
+
+class BmlpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("bmlp status %d (%s): %s" % (status, _STATUS.get(status, "?"), msg))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "_build", "libbmlp.so")
+
+
+def lib():
+    """Load (building first if needed) the CUDA library. Raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            try:
+                path = _build.build()
+            except Exception as e:  # no nvcc, compile error: fail loudly
+                raise RuntimeError("the bmlp CUDA library is not available: %s" % e) from e
+            L = ctypes.CDLL(path)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.bmlp_ctx_create.argtypes = [ctypes.POINTER(vp), i32]
+            L.bmlp_ctx_destroy.argtypes = [vp]
+            L.bmlp_last_error.argtypes = [vp]
+            L.bmlp_last_error.restype = ctypes.c_char_p
+            L.bmlp_default_options.argtypes = [ctypes.POINTER(bmlp_options)]
+            L.bmlp_default_options.restype = None
+            L.bmlp_get_stats.argtypes = [vp, ctypes.POINTER(bmlp_stats)]
+            L.bmlp_rms.argtypes = [vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options), ctypes.POINTER(i32), vp]
+            L.bmlp_smp.argtypes = [vp, vp, i64, i32, vp, i64, vp, ctypes.POINTER(bmlp_options),
+                                   ctypes.POINTER(i32), vp]
+            L.bmlp_compose.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
+                                       ctypes.POINTER(i32), vp]
+            for name in ("bmlp_ctx_create", "bmlp_ctx_destroy", "bmlp_get_stats", "bmlp_rms", "bmlp_smp",
+                         "bmlp_compose"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of every function declared in include/bmlp.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bmlp_\w+)\s*\(", text)))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):
+        return ctypes.c_void_p(a.ctypes.data)
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError("expected a torch.Tensor, a numpy array or an int address")
+
+
+def _stream(stream, device):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HOST, profile=False, timeout_ns=0):
+    o = bmlp_options()
+    lib().bmlp_default_options(ctypes.byref(o))
+    o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    o.reflexive = int(bool(reflexive))
+    o.max_iters = int(max_iters)
+    o.loop = int(loop)
+    o.profile = int(bool(profile))
+    o.timeout_ns = int(timeout_ns)
+    return o
+
+
+class Context:
+    """Owner of one ``bmlp_ctx`` on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        self._L = lib()
+        h = ctypes.c_void_p()
+        st = self._L.bmlp_ctx_create(ctypes.byref(h), self.device)
+        if st != BMLP_OK:
+            raise BmlpError(st, "bmlp_ctx_create(device=%d) failed" % self.device)
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.bmlp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self) -> str:
+        return self._L.bmlp_last_error(self.handle).decode()
+
+    def _check(self, st):
+        if st != BMLP_OK:
+            raise BmlpError(st, self.last_error())
+
+    def stats(self) -> dict:
+        s = bmlp_stats()
+        self._check(self._L.bmlp_get_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def rms(self, R, n, out, fmt=BMLP_FMT_U8, stream=None, **opt):
+        """bmlp_rms: out = R1+ (or I + R1+). Returns the number of products."""
+        o = make_options(**opt)
+        it = ctypes.c_int32(0)
+        self._check(self._L.bmlp_rms(self.handle, _ptr(R), int(n), int(fmt), _ptr(out), ctypes.byref(o),
+                                     ctypes.byref(it), _stream(stream, self.device)))
+        return it.value
+
+    def smp(self, R, n, src_rows, q, out_rows, fmt=BMLP_FMT_U8, stream=None, **opt):
+        """bmlp_smp: out_q = v_q R1+ for packed source rows. Returns the levels."""
+        o = make_options(**opt)
+        it = ctypes.c_int32(0)
+        self._check(self._L.bmlp_smp(self.handle, _ptr(R), int(n), int(fmt), _ptr(src_rows), int(q), _ptr(out_rows),
+                                     ctypes.byref(o), ctypes.byref(it), _stream(stream, self.device)))
+        return it.value
+
+    def compose(self, R1, R2, n, out, fmt=BMLP_FMT_U8, stream=None, **opt):
+        """bmlp_compose: out = (I + R2+) R1. Returns the closure's products."""
+        o = make_options(**opt)
+        it = ctypes.c_int32(0)
+        self._check(self._L.bmlp_compose(self.handle, _ptr(R1), _ptr(R2), int(n), int(fmt), _ptr(out),
+                                         ctypes.byref(o), ctypes.byref(it), _stream(stream, self.device)))
+        return it.value

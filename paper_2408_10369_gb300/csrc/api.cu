@@ -1,0 +1,728 @@
+// C ABI of the library (declared in include/bmlp.h): argument checks,
+// host/device staging, the fixpoint drivers of BMLP-RMS (Algorithm 1),
+// BMLP-SMP (Algorithm 2) and composition (Thm. 1), and the workspace.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace bmlp;
+
+namespace bmlp {
+
+bmlp_status set_err(bmlp_ctx* ctx, bmlp_status st, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+bmlp_status cuda_err(bmlp_ctx* ctx, cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_err(ctx, BMLP_ERR_OOM, "%s: out of device memory", what);
+    }
+    return set_err(ctx, BMLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bmlp_status ws_get(bmlp_ctx* ctx, int slot, size_t bytes, void** out) {
+    DevBuf& b = ctx->ws[slot];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaError_t e = cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+            if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFree(workspace)");
+        }
+        size_t want = bytes + bytes / 8;  // grow with headroom
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            b.p = nullptr;
+            return cuda_err(ctx, e, "cudaMalloc(workspace)");
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return BMLP_OK;
+}
+
+}  // namespace bmlp
+
+namespace {
+
+// Workspace slots.
+enum : int {
+    WS_IN0 = 0, WS_IN1 = 1, WS_OUT = 2,
+    WS_M0 = 3, WS_M1 = 4, WS_T0 = 5, WS_T1 = 6, WS_M2 = 7,
+    WS_WPTR = 8, WS_WIDX = 9, WS_WVAL = 10, WS_F0 = 11, WS_F1 = 12, WS_V = 13, WS_SRC = 14
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, what); \
+    } while (0)
+
+#define ST(call)                                  \
+    do {                                          \
+        bmlp_status s_ = (call);                  \
+        if (s_ != BMLP_OK) return s_;             \
+    } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t words_of(int64_t n) { return (n + 63) / 64; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t fmt_bytes(int32_t fmt, int64_t rows, int64_t n) {
+    return fmt == BMLP_FMT_U8 ? static_cast<size_t>(rows) * static_cast<size_t>(n)
+                              : static_cast<size_t>(rows) * static_cast<size_t>(words_of(n)) * 8;
+}
+
+// A caller's matrix: its device view (staged when the caller passed host memory).
+struct Operand {
+    const void* dev = nullptr;
+    bool host = false;
+};
+
+bmlp_status stage_in(bmlp_ctx* ctx, const void* p, size_t bytes, int slot, cudaStream_t s, Operand* o) {
+    if (is_device_ptr(p)) {
+        o->dev = p;
+        o->host = false;
+        return BMLP_OK;
+    }
+    void* d = nullptr;
+    ST(ws_get(ctx, slot, bytes, &d));
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s), "copy input to device");
+    o->dev = d;
+    o->host = true;
+    return BMLP_OK;
+}
+
+struct OutView {
+    void* dev = nullptr;
+    void* host = nullptr;
+    size_t bytes = 0;
+};
+
+bmlp_status stage_out(bmlp_ctx* ctx, void* p, size_t bytes, int slot, OutView* o) {
+    o->bytes = bytes;
+    if (is_device_ptr(p)) {
+        o->dev = p;
+        o->host = nullptr;
+        return BMLP_OK;
+    }
+    void* d = nullptr;
+    ST(ws_get(ctx, slot, bytes, &d));
+    o->dev = d;
+    o->host = p;
+    return BMLP_OK;
+}
+
+bmlp_status finish_out(bmlp_ctx* ctx, const OutView& o, cudaStream_t s) {
+    if (o.host) {
+        CK(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, s), "copy output to host");
+        CK(cudaStreamSynchronize(s), "synchronise output copy");
+    }
+    return BMLP_OK;
+}
+
+long long wait_cycles(bmlp_ctx* ctx, const bmlp_options& o) {
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+    if (khz <= 0) khz = 2100000;
+    const double ns = o.timeout_ns ? static_cast<double>(o.timeout_ns) : 2.0e9;
+    return static_cast<long long>(ns * static_cast<double>(khz) * 1e-6);
+}
+
+int log2_ceil(int64_t n) {
+    int k = 0;
+    while ((int64_t(1) << k) < n) ++k;
+    return k;
+}
+
+// Reads the control words after one iteration; maps device error words.
+bmlp_status read_ctl(bmlp_ctx* ctx, cudaStream_t s, int* changed) {
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, CTL_WORDS * sizeof(int), cudaMemcpyDeviceToHost, s), "read flags");
+    CK(cudaStreamSynchronize(s), "synchronise iteration");
+    if (ctx->h_ctl[CTL_ERROR] != 0)
+        return set_err(ctx, BMLP_ERR_TIMEOUT, "in-kernel wait timed out (code 0x%x)", ctx->h_ctl[CTL_ERROR]);
+    if (changed) *changed = ctx->h_ctl[CTL_CHANGED];
+    return BMLP_OK;
+}
+
+struct ProductTimer {
+    bmlp_ctx* ctx;
+    bool on;
+    cudaStream_t s;
+    bmlp_status begin() {
+        if (on) CK(cudaEventRecord(ctx->ev[0], s), "event record");
+        return BMLP_OK;
+    }
+    bmlp_status end() {
+        if (on) CK(cudaEventRecord(ctx->ev[1], s), "event record");
+        return BMLP_OK;
+    }
+    bmlp_status collect() {  // after the stream was synchronised
+        if (!on) return BMLP_OK;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "event elapsed");
+        ctx->stats.product_ms += ms;
+        return BMLP_OK;
+    }
+};
+
+// ------------------------------------------------------------------------
+// Tensor-core squaring fixpoint on E4M3 R / R^T buffers already encoded in
+// (M[0], T[0]). On return *res points at the buffer holding R1+ (and *res_t at
+// its transpose).
+bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
+                        const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t) {
+    CUtensorMap mapA[2], mapB[2];
+    for (int b = 0; b < 2; ++b) {
+        ST(make_tmap(ctx, &mapA[b], M[b], n_pad, n_pad, n_pad, TC_BM));
+        ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, TC_BN));
+    }
+    TcParams p{};
+    p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+    p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+    p.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
+    p.mode = TC_MODE_RMS;
+    p.ld = n_pad;
+    p.changed = ctx->d_ctl + CTL_CHANGED;
+    p.error = ctx->d_ctl + CTL_ERROR;
+    p.wait_cycles = wait_cycles(ctx, o);
+    const int tiles = p.m_tiles * p.n_tiles;
+    const int grid = tiles < ctx->sm_count ? tiles : ctx->sm_count;
+    ProductTimer tm{ctx, o.profile != 0, s};
+    int cur = 0;
+    *iters = 0;
+    for (int it = 0; it < max_iters; ++it) {
+        const int nxt = cur ^ 1;
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        p.old_r = M[cur];
+        p.out_r = M[nxt];
+        p.out_rt = T[nxt];
+        ST(tm.begin());
+        CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
+        ST(tm.end());
+        ctx->stats.product_launches++;
+        ctx->stats.launches += 2;
+        ctx->stats.issued_ops += 2.0 * double(n_pad) * double(n_pad) * double(n_pad);
+        int changed = 0;
+        ST(read_ctl(ctx, s, &changed));
+        ST(tm.collect());
+        *iters = it + 1;
+        cur = nxt;
+        if (!changed) {
+            *res = M[cur];
+            *res_t = T[cur];
+            return BMLP_OK;
+        }
+    }
+    *res = M[cur];
+    *res_t = T[cur];
+    return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
+}
+
+// Packed squaring fixpoint on P[0] (n rows x ldw words). *res = R1+.
+bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2], int max_iters,
+                            const bmlp_options& o, cudaStream_t s, int* iters, uint64_t** res) {
+    ProductTimer tm{ctx, o.profile != 0, s};
+    int cur = 0;
+    *iters = 0;
+    for (int it = 0; it < max_iters; ++it) {
+        const int nxt = cur ^ 1;
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        ST(tm.begin());
+        CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s),
+           "packed product launch");
+        ST(tm.end());
+        ctx->stats.product_launches++;
+        ctx->stats.launches += 2;
+        int changed = 0;
+        ST(read_ctl(ctx, s, &changed));
+        ST(tm.collect());
+        *iters = it + 1;
+        cur = nxt;
+        if (!changed) {
+            *res = P[cur];
+            return BMLP_OK;
+        }
+    }
+    *res = P[cur];
+    return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
+}
+
+// Packed copy of a caller matrix (any format) into n x ldw words.
+bmlp_status to_packed(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, uint64_t* P, int64_t ldw,
+                      cudaStream_t s) {
+    if (fmt == BMLP_FMT_U8)
+        launch_u8_to_packed(static_cast<const uint8_t*>(in.dev), n, P, ldw, s);
+    else
+        launch_packed_copy(static_cast<const uint64_t*>(in.dev), words_of(n), n, n, P, ldw, 0, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "encode launch");
+    return BMLP_OK;
+}
+
+// E4M3 R and R^T (n_pad) of a caller matrix.
+bmlp_status to_e4m3(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad,
+                    cudaStream_t s) {
+    if (fmt == BMLP_FMT_U8)
+        launch_u8_to_e4m3(static_cast<const uint8_t*>(in.dev), n, R, RT, n_pad, s);
+    else
+        launch_packed_to_e4m3(static_cast<const uint64_t*>(in.dev), words_of(n), n, n, R, RT, n_pad, n_pad, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "encode launch");
+    return BMLP_OK;
+}
+
+bmlp_status bytes_out(bmlp_ctx* ctx, const uint8_t* R, int64_t ld, int64_t n, int32_t fmt, void* out, int reflexive,
+                      cudaStream_t s) {
+    if (fmt == BMLP_FMT_U8)
+        launch_bytes_to_u8(R, ld, n, static_cast<uint8_t*>(out), reflexive, s);
+    else
+        launch_bytes_to_packed(R, ld, n, n, static_cast<uint64_t*>(out), words_of(n), reflexive, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "decode launch");
+    return BMLP_OK;
+}
+
+bmlp_status packed_out(bmlp_ctx* ctx, const uint64_t* P, int64_t ldw, int64_t n, int32_t fmt, void* out, int reflexive,
+                       cudaStream_t s) {
+    if (fmt == BMLP_FMT_U8)
+        launch_packed_to_u8(P, ldw, n, static_cast<uint8_t*>(out), reflexive, s);
+    else
+        launch_packed_copy(P, ldw, n, n, static_cast<uint64_t*>(out), words_of(n), reflexive, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "decode launch");
+    return BMLP_OK;
+}
+
+bmlp_options resolve(const bmlp_options* o) {
+    bmlp_options r;
+    bmlp_default_options(&r);
+    if (o) r = *o;
+    return r;
+}
+
+void reset_stats(bmlp_ctx* ctx, int variant, int64_t n_pad) {
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.variant = variant;
+    ctx->stats.n_pad = n_pad;
+}
+
+int pick_variant_rms(int64_t n) { return n >= 1024 ? BMLP_RMS_TC : BMLP_RMS_PACKED; }
+
+// Frontier expansion (Algorithm 2) on packed rows for the sources `src`
+// (device, q x ldw_src words). out: device, q x ldw_out words.
+bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t n, const uint64_t* src,
+                           int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out, const bmlp_options& o,
+                           cudaStream_t s, int* levels) {
+    const int64_t ldw = round_up(words_of(n), 2);
+    if (ldw > smp_packed_max_words())
+        return set_err(ctx, BMLP_ERR_UNSUPPORTED, "packed frontier path supports n <= %d", smp_packed_max_words() * 64);
+    void *P = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
+    ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &P));
+    ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 1) * 8), &wptr));
+    ST(ws_get(ctx, WS_WIDX, static_cast<size_t>(n * ldw * 4), &widx));
+    ST(ws_get(ctx, WS_WVAL, static_cast<size_t>(n * ldw * 8), &wval));
+    ST(to_packed(ctx, R, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+    CK(launch_wcsr_build(static_cast<uint64_t*>(P), n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                         static_cast<uint64_t*>(wval), s),
+       "word index build");
+    ctx->stats.launches += 3;
+    CK(cudaMemsetAsync(ctx->d_ctl, 0, CTL_WORDS * sizeof(int), s), "reset flags");
+    ProductTimer tm{ctx, o.profile != 0, s};
+    ST(tm.begin());
+    CK(launch_smp_packed(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval), n, ldw,
+                         src, ldw_src, q, out, ldw_out, ctx->d_ctl + CTL_LEVELS, ctx->d_ctl + CTL_QCOUNT, o.reflexive,
+                         ctx->sm_count, s),
+       "frontier kernel launch");
+    ST(tm.end());
+    ctx->stats.product_launches++;
+    ctx->stats.launches++;
+    ST(read_ctl(ctx, s, nullptr));
+    ST(tm.collect());
+    *levels = ctx->h_ctl[CTL_LEVELS];
+    const int cap = o.max_iters > 0 ? o.max_iters : static_cast<int>(n + 1);
+    if (*levels > cap) return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "frontier did not empty within %d levels", cap);
+    return BMLP_OK;
+}
+
+// Frontier expansion with the tensor-core frontier product. src/out packed.
+bmlp_status smp_tc_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t n, const uint64_t* src, int64_t ldw_src,
+                       int64_t q, uint64_t* out, int64_t ldw_out, const bmlp_options& o, cudaStream_t s, int* levels) {
+    const int64_t n_pad = round_up(n, TC_PAD);
+    const int64_t q_pad = round_up(q, TC_BM);
+    ctx->stats.n_pad = n_pad;
+    void *Rs = nullptr, *RT = nullptr, *D0 = nullptr, *D1 = nullptr, *V = nullptr, *F0 = nullptr, *F1 = nullptr;
+    ST(ws_get(ctx, WS_M0, static_cast<size_t>(n_pad * n_pad), &Rs));
+    ST(ws_get(ctx, WS_T0, static_cast<size_t>(n_pad * n_pad), &RT));
+    ST(ws_get(ctx, WS_M1, static_cast<size_t>(q_pad * n_pad), &D0));
+    ST(ws_get(ctx, WS_T1, static_cast<size_t>(q_pad * n_pad), &D1));
+    ST(ws_get(ctx, WS_V, static_cast<size_t>(q_pad * n_pad), &V));
+    const int64_t kb = n_pad / TC_BK, mbs = q_pad / TC_BM;
+    ST(ws_get(ctx, WS_F0, static_cast<size_t>(mbs * kb), &F0));
+    ST(ws_get(ctx, WS_F1, static_cast<size_t>(mbs * kb), &F1));
+    ST(to_e4m3(ctx, R, fmt, n, static_cast<uint8_t*>(Rs), static_cast<uint8_t*>(RT), n_pad, s));
+    launch_packed_to_e4m3(src, ldw_src, q, n, static_cast<uint8_t*>(D0), nullptr, n_pad, q_pad, s);
+    CK(cudaMemsetAsync(V, 0, static_cast<size_t>(q_pad * n_pad), s), "clear visited");
+    launch_block_flags(static_cast<uint8_t*>(D0), n_pad, q_pad, n_pad, static_cast<uint8_t*>(F0), s);
+    ctx->stats.launches += 2;
+    CK(cudaGetLastError(), "frontier encode");
+    uint8_t* D[2] = {static_cast<uint8_t*>(D0), static_cast<uint8_t*>(D1)};
+    uint8_t* F[2] = {static_cast<uint8_t*>(F0), static_cast<uint8_t*>(F1)};
+    CUtensorMap mapA[2], mapB;
+    ST(make_tmap(ctx, &mapA[0], D[0], q_pad, n_pad, n_pad, TC_BM));
+    ST(make_tmap(ctx, &mapA[1], D[1], q_pad, n_pad, n_pad, TC_BM));
+    ST(make_tmap(ctx, &mapB, RT, n_pad, n_pad, n_pad, TC_BN));
+    TcParams p{};
+    p.m_tiles = static_cast<int32_t>(mbs);
+    p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+    p.k_blocks = static_cast<int32_t>(kb);
+    p.mode = TC_MODE_SMP;
+    p.ld = n_pad;
+    p.visited = static_cast<uint8_t*>(V);
+    p.changed = ctx->d_ctl + CTL_CHANGED;
+    p.error = ctx->d_ctl + CTL_ERROR;
+    p.wait_cycles = wait_cycles(ctx, o);
+    const int tiles = p.m_tiles * p.n_tiles;
+    const int grid = tiles < ctx->sm_count ? tiles : ctx->sm_count;
+    const int cap = o.max_iters > 0 ? o.max_iters : static_cast<int>(n + 1);
+    ProductTimer tm{ctx, o.profile != 0, s};
+    int cur = 0;
+    *levels = 0;
+    bool converged = false;
+    for (int lv = 0; lv < cap + 1; ++lv) {
+        const int nxt = cur ^ 1;
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        CK(cudaMemsetAsync(F[nxt], 0, static_cast<size_t>(mbs * kb), s), "reset block flags");
+        p.kflags = F[cur];
+        p.kflags_next = F[nxt];
+        p.out_r = D[nxt];
+        ST(tm.begin());
+        CK(launch_tc_product(mapA[cur], mapB, p, grid, s), "tensor-core frontier launch");
+        ST(tm.end());
+        ctx->stats.product_launches++;
+        ctx->stats.launches += 3;
+        int changed = 0;
+        ST(read_ctl(ctx, s, &changed));
+        ST(tm.collect());
+        *levels = lv + 1;
+        cur = nxt;
+        if (!changed) {
+            converged = true;
+            break;
+        }
+    }
+    launch_bytes_to_packed(static_cast<uint8_t*>(V), n_pad, q, n, out, ldw_out, 0, s);
+    ctx->stats.launches++;
+    if (o.reflexive) launch_packed_or(out, ldw_out, src, ldw_src, q, n, s);
+    CK(cudaGetLastError(), "decode launch");
+    if (!converged) return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "frontier did not empty within %d levels", cap);
+    return BMLP_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI ===
+extern "C" {
+
+void bmlp_default_options(bmlp_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->variant = BMLP_AUTO;
+    o->loop = BMLP_LOOP_HOST;
+}
+
+bmlp_status bmlp_ctx_create(bmlp_ctx** out, int32_t device) {
+    if (!out) return BMLP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return BMLP_ERR_INVALID_ARG;
+    }
+    bmlp_ctx* ctx = new (std::nothrow) bmlp_ctx();
+    if (!ctx) return BMLP_ERR_OOM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        bmlp_ctx_destroy(ctx);
+        return BMLP_ERR_OOM;
+    }
+    cudaMemset(ctx->d_ctl, 0, CTL_WORDS * sizeof(int));
+    *out = ctx;
+    return BMLP_OK;
+}
+
+bmlp_status bmlp_ctx_destroy(bmlp_ctx* ctx) {
+    if (!ctx) return BMLP_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& b : ctx->ws)
+        if (b.p) cudaFree(b.p);
+    if (ctx->d_ctl) cudaFree(ctx->d_ctl);
+    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    return BMLP_OK;
+}
+
+const char* bmlp_last_error(const bmlp_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+bmlp_status bmlp_get_stats(const bmlp_ctx* ctx, bmlp_stats* out) {
+    if (!ctx || !out) return BMLP_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return BMLP_OK;
+}
+
+bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+                     int32_t* iters_out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (iters_out) *iters_out = 0;
+    if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n == 0) return BMLP_OK;
+    if (!R || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    DeviceGuard g(ctx->device);
+    bmlp_options o = resolve(opts);
+    int variant = o.variant == BMLP_AUTO ? pick_variant_rms(n) : o.variant;
+    reset_stats(ctx, variant, n);
+    const int max_iters = o.max_iters > 0 ? o.max_iters : log2_ceil(n) + 2;
+    Operand in;
+    OutView ov;
+    ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    int iters = 0;
+    bmlp_status st = BMLP_OK;
+    if (variant == BMLP_RMS_TC) {
+        const int64_t n_pad = round_up(n, TC_PAD);
+        ctx->stats.n_pad = n_pad;
+        void* b[4];
+        const size_t bytes = static_cast<size_t>(n_pad * n_pad);
+        ST(ws_get(ctx, WS_M0, bytes, &b[0]));
+        ST(ws_get(ctx, WS_M1, bytes, &b[1]));
+        ST(ws_get(ctx, WS_T0, bytes, &b[2]));
+        ST(ws_get(ctx, WS_T1, bytes, &b[3]));
+        uint8_t* M[2] = {static_cast<uint8_t*>(b[0]), static_cast<uint8_t*>(b[1])};
+        uint8_t* T[2] = {static_cast<uint8_t*>(b[2]), static_cast<uint8_t*>(b[3])};
+        ST(to_e4m3(ctx, in, fmt, n, M[0], T[0], n_pad, s));
+        uint8_t *res = nullptr, *res_t = nullptr;
+        st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
+        if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) ST(bytes_out(ctx, res, n_pad, n, fmt, ov.dev, o.reflexive, s));
+    } else if (variant == BMLP_RMS_PACKED) {
+        const int64_t ldw = round_up(words_of(n), 2);
+        ctx->stats.n_pad = ldw * 64;
+        void* b[2];
+        ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &b[0]));
+        ST(ws_get(ctx, WS_M1, static_cast<size_t>(n * ldw * 8), &b[1]));
+        uint64_t* P[2] = {static_cast<uint64_t*>(b[0]), static_cast<uint64_t*>(b[1])};
+        ST(to_packed(ctx, in, fmt, n, P[0], ldw, s));
+        uint64_t* res = nullptr;
+        st = rms_packed_loop(ctx, n, ldw, P, max_iters, o, s, &iters, &res);
+        if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) ST(packed_out(ctx, res, ldw, n, fmt, ov.dev, o.reflexive, s));
+    } else if (variant == BMLP_SMP_PACKED || variant == BMLP_SMP_TC) {
+        // the full closure as n selective queries, one per constant
+        const int64_t ldw_src = words_of(n);
+        void *src = nullptr, *dst = nullptr;
+        ST(ws_get(ctx, WS_SRC, static_cast<size_t>(n * ldw_src * 8), &src));
+        launch_identity_packed(static_cast<uint64_t*>(src), ldw_src, n, s);
+        ctx->stats.launches++;
+        uint64_t* outp = nullptr;
+        if (fmt == BMLP_FMT_PACKED64) {
+            outp = static_cast<uint64_t*>(ov.dev);
+        } else {
+            ST(ws_get(ctx, WS_M2, static_cast<size_t>(n * ldw_src * 8), &dst));
+            outp = static_cast<uint64_t*>(dst);
+        }
+        bmlp_options o2 = o;
+        o2.reflexive = 0;
+        o2.max_iters = 0;
+        if (variant == BMLP_SMP_PACKED)
+            st = smp_packed_run(ctx, in, fmt, n, static_cast<uint64_t*>(src), ldw_src, n, outp, ldw_src, o2, s, &iters);
+        else
+            st = smp_tc_run(ctx, in, fmt, n, static_cast<uint64_t*>(src), ldw_src, n, outp, ldw_src, o2, s, &iters);
+        if (st == BMLP_OK) {
+            if (fmt == BMLP_FMT_U8)
+                launch_packed_to_u8(outp, ldw_src, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
+            else if (o.reflexive)
+                launch_packed_copy(outp, ldw_src, n, n, outp, ldw_src, 1, s);
+            ctx->stats.launches++;
+            CK(cudaGetLastError(), "decode launch");
+        }
+    } else {
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a closure variant", variant);
+    }
+    ctx->stats.iterations = iters;
+    if (iters_out) *iters_out = iters;
+    if (st != BMLP_OK) return st;
+    return finish_out(ctx, ov, s);
+}
+
+bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
+                     uint64_t* out_rows, const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (iters_out) *iters_out = 0;
+    if (n < 0 || q < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "negative size");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n == 0 || q == 0) return BMLP_OK;
+    if (!R || !src_rows || !out_rows) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null pointer");
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    DeviceGuard g(ctx->device);
+    bmlp_options o = resolve(opts);
+    int variant = o.variant == BMLP_AUTO ? BMLP_SMP_PACKED : o.variant;
+    if (variant != BMLP_SMP_PACKED && variant != BMLP_SMP_TC)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a frontier variant", variant);
+    reset_stats(ctx, variant, n);
+    const int64_t ldw = words_of(n);
+    Operand in, src;
+    OutView ov;
+    ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
+    ST(stage_in(ctx, src_rows, static_cast<size_t>(q * ldw * 8), WS_IN1, s, &src));
+    ST(stage_out(ctx, out_rows, static_cast<size_t>(q * ldw * 8), WS_OUT, &ov));
+    int levels = 0;
+    bmlp_status st;
+    if (variant == BMLP_SMP_PACKED)
+        st = smp_packed_run(ctx, in, fmt, n, static_cast<const uint64_t*>(src.dev), ldw, q,
+                            static_cast<uint64_t*>(ov.dev), ldw, o, s, &levels);
+    else
+        st = smp_tc_run(ctx, in, fmt, n, static_cast<const uint64_t*>(src.dev), ldw, q, static_cast<uint64_t*>(ov.dev),
+                        ldw, o, s, &levels);
+    ctx->stats.iterations = levels;
+    if (iters_out) *iters_out = levels;
+    if (st != BMLP_OK) return st;
+    return finish_out(ctx, ov, s);
+}
+
+bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt, void* out,
+                         const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (iters_out) *iters_out = 0;
+    if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n == 0) return BMLP_OK;
+    if (!R1 || !R2 || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    DeviceGuard g(ctx->device);
+    bmlp_options o = resolve(opts);
+    int variant = o.variant == BMLP_AUTO ? pick_variant_rms(n) : o.variant;
+    if (variant != BMLP_RMS_TC && variant != BMLP_RMS_PACKED)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a composition variant", variant);
+    reset_stats(ctx, variant, n);
+    const int max_iters = o.max_iters > 0 ? o.max_iters : log2_ceil(n) + 2;
+    Operand a, b;
+    OutView ov;
+    ST(stage_in(ctx, R1, fmt_bytes(fmt, n, n), WS_IN0, s, &a));
+    ST(stage_in(ctx, R2, fmt_bytes(fmt, n, n), WS_IN1, s, &b));
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    int iters = 0;
+    bmlp_status st;
+    if (variant == BMLP_RMS_TC) {
+        const int64_t n_pad = round_up(n, TC_PAD);
+        ctx->stats.n_pad = n_pad;
+        const size_t bytes = static_cast<size_t>(n_pad * n_pad);
+        void* bb[5];
+        ST(ws_get(ctx, WS_M0, bytes, &bb[0]));
+        ST(ws_get(ctx, WS_M1, bytes, &bb[1]));
+        ST(ws_get(ctx, WS_T0, bytes, &bb[2]));
+        ST(ws_get(ctx, WS_T1, bytes, &bb[3]));
+        ST(ws_get(ctx, WS_M2, bytes, &bb[4]));
+        uint8_t* M[2] = {static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[1])};
+        uint8_t* T[2] = {static_cast<uint8_t*>(bb[2]), static_cast<uint8_t*>(bb[3])};
+        uint8_t* X = static_cast<uint8_t*>(bb[4]);
+        ST(to_e4m3(ctx, b, fmt, n, M[0], T[0], n_pad, s));
+        uint8_t *res = nullptr, *res_t = nullptr;
+        st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
+        if (st != BMLP_OK) return st;
+        // A = I + R2+ (row-major, in res); B^T = R1^T (written into the other R^T buffer)
+        launch_set_diag_e4m3(res, n_pad, n, s);
+        uint8_t* r1t = (res_t == T[0]) ? T[1] : T[0];
+        uint8_t* r1 = (res == M[0]) ? M[1] : M[0];
+        ST(to_e4m3(ctx, a, fmt, n, r1, r1t, n_pad, s));
+        CUtensorMap mapA, mapB;
+        ST(make_tmap(ctx, &mapA, res, n_pad, n_pad, n_pad, TC_BM));
+        ST(make_tmap(ctx, &mapB, r1t, n_pad, n_pad, n_pad, TC_BN));
+        TcParams p{};
+        p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+        p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+        p.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
+        p.mode = TC_MODE_PLAIN;
+        p.ld = n_pad;
+        p.out_r = X;
+        p.changed = ctx->d_ctl + CTL_CHANGED;
+        p.error = ctx->d_ctl + CTL_ERROR;
+        p.wait_cycles = wait_cycles(ctx, o);
+        const int tiles = p.m_tiles * p.n_tiles;
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        CK(launch_tc_product(mapA, mapB, p, tiles < ctx->sm_count ? tiles : ctx->sm_count, s), "product launch");
+        ctx->stats.product_launches++;
+        ctx->stats.launches += 3;
+        ST(read_ctl(ctx, s, nullptr));
+        ST(bytes_out(ctx, X, n_pad, n, fmt, ov.dev, 0, s));
+    } else {
+        const int64_t ldw = round_up(words_of(n), 2);
+        ctx->stats.n_pad = ldw * 64;
+        const size_t bytes = static_cast<size_t>(n * ldw * 8);
+        void* bb[4];
+        ST(ws_get(ctx, WS_M0, bytes, &bb[0]));
+        ST(ws_get(ctx, WS_M1, bytes, &bb[1]));
+        ST(ws_get(ctx, WS_T0, bytes, &bb[2]));
+        ST(ws_get(ctx, WS_T1, bytes, &bb[3]));
+        uint64_t* P[2] = {static_cast<uint64_t*>(bb[0]), static_cast<uint64_t*>(bb[1])};
+        uint64_t* A1 = static_cast<uint64_t*>(bb[2]);
+        uint64_t* X = static_cast<uint64_t*>(bb[3]);
+        ST(to_packed(ctx, b, fmt, n, P[0], ldw, s));
+        uint64_t* res = nullptr;
+        st = rms_packed_loop(ctx, n, ldw, P, max_iters, o, s, &iters, &res);
+        if (st != BMLP_OK) return st;
+        launch_packed_copy(res, ldw, n, n, res, ldw, 1, s);  // I + R2+
+        ST(to_packed(ctx, a, fmt, n, A1, ldw, s));
+        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        CK(launch_product_packed(res, A1, X, n, ldw, 0, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s), "product launch");
+        ctx->stats.product_launches++;
+        ctx->stats.launches += 2;
+        ST(read_ctl(ctx, s, nullptr));
+        ST(packed_out(ctx, X, ldw, n, fmt, ov.dev, 0, s));
+    }
+    ctx->stats.iterations = iters;
+    if (iters_out) *iters_out = iters;
+    return finish_out(ctx, ov, s);
+}
+
+}  // extern "C"

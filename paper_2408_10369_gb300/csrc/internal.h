@@ -1,0 +1,128 @@
+// Library-internal declarations shared by the C ABI and the kernel files.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/bmlp.h"
+
+// e4m3 encoding of 1.0 (sign 0, exponent 0111, mantissa 000) used for the
+// 0/1 tensor-core operands.
+#define BMLP_E4M3_ONE 0x38
+
+namespace bmlp {
+
+// Tile shape of the tensor-core product: BM x BN output tile, BK bytes
+// (= E4M3 elements) of the reduction dimension per pipeline stage.
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_BK = 128;
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int TC_PAD = 256;       // matrices are padded to a multiple of this
+
+// Epilogue modes of the tensor-core product kernel.
+enum TcMode : int {
+    TC_MODE_RMS = 0,    // out = old | (C > 0), also writes out^T; changed flag
+    TC_MODE_SMP = 1,    // N = (C > 0) & ~V ; V |= N ; next = N; block flags
+    TC_MODE_PLAIN = 2   // out = (C > 0)
+};
+
+struct TcParams {
+    int32_t m_tiles, n_tiles, k_blocks;
+    int32_t mode;
+    int64_t ld;                 // row stride (bytes) of every 8-bit matrix
+    const uint8_t* old_r;       // RMS: R of this iteration (row-major)
+    uint8_t* out_r;             // RMS: new R; SMP: next frontier; PLAIN: output
+    uint8_t* out_rt;            // RMS: new R^T
+    uint8_t* visited;           // SMP: V (row-major, 0 / 1 bytes)
+    const uint8_t* kflags;      // SMP: nonzero flag per (M block, K block) of A, or null
+    uint8_t* kflags_next;       // SMP: flags for the next frontier
+    int* changed;               // set to 1 when any output bit changed / is new
+    int* error;                 // set to a nonzero code when a wait timed out
+    long long wait_cycles;      // bound of each in-kernel wait
+};
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace bmlp
+
+struct bmlp_ctx {
+    int device = 0;
+    int sm_count = 0;
+    char err[512] = {0};
+    bmlp::DevBuf ws[16];
+    int* d_ctl = nullptr;        // device control words (see CTL_* below)
+    int* h_ctl = nullptr;        // pinned host mirror
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bmlp_stats stats{};
+    void* encode_fn = nullptr;   // cuTensorMapEncodeTiled from the driver
+};
+
+namespace bmlp {
+
+enum CtlWord : int { CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_WORDS = 16 };
+
+// ---- workspace / error helpers (api.cu)
+bmlp_status set_err(bmlp_ctx* ctx, bmlp_status st, const char* fmt, ...);
+bmlp_status cuda_err(bmlp_ctx* ctx, cudaError_t e, const char* what);
+bmlp_status ws_get(bmlp_ctx* ctx, int slot, size_t bytes, void** out);
+
+// ---- encoders / decoders (encode.cu). All launched on `s`.
+// u8 (any nonzero = 1) n x n, ld = n  ->  E4M3 0/1 R and R^T, n_pad x n_pad
+void launch_u8_to_e4m3(const uint8_t* in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad, cudaStream_t s);
+// packed rows (ldw_in words) -> E4M3 R and R^T (RT may be null)
+void launch_packed_to_e4m3(const uint64_t* in, int64_t ldw_in, int64_t rows, int64_t n, uint8_t* R, uint8_t* RT,
+                           int64_t n_pad, int64_t rows_pad, cudaStream_t s);
+// E4M3 / 0-1 bytes (ld) -> u8 n x n (diagonal forced to 1 when reflexive)
+void launch_bytes_to_u8(const uint8_t* R, int64_t ld, int64_t n, uint8_t* out, int reflexive, cudaStream_t s);
+// E4M3 / 0-1 bytes (ld) -> packed rows (ldw_out words), rows x n
+void launch_bytes_to_packed(const uint8_t* R, int64_t ld, int64_t rows, int64_t n, uint64_t* out, int64_t ldw_out,
+                            int reflexive, cudaStream_t s);
+// u8 n x n -> packed rows
+void launch_u8_to_packed(const uint8_t* in, int64_t n, uint64_t* out, int64_t ldw_out, cudaStream_t s);
+// packed (ldw_in) -> packed (ldw_out), masking bits >= n, optional diagonal
+void launch_packed_copy(const uint64_t* in, int64_t ldw_in, int64_t rows, int64_t n, uint64_t* out, int64_t ldw_out,
+                        int reflexive, cudaStream_t s);
+// packed -> u8 n x n
+void launch_packed_to_u8(const uint64_t* in, int64_t ldw, int64_t n, uint8_t* out, int reflexive, cudaStream_t s);
+// out rows |= src rows (bits < n)
+void launch_packed_or(uint64_t* out, int64_t ldw_out, const uint64_t* src, int64_t ldw_src, int64_t rows, int64_t n,
+                      cudaStream_t s);
+// identity as packed rows: row i has only bit i
+void launch_identity_packed(uint64_t* out, int64_t ldw, int64_t n, cudaStream_t s);
+// set the diagonal of an n x n byte matrix (ld) to E4M3 one
+void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s);
+// per (M block, K block) nonzero flags of a byte matrix rows_pad x n_pad
+void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t n_pad, uint8_t* flags,
+                        cudaStream_t s);
+
+// ---- tensor-core product (tc_product.cu)
+// Set up tensor maps for A (rows x K) and B^T (cols x K) byte matrices.
+bmlp_status make_tmap(bmlp_ctx* ctx, CUtensorMap* map, const void* base, int64_t rows, int64_t cols_bytes,
+                      int64_t ld, int box_rows);
+int tc_smem_bytes();
+cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int grid,
+                              cudaStream_t s);
+
+// ---- packed kernels (packed.cu)
+// dst_i = (or_a ? A_i : 0) | OR_{k : A_ik = 1} B_k over n packed rows of ldw
+// words; raises *changed when dst_i != A_i. With A = B and or_a = 1 this is
+// one squaring step R <- R + R R.
+cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
+                                  int or_a, int* changed, int sms, cudaStream_t s);
+// word-CSR of packed rows: counts -> (exclusive scan by caller kernel) -> fill
+// (widx / wval must hold n * ldw entries: the dense worst case)
+cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx,
+                              uint64_t* wval, cudaStream_t s);
+cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                              int64_t ldw, const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out,
+                              int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s);
+int smp_packed_max_words();
+
+}  // namespace bmlp

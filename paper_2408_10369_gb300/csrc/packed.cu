@@ -1,0 +1,313 @@
+// Bit-packed kernels: rows of R are uint64 bit codes (paper Sec. 3.2, bit j
+// of row i = R_ij, least significant bit first).
+//
+//  * product_packed  one Boolean product on bitsets, C_i = OR_{k : A_ik = 1} B_k,
+//                 optionally OR-ed with A_i; with A = B = R that is one
+//                 squaring step of Eq. 4: C_i = R_i | OR_{k : R_ik = 1} R_k.
+//                 One warp per row i; the set bits k of A_i are enumerated
+//                 with warp ballots and find-first-set, and row k is OR-ed in
+//                 with coalesced 128-bit loads into per-lane registers.
+//  * wcsr_build   the nonzero words of every row (word index + value), so
+//                 that frontier expansion touches only words that hold bits.
+//  * smp_packed   the selective product of Eq. 5 / Algorithm 2 per query row:
+//                 D = v; V = 0; repeat N = (OR_{k in D} R_k) & ~V; V |= N;
+//                 D = N until D is empty; out = V = v R+.
+//                 One warp per query row, frontier / visited / next bitsets in
+//                 shared memory, all frontier levels of a query in one launch
+//                 (queries are independent, so no grid-wide step is needed;
+//                 a warp takes the next query from a global counter when its
+//                 query has converged).
+#include "internal.h"
+
+namespace bmlp {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void or4(uint4& a, const uint4& b) {
+    a.x |= b.x;
+    a.y |= b.y;
+    a.z |= b.z;
+    a.w |= b.w;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                                                             uint64_t* __restrict__ dst, int64_t n, int64_t ldw, int or_a,
+                                                             int* changed) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t chunk_words = 64 * VEC;  // 32 lanes x VEC x 2 words
+    uint32_t any = 0;
+    for (int64_t i = warp_id; i < n; i += nwarps) {
+        const uint64_t* arow = A + i * ldw;
+        for (int64_t c0 = 0; c0 < ldw; c0 += chunk_words) {
+            uint4 acc[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t w = c0 + 2 * (lane + 32 * v);
+                acc[v] = (or_a && w < ldw) ? *reinterpret_cast<const uint4*>(arow + w) : make_uint4(0, 0, 0, 0);
+            }
+            for (int64_t wb = 0; wb < ldw; wb += 32) {
+                const uint64_t aw = (wb + lane < ldw) ? arow[wb + lane] : 0ull;
+                unsigned m = __ballot_sync(FULL, aw != 0ull);
+                while (m) {
+                    const int sl = __ffs(m) - 1;
+                    m &= m - 1;
+                    uint64_t bits = __shfl_sync(FULL, aw, sl);
+                    const int64_t kbase = (wb + sl) * 64;
+                    while (bits) {
+                        const int b0 = __ffsll(static_cast<long long>(bits)) - 1;
+                        bits &= bits - 1;
+                        int b1 = -1;
+                        if (bits) {
+                            b1 = __ffsll(static_cast<long long>(bits)) - 1;
+                            bits &= bits - 1;
+                        }
+                        const uint64_t* r0 = B + (kbase + b0) * ldw + c0;
+                        const uint64_t* r1 = B + (kbase + (b1 < 0 ? b0 : b1)) * ldw + c0;
+                        uint4 x0[VEC], x1[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const int64_t w = 2 * (lane + 32 * v);
+                            if (c0 + w < ldw) {
+                                x0[v] = __ldg(reinterpret_cast<const uint4*>(r0 + w));
+                                x1[v] = __ldg(reinterpret_cast<const uint4*>(r1 + w));
+                            } else {
+                                x0[v] = make_uint4(0, 0, 0, 0);
+                                x1[v] = x0[v];
+                            }
+                        }
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            or4(acc[v], x0[v]);
+                            or4(acc[v], x1[v]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t w = c0 + 2 * (lane + 32 * v);
+                if (w < ldw) {
+                    const uint4 o = *reinterpret_cast<const uint4*>(arow + w);  // A_i: the squaring's old row
+                    any |= (o.x ^ acc[v].x) | (o.y ^ acc[v].y) | (o.z ^ acc[v].z) | (o.w ^ acc[v].w);
+                    *reinterpret_cast<uint4*>(dst + i * ldw + w) = acc[v];
+                }
+            }
+        }
+    }
+    if (__any_sync(FULL, any != 0) && lane == 0) atomicOr(changed, 1);
+}
+
+// ---- word-CSR of packed rows
+__global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, int64_t* __restrict__ wptr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t i = warp_id; i < n; i += nwarps) {
+        int64_t c = 0;
+        for (int64_t wb = 0; wb < ldw; wb += 32) {
+            const uint64_t w = (wb + lane < ldw) ? P[i * ldw + wb + lane] : 0ull;
+            c += __popc(__ballot_sync(FULL, w != 0ull));
+        }
+        if (lane == 0) wptr[i + 1] = c;
+        if (i == 0 && lane == 0) wptr[0] = 0;
+    }
+}
+
+// In-place inclusive scan of wptr[1..n] by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t a = 1 + t * per, b = (a + per < n + 1) ? a + per : n + 1;
+    int64_t s = 0;
+    for (int64_t x = a; x < b; ++x) s += wptr[x];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int64_t v = (t >= off) ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = (t > 0) ? part[t - 1] : 0;
+    for (int64_t x = a; x < b; ++x) {
+        run += wptr[x];
+        wptr[x] = run;
+    }
+}
+
+__global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, const int64_t* __restrict__ wptr,
+                                 int32_t* __restrict__ widx, uint64_t* __restrict__ wval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t i = warp_id; i < n; i += nwarps) {
+        int64_t o = wptr[i];
+        for (int64_t wb = 0; wb < ldw; wb += 32) {
+            const uint64_t w = (wb + lane < ldw) ? P[i * ldw + wb + lane] : 0ull;
+            const unsigned m = __ballot_sync(FULL, w != 0ull);
+            if (w) {
+                const int64_t at = o + __popc(m & ((1u << lane) - 1u));
+                widx[at] = static_cast<int32_t>(wb + lane);
+                wval[at] = w;
+            }
+            o += __popc(m);
+        }
+    }
+}
+
+// ---- selective product per query row
+__global__ void __launch_bounds__(256) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
+                                                         const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
+                                                         const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
+                                                         uint64_t* __restrict__ out, int64_t ldw_out, int* levels_max,
+                                                         unsigned long long* qcounter, int reflexive, int max_levels) {
+    extern __shared__ uint64_t sm[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint64_t* V = sm + static_cast<int64_t>(wib) * 3 * ldw;
+    uint64_t* D = V + ldw;
+    uint64_t* N = D + ldw;
+    const int64_t wpr = (n + 63) / 64;
+    while (true) {
+        unsigned long long qi = 0;
+        if (lane == 0) qi = atomicAdd(qcounter, 1ull);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= static_cast<unsigned long long>(q)) break;
+        const uint64_t* srow = src + static_cast<int64_t>(qi) * ldw_src;
+        for (int64_t w = lane; w < ldw; w += 32) {
+            uint64_t s = 0;
+            if (w < wpr) {
+                s = srow[w];
+                const int64_t valid = n - w * 64;
+                if (valid < 64) s &= (1ull << valid) - 1ull;
+            }
+            D[w] = s;
+            V[w] = 0;
+            N[w] = 0;
+        }
+        __syncwarp();
+        int lv = 0;
+        while (true) {
+            for (int64_t wb = 0; wb < wpr; wb += 32) {
+                uint64_t d = (wb + lane < wpr) ? D[wb + lane] : 0ull;
+                while (__any_sync(FULL, d != 0ull)) {
+                    int64_t k = -1;
+                    if (d) {
+                        const int b = __ffsll(static_cast<long long>(d)) - 1;
+                        d &= d - 1;
+                        k = (wb + lane) * 64 + b;
+                    }
+                    int64_t e0 = 0, e1 = 0;
+                    if (k >= 0) {
+                        e0 = wptr[k];
+                        e1 = wptr[k + 1];
+                    }
+                    const bool heavy = (e1 - e0) > 16;
+                    if (k >= 0 && !heavy)
+                        for (int64_t e = e0; e < e1; ++e) atomicOr(reinterpret_cast<unsigned long long*>(&N[widx[e]]),
+                                                                   static_cast<unsigned long long>(wval[e]));
+                    unsigned hm = __ballot_sync(FULL, k >= 0 && heavy);
+                    while (hm) {
+                        const int sl = __ffs(hm) - 1;
+                        hm &= hm - 1;
+                        const int64_t h0 = __shfl_sync(FULL, e0, sl), h1 = __shfl_sync(FULL, e1, sl);
+                        for (int64_t e = h0 + lane; e < h1; e += 32)
+                            atomicOr(reinterpret_cast<unsigned long long*>(&N[widx[e]]),
+                                     static_cast<unsigned long long>(wval[e]));
+                    }
+                }
+            }
+            __syncwarp();
+            uint64_t anyw = 0;
+            for (int64_t w = lane; w < wpr; w += 32) {
+                const uint64_t nw = N[w] & ~V[w];
+                V[w] |= nw;
+                D[w] = nw;
+                N[w] = 0;
+                anyw |= nw;
+            }
+            __syncwarp();
+            ++lv;
+            if (!__any_sync(FULL, anyw != 0ull) || lv > max_levels) break;
+        }
+        uint64_t* orow = out + static_cast<int64_t>(qi) * ldw_out;
+        for (int64_t w = lane; w < ldw_out; w += 32) {
+            uint64_t v = 0;
+            if (w < wpr) {
+                v = V[w];
+                if (reflexive) {
+                    uint64_t s = srow[w];
+                    const int64_t valid = n - w * 64;
+                    if (valid < 64) s &= (1ull << valid) - 1ull;
+                    v |= s;
+                }
+            }
+            orow[w] = v;
+        }
+        if (lane == 0) atomicMax(levels_max, lv);
+        __syncwarp();
+    }
+}
+
+inline int warps_grid(int64_t rows, int sms) {
+    int64_t blocks = (rows + 7) / 8;  // 8 warps of 256 threads
+    const int64_t cap = static_cast<int64_t>(sms) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return static_cast<int>(blocks);
+}
+
+}  // namespace
+
+cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
+                                  int or_a, int* changed, int sms, cudaStream_t s) {
+    const int grid = warps_grid(n, sms);
+    if (ldw <= 128)
+        product_packed_kernel<2><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+    else if (ldw <= 256)
+        product_packed_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+    else
+        product_packed_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx, uint64_t* wval,
+                              cudaStream_t s) {
+    const int grid = warps_grid(n, 152);
+    wcsr_count_kernel<<<grid, 256, 0, s>>>(P, n, ldw, wptr);
+    scan_kernel<<<1, 1024, 0, s>>>(wptr, n);
+    wcsr_fill_kernel<<<grid, 256, 0, s>>>(P, n, ldw, wptr, widx, wval);
+    return cudaGetLastError();
+}
+
+int smp_packed_max_words() { return 8192; }
+
+cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n, int64_t ldw,
+                              const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out,
+                              int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s) {
+    const int64_t per_warp = 3 * ldw * static_cast<int64_t>(sizeof(uint64_t));
+    int warps = static_cast<int>((200 * 1024) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) return cudaErrorInvalidValue;
+    const size_t smem = static_cast<size_t>(warps) * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(smp_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (q + warps - 1) / warps;
+    int per_sm = static_cast<int>((220 * 1024) / (smem + 1024));
+    if (per_sm < 1) per_sm = 1;
+    if (blocks > static_cast<int64_t>(sms) * per_sm) blocks = static_cast<int64_t>(sms) * per_sm;
+    if (blocks < 1) blocks = 1;
+    const int max_levels = static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF);
+    smp_packed_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(
+        wptr, widx, wval, n, ldw, src, ldw_src, q, out, ldw_out, levels,
+        reinterpret_cast<unsigned long long*>(qcounter), reflexive, max_levels);
+    return cudaGetLastError();
+}
+
+}  // namespace bmlp

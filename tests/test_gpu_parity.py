@@ -1,0 +1,195 @@
+"""Bit-exact parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Sizes span several 128 x 256 tensor-core tiles and ragged tails (n not a
+multiple of 64 / 128 / 256), degenerate inputs (empty, n = 1, self-loop,
+complete graph, chain, cycle) and the paper's worked examples.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as wl
+from golden_io import matrix, read_facts
+
+pkg = pytest.importorskip("paper_2408_10369_gb300")
+
+pytestmark = pytest.mark.gpu
+
+CLOSURE_VARIANTS = ["rms_tc", "rms_packed", "smp_packed", "smp_tc"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_rms(ctx, dense, variant, fmt="u8", **kw):
+    n = dense.shape[0]
+    if fmt == "u8":
+        R = dev(dense)
+        out = torch.zeros_like(R)
+        it = ctx.rms(R, n, out, fmt=pkg.BMLP_FMT_U8, variant=variant, **kw)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), it
+    P = wl.pack_rows(dense)
+    R = dev(P.view(np.int64))
+    out = torch.zeros_like(R)
+    it = ctx.rms(R, n, out, fmt=pkg.BMLP_FMT_PACKED64, variant=variant, **kw)
+    torch.cuda.synchronize()
+    return wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), it
+
+
+def er_case(n, d, seed):
+    ip, ix = wl.er_graph(n, d, seed)
+    return ip, ix, wl.dense_u8(n, ip, ix)
+
+
+# ----------------------------------------------------------- closures --
+@pytest.mark.parametrize("variant", CLOSURE_VARIANTS)
+@pytest.mark.parametrize("n,d,seed", [(1, 0.0, 0), (2, 1.0, 1), (3, 1.0, 2), (63, 1.2, 3), (64, 1.5, 4),
+                                      (65, 2.0, 5), (127, 1.0, 6), (128, 1.3, 7), (129, 0.9, 8), (255, 1.1, 9),
+                                      (257, 1.6, 10), (600, 1.2, 11), (1000, 2.0, 12)])
+def test_closure_er(ctx, variant, n, d, seed):
+    ip, ix, m = er_case(n, d, seed)
+    want = oracle.closure(n, ip, ix)
+    got, it = run_rms(ctx, m, variant)
+    np.testing.assert_array_equal(got, want)
+    if variant.startswith("rms"):
+        assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+
+
+@pytest.mark.parametrize("variant", CLOSURE_VARIANTS)
+def test_closure_special(ctx, variant):
+    for n in (1, 5, 130, 300):
+        cases = {
+            "empty": np.zeros((n, n), np.uint8),
+            "self": np.eye(n, dtype=np.uint8),
+            "complete": (1 - np.eye(n, dtype=np.uint8)).astype(np.uint8),
+            "chain": np.eye(n, k=1, dtype=np.uint8),
+            "cycle": np.roll(np.eye(n, dtype=np.uint8), 1, axis=1),
+        }
+        for name, m in cases.items():
+            want = oracle.warshall(m) if n <= 130 else oracle.closure(n, *wl.csr_from_dense(m))
+            got, it = run_rms(ctx, m, variant)
+            np.testing.assert_array_equal(got, want, err_msg="%s n=%d" % (name, n))
+            if variant.startswith("rms") and name == "empty":
+                assert it == 1
+
+
+@pytest.mark.parametrize("variant", ["rms_tc", "rms_packed", "smp_packed"])
+def test_closure_packed_format_and_reflexive(ctx, variant):
+    n = 333
+    ip, ix, m = er_case(n, 1.4, 21)
+    want = oracle.closure(n, ip, ix)
+    got, _ = run_rms(ctx, m, variant, fmt="packed")
+    np.testing.assert_array_equal(got, want)
+    got, _ = run_rms(ctx, m, variant, reflexive=True)
+    np.testing.assert_array_equal(got, want | np.eye(n, dtype=np.uint8))
+
+
+def test_nonzero_bytes_count_as_one(ctx):
+    n = 200
+    ip, ix, m = er_case(n, 1.5, 3)
+    noisy = m * np.uint8(7) + (m * np.uint8(200))
+    got, _ = run_rms(ctx, noisy.astype(np.uint8), "rms_tc")
+    np.testing.assert_array_equal(got, oracle.closure(n, ip, ix))
+
+
+def test_host_buffers(ctx):
+    """Host (numpy) input and output: the library stages them itself."""
+    n = 400
+    ip, ix, m = er_case(n, 1.2, 4)
+    out = np.zeros_like(m)
+    ctx.rms(m, n, out, variant="rms_tc")
+    np.testing.assert_array_equal(out, oracle.closure(n, ip, ix))
+
+
+def test_p1_example_on_gpu(ctx):
+    consts, facts = read_facts("p1_edge_path.txt")
+    edge = matrix(consts, facts["edge"])
+    for v in CLOSURE_VARIANTS:
+        got, _ = run_rms(ctx, edge, v)
+        np.testing.assert_array_equal(got, matrix(consts, facts["path"]))
+
+
+def test_p3_p5_example_on_gpu(ctx):
+    consts, facts = read_facts("p3p5_isforeign.txt")
+    n = len(consts)
+    contains = matrix(consts, facts["contains"])
+    adjoins = matrix(consts, facts["adjoins"])
+    for v in ("rms_tc", "rms_packed"):
+        has_place, _ = run_rms(ctx, contains, v)
+        base = (adjoins | adjoins.T).astype(np.uint8)
+        rec = np.ascontiguousarray(has_place.T)
+        out = torch.zeros((n, n), dtype=torch.uint8, device="cuda")
+        ctx.compose(dev(base), dev(rec), n, out, variant=v)
+        torch.cuda.synchronize()
+        ipo = out.cpu().numpy()
+        np.testing.assert_array_equal(ipo, matrix(consts, facts["not_isForeign"]))
+        assert int((1 - ipo).sum()) == n * n - 4
+
+
+# ---------------------------------------------------------------- SMP --
+@pytest.mark.parametrize("variant", ["smp_packed", "smp_tc"])
+@pytest.mark.parametrize("n,d,q,seed", [(2000, 2000 * 2 / 2000, 1, 0), (2000, 2.0, 16, 1), (129, 1.0, 3, 2),
+                                        (700, 1.3, 200, 3), (1500, 0.8, 130, 4)])
+def test_smp_er(ctx, variant, n, d, q, seed):
+    ip, ix, m = er_case(n, d, seed)
+    src = wl.query_rows(n, q, 1, 16, seed)
+    want, levels = oracle.smp(n, ip, ix, src)
+    out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
+    it = ctx.smp(dev(m), n, dev(src.view(np.int64)), q, out, variant=variant)
+    torch.cuda.synchronize()
+    got = wl.unpack_rows(out.cpu().numpy().view(np.uint64), n)
+    np.testing.assert_array_equal(got, want)
+    assert it == int(levels.max()) + 1
+
+
+@pytest.mark.parametrize("variant", ["smp_packed", "smp_tc"])
+def test_smp_powerlaw_packed_input(ctx, variant):
+    n, q = 3000, 64
+    ip, ix = wl.powerlaw_csr(n, 2.1, 1000, 0)
+    P = wl.pack_rows(wl.dense_u8(n, ip, ix))
+    src = wl.query_rows(n, q, 1, 64, 1)
+    want, _ = oracle.smp(n, ip, ix, src)
+    out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
+    ctx.smp(dev(P.view(np.int64)), n, dev(src.view(np.int64)), q, out, fmt=pkg.BMLP_FMT_PACKED64, variant=variant)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
+
+
+# ------------------------------------------------------------ compose --
+@pytest.mark.parametrize("variant", ["rms_tc", "rms_packed"])
+@pytest.mark.parametrize("n,seed", [(1, 0), (77, 1), (256, 2), (513, 3)])
+def test_compose(ctx, variant, n, seed):
+    ip1, ix1, m1 = er_case(n, 1.0, seed)
+    ip2, ix2, m2 = er_case(n, 1.4, seed + 50)
+    want = oracle.compose_rows(n, (ip1, ix1), (ip2, ix2))
+    out = torch.zeros((n, n), dtype=torch.uint8, device="cuda")
+    ctx.compose(dev(m1), dev(m2), n, out, variant=variant)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+# --------------------------------------------------------- arguments --
+def test_argument_errors(ctx):
+    R = torch.zeros((4, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(pkg.BmlpError) as e:
+        ctx.rms(R, -1, R)
+    assert e.value.status == 1
+    with pytest.raises(pkg.BmlpError):
+        ctx.rms(R, 4, R, fmt=7)
+    assert ctx.rms(None, 0, None) == 0            # n = 0 is a no-op
+    with pytest.raises(pkg.BmlpError):
+        ctx.rms(R, 4, R, variant=99)
+    with pytest.raises(pkg.BmlpError) as e:
+        ctx.rms(dev(np.roll(np.eye(64, dtype=np.uint8), 1, axis=1)), 64,
+                torch.zeros((64, 64), dtype=torch.uint8, device="cuda"), variant="rms_tc", max_iters=2)
+    assert e.value.status == 5                   # a 64-cycle needs 7 products
