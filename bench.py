@@ -1,0 +1,312 @@
+"""Benchmark: BMLP-RMS transitive closure on the GB300 tensor cores.
+
+Workload (default): one directed Erdos-Renyi graph with n = 32,768 nodes and
+mean out-degree 4 (each ordered pair i != j an edge with p = 4 / (n - 1),
+seeded), given as a dense n x n uint8 0/1 matrix resident in HBM. One step is
+one call of ``bmlp_rms`` through the C ABI: encode to E4M3 R / R^T, the
+squaring fixpoint R <- R + R R with the changed-flag early exit, and decode of
+R1+ into a uint8 output matrix. The metric is effective Boolean TOPS =
+iterations * 2 n^3 / time (n logical, every product counted as dense).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank closes its own
+graph (seed = rank): the closures are independent, there is no collective on
+the data path, and ``value`` sums the work of all ranks over the slowest
+rank's time ("scaling": "weak").
+
+``--impl reference`` times the CPU oracle (per-source BFS) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Boolean closure eff. TOPS & graphs/s vs plain RMS, same GB300, bit-exact"
+UNIT = "eff. Boolean TOPS (iters*2n^3/s)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP8_PER_BF16 = 2.0          # nominal dense ratio fp8 / bf16 (4.5 / 2.25 PFLOP/s)
+FALLBACK_BF16_BURST = 1900.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--degree", type=float, default=4.0)
+    ap.add_argument("--variant", default="rms_tc")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]) * FP8_PER_BF16, float(p.get("hbm_gbs", 0.0)), "measured"
+    except Exception:
+        return FALLBACK_BF16_BURST * FP8_PER_BF16, 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2408_10369_gb300", "csrc", "tc_product.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(n):
+    """DRAM bytes per product launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "tc_product_kernel_er%d.md" % n)
+    try:
+        kv = {}
+        with open(path) as f:
+            for ln in f:
+                if ln.startswith("- ") and ":" in ln:
+                    k, v = ln[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_source_sha256_12") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_closure(n, ip, ix, rows):
+    """Time the oracle's BFS closure on `rows` source rows (materialised)."""
+    import numpy as np
+    import oracle
+    src = np.arange(rows, dtype=np.int32) * (n // rows)
+    t0 = time.perf_counter()
+    oracle.reach_rows(n, ip, ix, src)
+    return time.perf_counter() - t0
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, rank, world):
+    import workloads as wl
+    import oracle
+    import numpy as np
+    if rank != 0:
+        return
+    n = args.n
+    ip, ix = wl.er_graph(n, args.degree, 0)
+    _, depth, _ = oracle.reach_rows(n, ip, ix, np.arange(0, n, max(1, n // 512), dtype=np.int32), want_rows=False)
+    L = int(depth.max())
+    iters = oracle.rms_iterations(L)
+    rows = args.cpu_rows or max(64, n // 8)
+    times = []
+    for _ in range(args.warmup):
+        cpu_oracle_closure(n, ip, ix, rows)
+    for _ in range(args.steps):
+        times.append(cpu_oracle_closure(n, ip, ix, rows))
+    t_full = statistics.mean(times) * n / rows
+    value = iters * 2.0 * n ** 3 / t_full / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
+                       "seed": 0, "iterations_equivalent": iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": "BFS closure rows for %d of %d sources per step, scaled to the full closure" % (rows, n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import workloads as wl
+    import paper_2408_10369_gb300 as pkg
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    n = args.n
+    ip, ix = wl.er_graph(n, args.degree, rank)
+    dense = wl.dense_u8(n, ip, ix)
+    R = torch.from_numpy(dense).to(device)
+    out = torch.empty_like(R)
+    ctx = pkg.Context(local)
+    stream = torch.cuda.current_stream(device)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def step(profile):
+        return ctx.rms(R, n, out, variant=args.variant, profile=profile, stream=stream)
+
+    iters = 0
+    for _ in range(args.warmup):
+        iters = step(False)
+    torch.cuda.synchronize()
+    # ---- timed region: K closures, device-resident input and output
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    prod_ms, prod_n, launches, issued = 0.0, 0, 0, 0.0
+    for _ in range(args.steps):
+        iters = step(True)
+        st = ctx.stats()
+        prod_ms += st["product_ms"]
+        prod_n += st["product_launches"]
+        launches += st["launches"]
+        issued += st["issued_ops"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    work = args.steps * iters * 2.0 * n ** 3 * world
+    value = work / t / 1e12
+    # ---- end-to-end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(dense).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        ctx.rms(hin, n, hout, variant=args.variant, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.rms(hin, n, hout, variant=args.variant, stream=stream)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], device=device)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": args.steps * iters * 2.0 * n ** 3 * world / te / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": n * n, "d2h_bytes_per_step": n * n}
+    peak, _, peak_src = peaks()
+    avg_launch_s = prod_ms / max(prod_n, 1) / 1e3
+    achieved = 2.0 * n ** 3 / avg_launch_s / 1e12 if avg_launch_s > 0 else None
+    roof = {"bound": "tensor", "kernel": "tc_product_kernel", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(n),
+            "peak_source": "%s bf16 burst x %g (fp8/bf16 nominal); the product runs unthrottled at max SM clock" % (peak_src, FP8_PER_BF16),
+            "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None}
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu:
+        rows = args.cpu_rows or max(64, n // 4)
+        tc = cpu_oracle_closure(n, ip, ix, rows)
+        t_full = tc * n / rows
+        cpu = {"value": iters * 2.0 * n ** 3 / t_full / 1e12, "unit": UNIT, "cores": oracle_threads(),
+               "kind": "oracle", "sample": "BFS closure rows for %d of %d sources (%.1f s), scaled to the full closure"
+               % (rows, n, tc)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "e4m3 0/1 operands, fp32 accumulate", "data": "synthetic",
+            "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
+                       "seed": "rank", "variant": args.variant, "iterations": iters, "nnz": int(len(ix)),
+                       "graphs_per_s": args.steps * world / t, "l2": "inputs larger than L2 (1 GiB per matrix)",
+                       "parallelism": "independent replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
