@@ -168,6 +168,44 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
 bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt,
                          void* out, const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
 
+/*
+ * bmlp_rms_tc_noalloc - the tensor-core closure of bmlp_rms (variant
+ * BMLP_RMS_TC) for callers that must not allocate device memory. The paper
+ * has no counterpart: this is a deployment form of the same computation.
+ *
+ * Who needs it: code whose device memory is owned by someone else (a pool
+ * or caching allocator that has reserved the GPU, a plugin inside a host
+ * framework with a fixed memory budget) and code on latency-critical paths
+ * where cudaMalloc / cudaFree, which may synchronise the device, is not
+ * acceptable. Such callers cannot create a bmlp_ctx, whose workspace grows
+ * with cudaMalloc.
+ *
+ * Scratch: the ping-pong E4M3 R / R^T matrices and two control words live in
+ * one file-scope __device__ array of 4 * 2048 * 2048 + 256 bytes (16 MiB),
+ * which every GPU that loads this library holds until the process exits.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * Arguments: as bmlp_rms, on the calling thread's current CUDA device. R and
+ * out must be device memory (host pointers give BMLP_ERR_INVALID_ARG, since
+ * staging them would need an allocation). reflexive: 0 gives R1+, 1 gives
+ * I + R1+. max_iters: 0 = ceil(log2 n) + 2. Sizes n > BMLP_NOALLOC_MAX_N give
+ * BMLP_ERR_UNSUPPORTED. Errors are status codes only (there is no context to
+ * hold a message).
+ *
+ * Set-up: the first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture on the device.
+ *
+ * Sharing: every call on a device uses the same scratch, which keeps the last
+ * call's contents (each call rewrites all of it that it reads). Calls whose
+ * work overlaps on the GPU (other host threads, other streams) race on it:
+ * serialise them.
+ */
+#define BMLP_NOALLOC_MAX_N 2048
+bmlp_status bmlp_rms_tc_noalloc(const void* R, int64_t n, int32_t fmt, void* out, int32_t reflexive,
+                                int32_t max_iters, int32_t* iters_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

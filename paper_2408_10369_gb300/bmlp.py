@@ -209,3 +209,24 @@ class Context:
         self._check(self._L.bmlp_compose(self.handle, _ptr(R1), _ptr(R2), int(n), int(fmt), _ptr(out),
                                          ctypes.byref(o), ctypes.byref(it), _stream(stream, self.device)))
         return it.value
+
+
+def rms_tc_noalloc(R, n, out, fmt=BMLP_FMT_U8, reflexive=False, max_iters=0, stream=None, device=0):
+    """bmlp_rms_tc_noalloc: the tensor-core closure with no device allocation.
+
+    For callers that must not allocate device memory (memory owned by a pool
+    allocator or a fixed budget; latency-critical paths that cannot afford the
+    device synchronisation of cudaMalloc / cudaFree). R and out must be device
+    memory, n <= 2048. Returns the number of products; raises BmlpError.
+    """
+    L = lib()
+    fn = L.bmlp_rms_tc_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    it = ctypes.c_int32(0)
+    st = fn(_ptr(R), int(n), int(fmt), _ptr(out), int(bool(reflexive)), int(max_iters), ctypes.byref(it),
+            _stream(stream, device))
+    if st != BMLP_OK:
+        raise BmlpError(st, "bmlp_rms_tc_noalloc failed")
+    return it.value

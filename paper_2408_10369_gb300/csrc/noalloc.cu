@@ -1,0 +1,162 @@
+// bmlp_rms_tc_noalloc: the tensor-core squaring closure for callers that may
+// not allocate device memory. Its scratch (the ping-pong E4M3 R / R^T
+// matrices and the control words) lives in one file-scope __device__ array of
+// fixed size, so the call itself never allocates.
+#include <cstring>
+#include <cudaTypedefs.h>
+#include <mutex>
+
+#include "internal.h"
+
+namespace bmlp {
+namespace {
+
+constexpr int64_t NA_MAX_N = BMLP_NOALLOC_MAX_N;                 // largest padded n
+constexpr size_t NA_MAT = static_cast<size_t>(NA_MAX_N) * NA_MAX_N;
+constexpr size_t NA_CTL = 256;                                  // control words
+constexpr size_t NA_BYTES = 4 * NA_MAT + NA_CTL;                // 16 MiB + 256 B
+
+// The scratch every call on a device shares; each GPU that loads the library
+// holds it until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_mu;
+uint8_t* g_addr[NA_MAX_DEVICES] = {nullptr};   // device address of the scratch, per device
+void* g_encode = nullptr;                      // cuTensorMapEncodeTiled
+
+// Device address of the scratch on the current device (looked up once per
+// device, with that device current; the host-side symbol is only a handle).
+bmlp_status scratch_on_current_device(int* dev_out, uint8_t** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+        cudaGetLastError();
+        return BMLP_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_addr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return BMLP_ERR_CUDA;
+        }
+        g_addr[dev] = static_cast<uint8_t*>(p);
+    }
+    if (g_encode == nullptr) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) {
+            cudaGetLastError();
+            return BMLP_ERR_CUDA;
+        }
+        g_encode = fn;
+    }
+    *dev_out = dev;
+    *out = g_addr[dev];
+    return BMLP_OK;
+}
+
+bool tmap(CUtensorMap* map, const void* base, int64_t n_pad, int box_rows) {
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(g_encode);
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(n_pad), static_cast<cuuint64_t>(n_pad)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(n_pad)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace bmlp
+
+using namespace bmlp;
+
+extern "C" bmlp_status bmlp_rms_tc_noalloc(const void* R, int64_t n, int32_t fmt, void* out, int32_t reflexive,
+                                           int32_t max_iters, int32_t* iters_out, cudaStream_t s) {
+    if (iters_out) *iters_out = 0;
+    if (n < 0 || (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64)) return BMLP_ERR_INVALID_ARG;
+    if (n == 0) return BMLP_OK;
+    if (R == nullptr || out == nullptr) return BMLP_ERR_INVALID_ARG;
+    if (n > NA_MAX_N) return BMLP_ERR_UNSUPPORTED;
+    if (!on_device(R) || !on_device(out)) return BMLP_ERR_INVALID_ARG;
+    int dev = 0;
+    uint8_t* base = nullptr;
+    bmlp_status st = scratch_on_current_device(&dev, &base);
+    if (st != BMLP_OK) return st;
+    int sms = 0, khz = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2100000;
+
+    const int64_t n_pad = (n + TC_PAD - 1) / TC_PAD * TC_PAD;
+    const size_t mat = static_cast<size_t>(n_pad * n_pad);
+    uint8_t* M[2] = {base, base + mat};
+    uint8_t* T[2] = {base + 2 * mat, base + 3 * mat};
+    int* ctl = reinterpret_cast<int*>(base + 4 * NA_MAT);
+
+    // the encoder writes every byte of R and R^T (padding included)
+    if (fmt == BMLP_FMT_U8)
+        launch_u8_to_e4m3(static_cast<const uint8_t*>(R), n, M[0], T[0], n_pad, s);
+    else
+        launch_packed_to_e4m3(static_cast<const uint64_t*>(R), (n + 63) / 64, n, n, M[0], T[0], n_pad, n_pad, s);
+    if (cudaGetLastError() != cudaSuccess) return BMLP_ERR_CUDA;
+
+    CUtensorMap mapA[2], mapB[2];
+    for (int b = 0; b < 2; ++b)
+        if (!tmap(&mapA[b], M[b], n_pad, TC_BM) || !tmap(&mapB[b], T[b], n_pad, TC_BN)) return BMLP_ERR_CUDA;
+    TcParams p{};
+    p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+    p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+    p.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
+    p.mode = TC_MODE_RMS;
+    p.ld = n_pad;
+    p.changed = ctl;
+    p.error = ctl + 1;
+    p.wait_cycles = static_cast<long long>(2.0e9 * static_cast<double>(khz) * 1e-6);
+    const int tiles = p.m_tiles * p.n_tiles;
+    const int grid = tiles < sms ? tiles : sms;
+    int cap = max_iters;
+    if (cap <= 0) {
+        cap = 2;
+        while ((int64_t(1) << (cap - 2)) < n) ++cap;   // ceil(log2 n) + 2
+    }
+    int cur = 0, iters = 0;
+    bool converged = false;
+    for (int it = 0; it < cap; ++it) {
+        const int nxt = cur ^ 1;
+        int h[2] = {0, 0};
+        if (cudaMemsetAsync(ctl, 0, 2 * sizeof(int), s) != cudaSuccess) return BMLP_ERR_CUDA;
+        p.old_r = M[cur];
+        p.out_r = M[nxt];
+        p.out_rt = T[nxt];
+        if (launch_tc_product(mapA[cur], mapB[cur], p, grid, s) != cudaSuccess) return BMLP_ERR_CUDA;
+        if (cudaMemcpyAsync(h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BMLP_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return BMLP_ERR_CUDA;
+        if (h[1] != 0) return BMLP_ERR_TIMEOUT;
+        iters = it + 1;
+        cur = nxt;
+        if (!h[0]) {
+            converged = true;
+            break;
+        }
+    }
+    if (iters_out) *iters_out = iters;
+    if (fmt == BMLP_FMT_U8)
+        launch_bytes_to_u8(M[cur], n_pad, n, static_cast<uint8_t*>(out), reflexive, s);
+    else
+        launch_bytes_to_packed(M[cur], n_pad, n, n, static_cast<uint64_t*>(out), (n + 63) / 64, reflexive, s);
+    if (cudaGetLastError() != cudaSuccess) return BMLP_ERR_CUDA;
+    return converged ? BMLP_OK : BMLP_ERR_NOT_CONVERGED;
+}
