@@ -168,6 +168,56 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
 bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt,
                          void* out, const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
 
+/* One problem of a grouped batch. */
+typedef enum bmlp_problem_kind {
+    BMLP_PROBLEM_CLOSURE = 0,  /* out = R1+ (or I + R1+): program P2 of Sec. 3.3   */
+    BMLP_PROBLEM_COMPOSE = 1   /* out = (I + R2+) R1: p <- r1 ; p <- r2, p (Thm. 1) */
+} bmlp_problem_kind;
+
+typedef struct bmlp_problem {
+    int32_t kind;       /* bmlp_problem_kind                                      */
+    int32_t fmt;        /* bmlp_format of R1, R2 and out                          */
+    int32_t reflexive;  /* closures only: 1 gives I + R1+                         */
+    int32_t reserved;
+    int64_t n;          /* matrix size (0 = nothing to do)                        */
+    const void* R1;     /* device memory                                          */
+    const void* R2;     /* device memory, compositions only                       */
+    void* out;          /* device memory                                          */
+} bmlp_problem;
+
+/*
+ * bmlp_batch_run - evaluate many independent linear recursive programs of
+ * uneven sizes together (the grouped form of bmlp_rms / bmlp_compose; paper
+ * Sec. 3.3-3.4, composability by reuse of outputs).
+ *
+ * All squaring steps of all unconverged problems of one iteration run in ONE
+ * persistent launch over a device work list of (problem, tile) items; a
+ * planner kernel retires problems whose changed flag stayed 0 (or that hit
+ * their cap of ceil(log2 n) + 2 products) and builds the next work list; the
+ * iteration runs inside a CUDA graph conditional WHILE node, so the host does
+ * not take part until the whole batch has converged. Each problem runs on
+ * the tensor cores or on packed rows, chosen per size bucket by the autotuner
+ * (bmlp_batch_autotune) or forced by opts->variant (BMLP_RMS_TC /
+ * BMLP_RMS_PACKED; compositions always use the tensor cores).
+ * iters_out (count entries, may be null) receives each problem's products.
+ * All matrix pointers must be device memory. The instantiated graph is cached
+ * in the context and reused while the problem list is unchanged.
+ * Returns BMLP_ERR_NOT_CONVERGED if any problem hit its cap.
+ */
+bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const bmlp_options* opts,
+                           int32_t* iters_out, cudaStream_t stream);
+
+/*
+ * bmlp_batch_autotune - time the tensor-core and the packed engine on the
+ * closures of `probs`, per size bucket (n rounded up to a power of two), and
+ * keep the faster one per bucket in the context for later bmlp_batch_run
+ * calls with variant BMLP_AUTO. When cache_path is not null the table is
+ * read from that file if it holds an entry for this GPU, else measured and
+ * written there (one line per GPU name and bucket).
+ */
+bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const char* cache_path,
+                                cudaStream_t stream);
+
 /*
  * bmlp_rms_tc_noalloc - the tensor-core closure of bmlp_rms (variant
  * BMLP_RMS_TC) for callers that must not allocate device memory. The paper

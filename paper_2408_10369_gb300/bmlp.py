@@ -57,6 +57,16 @@ class bmlp_stats(ctypes.Structure):
                 ("issued_ops", ctypes.c_double)]
 
 
+class bmlp_problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("fmt", ctypes.c_int32), ("reflexive", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n", ctypes.c_int64), ("R1", ctypes.c_void_p),
+                ("R2", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+BMLP_PROBLEM_CLOSURE = 0
+BMLP_PROBLEM_COMPOSE = 1
+
+
 class BmlpError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("bmlp status %d (%s): %s" % (status, _STATUS.get(status, "?"), msg))
@@ -95,8 +105,11 @@ def lib():
                                    ctypes.POINTER(i32), vp]
             L.bmlp_compose.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
                                        ctypes.POINTER(i32), vp]
+            L.bmlp_batch_run.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.POINTER(bmlp_options),
+                                         ctypes.POINTER(i32), vp]
+            L.bmlp_batch_autotune.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.c_char_p, vp]
             for name in ("bmlp_ctx_create", "bmlp_ctx_destroy", "bmlp_get_stats", "bmlp_rms", "bmlp_smp",
-                         "bmlp_compose"):
+                         "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -201,6 +214,37 @@ class Context:
         self._check(self._L.bmlp_smp(self.handle, _ptr(R), int(n), int(fmt), _ptr(src_rows), int(q), _ptr(out_rows),
                                      ctypes.byref(o), ctypes.byref(it), _stream(stream, self.device)))
         return it.value
+
+    @staticmethod
+    def problems(items):
+        """ctypes array of bmlp_problem from dicts {kind, n, R1, R2, out, fmt, reflexive}."""
+        arr = (bmlp_problem * max(len(items), 1))()
+        for i, it in enumerate(items):
+            p = arr[i]
+            p.kind = int(it.get("kind", BMLP_PROBLEM_CLOSURE))
+            p.fmt = int(it.get("fmt", BMLP_FMT_U8))
+            p.reflexive = int(bool(it.get("reflexive", False)))
+            p.n = int(it["n"])
+            p.R1 = _ptr(it["R1"]).value if it.get("R1") is not None else None
+            p.R2 = _ptr(it["R2"]).value if it.get("R2") is not None else None
+            p.out = _ptr(it["out"]).value if it.get("out") is not None else None
+        return arr
+
+    def batch_run(self, items, stream=None, **opt):
+        """bmlp_batch_run over dicts (see ``problems``). Returns per-problem products."""
+        arr = items if isinstance(items, ctypes.Array) else self.problems(items)
+        count = len(items)
+        o = make_options(**opt)
+        iters = (ctypes.c_int32 * max(count, 1))()
+        self._check(self._L.bmlp_batch_run(self.handle, arr, count, ctypes.byref(o), iters,
+                                           _stream(stream, self.device)))
+        return list(iters)[:count]
+
+    def batch_autotune(self, items, cache_path=None, stream=None):
+        """bmlp_batch_autotune: choose tensor cores or packed rows per size bucket."""
+        arr = items if isinstance(items, ctypes.Array) else self.problems(items)
+        path = cache_path.encode() if cache_path else None
+        self._check(self._L.bmlp_batch_autotune(self.handle, arr, len(items), path, _stream(stream, self.device)))
 
     def compose(self, R1, R2, n, out, fmt=BMLP_FMT_U8, stream=None, **opt):
         """bmlp_compose: out = (I + R2+) R1. Returns the closure's products."""

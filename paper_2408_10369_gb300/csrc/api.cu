@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -475,6 +477,7 @@ bmlp_status bmlp_ctx_create(bmlp_ctx** out, int32_t device) {
     bmlp_ctx* ctx = new (std::nothrow) bmlp_ctx();
     if (!ctx) return BMLP_ERR_OOM;
     ctx->device = device;
+    for (int& t : ctx->tune) t = -1;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
@@ -493,6 +496,7 @@ bmlp_status bmlp_ctx_destroy(bmlp_ctx* ctx) {
     if (!ctx) return BMLP_OK;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
+    batch_cache_free(ctx);
     for (auto& b : ctx->ws)
         if (b.p) cudaFree(b.p);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
@@ -531,7 +535,19 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
     ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
     int iters = 0;
     bmlp_status st = BMLP_OK;
-    if (variant == BMLP_RMS_TC) {
+    if (o.loop == BMLP_LOOP_GRAPH && (variant == BMLP_RMS_TC || variant == BMLP_RMS_PACKED)) {
+        // device-side loop: a batch of one problem inside the graph WHILE node
+        bmlp_problem pr{};
+        pr.kind = BMLP_PROBLEM_CLOSURE;
+        pr.fmt = fmt;
+        pr.reflexive = o.reflexive;
+        pr.n = n;
+        pr.R1 = in.dev;
+        pr.out = ov.dev;
+        int32_t it = 0;
+        st = batch_run_impl(ctx, &pr, 1, variant, wait_cycles(ctx, o), &it, s);
+        iters = it;
+    } else if (variant == BMLP_RMS_TC) {
         const int64_t n_pad = round_up(n, TC_PAD);
         ctx->stats.n_pad = n_pad;
         void* b[4];
@@ -723,6 +739,93 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
     ctx->stats.iterations = iters;
     if (iters_out) *iters_out = iters;
     return finish_out(ctx, ov, s);
+}
+
+bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const bmlp_options* opts,
+                           int32_t* iters_out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (count < 0 || (count > 0 && !probs)) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad problem list");
+    if (count == 0) return BMLP_OK;
+    DeviceGuard g(ctx->device);
+    bmlp_options o = resolve(opts);
+    if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC && o.variant != BMLP_RMS_PACKED)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a batch variant", o.variant);
+    reset_stats(ctx, o.variant, 0);
+    ProductTimer tm{ctx, o.profile != 0, s};
+    ST(tm.begin());
+    bmlp_status st = batch_run_impl(ctx, probs, count, o.variant, wait_cycles(ctx, o), iters_out, s);
+    ST(tm.end());
+    if (o.profile) {
+        CK(cudaStreamSynchronize(s), "synchronise batch");
+        ST(tm.collect());
+    }
+    return st;
+}
+
+bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const char* cache_path,
+                                cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (count < 0 || (count > 0 && !probs)) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad problem list");
+    DeviceGuard g(ctx->device);
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, ctx->device), "device properties");
+    std::string gpu(prop.name);
+    for (char& ch : gpu)
+        if (ch == ' ') ch = '_';
+    bool from_file = false;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            char name[256];
+            int b = 0, eng = 0;
+            double t0 = 0, t1 = 0;
+            while (fscanf(f, "%255s %d %d %lf %lf", name, &b, &eng, &t0, &t1) == 5)
+                if (gpu == name && b >= 0 && b < 32 && (eng == 0 || eng == 1)) {
+                    ctx->tune[b] = eng;
+                    from_file = true;
+                }
+            fclose(f);
+        }
+    }
+    if (from_file) return BMLP_OK;
+    bmlp_options o;
+    bmlp_default_options(&o);
+    const long long wc = wait_cycles(ctx, o);
+    std::vector<std::string> lines;
+    for (int b = 0; b < 32; ++b) {
+        std::vector<bmlp_problem> sub;
+        for (int64_t i = 0; i < count; ++i)
+            if (probs[i].kind == BMLP_PROBLEM_CLOSURE && probs[i].n > 0 && (int64_t(1) << b) >= probs[i].n &&
+                (b == 0 || (int64_t(1) << (b - 1)) < probs[i].n))
+                sub.push_back(probs[i]);
+        if (sub.empty()) continue;
+        double ms[2] = {0, 0};
+        for (int eng = 0; eng < 2; ++eng) {
+            const int variant = eng == 0 ? BMLP_RMS_TC : BMLP_RMS_PACKED;
+            bmlp_status st = batch_run_impl(ctx, sub.data(), static_cast<int64_t>(sub.size()), variant, wc, nullptr, s);
+            if (st != BMLP_OK && st != BMLP_ERR_NOT_CONVERGED) return st;
+            CK(cudaEventRecord(ctx->ev[0], s), "event");
+            st = batch_run_impl(ctx, sub.data(), static_cast<int64_t>(sub.size()), variant, wc, nullptr, s);
+            if (st != BMLP_OK && st != BMLP_ERR_NOT_CONVERGED) return st;
+            CK(cudaEventRecord(ctx->ev[1], s), "event");
+            CK(cudaEventSynchronize(ctx->ev[1]), "event");
+            float t = 0;
+            CK(cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]), "event");
+            ms[eng] = t;
+        }
+        ctx->tune[b] = ms[1] < ms[0] ? 1 : 0;
+        char buf[512];
+        snprintf(buf, sizeof(buf), "%s %d %d %.6f %.6f\n", gpu.c_str(), b, ctx->tune[b], ms[0], ms[1]);
+        lines.push_back(buf);
+    }
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            for (auto& l : lines) fputs(l.c_str(), f);
+            fclose(f);
+        }
+    }
+    return BMLP_OK;
 }
 
 }  // extern "C"

@@ -44,6 +44,43 @@ struct TcParams {
     long long wait_cycles;      // bound of each in-kernel wait
 };
 
+// One problem of a grouped batch (device copy; built on the host).
+struct GroupProblem {  // aligned as CUtensorMap (TMA descriptors must be 64-byte aligned)
+    CUtensorMap mapA[2];   // A operand: M[parity] (row-major R)
+    CUtensorMap mapB[2];   // B operand: T[parity] (R^T)
+    CUtensorMap mapBF;     // composition: B of the final product = R1^T
+    uint8_t* M[2];         // E4M3 R ping-pong (tensor-core engine)
+    uint8_t* T[2];         // E4M3 R^T ping-pong
+    uint8_t* X;            // composition: final product
+    uint8_t* R1T;          // composition: E4M3 R1^T
+    uint64_t* P[2];        // packed ping-pong (packed engine)
+    const void* in1;       // caller's R1 (closure input, or composition r1)
+    const void* in2;       // caller's R2 (composition r2)
+    void* out;             // caller's output
+    int64_t n;
+    int64_t ld;            // n_pad (tensor-core engine)
+    int64_t ldw;           // words per packed row (packed engine)
+    int32_t m_tiles, n_tiles, k_blocks;
+    int32_t kind;          // 0 closure, 1 composition
+    int32_t engine;        // 0 tensor cores, 1 packed
+    int32_t fmt;           // caller's format
+    int32_t reflexive;
+    int32_t cap;           // iteration cap
+};
+
+// Per-problem loop state of a grouped batch (device memory).
+struct GroupState {
+    int* parity;     // buffer holding the current R
+    int* active;     // still iterating
+    int* iters;      // products issued
+    int* changed;    // set by the last product
+    int* notconv;    // stopped at the cap while still changing
+    int* tc_offs;    // exclusive prefix of active tensor-core tiles (nprob + 1)
+    int* tc_total;
+    int* pk_offs;    // exclusive prefix of active packed rows (nprob + 1)
+    int* pk_total;
+};
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
     void* p = nullptr;
@@ -56,7 +93,9 @@ struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
     char err[512] = {0};
-    bmlp::DevBuf ws[16];
+    bmlp::DevBuf ws[20];
+    void* batch = nullptr;       // cached grouped-batch graph (batch.cu)
+    int tune[32];                // autotuned engine per size bucket (-1 = unknown)
     int* d_ctl = nullptr;        // device control words (see CTL_* below)
     int* h_ctl = nullptr;        // pinned host mirror
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -67,6 +106,14 @@ struct bmlp_ctx {
 namespace bmlp {
 
 enum CtlWord : int { CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_WORDS = 16 };
+
+// Workspace slot of the grouped batch (the others are private to api.cu).
+constexpr int WS_BATCH = 15;
+
+// ---- grouped batch (batch.cu)
+bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, int variant, long long wait_cycles,
+                           int32_t* iters_out, cudaStream_t s);
+void batch_cache_free(bmlp_ctx* ctx);
 
 // ---- workspace / error helpers (api.cu)
 bmlp_status set_err(bmlp_ctx* ctx, bmlp_status st, const char* fmt, ...);
@@ -109,6 +156,10 @@ bmlp_status make_tmap(bmlp_ctx* ctx, CUtensorMap* map, const void* base, int64_t
 int tc_smem_bytes();
 cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int grid,
                               cudaStream_t s);
+// grouped form: tc_group_kernel(const GroupProblem*, const GroupState*, int nprob, int phase, int* error,
+// long long wait_cycles); phase 0 = squaring step of every active problem, 1 = final products of compositions
+void* tc_group_kernel_ptr();
+cudaError_t prepare_tc_group();
 
 // ---- packed kernels (packed.cu)
 // dst_i = (or_a ? A_i : 0) | OR_{k : A_ik = 1} B_k over n packed rows of ldw

@@ -23,6 +23,9 @@
 //         writes N as the next frontier, marks its nonzero 128 x 128 blocks
 //         so that the next level skips all-zero K blocks of the frontier.
 //   PLAIN out = [C > 0] (the final product of a composition).
+// Tile sources: one problem (tc_product_kernel, tensor maps as kernel
+// parameters) or a device work list over many problems (tc_group_kernel,
+// tensor maps in global memory; used by the grouped batch runner).
 // Every wait on an mbarrier is bounded; on expiry the CTA records an error
 // code, stops issuing work, waits (bounded) for its own copies and MMAs in
 // flight, frees its TMEM and exits.
@@ -97,8 +100,89 @@ __device__ __forceinline__ bool wait_lane0(uint64_t* bar, uint32_t parity, volat
     return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+// Everything one output tile needs.
+struct Tile {
+    const CUtensorMap* mapA;
+    const CUtensorMap* mapB;
+    int mb, nb, k_blocks, mode;
+    int64_t ld;
+    const uint8_t* old_r;
+    uint8_t* out_r;
+    uint8_t* out_rt;
+    uint8_t* visited;
+    const uint8_t* kflags;
+    uint8_t* kflags_next;
+    int* changed;
+};
+
+// One problem: the tensor maps are kernel parameters.
+struct SingleSource {
+    const CUtensorMap* a;
+    const CUtensorMap* b;
+    const TcParams* p;
+    __device__ int count() const { return p->m_tiles * p->n_tiles; }
+    __device__ void get(int t, Tile& x) const {
+        tile_coords(t, p->m_tiles, p->n_tiles, x.mb, x.nb);
+        x.mapA = a;
+        x.mapB = b;
+        x.k_blocks = p->k_blocks;
+        x.mode = p->mode;
+        x.ld = p->ld;
+        x.old_r = p->old_r;
+        x.out_r = p->out_r;
+        x.out_rt = p->out_rt;
+        x.visited = p->visited;
+        x.kflags = p->kflags;
+        x.kflags_next = p->kflags_next;
+        x.changed = p->changed;
+    }
+};
+
+// Many problems: items are numbered problem by problem; offs[p] is the first
+// item of problem p (exclusive prefix of its active tile count).
+struct GroupSource {
+    const GroupProblem* probs;
+    const GroupState* st;
+    int nprob;
+    int total;
+    int phase;
+    __device__ int count() const { return total; }
+    __device__ void get(int t, Tile& x) const {
+        const int* offs = st->tc_offs;
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {  // largest p with offs[p] <= t (that problem is nonempty)
+            const int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const GroupProblem& g = probs[lo];
+        const int par = st->parity[lo];
+        tile_coords(t - offs[lo], g.m_tiles, g.n_tiles, x.mb, x.nb);
+        x.k_blocks = g.k_blocks;
+        x.ld = g.ld;
+        x.mapA = &g.mapA[par];
+        x.visited = nullptr;
+        x.kflags = nullptr;
+        x.kflags_next = nullptr;
+        if (phase == 0) {
+            x.mode = TC_MODE_RMS;
+            x.mapB = &g.mapB[par];
+            x.old_r = g.M[par];
+            x.out_r = g.M[par ^ 1];
+            x.out_rt = g.T[par ^ 1];
+            x.changed = &st->changed[lo];
+        } else {
+            x.mode = TC_MODE_PLAIN;
+            x.mapB = &g.mapBF;
+            x.old_r = nullptr;
+            x.out_r = g.X;
+            x.out_rt = nullptr;
+            x.changed = &st->changed[lo];
+        }
+    }
+};
+
+template <class Src>
+__device__ __forceinline__ void tc_body(const Src& src, int* error, long long limit) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem + OFF_A;
@@ -113,8 +197,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int num_tiles = p.m_tiles * p.n_tiles;
-    const long long limit = p.wait_cycles;
+    const int num_tiles = src.count();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -128,10 +211,6 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         mbar_init(done, 1);
         *abort_flag = 0;
         fence_mbar_init();
-    }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, TMEM_COLS);
@@ -152,17 +231,17 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             for (int s = 0; s < TC_STAGES; ++s) last_par[s] = -1;
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                int mb, nb;
-                tile_coords(t, p.m_tiles, p.n_tiles, mb, nb);
-                for (int kb = 0; kb < p.k_blocks; ++kb) {
-                    if (p.kflags != nullptr && p.kflags[mb * p.k_blocks + kb] == 0) continue;
+                Tile x;
+                src.get(t, x);
+                for (int kb = 0; kb < x.k_blocks; ++kb) {
+                    if (x.kflags != nullptr && x.kflags[x.mb * x.k_blocks + kb] == 0) continue;
                     if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
                         ok = false;
                         break;
                     }
                     mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
-                    tma_load_2d(sA + stage * A_BYTES, &tmA, kb * TC_BK, mb * TC_BM, &full[stage]);
-                    tma_load_2d(sB + stage * B_BYTES, &tmB, kb * TC_BK, nb * TC_BN, &full[stage]);
+                    tma_load_2d(sA + stage * A_BYTES, x.mapA, kb * TC_BK, x.mb * TC_BM, &full[stage]);
+                    tma_load_2d(sB + stage * B_BYTES, x.mapB, kb * TC_BK, x.nb * TC_BN, &full[stage]);
                     last_par[stage] = static_cast<int>(phase);
                     if (++stage == TC_STAGES) {
                         stage = 0;
@@ -171,7 +250,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 }
             }
             if (!ok) {
-                atomicCAS(p.error, 0, ERR_WAIT_PRODUCER);
+                atomicCAS(error, 0, ERR_WAIT_PRODUCER);
                 // let every copy this CTA issued land before the CTA exits
                 volatile int never = 0;
                 for (int s = 0; s < TC_STAGES; ++s)
@@ -187,8 +266,8 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-            int mb, nb;
-            tile_coords(t, p.m_tiles, p.n_tiles, mb, nb);
+            Tile x;
+            src.get(t, x);
             if (!wait_lane0(&tempty[acc], acc_phase ^ 1u, abort_flag, limit, lane)) {
                 ok = false;
                 break;
@@ -196,8 +275,8 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * ACC_COLS);
             uint32_t accumulate = 0;
-            for (int kb = 0; kb < p.k_blocks; ++kb) {
-                if (p.kflags != nullptr && p.kflags[mb * p.k_blocks + kb] == 0) continue;
+            for (int kb = 0; kb < x.k_blocks; ++kb) {
+                if (x.kflags != nullptr && x.kflags[x.mb * x.k_blocks + kb] == 0) continue;
                 if (!wait_lane0(&full[stage], phase, abort_flag, limit, lane)) {
                     ok = false;
                     break;
@@ -227,7 +306,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
-        if (!ok && lane == 0) atomicCAS(p.error, 0, ERR_WAIT_MMA);
+        if (!ok && lane == 0) atomicCAS(error, 0, ERR_WAIT_MMA);
         // every MMA this thread issued must finish before TMEM is freed
         if (lane == 0) {
             tc_commit(done);
@@ -242,19 +321,19 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x) {
-            int mb, nb;
-            tile_coords(t, p.m_tiles, p.n_tiles, mb, nb);
+            Tile x;
+            src.get(t, x);
             if (!wait_lane0(&tfull[acc], acc_phase, abort_flag, limit, lane)) {
-                if (lane == 0) atomicCAS(p.error, 0, ERR_WAIT_EPILOGUE);
+                if (lane == 0) atomicCAS(error, 0, ERR_WAIT_EPILOGUE);
                 break;
             }
             tc_fence_after();
             bool active = true;
-            if (p.kflags != nullptr) {
+            if (x.kflags != nullptr) {
                 active = false;
-                for (int kb = 0; kb < p.k_blocks && !active; ++kb) active = p.kflags[mb * p.k_blocks + kb] != 0;
+                for (int kb = 0; kb < x.k_blocks && !active; ++kb) active = x.kflags[x.mb * x.k_blocks + kb] != 0;
             }
-            const int64_t row = static_cast<int64_t>(mb) * TC_BM + row_in_tile;
+            const int64_t row = static_cast<int64_t>(x.mb) * TC_BM + row_in_tile;
             uint32_t any = 0;
 #pragma unroll 1
             for (int c0 = 0; c0 < TC_BN; c0 += 32) {
@@ -270,22 +349,22 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 uint32_t cbits = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) cbits |= (v[j] != 0u ? 1u : 0u) << j;
-                const int64_t col0 = static_cast<int64_t>(nb) * TC_BN + c0;
-                const int64_t off = row * p.ld + col0;
-                if (p.mode == TC_MODE_RMS) {
-                    const uint4* o = reinterpret_cast<const uint4*>(p.old_r + off);
+                const int64_t col0 = static_cast<int64_t>(x.nb) * TC_BN + c0;
+                const int64_t off = row * x.ld + col0;
+                if (x.mode == TC_MODE_RMS) {
+                    const uint4* o = reinterpret_cast<const uint4*>(x.old_r + off);
                     const uint32_t obits = nz_mask32(o[0], o[1]);
                     const uint32_t nbits = obits | cbits;
                     any |= nbits ^ obits;
-                    uint4* w = reinterpret_cast<uint4*>(p.out_r + off);
+                    uint4* w = reinterpret_cast<uint4*>(x.out_r + off);
                     w[0] = mask_to_bytes16(nbits & 0xFFFFu);
                     w[1] = mask_to_bytes16(nbits >> 16);
-                    uint8_t* tcol = p.out_rt + col0 * p.ld + row;
+                    uint8_t* tcol = x.out_rt + col0 * x.ld + row;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        tcol[j * p.ld] = ((nbits >> j) & 1u) ? static_cast<uint8_t>(BMLP_E4M3_ONE) : 0;
-                } else if (p.mode == TC_MODE_SMP) {
-                    uint4* vp = reinterpret_cast<uint4*>(p.visited + off);
+                        tcol[j * x.ld] = ((nbits >> j) & 1u) ? static_cast<uint8_t>(BMLP_E4M3_ONE) : 0;
+                } else if (x.mode == TC_MODE_SMP) {
+                    uint4* vp = reinterpret_cast<uint4*>(x.visited + off);
                     const uint32_t vbits = nz_mask32(vp[0], vp[1]);
                     const uint32_t nbits = cbits & ~vbits;
                     any |= nbits;
@@ -293,20 +372,20 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                         const uint32_t nv = vbits | nbits;
                         vp[0] = mask_to_bytes16(nv & 0xFFFFu);
                         vp[1] = mask_to_bytes16(nv >> 16);
-                        p.kflags_next[mb * p.k_blocks + static_cast<int>(col0 / TC_BK)] = 1;
+                        x.kflags_next[x.mb * x.k_blocks + static_cast<int>(col0 / TC_BK)] = 1;
                     }
-                    uint4* w = reinterpret_cast<uint4*>(p.out_r + off);
+                    uint4* w = reinterpret_cast<uint4*>(x.out_r + off);
                     w[0] = mask_to_bytes16(nbits & 0xFFFFu);
                     w[1] = mask_to_bytes16(nbits >> 16);
                 } else {
-                    uint4* w = reinterpret_cast<uint4*>(p.out_r + off);
+                    uint4* w = reinterpret_cast<uint4*>(x.out_r + off);
                     w[0] = mask_to_bytes16(cbits & 0xFFFFu);
                     w[1] = mask_to_bytes16(cbits >> 16);
                 }
             }
             tc_fence_before();
             mbar_arrive(&tempty[acc]);
-            if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
+            if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(x.changed, 1);
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
@@ -318,6 +397,23 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         tc_fence_after();
         tmem_dealloc(tmem_base, TMEM_COLS);
     }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+    if (threadIdx.x == 0) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    SingleSource src{&tmA, &tmB, &p};
+    tc_body(src, p.error, p.wait_cycles);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_group_kernel(const GroupProblem* probs, const GroupState* st, int nprob, int phase, int* error,
+                long long wait_cycles) {
+    GroupSource src{probs, st, nprob, *st->tc_total, phase};
+    tc_body(src, error, wait_cycles);
 }
 
 }  // namespace
@@ -351,6 +447,12 @@ cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const 
     if (e != cudaSuccess) return e;
     tc_product_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(a, b, p);
     return cudaGetLastError();
+}
+
+void* tc_group_kernel_ptr() { return reinterpret_cast<void*>(&tc_group_kernel); }
+
+cudaError_t prepare_tc_group() {
+    return cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 }  // namespace bmlp

@@ -1,0 +1,124 @@
+"""Grouped batch (one persistent launch per iteration, device loop in a CUDA
+graph) and the single-problem device loop: bit-exact against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as wl
+
+pkg = pytest.importorskip("paper_2408_10369_gb300")
+from paper_2408_10369_gb300 import bmlp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def kg_problem_set(n_ent, n_rel, n_triples, n_pairs, seed, fmt):
+    rels = wl.kg_relations(n_ent=n_ent, n_rel=n_rel, n_triples=n_triples, seed=seed)
+    items, expect, keep = [], [], []
+    for r in rels:
+        n = r["n"]
+        m = wl.dense_u8(n, r["indptr"], r["indices"])
+        R = dev(m if fmt == bmlp.BMLP_FMT_U8 else wl.pack_rows(m).view(np.int64))
+        out = torch.zeros_like(R)
+        keep += [R, out]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_CLOSURE, n=n, R1=R, out=out, fmt=fmt))
+        expect.append(("closure", n, r["indptr"], r["indices"]))
+    for a, b in wl.kg_compose_pairs(rels, n_pairs, seed):
+        n, ents, c1, c2 = wl.union_space(rels[a], rels[b])
+        m1, m2 = wl.dense_u8(n, *c1), wl.dense_u8(n, *c2)
+        if fmt != bmlp.BMLP_FMT_U8:
+            m1, m2 = wl.pack_rows(m1).view(np.int64), wl.pack_rows(m2).view(np.int64)
+        R1, R2 = dev(m1), dev(m2)
+        out = torch.zeros_like(R1)
+        keep += [R1, R2, out]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=out, fmt=fmt))
+        expect.append(("compose", n, c1, c2))
+    return items, expect, keep
+
+
+def check(items, expect, iters=None):
+    for it, ex in zip(items, expect):
+        got = it["out"].cpu().numpy()
+        n = ex[1]
+        if it["fmt"] == bmlp.BMLP_FMT_PACKED64:
+            got = wl.unpack_rows(got.view(np.uint64), n)
+        if ex[0] == "closure":
+            want = oracle.closure(n, ex[2], ex[3])
+        else:
+            want = oracle.compose_rows(n, ex[2], ex[3])
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", ["auto", "rms_tc", "rms_packed"])
+@pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
+def test_batch_kg_small(ctx, variant, fmt):
+    items, expect, keep = kg_problem_set(1500, 40, 9000, 8, 3, fmt)
+    iters = ctx.batch_run(items, variant=variant)
+    torch.cuda.synchronize()
+    check(items, expect)
+    # closure iteration counts follow the closed form
+    for it, ex, k in zip(items, expect, iters):
+        if ex[0] == "closure":
+            assert k == oracle.rms_iterations(oracle.longest_shortest_path(ex[1], ex[2], ex[3]))
+
+
+def test_batch_repeat_uses_cached_graph(ctx):
+    items, expect, keep = kg_problem_set(800, 20, 4000, 4, 5, bmlp.BMLP_FMT_U8)
+    a = ctx.batch_run(items)
+    for it in items:
+        it["out"].zero_()
+    b = ctx.batch_run(items)
+    torch.cuda.synchronize()
+    assert a == b
+    check(items, expect)
+
+
+def test_batch_autotune_then_run(ctx, tmp_path):
+    items, expect, keep = kg_problem_set(1200, 30, 7000, 0, 7, bmlp.BMLP_FMT_U8)
+    cache = str(tmp_path / "tune.txt")
+    ctx.batch_autotune(items, cache)
+    with open(cache) as f:
+        lines = f.read().strip().splitlines()
+    assert lines and all(len(ln.split()) == 5 for ln in lines)
+    ctx.batch_autotune(items, cache)        # second call reads the cache
+    ctx.batch_run(items)
+    torch.cuda.synchronize()
+    check(items, expect)
+
+
+def test_batch_edge_cases(ctx):
+    n = 5
+    R = dev(np.roll(np.eye(n, dtype=np.uint8), 1, axis=1))
+    out = torch.zeros_like(R)
+    E = torch.zeros((1, 1), dtype=torch.uint8, device="cuda")
+    items = [dict(n=0, R1=None, out=None), dict(n=n, R1=R, out=out, reflexive=True),
+             dict(n=1, R1=E, out=torch.zeros_like(E))]
+    iters = ctx.batch_run(items)
+    torch.cuda.synchronize()
+    assert iters[0] == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), np.ones((n, n), np.uint8))
+    assert items[2]["out"].item() == 0
+
+
+@pytest.mark.parametrize("variant", ["rms_tc", "rms_packed"])
+@pytest.mark.parametrize("n,d,seed", [(1, 0.0, 0), (65, 1.5, 1), (300, 1.2, 2), (1000, 2.0, 3), (2000, 1.0, 4)])
+def test_single_problem_device_loop(ctx, variant, n, d, seed):
+    ip, ix = wl.er_graph(n, d, seed)
+    R = dev(wl.dense_u8(n, ip, ix))
+    out = torch.zeros_like(R)
+    it = ctx.rms(R, n, out, variant=variant, loop=bmlp.BMLP_LOOP_GRAPH)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.closure(n, ip, ix))
+    assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
