@@ -52,7 +52,8 @@ typedef enum bmlp_status {
     BMLP_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed         */
     BMLP_ERR_TIMEOUT = 4,       /* a bounded in-kernel wait ran out           */
     BMLP_ERR_NOT_CONVERGED = 5, /* fixpoint not reached within max_iters      */
-    BMLP_ERR_UNSUPPORTED = 6    /* size or variant outside what is built      */
+    BMLP_ERR_UNSUPPORTED = 6,   /* size or variant outside what is built      */
+    BMLP_ERR_BUDGET = 7         /* stopped at options.budget_ns; output undefined */
 } bmlp_status;
 
 typedef enum bmlp_format {
@@ -88,6 +89,12 @@ typedef struct bmlp_options {
     int32_t profile;     /* 1: time the product kernel with CUDA events        */
     int32_t reserved;
     uint64_t timeout_ns; /* bound of every in-kernel wait; 0 = 2 s             */
+    uint64_t budget_ns;  /* 0 = none; else the call gives up (BMLP_ERR_BUDGET)
+                            once about this much time has passed: checked
+                            between launches and, in the packed kernels, by
+                            every warp before each row / query (used to time
+                            variants with a cap, e.g. by the dispatcher's
+                            training sweep)                                    */
 } bmlp_options;
 
 /* Per-call statistics of the last call on a context. */
@@ -178,7 +185,8 @@ typedef struct bmlp_problem {
     int32_t kind;       /* bmlp_problem_kind                                      */
     int32_t fmt;        /* bmlp_format of R1, R2 and out                          */
     int32_t reflexive;  /* closures only: 1 gives I + R1+                         */
-    int32_t reserved;
+    int32_t variant;    /* closures only: 0 = the batch's choice, else
+                           BMLP_RMS_TC or BMLP_RMS_PACKED for this problem       */
     int64_t n;          /* matrix size (0 = nothing to do)                        */
     const void* R1;     /* device memory                                          */
     const void* R2;     /* device memory, compositions only                       */
@@ -217,6 +225,75 @@ bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
  */
 bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const char* cache_path,
                                 cudaStream_t stream);
+
+/*
+ * Learned dispatcher. Every variant returns the same bits; which is fastest
+ * depends on the graph (Appendix C: squaring costs O(n^3 log n) whatever the
+ * density, frontier expansion O(n^3) in the worst case but far less on sparse
+ * inputs). A small MLP predicts the log2 run time (ms) of the four variants
+ * from 16 features computed on the GPU, and BMLP_AUTO runs the argmin once a
+ * model is trained or loaded (without one, BMLP_AUTO means BMLP_RMS_TC).
+ *
+ * Features (index: meaning): 0 log2 n; 1 log2(1 + nnz); 2 mean out-degree;
+ * 3 std out-degree; 4 max out-degree / n; 5 fraction of empty rows; 6 std
+ * in-degree and 7 max in-degree / n, 8 fraction of empty columns (estimated
+ * from min(n, 1024) evenly spaced rows); 9 self-loop fraction; 10 reciprocity
+ * of the sampled edges; 11 nonzero 64-bit words / all words; 12 mean |i - j|
+ * / n of the sampled edges; 13 mean two-step probe reach / n; 14 log2 of the
+ * probe growth from step one to step two; 15 fraction of probes whose second
+ * step is empty. Probes: the first 64 sampled rows, second step = OR of up to
+ * 64 rows of the first-step frontier.
+ *
+ * Network: 16 -> 64 -> 64 -> 4, ReLU, inputs normalised by (x - mu) / sigma
+ * of the training features. Parameters (BMLP_MLP_PARAMS floats, this order):
+ * W1[64][16], b1[64], W2[64][64], b2[64], W3[4][64], b3[4]. Weights are used
+ * in FP16 with FP32 accumulation; training keeps FP32 master weights (Adam).
+ * Outputs are ordered BMLP_RMS_TC, BMLP_RMS_PACKED, BMLP_SMP_TC,
+ * BMLP_SMP_PACKED. Loss: mean squared error of the log2 times, where a
+ * censored time (the run hit its budget) only penalises predictions below it.
+ */
+#define BMLP_NFEAT 16
+#define BMLP_NVAR 4
+#define BMLP_MLP_PARAMS 5508
+
+typedef struct bmlp_train_cfg {
+    int32_t epochs;      /* passes over the training set                       */
+    int32_t batch;       /* mini-batch size (0 = 256)                          */
+    float lr;            /* Adam step size                                      */
+    float weight_decay;  /* L2 added to the gradient                            */
+    uint64_t seed;       /* initialisation and shuffling                       */
+} bmlp_train_cfg;
+
+/* The 16 features of an n x n matrix R (format fmt, device or host memory);
+ * feats is a host array of BMLP_NFEAT floats. */
+bmlp_status bmlp_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats,
+                                   cudaStream_t stream);
+
+/* Train the network on m samples (host arrays): feats m x 16, log2_ms m x 4,
+ * censored m x 4 (1 = that run hit its budget). Re-initialises the weights
+ * from cfg->seed, sets the normalisation from feats, runs on the GPU and
+ * leaves the model active. final_loss (may be null) gets the last epoch's
+ * mean loss. */
+bmlp_status bmlp_dispatch_train(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,
+                                int64_t m, const bmlp_train_cfg* cfg, float* final_loss);
+
+/* Predicted log2 ms (m x 4, may be null) and chosen bmlp_variant (m, may be
+ * null) for m host feature rows. */
+bmlp_status bmlp_dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float* pred, int32_t* choice);
+
+/* Loss and gradient (BMLP_MLP_PARAMS floats) over m samples at the current
+ * weights, computed by the training kernels' forward and backward code. */
+bmlp_status bmlp_dispatch_loss_grad(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,
+                                    int64_t m, float* loss, float* grad);
+
+/* Set / get the FP32 parameters and the normalisation (mu, sigma: 16 each;
+ * any pointer may be null). Setting marks the model active. */
+bmlp_status bmlp_dispatch_set_params(bmlp_ctx* ctx, const float* params, const float* mu, const float* sigma);
+bmlp_status bmlp_dispatch_get_params(bmlp_ctx* ctx, float* params, float* mu, float* sigma);
+
+/* Save / load the model (binary: magic, sizes, mu, sigma, parameters). */
+bmlp_status bmlp_dispatch_save(bmlp_ctx* ctx, const char* path);
+bmlp_status bmlp_dispatch_load(bmlp_ctx* ctx, const char* path);
 
 /*
  * bmlp_rms_tc_noalloc - the tensor-core closure of bmlp_rms (variant

@@ -26,6 +26,7 @@ BMLP_ERR_CUDA = 3
 BMLP_ERR_TIMEOUT = 4
 BMLP_ERR_NOT_CONVERGED = 5
 BMLP_ERR_UNSUPPORTED = 6
+BMLP_ERR_BUDGET = 7
 
 BMLP_FMT_U8 = 0
 BMLP_FMT_PACKED64 = 1
@@ -42,13 +43,14 @@ BMLP_LOOP_GRAPH = 1
 VARIANTS = {"auto": BMLP_AUTO, "rms_tc": BMLP_RMS_TC, "rms_packed": BMLP_RMS_PACKED,
             "smp_tc": BMLP_SMP_TC, "smp_packed": BMLP_SMP_PACKED}
 
-_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_CONVERGED", 6: "UNSUPPORTED"}
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_CONVERGED", 6: "UNSUPPORTED",
+           7: "BUDGET"}
 
 
 class bmlp_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("reflexive", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("loop", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("timeout_ns", ctypes.c_uint64)]
+                ("timeout_ns", ctypes.c_uint64), ("budget_ns", ctypes.c_uint64)]
 
 
 class bmlp_stats(ctypes.Structure):
@@ -59,12 +61,21 @@ class bmlp_stats(ctypes.Structure):
 
 class bmlp_problem(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("fmt", ctypes.c_int32), ("reflexive", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("n", ctypes.c_int64), ("R1", ctypes.c_void_p),
+                ("variant", ctypes.c_int32), ("n", ctypes.c_int64), ("R1", ctypes.c_void_p),
                 ("R2", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
 BMLP_PROBLEM_CLOSURE = 0
 BMLP_PROBLEM_COMPOSE = 1
+
+BMLP_NFEAT = 16
+BMLP_NVAR = 4
+BMLP_MLP_PARAMS = 5508
+
+
+class bmlp_train_cfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("weight_decay", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 class BmlpError(RuntimeError):
@@ -108,8 +119,20 @@ def lib():
             L.bmlp_batch_run.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.POINTER(bmlp_options),
                                          ctypes.POINTER(i32), vp]
             L.bmlp_batch_autotune.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.c_char_p, vp]
+            fp, u8p = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint8)
+            L.bmlp_dispatch_features.argtypes = [vp, vp, i64, i32, fp, vp]
+            L.bmlp_dispatch_train.argtypes = [vp, fp, fp, u8p, i64, ctypes.POINTER(bmlp_train_cfg), fp]
+            L.bmlp_dispatch_predict.argtypes = [vp, fp, i64, fp, ctypes.POINTER(i32)]
+            L.bmlp_dispatch_loss_grad.argtypes = [vp, fp, fp, u8p, i64, fp, fp]
+            L.bmlp_dispatch_set_params.argtypes = [vp, fp, fp, fp]
+            L.bmlp_dispatch_get_params.argtypes = [vp, fp, fp, fp]
+            L.bmlp_dispatch_save.argtypes = [vp, ctypes.c_char_p]
+            L.bmlp_dispatch_load.argtypes = [vp, ctypes.c_char_p]
             for name in ("bmlp_ctx_create", "bmlp_ctx_destroy", "bmlp_get_stats", "bmlp_rms", "bmlp_smp",
-                         "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune"):
+                         "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune", "bmlp_dispatch_features",
+                         "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_loss_grad",
+                         "bmlp_dispatch_set_params", "bmlp_dispatch_get_params", "bmlp_dispatch_save",
+                         "bmlp_dispatch_load"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -135,6 +158,14 @@ def _ptr(a):
     raise TypeError("expected a torch.Tensor, a numpy array or an int address")
 
 
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _u8ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
 def _stream(stream, device):
     if stream is None:
         import torch
@@ -146,7 +177,8 @@ def _stream(stream, device):
     return ctypes.c_void_p(int(stream))
 
 
-def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HOST, profile=False, timeout_ns=0):
+def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HOST, profile=False, timeout_ns=0,
+                 budget_ns=0):
     o = bmlp_options()
     lib().bmlp_default_options(ctypes.byref(o))
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -155,6 +187,7 @@ def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HO
     o.loop = int(loop)
     o.profile = int(bool(profile))
     o.timeout_ns = int(timeout_ns)
+    o.budget_ns = int(budget_ns)
     return o
 
 
@@ -224,6 +257,8 @@ class Context:
             p.kind = int(it.get("kind", BMLP_PROBLEM_CLOSURE))
             p.fmt = int(it.get("fmt", BMLP_FMT_U8))
             p.reflexive = int(bool(it.get("reflexive", False)))
+            v = it.get("variant", 0)
+            p.variant = VARIANTS[v] if isinstance(v, str) else int(v)
             p.n = int(it["n"])
             p.R1 = _ptr(it["R1"]).value if it.get("R1") is not None else None
             p.R2 = _ptr(it["R2"]).value if it.get("R2") is not None else None
@@ -245,6 +280,68 @@ class Context:
         arr = items if isinstance(items, ctypes.Array) else self.problems(items)
         path = cache_path.encode() if cache_path else None
         self._check(self._L.bmlp_batch_autotune(self.handle, arr, len(items), path, _stream(stream, self.device)))
+
+    # ---------------------------------------------------- dispatcher --
+    def dispatch_features(self, R, n, fmt=BMLP_FMT_U8, stream=None):
+        """bmlp_dispatch_features: the 16 features (numpy float32)."""
+        import numpy as np
+        f = np.zeros(BMLP_NFEAT, np.float32)
+        self._check(self._L.bmlp_dispatch_features(self.handle, _ptr(R), int(n), int(fmt), _fptr(f),
+                                                   _stream(stream, self.device)))
+        return f
+
+    def dispatch_train(self, feats, log2_ms, censored, epochs=200, batch=256, lr=1e-3, weight_decay=1e-4, seed=0):
+        """bmlp_dispatch_train on host arrays; returns the last epoch's loss."""
+        import numpy as np
+        X = np.ascontiguousarray(feats, np.float32)
+        Y = np.ascontiguousarray(log2_ms, np.float32)
+        C = np.ascontiguousarray(censored, np.uint8)
+        cfg = bmlp_train_cfg(int(epochs), int(batch), float(lr), float(weight_decay), int(seed))
+        loss = ctypes.c_float(0)
+        self._check(self._L.bmlp_dispatch_train(self.handle, _fptr(X), _fptr(Y), _u8ptr(C), X.shape[0],
+                                                ctypes.byref(cfg), ctypes.byref(loss)))
+        return loss.value
+
+    def dispatch_predict(self, feats):
+        """bmlp_dispatch_predict: (pred m x 4 log2 ms, chosen bmlp_variant m)."""
+        import numpy as np
+        X = np.ascontiguousarray(np.atleast_2d(feats), np.float32)
+        m = X.shape[0]
+        pred = np.zeros((m, BMLP_NVAR), np.float32)
+        choice = np.zeros(m, np.int32)
+        self._check(self._L.bmlp_dispatch_predict(self.handle, _fptr(X), m, _fptr(pred),
+                                                  choice.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return pred, choice
+
+    def dispatch_loss_grad(self, feats, log2_ms, censored):
+        import numpy as np
+        X = np.ascontiguousarray(feats, np.float32)
+        Y = np.ascontiguousarray(log2_ms, np.float32)
+        C = np.ascontiguousarray(censored, np.uint8)
+        g = np.zeros(BMLP_MLP_PARAMS, np.float32)
+        loss = ctypes.c_float(0)
+        self._check(self._L.bmlp_dispatch_loss_grad(self.handle, _fptr(X), _fptr(Y), _u8ptr(C), X.shape[0],
+                                                    ctypes.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def dispatch_set_params(self, params=None, mu=None, sigma=None):
+        import numpy as np
+        a = [None if x is None else np.ascontiguousarray(x, np.float32) for x in (params, mu, sigma)]
+        self._check(self._L.bmlp_dispatch_set_params(self.handle, *[_fptr(x) if x is not None else None for x in a]))
+
+    def dispatch_get_params(self):
+        import numpy as np
+        p = np.zeros(BMLP_MLP_PARAMS, np.float32)
+        mu = np.zeros(BMLP_NFEAT, np.float32)
+        sg = np.zeros(BMLP_NFEAT, np.float32)
+        self._check(self._L.bmlp_dispatch_get_params(self.handle, _fptr(p), _fptr(mu), _fptr(sg)))
+        return p, mu, sg
+
+    def dispatch_save(self, path):
+        self._check(self._L.bmlp_dispatch_save(self.handle, str(path).encode()))
+
+    def dispatch_load(self, path):
+        self._check(self._L.bmlp_dispatch_load(self.handle, str(path).encode()))
 
     def compose(self, R1, R2, n, out, fmt=BMLP_FMT_U8, stream=None, **opt):
         """bmlp_compose: out = (I + R2+) R1. Returns the closure's products."""

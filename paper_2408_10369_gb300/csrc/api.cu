@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/bmlp.h): argument checks,
 // host/device staging, the fixpoint drivers of BMLP-RMS (Algorithm 1),
 // BMLP-SMP (Algorithm 2) and composition (Thm. 1), and the workspace.
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,7 +64,8 @@ namespace {
 enum : int {
     WS_IN0 = 0, WS_IN1 = 1, WS_OUT = 2,
     WS_M0 = 3, WS_M1 = 4, WS_T0 = 5, WS_T1 = 6, WS_M2 = 7,
-    WS_WPTR = 8, WS_WIDX = 9, WS_WVAL = 10, WS_F0 = 11, WS_F1 = 12, WS_V = 13, WS_SRC = 14
+    WS_WPTR = 8, WS_WIDX = 9, WS_WVAL = 10, WS_F0 = 11, WS_F1 = 12, WS_V = 13, WS_SRC = 14,
+    WS_FEAT = 16
 };
 
 struct DeviceGuard {
@@ -171,11 +173,31 @@ int log2_ceil(int64_t n) {
 }
 
 // Reads the control words after one iteration; maps device error words.
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Start of a call: clock for the time budget, all control words cleared.
+bmlp_status begin_call(bmlp_ctx* ctx, const bmlp_options& o, cudaStream_t s) {
+    ctx->t_call = now_s();
+    ctx->budget_ns = o.budget_ns;
+    CK(cudaMemsetAsync(ctx->d_ctl, 0, CTL_WORDS * sizeof(int), s), "reset flags");
+    return BMLP_OK;
+}
+
+Deadline deadline_of(bmlp_ctx* ctx) {
+    return Deadline{ctx->budget_ns, reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_T0),
+                    ctx->d_ctl + CTL_BUDGET};
+}
+
 bmlp_status read_ctl(bmlp_ctx* ctx, cudaStream_t s, int* changed) {
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, CTL_WORDS * sizeof(int), cudaMemcpyDeviceToHost, s), "read flags");
     CK(cudaStreamSynchronize(s), "synchronise iteration");
     if (ctx->h_ctl[CTL_ERROR] != 0)
         return set_err(ctx, BMLP_ERR_TIMEOUT, "in-kernel wait timed out (code 0x%x)", ctx->h_ctl[CTL_ERROR]);
+    if (ctx->budget_ns &&
+        (ctx->h_ctl[CTL_BUDGET] != 0 || (now_s() - ctx->t_call) * 1e9 > static_cast<double>(ctx->budget_ns)))
+        return set_err(ctx, BMLP_ERR_BUDGET, "time budget of %.3f ms used up", ctx->budget_ns * 1e-6);
     if (changed) *changed = ctx->h_ctl[CTL_CHANGED];
     return BMLP_OK;
 }
@@ -264,7 +286,8 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
         ST(tm.begin());
-        CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s),
+        CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s,
+                                 deadline_of(ctx)),
            "packed product launch");
         ST(tm.end());
         ctx->stats.product_launches++;
@@ -342,7 +365,8 @@ void reset_stats(bmlp_ctx* ctx, int variant, int64_t n_pad) {
     ctx->stats.n_pad = n_pad;
 }
 
-int pick_variant_rms(int64_t n) { return n >= 1024 ? BMLP_RMS_TC : BMLP_RMS_PACKED; }
+// Without a trained dispatcher the fixed choice is squaring on the tensor cores.
+int pick_variant_rms(int64_t) { return BMLP_RMS_TC; }
 
 // Frontier expansion (Algorithm 2) on packed rows for the sources `src`
 // (device, q x ldw_src words). out: device, q x ldw_out words.
@@ -362,12 +386,12 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                          static_cast<uint64_t*>(wval), s),
        "word index build");
     ctx->stats.launches += 3;
-    CK(cudaMemsetAsync(ctx->d_ctl, 0, CTL_WORDS * sizeof(int), s), "reset flags");
+    CK(cudaMemsetAsync(ctx->d_ctl + CTL_LEVELS, 0, 3 * sizeof(int), s), "reset level and query counters");
     ProductTimer tm{ctx, o.profile != 0, s};
     ST(tm.begin());
     CK(launch_smp_packed(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval), n, ldw,
                          src, ldw_src, q, out, ldw_out, ctx->d_ctl + CTL_LEVELS, ctx->d_ctl + CTL_QCOUNT, o.reflexive,
-                         ctx->sm_count, s),
+                         ctx->sm_count, s, deadline_of(ctx)),
        "frontier kernel launch");
     ST(tm.end());
     ctx->stats.product_launches++;
@@ -497,6 +521,7 @@ bmlp_status bmlp_ctx_destroy(bmlp_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     batch_cache_free(ctx);
+    dispatch_free(ctx);
     for (auto& b : ctx->ws)
         if (b.p) cudaFree(b.p);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
@@ -528,11 +553,25 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
     bmlp_options o = resolve(opts);
     int variant = o.variant == BMLP_AUTO ? pick_variant_rms(n) : o.variant;
     reset_stats(ctx, variant, n);
+    ST(begin_call(ctx, o, s));
     const int max_iters = o.max_iters > 0 ? o.max_iters : log2_ceil(n) + 2;
     Operand in;
     OutView ov;
     ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
     ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    if (o.variant == BMLP_AUTO && dispatch_trained(ctx)) {
+        // learned choice: features on the GPU, MLP prediction, argmin
+        const int64_t ldw = round_up(words_of(n), 2);
+        void* P = nullptr;
+        ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
+        ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+        float feats[BMLP_NFEAT];
+        ST(dispatch_features_packed(ctx, static_cast<uint64_t*>(P), n, ldw, feats, s));
+        int32_t choice = BMLP_RMS_TC;
+        ST(dispatch_predict(ctx, feats, 1, nullptr, &choice, s));
+        variant = choice;
+        ctx->stats.variant = variant;
+    }
     int iters = 0;
     bmlp_status st = BMLP_OK;
     if (o.loop == BMLP_LOOP_GRAPH && (variant == BMLP_RMS_TC || variant == BMLP_RMS_PACKED)) {
@@ -626,6 +665,7 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const
     if (variant != BMLP_SMP_PACKED && variant != BMLP_SMP_TC)
         return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a frontier variant", variant);
     reset_stats(ctx, variant, n);
+    ST(begin_call(ctx, o, s));
     const int64_t ldw = words_of(n);
     Operand in, src;
     OutView ov;
@@ -661,6 +701,7 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
     if (variant != BMLP_RMS_TC && variant != BMLP_RMS_PACKED)
         return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a composition variant", variant);
     reset_stats(ctx, variant, n);
+    ST(begin_call(ctx, o, s));
     const int max_iters = o.max_iters > 0 ? o.max_iters : log2_ceil(n) + 2;
     Operand a, b;
     OutView ov;
@@ -826,6 +867,70 @@ bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_
         }
     }
     return BMLP_OK;
+}
+
+bmlp_status bmlp_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats, cudaStream_t s) {
+    if (!ctx || !feats) return BMLP_ERR_INVALID_ARG;
+    if (n <= 0 || !R) return set_err(ctx, BMLP_ERR_INVALID_ARG, "features need n > 0 and a matrix");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    DeviceGuard g(ctx->device);
+    Operand in;
+    ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
+    const int64_t ldw = round_up(words_of(n), 2);
+    void* P = nullptr;
+    ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
+    ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+    return dispatch_features_packed(ctx, static_cast<uint64_t*>(P), n, ldw, feats, s);
+}
+
+bmlp_status bmlp_dispatch_train(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,
+                                int64_t m, const bmlp_train_cfg* cfg, float* final_loss) {
+    if (!ctx || !cfg) return BMLP_ERR_INVALID_ARG;
+    if (m <= 0 || !feats || !log2_ms || !censored) return set_err(ctx, BMLP_ERR_INVALID_ARG, "empty training set");
+    if (cfg->epochs < 0 || cfg->batch < 0 || m > (int64_t(1) << 26))
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad training configuration");
+    DeviceGuard g(ctx->device);
+    return dispatch_train(ctx, feats, log2_ms, censored, m, cfg, final_loss);
+}
+
+bmlp_status bmlp_dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float* pred, int32_t* choice) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (m < 0 || (m > 0 && !feats)) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad feature rows");
+    DeviceGuard g(ctx->device);
+    return dispatch_predict(ctx, feats, m, pred, choice, nullptr);
+}
+
+bmlp_status bmlp_dispatch_loss_grad(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,
+                                    int64_t m, float* loss, float* grad) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (m <= 0 || !feats || !log2_ms || !censored || !loss || !grad)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(ctx->device);
+    return dispatch_loss_grad(ctx, feats, log2_ms, censored, m, loss, grad);
+}
+
+bmlp_status bmlp_dispatch_set_params(bmlp_ctx* ctx, const float* params, const float* mu, const float* sigma) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return dispatch_set_params(ctx, params, mu, sigma);
+}
+
+bmlp_status bmlp_dispatch_get_params(bmlp_ctx* ctx, float* params, float* mu, float* sigma) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return dispatch_get_params(ctx, params, mu, sigma);
+}
+
+bmlp_status bmlp_dispatch_save(bmlp_ctx* ctx, const char* path) {
+    if (!ctx || !path) return BMLP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return dispatch_save(ctx, path);
+}
+
+bmlp_status bmlp_dispatch_load(bmlp_ctx* ctx, const char* path) {
+    if (!ctx || !path) return BMLP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return dispatch_load(ctx, path);
 }
 
 }  // extern "C"

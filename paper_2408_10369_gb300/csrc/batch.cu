@@ -400,6 +400,8 @@ bmlp_status add_kernel(bmlp_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* node, cons
 
 int engine_for(bmlp_ctx* ctx, const bmlp_problem& p, int variant) {
     if (p.kind == BMLP_PROBLEM_COMPOSE) return 0;
+    if (p.variant == BMLP_RMS_TC) return 0;
+    if (p.variant == BMLP_RMS_PACKED) return 1;
     if (variant == BMLP_RMS_TC) return 0;
     if (variant == BMLP_RMS_PACKED) return 1;
     const int b = bucket_of(p.n);

@@ -81,6 +81,32 @@ struct GroupState {
     int* pk_total;
 };
 
+// Optional time budget of a long kernel: the first warp to look records the
+// start (%globaltimer) in *t0; any warp that finds more than budget_ns
+// elapsed raises *hit and stops taking work. budget_ns = 0: no budget.
+struct Deadline {
+    unsigned long long budget_ns;
+    unsigned long long* t0;
+    int* hit;
+#ifdef __CUDACC__
+    __device__ __forceinline__ bool past() const {
+        if (budget_ns == 0) return false;
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        unsigned long long s = *reinterpret_cast<volatile unsigned long long*>(t0);
+        if (s == 0) {
+            atomicCAS(t0, 0ull, now);
+            s = *reinterpret_cast<volatile unsigned long long*>(t0);
+        }
+        if (now > s && now - s > budget_ns) {
+            *reinterpret_cast<volatile int*>(hit) = 1;
+            return true;
+        }
+        return false;
+    }
+#endif
+};
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
     void* p = nullptr;
@@ -101,11 +127,18 @@ struct bmlp_ctx {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     bmlp_stats stats{};
     void* encode_fn = nullptr;   // cuTensorMapEncodeTiled from the driver
+    double t_call = 0.0;         // host time at the start of the current call (s)
+    uint64_t budget_ns = 0;      // time budget of the current call (0 = none)
+    void* dispatch = nullptr;    // learned dispatcher state (dispatch.cu)
 };
 
 namespace bmlp {
 
-enum CtlWord : int { CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_WORDS = 16 };
+// CTL_QCOUNT and CTL_T0 are 64-bit words (two ints each, 8-byte aligned).
+enum CtlWord : int {
+    CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
+    CTL_WORDS = 16
+};
 
 // Workspace slot of the grouped batch (the others are private to api.cu).
 constexpr int WS_BATCH = 15;
@@ -114,6 +147,22 @@ constexpr int WS_BATCH = 15;
 bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, int variant, long long wait_cycles,
                            int32_t* iters_out, cudaStream_t s);
 void batch_cache_free(bmlp_ctx* ctx);
+
+// ---- learned dispatcher (dispatch.cu)
+bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, float* feat_host,
+                                     cudaStream_t s);
+bool dispatch_trained(const bmlp_ctx* ctx);
+bmlp_status dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float* pred, int32_t* choice,
+                             cudaStream_t s);
+bmlp_status dispatch_set_params(bmlp_ctx* ctx, const float* params, const float* mu, const float* sig);
+bmlp_status dispatch_get_params(bmlp_ctx* ctx, float* params, float* mu, float* sig);
+bmlp_status dispatch_loss_grad(bmlp_ctx* ctx, const float* X, const float* Y, const uint8_t* C, int64_t m, float* loss,
+                               float* grad);
+bmlp_status dispatch_train(bmlp_ctx* ctx, const float* X, const float* Y, const uint8_t* C, int64_t m,
+                           const bmlp_train_cfg* cfg, float* final_loss);
+bmlp_status dispatch_save(bmlp_ctx* ctx, const char* path);
+bmlp_status dispatch_load(bmlp_ctx* ctx, const char* path);
+void dispatch_free(bmlp_ctx* ctx);
 
 // ---- workspace / error helpers (api.cu)
 bmlp_status set_err(bmlp_ctx* ctx, bmlp_status st, const char* fmt, ...);
@@ -166,14 +215,15 @@ cudaError_t prepare_tc_group();
 // words; raises *changed when dst_i != A_i. With A = B and or_a = 1 this is
 // one squaring step R <- R + R R.
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
-                                  int or_a, int* changed, int sms, cudaStream_t s);
+                                  int or_a, int* changed, int sms, cudaStream_t s, Deadline dl = Deadline{0, nullptr, nullptr});
 // word-CSR of packed rows: counts -> (exclusive scan by caller kernel) -> fill
 // (widx / wval must hold n * ldw entries: the dense worst case)
 cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx,
                               uint64_t* wval, cudaStream_t s);
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
                               int64_t ldw, const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out,
-                              int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s);
+                              int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s,
+                              Deadline dl = Deadline{0, nullptr, nullptr});
 int smp_packed_max_words();
 
 }  // namespace bmlp

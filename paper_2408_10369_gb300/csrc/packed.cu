@@ -34,13 +34,14 @@ __device__ __forceinline__ void or4(uint4& a, const uint4& b) {
 template <int VEC>
 __global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
                                                              uint64_t* __restrict__ dst, int64_t n, int64_t ldw, int or_a,
-                                                             int* changed) {
+                                                             int* changed, Deadline dl) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t chunk_words = 64 * VEC;  // 32 lanes x VEC x 2 words
     uint32_t any = 0;
     for (int64_t i = warp_id; i < n; i += nwarps) {
+        if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
         const uint64_t* arow = A + i * ldw;
         for (int64_t c0 = 0; c0 < ldw; c0 += chunk_words) {
             uint4 acc[VEC];
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(256) smp_packed_kernel(const int64_t* __restri
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
                                                          const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
                                                          uint64_t* __restrict__ out, int64_t ldw_out, int* levels_max,
-                                                         unsigned long long* qcounter, int reflexive, int max_levels) {
+                                                         unsigned long long* qcounter, int reflexive, int max_levels,
+                                                         Deadline dl) {
     extern __shared__ uint64_t sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) smp_packed_kernel(const int64_t* __restri
         __syncwarp();
         int lv = 0;
         while (true) {
+            if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
             for (int64_t wb = 0; wb < wpr; wb += 32) {
                 uint64_t d = (wb + lane < wpr) ? D[wb + lane] : 0ull;
                 while (__any_sync(FULL, d != 0ull)) {
@@ -265,14 +268,14 @@ inline int warps_grid(int64_t rows, int sms) {
 }  // namespace
 
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
-                                  int or_a, int* changed, int sms, cudaStream_t s) {
+                                  int or_a, int* changed, int sms, cudaStream_t s, Deadline dl) {
     const int grid = warps_grid(n, sms);
     if (ldw <= 128)
-        product_packed_kernel<2><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+        product_packed_kernel<2><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
     else if (ldw <= 256)
-        product_packed_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+        product_packed_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
     else
-        product_packed_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed);
+        product_packed_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
     return cudaGetLastError();
 }
 
@@ -289,7 +292,7 @@ int smp_packed_max_words() { return 8192; }
 
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n, int64_t ldw,
                               const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out,
-                              int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s) {
+                              int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s, Deadline dl) {
     const int64_t per_warp = 3 * ldw * static_cast<int64_t>(sizeof(uint64_t));
     int warps = static_cast<int>((200 * 1024) / per_warp);
     if (warps > 8) warps = 8;
@@ -306,7 +309,7 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
     const int max_levels = static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF);
     smp_packed_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(
         wptr, widx, wval, n, ldw, src, ldw_src, q, out, ldw_out, levels,
-        reinterpret_cast<unsigned long long*>(qcounter), reflexive, max_levels);
+        reinterpret_cast<unsigned long long*>(qcounter), reflexive, max_levels, dl);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,104 @@
+"""Learned dispatcher on the GPU: features and gradients against the CPU
+reference, on-GPU training, save/load, and BMLP_AUTO using the model."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import dispatch_ref as ref
+import workloads as wl
+
+pkg = pytest.importorskip("paper_2408_10369_gb300")
+from paper_2408_10369_gb300 import bmlp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def ctx():
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("index", [0, 1, 2, 3, 7, 11, 12, 21])
+def test_features_match_reference(ctx, index):
+    g = wl.corpus_graph(index, n_min=200, n_max=3000)
+    n = g["n"]
+    m = wl.dense_u8(n, g["indptr"], g["indices"])
+    for fmt, R in ((bmlp.BMLP_FMT_U8, m), (bmlp.BMLP_FMT_PACKED64, wl.pack_rows(m).view(np.int64))):
+        f = ctx.dispatch_features(torch.from_numpy(np.ascontiguousarray(R)).cuda(), n, fmt=fmt)
+        np.testing.assert_allclose(f, ref.features(m), rtol=2e-5, atol=1e-6)
+
+
+def test_gradient_matches_reference(ctx):
+    rng = np.random.default_rng(1)
+    p = rng.normal(0, 0.2, ref.NP).astype(np.float32)
+    mu = rng.normal(0, 1, ref.NF).astype(np.float32)
+    sig = rng.uniform(0.5, 2.0, ref.NF).astype(np.float32)
+    X = (rng.normal(0, 1, (300, ref.NF)) * sig + mu).astype(np.float32)
+    Y = rng.normal(0, 2, (300, ref.NV)).astype(np.float32)
+    C = (rng.random((300, ref.NV)) < 0.25).astype(np.uint8)
+    ctx.dispatch_set_params(p, mu, sig)
+    loss, g = ctx.dispatch_loss_grad(X, Y, C)
+    p16 = p.astype(np.float16).astype(np.float64)      # the kernels use FP16 weights
+    want_loss, want_g = ref.loss_grad(p16, mu, sig, X, Y, C)
+    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss) + 1e-6
+    np.testing.assert_allclose(g, want_g, rtol=2e-3, atol=2e-5 * np.abs(want_g).max())
+    pred, choice = ctx.dispatch_predict(X[:50])
+    want = ref.forward(p16, mu, sig, X[:50])
+    np.testing.assert_allclose(pred, want, rtol=1e-3, atol=1e-3)
+    np.testing.assert_array_equal(choice, np.argmin(pred, 1) + 1)
+
+
+def test_training_learns_and_roundtrips(ctx, tmp_path):
+    rng = np.random.default_rng(2)
+    X = rng.normal(0, 1, (3000, ref.NF)).astype(np.float32)
+    A = rng.normal(0, 1, (ref.NF, ref.NV))
+    Y = (np.tanh(X @ A) * 3 + X[:, :4] ** 2).astype(np.float32)
+    C = np.zeros_like(Y, np.uint8)
+    base = float(((Y - Y.mean(0)) ** 2).mean())
+    loss = ctx.dispatch_train(X, Y, C, epochs=60, batch=256, lr=3e-3, weight_decay=0.0, seed=3)
+    assert loss < 0.15 * base, (loss, base)
+    pred, _ = ctx.dispatch_predict(X[:100])
+    path = tmp_path / "model.bin"
+    ctx.dispatch_save(path)
+    c2 = pkg.Context(0)
+    try:
+        c2.dispatch_load(path)
+        pred2, _ = c2.dispatch_predict(X[:100])
+        np.testing.assert_array_equal(pred, pred2)
+        p, mu, sg = c2.dispatch_get_params()
+        p1, mu1, sg1 = ctx.dispatch_get_params()
+        np.testing.assert_array_equal(p, p1)
+    finally:
+        c2.close()
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4])
+def test_auto_runs_the_predicted_variant(ctx, variant):
+    """With a model whose output biases favour one variant, BMLP_AUTO runs it
+    and the closure is still exact."""
+    p = np.zeros(ref.NP, np.float32)
+    p[ref.OB3:ref.NP] = 5.0
+    p[ref.OB3 + variant - 1] = -5.0
+    ctx.dispatch_set_params(p, np.zeros(ref.NF, np.float32), np.ones(ref.NF, np.float32))
+    n = 700
+    ip, ix = wl.er_graph(n, 1.3, 4)
+    R = torch.from_numpy(wl.dense_u8(n, ip, ix)).cuda()
+    out = torch.zeros_like(R)
+    ctx.rms(R, n, out)
+    torch.cuda.synchronize()
+    assert ctx.stats()["variant"] == variant
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.closure(n, ip, ix))
+
+
+def test_budget_censors_a_long_run(ctx):
+    n = 8192
+    ip, ix = wl.er_graph(n, 4.0, 0)
+    P = torch.from_numpy(wl.pack_rows(wl.dense_u8(n, ip, ix)).view(np.int64)).cuda()
+    out = torch.zeros_like(P)
+    with pytest.raises(bmlp.BmlpError) as e:
+        ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_packed", budget_ns=200_000)
+    assert e.value.status == bmlp.BMLP_ERR_BUDGET
+    ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_packed")   # the context is still usable

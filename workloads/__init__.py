@@ -70,6 +70,11 @@ def _L():
             lib.wl_sbm_fill.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_uint64, _i64p, _i32p]
             lib.wl_random_pairs.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, _i32p, _i32p]
+            lib.wl_sbm_sparse_count.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_uint64, _i64p]
+            lib.wl_sbm_sparse_fill.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_uint64, _i64p, _i32p]
+            lib.wl_csr_to_packed.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int64, _u64p]
             _lib = lib
     return _lib
 
@@ -265,3 +270,88 @@ def union_space(rel1, rel2):
         return csr_from_pairs(n, s, d)
 
     return n, ents, remap(rel1), remap(rel2)
+
+
+# ------------------------------------------------------- mixed corpus --
+def sbm_sparse_csr(n: int, nb: int, p_in: float, p_out: float, seed: int):
+    """Sparse SBM (nb = 1: ER) by geometric skip sampling, O(n + m)."""
+    L = _L()
+    cnt = np.zeros(max(n, 1), np.int64)
+    if n > 0:
+        L.wl_sbm_sparse_count(n, nb, float(p_in), float(p_out), seed, _p(cnt, _i64p))
+    indptr = np.zeros(n + 1, np.int64)
+    np.cumsum(cnt[:n], out=indptr[1:])
+    indices = np.zeros(max(int(indptr[-1]), 1), np.int32)
+    if n > 0:
+        L.wl_sbm_sparse_fill(n, nb, float(p_in), float(p_out), seed, _p(indptr, _i64p), _p(indices, _i32p))
+    return indptr, indices[: int(indptr[-1])]
+
+
+def csr_to_packed(n: int, indptr, indices) -> np.ndarray:
+    """Packed LSB-first rows (n x words(n) uint64) straight from CSR."""
+    ld = words(n)
+    rows = np.zeros((max(n, 1), max(ld, 1)), np.uint64)
+    ip = np.ascontiguousarray(indptr, np.int64)
+    ix = np.ascontiguousarray(indices, np.int32)
+    if ix.size == 0:
+        ix = np.zeros(1, np.int32)
+    if n > 0:
+        _L().wl_csr_to_packed(n, _p(ip, _i64p), _p(ix, _i32p), ld, _p(rows, _u64p))
+    return rows[:n, :ld]
+
+
+FAMILIES = ("er", "powerlaw", "chain_grid", "sbm")
+
+
+def _unit(seed, tag, c):
+    return (draw(seed, tag, c) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def corpus_graph(index: int, n_min: int = 256, n_max: int = 32768):
+    """Graph `index` of the mixed corpus (seed = index).
+
+    n is log-uniform in [n_min, n_max]; the family is uniform over ER (mean
+    out-degree U[0.5, 8]), power law (alpha U[1.8, 3], degrees <= 1000),
+    chain or 2-D grid (right/down edges) plus round(1 % of n) random
+    shortcuts, and an 8-block SBM (mean out-degree U[0.5, 8], in:out
+    probability ratio U[4, 32]). Returns a dict with n, family, params, CSR.
+    """
+    s = 1_000_003 + int(index)
+    fam = FAMILIES[draw(s, 20, 0) % 4]
+    u = _unit(s, 20, 1)
+    n = int(round(n_min * (n_max / n_min) ** u))
+    n = max(n_min, min(n_max, n))
+    params = {}
+    if fam == "er":
+        d = 0.5 + 7.5 * _unit(s, 20, 2)
+        params["mean_degree"] = d
+        ip, ix = sbm_sparse_csr(n, 1, d / (n - 1), d / (n - 1), s)
+    elif fam == "powerlaw":
+        a = 1.8 + 1.2 * _unit(s, 20, 2)
+        params["alpha"] = a
+        ip, ix = powerlaw_csr(n, a, 1000, s)
+    elif fam == "chain_grid":
+        grid = draw(s, 20, 2) % 2 == 1
+        params["shape"] = "grid" if grid else "chain"
+        if grid:
+            side = max(2, int(np.sqrt(n)))
+            idx = np.arange(n)
+            r, c = idx // side, idx % side
+            right = idx[(c + 1 < side) & (idx + 1 < n)]
+            down = idx[idx + side < n]
+            src = np.concatenate([right, down])
+            dst = np.concatenate([right + 1, down + side])
+        else:
+            src = np.arange(n - 1)
+            dst = src + 1
+        m = max(1, int(round(0.01 * n)))
+        a, b = random_pairs(n, m, s)
+        ip, ix = csr_from_pairs(n, np.concatenate([src, a]), np.concatenate([dst, b]))
+    else:
+        d = 0.5 + 7.5 * _unit(s, 20, 2)
+        ratio = 4.0 + 28.0 * _unit(s, 20, 3)
+        B = n / 8.0
+        p_out = d / (ratio * (B - 1) + (n - B))
+        params.update(mean_degree=d, ratio=ratio)
+        ip, ix = sbm_sparse_csr(n, 8, min(1.0, ratio * p_out), p_out, s)
+    return dict(index=int(index), family=fam, n=n, params=params, indptr=ip, indices=ix)

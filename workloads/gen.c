@@ -206,6 +206,74 @@ void wl_sbm_fill(int64_t n, int64_t nb, double p_in, double p_out, uint64_t seed
     }
 }
 
+/* --------------------------------------------- sparse skip sampling -- */
+/* Bernoulli(p) trials over columns [lo, hi) of row i, by geometric gaps
+ * (number of failures before a success = floor(log U / log(1 - p))), in
+ * O(successes). Uses log(), so graphs are reproducible per platform only;
+ * meant for large corpora. Writes at most cap columns (self-loop skipped). */
+static int64_t skip_row(int64_t i, int64_t lo, int64_t hi, double p, uint64_t key, uint64_t* ctr, int32_t* out,
+                        int64_t cap) {
+    int64_t c = 0;
+    if (p <= 0.0 || hi <= lo) return 0;
+    if (p >= 1.0) {
+        for (int64_t j = lo; j < hi && c < cap; ++j)
+            if (j != i) { if (out) out[c] = (int32_t)j; ++c; }
+        return c;
+    }
+    const double lq = log1p(-p);
+    int64_t j = lo - 1;
+    for (;;) {
+        double u = ((double)(draw(key, (*ctr)++) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        double g = floor(log(u) / lq);
+        if (g > (double)(hi - j)) break;
+        j += (int64_t)g + 1;
+        if (j >= hi) break;
+        if (j == i) continue;
+        if (c >= cap) break;
+        if (out) out[c] = (int32_t)j;
+        ++c;
+    }
+    return c;
+}
+
+/* Sparse directed ER / SBM in O(n + m): block of i = i*nb/n, probability
+ * p_in inside a block and p_out across (nb = 1: plain ER). Two passes as the
+ * dense generators; both passes draw the same numbers (per-row streams). */
+static int64_t sbm_row(int64_t n, int64_t nb, double p_in, double p_out, uint64_t key, int64_t i, int32_t* out,
+                       int64_t cap) {
+    uint64_t ctr = (uint64_t)i << 32;
+    int64_t bi = i * nb / n;
+    int64_t b0 = (bi * n + nb - 1) / nb, b1 = ((bi + 1) * n + nb - 1) / nb; /* columns of block bi */
+    int64_t c = 0;
+    c += skip_row(i, 0, b0, p_out, key, &ctr, out ? out + c : 0, cap - c);
+    c += skip_row(i, b0, b1, p_in, key, &ctr, out ? out + c : 0, cap - c);
+    c += skip_row(i, b1, n, p_out, key, &ctr, out ? out + c : 0, cap - c);
+    return c;
+}
+
+void wl_sbm_sparse_count(int64_t n, int64_t nb, double p_in, double p_out, uint64_t seed, int64_t* row_counts) {
+    uint64_t key = wl_key(seed, 13);
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) row_counts[i] = sbm_row(n, nb, p_in, p_out, key, i, 0, n);
+}
+
+void wl_sbm_sparse_fill(int64_t n, int64_t nb, double p_in, double p_out, uint64_t seed, const int64_t* indptr,
+                        int32_t* indices) {
+    uint64_t key = wl_key(seed, 13);
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) sbm_row(n, nb, p_in, p_out, key, i, indices + indptr[i], indptr[i + 1] - indptr[i]);
+}
+
+/* CSR -> packed LSB-first rows of ld words (layout change only). */
+void wl_csr_to_packed(int64_t n, const int64_t* indptr, const int32_t* indices, int64_t ld, uint64_t* rows) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t* r = rows + i * ld;
+        memset(r, 0, sizeof(uint64_t) * (size_t)ld);
+        for (int64_t e = indptr[i]; e < indptr[i + 1]; ++e) r[indices[e] >> 6] |= 1ULL << (indices[e] & 63);
+    }
+}
+
 /* uniform random pairs (i, j), i != j, count m: used for shortcut edges */
 void wl_random_pairs(int64_t n, int64_t m, uint64_t seed, int32_t* src, int32_t* dst) {
     uint64_t ka = wl_key(seed, 10), kb = wl_key(seed, 11);
