@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--variant", default="rms_tc")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
     return ap.parse_args()
 
@@ -273,6 +274,42 @@ def main():
             te = float(tt.item())
         e2e = {"value": args.steps * iters * 2.0 * n ** 3 * world / te / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": n * n, "d2h_bytes_per_step": n * n}
+    # ---- the other closure variants and the learned choice on the same graph (same bits, other kernels)
+    variants = None
+    if not args.no_variants:
+        from paper_2408_10369_gb300 import bmlp as _b
+        variants = {}
+        ms_tc = t / args.steps * 1e3
+        for v in ("smp_packed", "smp_tc", "rms_packed"):
+            o2 = torch.empty_like(R)
+            try:
+                ctx.rms(R, n, o2, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.rms(R, n, o2, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                variants[v] = {"ms": e0.elapsed_time(e1), "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
+            except _b.BmlpError as e:
+                if e.status != _b.BMLP_ERR_BUDGET:
+                    raise
+                variants[v] = {"ms": None, "censored_above_ms": 8 * ms_tc}
+        model = os.path.join(ROOT, "paper_2408_10369_gb300", "dispatch_model.bin")
+        if os.path.exists(model):
+            ctx.dispatch_load(model)
+            o2 = torch.empty_like(R)
+            ctx.rms(R, n, o2, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                ctx.rms(R, n, o2, stream=stream)
+            torch.cuda.synchronize()
+            ta = (time.perf_counter() - t0) / args.steps
+            chosen = pkg.bmlp.VARIANT_LIST[ctx.stats()["variant"]]
+            variants["auto"] = {"ms": ta * 1e3, "chosen": chosen, "graphs_per_s": 1.0 / ta,
+                                "eff_tops": iters * 2.0 * n ** 3 / ta / 1e12,
+                                "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
     peak, _, peak_src = peaks()
     avg_launch_s = prod_ms / max(prod_n, 1) / 1e3
     achieved = 2.0 * n ** 3 / avg_launch_s / 1e12 if avg_launch_s > 0 else None
@@ -301,7 +338,7 @@ def main():
                        "graphs_per_s": args.steps * world / t, "l2": "inputs larger than L2 (1 GiB per matrix)",
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "variants": variants}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -42,6 +42,7 @@ BMLP_LOOP_GRAPH = 1
 
 VARIANTS = {"auto": BMLP_AUTO, "rms_tc": BMLP_RMS_TC, "rms_packed": BMLP_RMS_PACKED,
             "smp_tc": BMLP_SMP_TC, "smp_packed": BMLP_SMP_PACKED}
+VARIANT_LIST = ["auto", "rms_tc", "rms_packed", "smp_tc", "smp_packed"]   # index = bmlp_variant
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_CONVERGED", 6: "UNSUPPORTED",
            7: "BUDGET"}

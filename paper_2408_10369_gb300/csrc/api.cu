@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -65,8 +66,9 @@ enum : int {
     WS_IN0 = 0, WS_IN1 = 1, WS_OUT = 2,
     WS_M0 = 3, WS_M1 = 4, WS_T0 = 5, WS_T1 = 6, WS_M2 = 7,
     WS_WPTR = 8, WS_WIDX = 9, WS_WVAL = 10, WS_F0 = 11, WS_F1 = 12, WS_V = 13, WS_SRC = 14,
-    WS_FEAT = 16
+    WS_FEAT = 16, WS_PT = 17, WS_WPTRT = 18, WS_WIDXT = 19
 };
+constexpr int WS_WVALT = 20;
 
 struct DeviceGuard {
     int prev = -1;
@@ -223,16 +225,27 @@ struct ProductTimer {
     }
 };
 
+// The squaring product runs as 2-CTA clusters sharing each B tile by TMA
+// multicast unless BMLP_TC_PAIR=0 is set in the environment.
+bool tc_pairs_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_TC_PAIR");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // ------------------------------------------------------------------------
 // Tensor-core squaring fixpoint on E4M3 R / R^T buffers already encoded in
 // (M[0], T[0]). On return *res points at the buffer holding R1+ (and *res_t at
 // its transpose).
 bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t) {
+    const bool pair = tc_pairs_enabled();
     CUtensorMap mapA[2], mapB[2];
     for (int b = 0; b < 2; ++b) {
         ST(make_tmap(ctx, &mapA[b], M[b], n_pad, n_pad, n_pad, TC_BM));
-        ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, TC_BN));
+        ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, pair ? TC_BN / 2 : TC_BN));
     }
     TcParams p{};
     p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
@@ -255,7 +268,10 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         p.out_r = M[nxt];
         p.out_rt = T[nxt];
         ST(tm.begin());
-        CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
+        if (pair)
+            CK(launch_tc_product_pair(mapA[cur], mapB[cur], p, ctx->sm_count, s), "tensor-core product launch");
+        else
+            CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
         ST(tm.end());
         ctx->stats.product_launches++;
         ctx->stats.launches += 2;
@@ -386,12 +402,24 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                          static_cast<uint64_t*>(wval), s),
        "word index build");
     ctx->stats.launches += 3;
+    // transposed word index for the pull direction (levels whose frontier is large)
+    void *PT = nullptr, *wptrT = nullptr, *widxT = nullptr, *wvalT = nullptr;
+    ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &PT));
+    ST(ws_get(ctx, WS_WPTRT, static_cast<size_t>((n + 1) * 8), &wptrT));
+    ST(ws_get(ctx, WS_WIDXT, static_cast<size_t>(n * ldw * 4), &widxT));
+    ST(ws_get(ctx, WS_WVALT, static_cast<size_t>(n * ldw * 8), &wvalT));
+    CK(launch_bit_transpose(static_cast<uint64_t*>(P), static_cast<uint64_t*>(PT), n, ldw, s), "bit transpose");
+    CK(launch_wcsr_build(static_cast<uint64_t*>(PT), n, ldw, static_cast<int64_t*>(wptrT),
+                         static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT), s),
+       "transposed word index build");
+    ctx->stats.launches += 4;
     CK(cudaMemsetAsync(ctx->d_ctl + CTL_LEVELS, 0, 3 * sizeof(int), s), "reset level and query counters");
     ProductTimer tm{ctx, o.profile != 0, s};
     ST(tm.begin());
     CK(launch_smp_packed(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval), n, ldw,
                          src, ldw_src, q, out, ldw_out, ctx->d_ctl + CTL_LEVELS, ctx->d_ctl + CTL_QCOUNT, o.reflexive,
-                         ctx->sm_count, s, deadline_of(ctx)),
+                         ctx->sm_count, s, deadline_of(ctx), static_cast<int64_t*>(wptrT),
+                         static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT)),
        "frontier kernel launch");
     ST(tm.end());
     ctx->stats.product_launches++;

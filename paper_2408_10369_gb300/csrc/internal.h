@@ -119,7 +119,7 @@ struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
     char err[512] = {0};
-    bmlp::DevBuf ws[20];
+    bmlp::DevBuf ws[24];
     void* batch = nullptr;       // cached grouped-batch graph (batch.cu)
     int tune[32];                // autotuned engine per size bucket (-1 = unknown)
     int* d_ctl = nullptr;        // device control words (see CTL_* below)
@@ -205,6 +205,10 @@ bmlp_status make_tmap(bmlp_ctx* ctx, CUtensorMap* map, const void* base, int64_t
 int tc_smem_bytes();
 cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int grid,
                               cudaStream_t s);
+// 2-CTA-cluster form (RMS / PLAIN modes): b_half is a tensor map of B^T with
+// a box of TC_BN / 2 rows; m_tiles must be even
+cudaError_t launch_tc_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                   cudaStream_t s);
 // grouped form: tc_group_kernel(const GroupProblem*, const GroupState*, int nprob, int phase, int* error,
 // long long wait_cycles); phase 0 = squaring step of every active problem, 1 = final products of compositions
 void* tc_group_kernel_ptr();
@@ -223,7 +227,10 @@ cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
                               int64_t ldw, const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out,
                               int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s,
-                              Deadline dl = Deadline{0, nullptr, nullptr});
+                              Deadline dl = Deadline{0, nullptr, nullptr}, const int64_t* wptrT = nullptr,
+                              const int32_t* widxT = nullptr, const uint64_t* wvalT = nullptr);
+// out = in^T on n x n packed rows of ldw words (out cleared first)
+cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s);
 int smp_packed_max_words();
 
 }  // namespace bmlp

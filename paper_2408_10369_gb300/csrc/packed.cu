@@ -161,13 +161,35 @@ __global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int6
     }
 }
 
+// Bit-matrix transpose of n x n packed rows (ldw words each), one 64 x 64
+// tile per 64-thread block: out row c, word bi = bit c of the tile's rows.
+__global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
+                                     int64_t ldw) {
+    __shared__ uint64_t t[64];
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int64_t r = bi * 64 + tid;
+    t[tid] = r < n ? in[r * ldw + bj] : 0ull;
+    __syncthreads();
+    uint64_t o = 0;
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) o |= ((t[k] >> tid) & 1ull) << k;
+    const int64_t c = bj * 64 + tid;
+    if (c < n) out[c * ldw + bi] = o;
+}
+
+// Frontier share of the unvisited above which a level pulls instead of pushing.
+constexpr int PULL_RATIO = 4;
+
 // ---- selective product per query row
-__global__ void __launch_bounds__(256) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
+__global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
                                                          const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
                                                          uint64_t* __restrict__ out, int64_t ldw_out, int* levels_max,
                                                          unsigned long long* qcounter, int reflexive, int max_levels,
-                                                         Deadline dl) {
+                                                         Deadline dl, const int64_t* __restrict__ wptrT,
+                                                         const int32_t* __restrict__ widxT,
+                                                         const uint64_t* __restrict__ wvalT) {
     extern __shared__ uint64_t sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -194,49 +216,105 @@ __global__ void __launch_bounds__(256) smp_packed_kernel(const int64_t* __restri
         }
         __syncwarp();
         int lv = 0;
+        bool pull = false;
+        // [dlo, dhi): words that may hold frontier bits; D is zero outside it
+        int64_t dlo = 0, dhi = wpr;
+        int64_t nu = n;  // unvisited constants
         while (true) {
             if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
-            for (int64_t wb = 0; wb < wpr; wb += 32) {
-                uint64_t d = (wb + lane < wpr) ? D[wb + lane] : 0ull;
-                while (__any_sync(FULL, d != 0ull)) {
-                    int64_t k = -1;
-                    if (d) {
-                        const int b = __ffsll(static_cast<long long>(d)) - 1;
-                        d &= d - 1;
-                        k = (wb + lane) * 64 + b;
+            int64_t nlo = 0, nhi = wpr;  // words of N that may be nonzero after this level's expansion
+            if (pull) {
+                // pull: unvisited j joins the next frontier iff some word of column j (row j of R^T) meets D;
+                // each lane owns whole words of N, so no atomics
+                for (int64_t w = lane; w < wpr; w += 32) {
+                    uint64_t u = ~V[w];
+                    const int64_t valid = n - w * 64;
+                    if (valid < 64) u &= (1ull << valid) - 1ull;
+                    uint64_t nw = 0;
+                    while (u) {
+                        const int b = __ffsll(static_cast<long long>(u)) - 1;
+                        u &= u - 1;
+                        const int64_t j = w * 64 + b;
+                        const int64_t e1 = wptrT[j + 1];
+                        for (int64_t e = wptrT[j]; e < e1; ++e)
+                            if (wvalT[e] & D[widxT[e]]) {
+                                nw |= 1ull << b;
+                                break;
+                            }
                     }
-                    int64_t e0 = 0, e1 = 0;
-                    if (k >= 0) {
-                        e0 = wptr[k];
-                        e1 = wptr[k + 1];
-                    }
-                    const bool heavy = (e1 - e0) > 16;
-                    if (k >= 0 && !heavy)
-                        for (int64_t e = e0; e < e1; ++e) atomicOr(reinterpret_cast<unsigned long long*>(&N[widx[e]]),
-                                                                   static_cast<unsigned long long>(wval[e]));
-                    unsigned hm = __ballot_sync(FULL, k >= 0 && heavy);
-                    while (hm) {
-                        const int sl = __ffs(hm) - 1;
-                        hm &= hm - 1;
-                        const int64_t h0 = __shfl_sync(FULL, e0, sl), h1 = __shfl_sync(FULL, e1, sl);
-                        for (int64_t e = h0 + lane; e < h1; e += 32)
-                            atomicOr(reinterpret_cast<unsigned long long*>(&N[widx[e]]),
-                                     static_cast<unsigned long long>(wval[e]));
+                    N[w] = nw;
+                }
+            } else {
+                // push: OR the nonzero words of every frontier row into N; track the words written
+                int64_t tlo = wpr, thi = -1;
+                for (int64_t wb = dlo & ~int64_t(31); wb < dhi; wb += 32) {
+                    uint64_t d = (wb + lane < dhi) ? D[wb + lane] : 0ull;
+                    while (__any_sync(FULL, d != 0ull)) {
+                        int64_t k = -1;
+                        if (d) {
+                            const int b = __ffsll(static_cast<long long>(d)) - 1;
+                            d &= d - 1;
+                            k = (wb + lane) * 64 + b;
+                        }
+                        int64_t e0 = 0, e1 = 0;
+                        if (k >= 0) {
+                            e0 = wptr[k];
+                            e1 = wptr[k + 1];
+                        }
+                        const bool heavy = (e1 - e0) > 16;
+                        if (k >= 0 && !heavy)
+                            for (int64_t e = e0; e < e1; ++e) {
+                                const int64_t x = widx[e];
+                                atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
+                                         static_cast<unsigned long long>(wval[e]));
+                                tlo = x < tlo ? x : tlo;
+                                thi = x > thi ? x : thi;
+                            }
+                        unsigned hm = __ballot_sync(FULL, k >= 0 && heavy);
+                        while (hm) {
+                            const int sl = __ffs(hm) - 1;
+                            hm &= hm - 1;
+                            const int64_t h0 = __shfl_sync(FULL, e0, sl), h1 = __shfl_sync(FULL, e1, sl);
+                            for (int64_t e = h0 + lane; e < h1; e += 32) {
+                                const int64_t x = widx[e];
+                                atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
+                                         static_cast<unsigned long long>(wval[e]));
+                                tlo = x < tlo ? x : tlo;
+                                thi = x > thi ? x : thi;
+                            }
+                        }
                     }
                 }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int64_t a = __shfl_xor_sync(FULL, tlo, o), b = __shfl_xor_sync(FULL, thi, o);
+                    tlo = a < tlo ? a : tlo;
+                    thi = b > thi ? b : thi;
+                }
+                nlo = tlo;
+                nhi = thi + 1;
+                if (nhi <= nlo) nlo = nhi = 0;
             }
             __syncwarp();
-            uint64_t anyw = 0;
-            for (int64_t w = lane; w < wpr; w += 32) {
+            // D := 0 over its old range, then D := N & ~V over N's range (V |= D, N := 0)
+            for (int64_t w = dlo + lane; w < dhi; w += 32) D[w] = 0;
+            __syncwarp();
+            int nf = 0;
+            for (int64_t w = nlo + lane; w < nhi; w += 32) {
                 const uint64_t nw = N[w] & ~V[w];
                 V[w] |= nw;
                 D[w] = nw;
                 N[w] = 0;
-                anyw |= nw;
+                nf += __popcll(nw);
             }
+            for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(FULL, nf, o);
             __syncwarp();
+            dlo = nlo;
+            dhi = nhi;
+            nu -= nf;
             ++lv;
-            if (!__any_sync(FULL, anyw != 0ull) || lv > max_levels) break;
+            if (nf == 0 || lv > max_levels) break;
+            // direction choice for the next level: pull once the frontier is a sizeable share of the unvisited
+            pull = wptrT != nullptr && static_cast<int64_t>(nf) * PULL_RATIO >= nu;
         }
         uint64_t* orow = out + static_cast<int64_t>(qi) * ldw_out;
         for (int64_t w = lane; w < ldw_out; w += 32) {
@@ -292,7 +370,8 @@ int smp_packed_max_words() { return 8192; }
 
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n, int64_t ldw,
                               const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out,
-                              int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s, Deadline dl) {
+                              int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s, Deadline dl,
+                              const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT) {
     const int64_t per_warp = 3 * ldw * static_cast<int64_t>(sizeof(uint64_t));
     int warps = static_cast<int>((200 * 1024) / per_warp);
     if (warps > 8) warps = 8;
@@ -309,7 +388,15 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
     const int max_levels = static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF);
     smp_packed_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(
         wptr, widx, wval, n, ldw, src, ldw_src, q, out, ldw_out, levels,
-        reinterpret_cast<unsigned long long*>(qcounter), reflexive, max_levels, dl);
+        reinterpret_cast<unsigned long long*>(qcounter), reflexive, max_levels, dl, wptrT, widxT, wvalT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(n * ldw * 8), s);
+    if (e != cudaSuccess) return e;
+    const int64_t wpr = (n + 63) / 64;
+    bit_transpose_kernel<<<dim3(static_cast<unsigned>(wpr), static_cast<unsigned>(wpr)), 64, 0, s>>>(in, out, n, ldw);
     return cudaGetLastError();
 }
 
