@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
+    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch"],
+                    help="er: the closure benchmark (default); powerlaw_smp: 4,096 selective query rows on the "
+                         "n = 65,536 power-law graph; kg_batch: every relation closure and 200 compositions of "
+                         "the knowledge-graph workload in one grouped batch")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
     return ap.parse_args()
 
@@ -61,6 +65,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(seconds, world, device):
+    """The slowest rank's time (every rank gets it); one process: unchanged.
+    Works with any torch.distributed backend (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, seconds):
+    """Throughput of the whole job: every rank's units over the slowest time."""
+    return units_per_rank * world / seconds
 
 
 def peaks():
@@ -131,10 +151,10 @@ def kernel_hash():
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(n):
+def profiled_traffic(kernel, n):
     """DRAM bytes per product launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "tc_product_kernel_er%d.md" % n)
+    path = os.path.join(ROOT, "profiles", "%s_er%d.md" % (kernel, n))
     try:
         kv = {}
         with open(path) as f:
@@ -193,11 +213,73 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_aux(args):
+    """Secondary workloads (one GPU): selective queries and the grouped batch."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    import paper_2408_10369_gb300 as pkg
+    from paper_2408_10369_gb300 import bmlp
+    ctx = pkg.Context(0)
+    stream = torch.cuda.current_stream()
+    if args.workload == "powerlaw_smp":
+        n, q = 65536, 4096
+        ip, ix = wl.powerlaw_csr(n, 2.1, 1000, 0)
+        P = torch.from_numpy(wl.csr_to_packed(n, ip, ix).view(np.int64)).cuda()
+        src = torch.from_numpy(wl.query_rows(n, q, 1, 64, 0).view(np.int64)).cuda()
+        out = torch.zeros_like(src)
+
+        def step():
+            return ctx.smp(P, n, src, q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant, profile=True)
+        unit, units_per_step, name = "queries/s", q, "powerlaw_n65536_q4096"
+    else:
+        rels = wl.kg_relations()
+        items, keep = [], []
+        for r in rels:
+            R = torch.from_numpy(wl.csr_to_packed(r["n"], r["indptr"], r["indices"]).view(np.int64)).cuda()
+            o = torch.zeros_like(R)
+            keep += [R, o]
+            items.append(dict(n=r["n"], R1=R, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
+        for a, b in wl.kg_compose_pairs(rels, 200, 0):
+            n, ents, c1, c2 = wl.union_space(rels[a], rels[b])
+            R1 = torch.from_numpy(wl.csr_to_packed(n, *c1).view(np.int64)).cuda()
+            R2 = torch.from_numpy(wl.csr_to_packed(n, *c2).view(np.int64)).cuda()
+            o = torch.zeros_like(R1)
+            keep += [R1, R2, o]
+            items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
+        arr = ctx.problems(items)
+        variant = args.variant if args.variant in ("rms_tc", "rms_packed") else "auto"
+
+        def step():
+            return max(ctx.batch_run(arr, variant=variant))
+        unit, units_per_step, name = "programs/s", len(items), "kg15000_r1345_t483000_plus200"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        it = step()
+        launches += ctx.stats()["launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    print(json.dumps({"workload": name, "variant": args.variant, "value": args.steps * units_per_step / t,
+                      "unit": unit, "ms_per_step": t / args.steps * 1e3, "steps": args.steps,
+                      "warmup": args.warmup, "iterations": it, "gpu_launches": launches}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "er":
+        if rank == 0:
+            run_aux(args)
         return
     import numpy as np
     import torch
@@ -248,13 +330,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device=device)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
-    work = args.steps * iters * 2.0 * n ** 3 * world
-    value = work / t / 1e12
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, device)
+    value = whole_job_value(args.steps * iters * 2.0 * n ** 3, world, t) / 1e12
     # ---- end-to-end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -267,11 +344,7 @@ def main():
         for _ in range(args.steps):
             ctx.rms(hin, n, hout, variant=args.variant, stream=stream)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device=device)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0, world, device)
         e2e = {"value": args.steps * iters * 2.0 * n ** 3 * world / te / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": n * n, "d2h_bytes_per_step": n * n}
     # ---- the other closure variants and the learned choice on the same graph (same bits, other kernels)
@@ -313,8 +386,9 @@ def main():
     peak, _, peak_src = peaks()
     avg_launch_s = prod_ms / max(prod_n, 1) / 1e3
     achieved = 2.0 * n ** 3 / avg_launch_s / 1e12 if avg_launch_s > 0 else None
-    roof = {"bound": "tensor", "kernel": "tc_product_kernel", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(n),
+    kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
+    roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
             "peak_source": "%s bf16 burst x %g (fp8/bf16 nominal); the product runs unthrottled at max SM clock" % (peak_src, FP8_PER_BF16),
             "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None}
     if rank != 0:
