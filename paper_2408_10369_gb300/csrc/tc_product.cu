@@ -93,6 +93,13 @@ __device__ __forceinline__ uint4 mask_to_bytes16(uint32_t m) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// Waits for this CTA's own copies / MMAs in flight before it frees its shared
+// memory and TMEM get at least ~1 s (at 2 GHz) even when the caller chose a
+// very short timeout: they finish in microseconds once issued.
+__device__ __forceinline__ long long drain_cycles(long long limit) {
+    return limit > 2000000000LL ? limit : 2000000000LL;
+}
+
 __device__ __forceinline__ bool wait_lane0(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit,
                                            int lane) {
     int ok = 1;
@@ -292,7 +299,8 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                 // let every copy this CTA issued land before the CTA exits
                 volatile int never = 0;
                 for (int s = 0; s < TC_STAGES; ++s)
-                    if (last_par[s] >= 0) mbar_wait_bounded(&full[s], static_cast<uint32_t>(last_par[s]), &never, limit);
+                    if (last_par[s] >= 0)
+                        mbar_wait_bounded(&full[s], static_cast<uint32_t>(last_par[s]), &never, drain_cycles(limit));
             }
         }
     } else if (warp == 1) {
@@ -352,7 +360,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
         if (lane == 0) {
             tc_commit(done);
             volatile int never = 0;
-            mbar_wait_bounded(done, 0, &never, limit);
+            mbar_wait_bounded(done, 0, &never, drain_cycles(limit));
         }
         __syncwarp();
     } else {
