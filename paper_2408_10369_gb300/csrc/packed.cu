@@ -182,7 +182,12 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
 constexpr int PULL_RATIO = 4;
 
 // ---- selective product per query row
-__global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
+// Per warp in shared memory: V, D, N (ldw words each) and FL, the list of
+// the frontier's nonzero words (ldw 16-bit word indices).
+// The stride is rounded up to 16 bytes so every warp's uint64 arrays stay aligned.
+__host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) { return (26 * ldw + 16 + 15) & ~int64_t(15); }
+
+__global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
                                                          const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
                                                          uint64_t* __restrict__ out, int64_t ldw_out, int* levels_max,
@@ -193,9 +198,11 @@ __global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __res
     extern __shared__ uint64_t sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint64_t* V = sm + static_cast<int64_t>(wib) * 3 * ldw;
+    const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+    uint64_t* V = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw));
     uint64_t* D = V + ldw;
     uint64_t* N = D + ldw;
+    uint16_t* FL = reinterpret_cast<uint16_t*>(N + ldw);
     const int64_t wpr = (n + 63) / 64;
     while (true) {
         unsigned long long qi = 0;
@@ -203,58 +210,69 @@ __global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __res
         qi = __shfl_sync(FULL, qi, 0);
         if (qi >= static_cast<unsigned long long>(q)) break;
         const uint64_t* srow = src + static_cast<int64_t>(qi) * ldw_src;
-        for (int64_t w = lane; w < ldw; w += 32) {
+        // D = sources; FL = their nonzero words (ballot compaction)
+        int fcount = 0;
+        for (int64_t w0 = 0; w0 < ldw; w0 += 32) {
+            const int64_t w = w0 + lane;
             uint64_t s = 0;
             if (w < wpr) {
                 s = srow[w];
                 const int64_t valid = n - w * 64;
                 if (valid < 64) s &= (1ull << valid) - 1ull;
             }
-            D[w] = s;
-            V[w] = 0;
-            N[w] = 0;
+            if (w < ldw) {
+                D[w] = s;
+                V[w] = 0;
+                N[w] = 0;
+            }
+            const unsigned m = __ballot_sync(FULL, s != 0ull);
+            if (s) FL[fcount + __popc(m & lt)] = static_cast<uint16_t>(w);
+            fcount += __popc(m);
         }
         __syncwarp();
         int lv = 0;
         bool pull = false;
-        // [dlo, dhi): words that may hold frontier bits; D is zero outside it
-        int64_t dlo = 0, dhi = wpr;
         int64_t nu = n;  // unvisited constants
         while (true) {
             if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
-            int64_t nlo = 0, nhi = wpr;  // words of N that may be nonzero after this level's expansion
+            int nlo = 0, nhi = static_cast<int>(wpr);  // words of N that may be nonzero after this expansion
             if (pull) {
                 // pull: unvisited j joins the next frontier iff some word of column j (row j of R^T) meets D;
-                // each lane owns whole words of N, so no atomics
+                // each lane owns whole words of N (no atomics)
                 for (int64_t w = lane; w < wpr; w += 32) {
-                    uint64_t u = ~V[w];
-                    const int64_t valid = n - w * 64;
-                    if (valid < 64) u &= (1ull << valid) - 1ull;
                     uint64_t nw = 0;
-                    while (u) {
-                        const int b = __ffsll(static_cast<long long>(u)) - 1;
-                        u &= u - 1;
-                        const int64_t j = w * 64 + b;
-                        const int64_t e1 = wptrT[j + 1];
-                        for (int64_t e = wptrT[j]; e < e1; ++e)
-                            if (wvalT[e] & D[widxT[e]]) {
-                                nw |= 1ull << b;
-                                break;
-                            }
+                    {
+                        uint64_t u = ~V[w];
+                        const int64_t valid = n - w * 64;
+                        if (valid < 64) u &= (1ull << valid) - 1ull;
+                        while (u) {
+                            const int b = __ffsll(static_cast<long long>(u)) - 1;
+                            u &= u - 1;
+                            const int64_t j = w * 64 + b;
+                            const int64_t e1 = wptrT[j + 1];
+                            for (int64_t e = wptrT[j]; e < e1; ++e)
+                                if (wvalT[e] & D[widxT[e]]) {
+                                    nw |= 1ull << b;
+                                    break;
+                                }
+                        }
+                        N[w] = nw;
                     }
-                    N[w] = nw;
                 }
             } else {
-                // push: OR the nonzero words of every frontier row into N; track the words written
-                int64_t tlo = wpr, thi = -1;
-                for (int64_t wb = dlo & ~int64_t(31); wb < dhi; wb += 32) {
-                    uint64_t d = (wb + lane < dhi) ? D[wb + lane] : 0ull;
+                // push: OR the nonzero words of every frontier row into N (no return values, so the
+                // atomics are reductions); track the range of words written
+                int tlo = static_cast<int>(wpr), thi = -1;
+                for (int i0 = 0; i0 < fcount; i0 += 32) {
+                    const int i = i0 + lane;
+                    const int64_t w = i < fcount ? FL[i] : 0;
+                    uint64_t d = i < fcount ? D[w] : 0ull;
                     while (__any_sync(FULL, d != 0ull)) {
                         int64_t k = -1;
                         if (d) {
                             const int b = __ffsll(static_cast<long long>(d)) - 1;
                             d &= d - 1;
-                            k = (wb + lane) * 64 + b;
+                            k = w * 64 + b;
                         }
                         int64_t e0 = 0, e1 = 0;
                         if (k >= 0) {
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __res
                         const bool heavy = (e1 - e0) > 16;
                         if (k >= 0 && !heavy)
                             for (int64_t e = e0; e < e1; ++e) {
-                                const int64_t x = widx[e];
+                                const int x = widx[e];
                                 atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
                                          static_cast<unsigned long long>(wval[e]));
                                 tlo = x < tlo ? x : tlo;
@@ -276,7 +294,7 @@ __global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __res
                             hm &= hm - 1;
                             const int64_t h0 = __shfl_sync(FULL, e0, sl), h1 = __shfl_sync(FULL, e1, sl);
                             for (int64_t e = h0 + lane; e < h1; e += 32) {
-                                const int64_t x = widx[e];
+                                const int x = widx[e];
                                 atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
                                          static_cast<unsigned long long>(wval[e]));
                                 tlo = x < tlo ? x : tlo;
@@ -285,31 +303,35 @@ __global__ void __launch_bounds__(256, 2) smp_packed_kernel(const int64_t* __res
                         }
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const int64_t a = __shfl_xor_sync(FULL, tlo, o), b = __shfl_xor_sync(FULL, thi, o);
-                    tlo = a < tlo ? a : tlo;
-                    thi = b > thi ? b : thi;
-                }
-                nlo = tlo;
-                nhi = thi + 1;
+                nlo = __reduce_min_sync(FULL, tlo);
+                nhi = __reduce_max_sync(FULL, thi) + 1;
                 if (nhi <= nlo) nlo = nhi = 0;
             }
             __syncwarp();
-            // D := 0 over its old range, then D := N & ~V over N's range (V |= D, N := 0)
-            for (int64_t w = dlo + lane; w < dhi; w += 32) D[w] = 0;
+            // D := 0 on the old frontier words, then D := N & ~V on N's range (V |= D, N := 0);
+            // the words that come out nonzero become the new frontier list FL
+            for (int i = lane; i < fcount; i += 32) D[FL[i]] = 0;
             __syncwarp();
-            int nf = 0;
-            for (int64_t w = nlo + lane; w < nhi; w += 32) {
-                const uint64_t nw = N[w] & ~V[w];
-                V[w] |= nw;
-                D[w] = nw;
-                N[w] = 0;
+            int nf = 0, fnew = 0;
+            for (int w0 = nlo; w0 < nhi; w0 += 32) {
+                const int w = w0 + lane;
+                uint64_t nw = 0;
+                if (w < nhi) {
+                    nw = N[w] & ~V[w];
+                    N[w] = 0;
+                    if (nw) {
+                        V[w] |= nw;
+                        D[w] = nw;
+                    }
+                }
+                const unsigned m = __ballot_sync(FULL, nw != 0ull);
+                if (nw) FL[fnew + __popc(m & lt)] = static_cast<uint16_t>(w);
+                fnew += __popc(m);
                 nf += __popcll(nw);
             }
-            for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(FULL, nf, o);
+            nf = __reduce_add_sync(FULL, nf);
+            fcount = fnew;
             __syncwarp();
-            dlo = nlo;
-            dhi = nhi;
             nu -= nf;
             ++lv;
             if (nf == 0 || lv > max_levels) break;
@@ -366,16 +388,17 @@ cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t
     return cudaGetLastError();
 }
 
-int smp_packed_max_words() { return 8192; }
+int smp_packed_max_words() { return 7168; }
 
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n, int64_t ldw,
                               const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out,
                               int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s, Deadline dl,
                               const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT) {
-    const int64_t per_warp = 3 * ldw * static_cast<int64_t>(sizeof(uint64_t));
-    int warps = static_cast<int>((200 * 1024) / per_warp);
-    if (warps > 8) warps = 8;
-    if (warps < 1) return cudaErrorInvalidValue;
+    // blocks of 1-8 warps, chosen so that as many warps as possible fit an SM's shared memory
+    const int64_t per_warp = smp_warp_bytes(ldw);
+    if (per_warp > 200 * 1024) return cudaErrorInvalidValue;
+    int warps = 8;
+    while (warps > 1 && warps * per_warp > (227 * 1024) / 4) warps >>= 1;
     const size_t smem = static_cast<size_t>(warps) * per_warp;
     cudaError_t e = cudaFuncSetAttribute(smp_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
