@@ -182,10 +182,11 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
 constexpr int PULL_RATIO = 4;
 
 // ---- selective product per query row
-// Per warp in shared memory: V, D, N (ldw words each) and FL, the list of
-// the frontier's nonzero words (ldw 16-bit word indices).
+// Per warp in shared memory: D, N (ldw words each) and FL, the list of the
+// frontier's nonzero words (ldw 16-bit word indices). The visited set V is
+// the query's own output row in global memory (only its warp touches it).
 // The stride is rounded up to 16 bytes so every warp's uint64 arrays stay aligned.
-__host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) { return (26 * ldw + 16 + 15) & ~int64_t(15); }
+__host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) { return (18 * ldw + 16 + 15) & ~int64_t(15); }
 
 __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
@@ -199,8 +200,7 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;  // lanes below this one
-    uint64_t* V = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw));
-    uint64_t* D = V + ldw;
+    uint64_t* D = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw));
     uint64_t* N = D + ldw;
     uint16_t* FL = reinterpret_cast<uint16_t*>(N + ldw);
     const int64_t wpr = (n + 63) / 64;
@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
         qi = __shfl_sync(FULL, qi, 0);
         if (qi >= static_cast<unsigned long long>(q)) break;
         const uint64_t* srow = src + static_cast<int64_t>(qi) * ldw_src;
-        // D = sources; FL = their nonzero words (ballot compaction)
+        uint64_t* V = out + static_cast<int64_t>(qi) * ldw_out;
+        // D = sources; FL = their nonzero words (ballot compaction); V = 0
         int fcount = 0;
         for (int64_t w0 = 0; w0 < ldw; w0 += 32) {
             const int64_t w = w0 + lane;
@@ -222,9 +223,9 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
             }
             if (w < ldw) {
                 D[w] = s;
-                V[w] = 0;
                 N[w] = 0;
             }
+            if (w < ldw_out) V[w] = 0;
             const unsigned m = __ballot_sync(FULL, s != 0ull);
             if (s) FL[fcount + __popc(m & lt)] = static_cast<uint16_t>(w);
             fcount += __popc(m);
@@ -338,20 +339,13 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
             // direction choice for the next level: pull once the frontier is a sizeable share of the unvisited
             pull = wptrT != nullptr && static_cast<int64_t>(nf) * PULL_RATIO >= nu;
         }
-        uint64_t* orow = out + static_cast<int64_t>(qi) * ldw_out;
-        for (int64_t w = lane; w < ldw_out; w += 32) {
-            uint64_t v = 0;
-            if (w < wpr) {
-                v = V[w];
-                if (reflexive) {
-                    uint64_t s = srow[w];
-                    const int64_t valid = n - w * 64;
-                    if (valid < 64) s &= (1ull << valid) - 1ull;
-                    v |= s;
-                }
+        if (reflexive)
+            for (int64_t w = lane; w < wpr; w += 32) {
+                uint64_t s = srow[w];
+                const int64_t valid = n - w * 64;
+                if (valid < 64) s &= (1ull << valid) - 1ull;
+                V[w] |= s;
             }
-            orow[w] = v;
-        }
         if (lane == 0) atomicMax(levels_max, lv);
         __syncwarp();
     }
@@ -398,7 +392,7 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
     const int64_t per_warp = smp_warp_bytes(ldw);
     if (per_warp > 200 * 1024) return cudaErrorInvalidValue;
     int warps = 8;
-    while (warps > 1 && warps * per_warp > (227 * 1024) / 4) warps >>= 1;
+    while (warps > 1 && warps * per_warp > 32 * 1024) warps >>= 1;
     const size_t smem = static_cast<size_t>(warps) * per_warp;
     cudaError_t e = cudaFuncSetAttribute(smp_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
