@@ -69,6 +69,8 @@ enum : int {
     WS_FEAT = 16, WS_PT = 17, WS_WPTRT = 18, WS_WIDXT = 19
 };
 constexpr int WS_WVALT = 20;
+// Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
+constexpr double kSkipMaxDensity = 0.5;
 
 struct DeviceGuard {
     int prev = -1;
@@ -235,6 +237,15 @@ bool tc_pairs_enabled() {
     return on;
 }
 
+// K-block skipping by the block-occupancy map of R, unless BMLP_TC_SKIP=0.
+bool tc_skip_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_TC_SKIP");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // ------------------------------------------------------------------------
 // Tensor-core squaring fixpoint on E4M3 R / R^T buffers already encoded in
 // (M[0], T[0]). On return *res points at the buffer holding R1+ (and *res_t at
@@ -258,12 +269,60 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     p.wait_cycles = wait_cycles(ctx, o);
     const int tiles = p.m_tiles * p.n_tiles;
     const int grid = tiles < ctx->sm_count ? tiles : ctx->sm_count;
+    // 128 x 128 block-occupancy maps of R (this iteration's and the next): K blocks whose A or B^T block
+    // is empty are skipped, which removes most of the work of the early, block-sparse squarings
+    // (maps F[b] and their transposes FT[b], rows padded to fm_ld bytes; up to 256 x 256 blocks)
+    uint8_t* F[2] = {nullptr, nullptr};
+    uint8_t* FT[2] = {nullptr, nullptr};
+    p.fm_ld = static_cast<int32_t>(round_up(p.k_blocks, 16));
+    const size_t fbytes = static_cast<size_t>(p.k_blocks) * static_cast<size_t>(p.fm_ld);
+    if (tc_skip_enabled() && p.k_blocks <= 256) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        ST(ws_get(ctx, WS_F0, 2 * fbytes, &f0));
+        ST(ws_get(ctx, WS_F1, 2 * fbytes, &f1));
+        F[0] = static_cast<uint8_t*>(f0);
+        FT[0] = F[0] + fbytes;
+        F[1] = static_cast<uint8_t*>(f1);
+        FT[1] = F[1] + fbytes;
+        CK(cudaMemsetAsync(F[0], 0, 2 * fbytes, s), "clear block map");
+        launch_block_flags(M[0], n_pad, n_pad, n_pad, F[0], s, p.fm_ld);
+        launch_block_flags(T[0], n_pad, n_pad, n_pad, FT[0], s, p.fm_ld);
+        CK(cudaGetLastError(), "block map");
+        ctx->stats.launches += 2;
+    }
+    // Skipping pays only while many blocks are empty; R only gains bits, so once the map is dense it stays
+    // dense and the maps are dropped for the rest of the closure.
+    std::vector<uint8_t> hmap;
+    auto sparse_map = [&](const uint8_t* dmap, bool* sparse) -> bmlp_status {
+        hmap.resize(fbytes);
+        CK(cudaMemcpyAsync(hmap.data(), dmap, fbytes, cudaMemcpyDeviceToHost, s), "read block map");
+        CK(cudaStreamSynchronize(s), "read block map");
+        size_t nz = 0;
+        for (size_t i = 0; i < fbytes; ++i) nz += hmap[i] != 0;
+        *sparse = static_cast<double>(nz) < kSkipMaxDensity * double(p.k_blocks) * double(p.k_blocks);
+        return BMLP_OK;
+    };
+    bool use_maps = false;
+    if (F[0] != nullptr) ST(sparse_map(F[0], &use_maps));
     ProductTimer tm{ctx, o.profile != 0, s};
+    p.issued = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_ISSUED);
+    CK(cudaMemsetAsync(p.issued, 0, sizeof(unsigned long long), s), "reset issued counter");
     int cur = 0;
     *iters = 0;
     for (int it = 0; it < max_iters; ++it) {
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        if (use_maps) {
+            CK(cudaMemsetAsync(F[nxt], 0, 2 * fbytes, s), "clear block map");
+            p.fmap = F[cur];
+            p.fmapT = FT[cur];
+            p.fmap_next = F[nxt];
+            p.fmapT_next = FT[nxt];
+        } else {
+            p.fmap = p.fmapT = nullptr;
+            p.fmap_next = p.fmapT_next = nullptr;
+        }
         p.old_r = M[cur];
         p.out_r = M[nxt];
         p.out_rt = T[nxt];
@@ -275,10 +334,13 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         ST(tm.end());
         ctx->stats.product_launches++;
         ctx->stats.launches += 2;
-        ctx->stats.issued_ops += 2.0 * double(n_pad) * double(n_pad) * double(n_pad);
         int changed = 0;
         ST(read_ctl(ctx, s, &changed));
         ST(tm.collect());
+        // multiply-adds actually issued: K blocks run x (128 x 256 x 128) each, times 2
+        unsigned long long kbs = 0;
+        memcpy(&kbs, ctx->h_ctl + CTL_ISSUED, sizeof(kbs));
+        ctx->stats.issued_ops = 2.0 * TC_BM * TC_BN * TC_BK * static_cast<double>(kbs);
         *iters = it + 1;
         cur = nxt;
         if (!changed) {
@@ -286,6 +348,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             *res_t = T[cur];
             return BMLP_OK;
         }
+        if (use_maps) ST(sparse_map(F[cur], &use_maps));
     }
     *res = M[cur];
     *res_t = T[cur];

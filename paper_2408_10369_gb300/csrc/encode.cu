@@ -296,9 +296,9 @@ void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s) {
 }
 
 void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t n_pad, uint8_t* flags,
-                        cudaStream_t s) {
+                        cudaStream_t s, int64_t flags_ld) {
     dim3 grid(static_cast<unsigned>(n_pad / 128), static_cast<unsigned>(rows_pad / 128));
-    block_flags_kernel<<<grid, 256, 0, s>>>(A, ld, n_pad / 128, flags);
+    block_flags_kernel<<<grid, 256, 0, s>>>(A, ld, flags_ld > 0 ? flags_ld : n_pad / 128, flags);
 }
 
 }  // namespace bmlp

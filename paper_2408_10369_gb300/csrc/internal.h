@@ -42,6 +42,15 @@ struct TcParams {
     int* changed;               // set to 1 when any output bit changed / is new
     int* error;                 // set to a nonzero code when a wait timed out
     long long wait_cycles;      // bound of each in-kernel wait
+    // RMS block maps (only when k_blocks <= 256): fmap[rb * fm_ld + cb] = 1 iff the 128 x 128 block (rb, cb)
+    // of R is nonzero, fmapT the transpose (fmapT[cb * fm_ld + rb]); rows padded with zeros to fm_ld, a
+    // multiple of 16. The epilogue fills the maps of the new R (cleared by the caller).
+    const uint8_t* fmap;
+    const uint8_t* fmapT;
+    uint8_t* fmap_next;
+    uint8_t* fmapT_next;
+    int32_t fm_ld;
+    unsigned long long* issued; // K blocks actually multiplied (one MMA group each), or null
 };
 
 // One problem of a grouped batch (device copy; built on the host).
@@ -137,7 +146,7 @@ namespace bmlp {
 // CTL_QCOUNT and CTL_T0 are 64-bit words (two ints each, 8-byte aligned).
 enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
-    CTL_WORDS = 16
+    CTL_ISSUED = 10, CTL_WORDS = 16
 };
 
 // Workspace slot of the grouped batch (the others are private to api.cu).
@@ -195,8 +204,9 @@ void launch_identity_packed(uint64_t* out, int64_t ldw, int64_t n, cudaStream_t 
 // set the diagonal of an n x n byte matrix (ld) to E4M3 one
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s);
 // per (M block, K block) nonzero flags of a byte matrix rows_pad x n_pad
+// (row stride of flags: flags_ld, default n_pad / 128)
 void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t n_pad, uint8_t* flags,
-                        cudaStream_t s);
+                        cudaStream_t s, int64_t flags_ld = 0);
 
 // ---- tensor-core product (tc_product.cu)
 // Set up tensor maps for A (rows x K) and B^T (cols x K) byte matrices.

@@ -120,7 +120,57 @@ struct Tile {
     const uint8_t* kflags;
     uint8_t* kflags_next;
     int* changed;
+    bool masked;             // RMS with block maps: kmask lists the K blocks to run
+    uint64_t kmask[4];
+    uint8_t* fmap_next;      // block maps of the new R (RMS) or null
+    uint8_t* fmapT_next;
+    int fm_ld;
 };
+
+// 16 map bytes -> 16-bit mask of nonzero bytes
+__device__ __forceinline__ uint32_t nz16(const uint4& v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) m |= (((w[k] >> (8 * b)) & 0xFFu) != 0 ? 1u : 0u) << (4 * k + b);
+    return m;
+}
+
+// K blocks kb that contribute to output tile (A row blocks a0, a1; 256 output
+// columns = column blocks 2 nb, 2 nb + 1): the A block (a0 or a1, kb) and the
+// B^T block, i.e. R block (kb, 2 nb or 2 nb + 1), are both nonzero. Built from
+// four contiguous map rows with 16-byte loads; a CTA pair passes both of its
+// row blocks, so both CTAs run the same K sequence.
+__device__ __forceinline__ void build_kmask(const TcParams* p, int a0, int a1, int nb, uint64_t (&km)[4]) {
+    const uint4* ra0 = reinterpret_cast<const uint4*>(p->fmap + static_cast<int64_t>(a0) * p->fm_ld);
+    const uint4* ra1 = reinterpret_cast<const uint4*>(p->fmap + static_cast<int64_t>(a1) * p->fm_ld);
+    const uint4* rb0 = reinterpret_cast<const uint4*>(p->fmapT + static_cast<int64_t>(2 * nb) * p->fm_ld);
+    const uint4* rb1 = reinterpret_cast<const uint4*>(p->fmapT + static_cast<int64_t>(2 * nb + 1) * p->fm_ld);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) km[w] = 0;
+    const int chunks = p->fm_ld / 16;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {  // fully unrolled: km stays in registers
+        if (c < chunks) {
+            const uint32_t a = nz16(ra0[c]) | nz16(ra1[c]);
+            const uint32_t b = nz16(rb0[c]) | nz16(rb1[c]);
+            km[c >> 2] |= static_cast<uint64_t>(a & b) << (16 * (c & 3));
+        }
+    }
+}
+
+// Does K block kb contribute to this tile? SMP: the frontier block is nonzero;
+// RMS with block maps: the tile's mask; otherwise every K block.
+__device__ __forceinline__ bool kactive(const Tile& x, int kb) {
+    if (x.kflags != nullptr) return x.kflags[x.mb * x.k_blocks + kb] != 0;
+    if (x.masked) {
+        const uint64_t w = kb < 64 ? x.kmask[0] : kb < 128 ? x.kmask[1] : kb < 192 ? x.kmask[2] : x.kmask[3];
+        return (w >> (kb & 63)) & 1ull;
+    }
+    return true;
+}
 
 // One problem: the tensor maps are kernel parameters.
 struct SingleSource {
@@ -142,6 +192,11 @@ struct SingleSource {
         x.kflags = p->kflags;
         x.kflags_next = p->kflags_next;
         x.changed = p->changed;
+        x.masked = p->fmap != nullptr;
+        if (x.masked) build_kmask(p, x.mb, x.mb, x.nb, x.kmask);
+        x.fmap_next = p->fmap_next;
+        x.fmapT_next = p->fmapT_next;
+        x.fm_ld = p->fm_ld;
     }
 };
 
@@ -171,6 +226,11 @@ struct PairSource {
         x.kflags = nullptr;
         x.kflags_next = nullptr;
         x.changed = p->changed;
+        x.masked = p->fmap != nullptr;
+        if (x.masked) build_kmask(p, 2 * mp, 2 * mp + 1, x.nb, x.kmask);
+        x.fmap_next = p->fmap_next;
+        x.fmapT_next = p->fmapT_next;
+        x.fm_ld = p->fm_ld;
     }
 };
 
@@ -199,6 +259,10 @@ struct GroupSource {
         x.visited = nullptr;
         x.kflags = nullptr;
         x.kflags_next = nullptr;
+        x.masked = false;
+        x.fmap_next = nullptr;
+        x.fmapT_next = nullptr;
+        x.fm_ld = 0;
         if (phase == 0) {
             x.mode = TC_MODE_RMS;
             x.mapB = &g.mapB[par];
@@ -218,7 +282,8 @@ struct GroupSource {
 };
 
 template <class Src, bool kPair = false>
-__device__ __forceinline__ void tc_body(const Src& src, int* error, long long limit) {
+__device__ __forceinline__ void tc_body(const Src& src, int* error, long long limit,
+                                        unsigned long long* issued = nullptr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem + OFF_A;
@@ -275,7 +340,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                 Tile x;
                 src.get(t, x);
                 for (int kb = 0; kb < x.k_blocks; ++kb) {
-                    if (x.kflags != nullptr && x.kflags[x.mb * x.k_blocks + kb] == 0) continue;
+                    if (!kactive(x, kb)) continue;
                     if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
                         ok = false;
                         break;
@@ -321,8 +386,10 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * ACC_COLS);
             uint32_t accumulate = 0;
+            unsigned long long nk = 0;
             for (int kb = 0; kb < x.k_blocks; ++kb) {
-                if (x.kflags != nullptr && x.kflags[x.mb * x.k_blocks + kb] == 0) continue;
+                if (!kactive(x, kb)) continue;
+                ++nk;
                 if (!wait_lane0(&full[stage], phase, abort_flag, limit, lane)) {
                     ok = false;
                     break;
@@ -350,6 +417,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                 }
             }
             if (!ok) break;
+            if (lane == 0 && issued != nullptr) atomicAdd(issued, nk);
             if (lane == 0) tc_commit(&tfull[acc]);
             __syncwarp();
             acc ^= 1;
@@ -377,10 +445,13 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                 break;
             }
             tc_fence_after();
+            // no MMA ran for a tile whose K blocks were all skipped: its product is zero
             bool active = true;
-            if (x.kflags != nullptr) {
+            if (x.masked) {
+                active = (x.kmask[0] | x.kmask[1] | x.kmask[2] | x.kmask[3]) != 0ull;
+            } else if (x.kflags != nullptr) {
                 active = false;
-                for (int kb = 0; kb < x.k_blocks && !active; ++kb) active = x.kflags[x.mb * x.k_blocks + kb] != 0;
+                for (int kb = 0; kb < x.k_blocks && !active; ++kb) active = kactive(x, kb);
             }
             const int64_t row = static_cast<int64_t>(x.mb) * TC_BM + row_in_tile;
             uint32_t any = 0;
@@ -412,6 +483,11 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         tcol[j * x.ld] = ((nbits >> j) & 1u) ? static_cast<uint8_t>(BMLP_E4M3_ONE) : 0;
+                    if (x.fmap_next != nullptr && nbits != 0u) {
+                        const int64_t cb = col0 / TC_BK;
+                        x.fmap_next[static_cast<int64_t>(x.mb) * x.fm_ld + cb] = 1;
+                        x.fmapT_next[cb * x.fm_ld + x.mb] = 1;
+                    }
                 } else if (x.mode == TC_MODE_SMP) {
                     uint4* vp = reinterpret_cast<uint4*>(x.visited + off);
                     const uint32_t vbits = nz_mask32(vp[0], vp[1]);
@@ -456,7 +532,7 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         tma_prefetch_desc(&tmB);
     }
     SingleSource src{&tmA, &tmB, &p};
-    tc_body(src, p.error, p.wait_cycles);
+    tc_body(src, p.error, p.wait_cycles, p.issued);
 }
 
 // Launched as 2-CTA clusters (RMS and PLAIN modes; no K-block skipping).
@@ -467,7 +543,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tma_prefetch_desc(&tmBh);
     }
     PairSource src{&tmA, &tmBh, &p, static_cast<int>(cluster_ctarank())};
-    tc_body<PairSource, true>(src, p.error, p.wait_cycles);
+    tc_body<PairSource, true>(src, p.error, p.wait_cycles, p.issued);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
