@@ -48,16 +48,21 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--degree", type=float, default=4.0)
-    ap.add_argument("--variant", default="rms_tc")
+    ap.add_argument("--variant", default=None,
+                    help="default: rms_tc (er), smp_packed (powerlaw_smp), auto (kg_batch, isforeign)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
-    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch"],
+    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch", "isforeign"],
                     help="er: the closure benchmark (default); powerlaw_smp: 4,096 selective query rows on the "
                          "n = 65,536 power-law graph; kg_batch: every relation closure and 200 compositions of "
-                         "the knowledge-graph workload in one grouped batch")
+                         "the knowledge-graph workload in one grouped batch; isforeign: the composed program "
+                         "hasPlace / indirectlyPartOf / isForeign on a 14,541-entity, 7,991-fact place hierarchy")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.variant is None:
+        args.variant = {"er": "rms_tc", "powerlaw_smp": "smp_packed"}.get(args.workload, "auto")
+    return args
 
 
 def dist_env():
@@ -232,6 +237,16 @@ def run_aux(args):
         def step():
             return ctx.smp(P, n, src, q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant, profile=True)
         unit, units_per_step, name = "queries/s", q, "powerlaw_n65536_q4096"
+    elif args.workload == "isforeign":
+        n = 14541
+        (ci, cx), (ai, ax) = wl.geo_kg(n=n)
+        C = torch.from_numpy(wl.csr_to_packed(n, ci, cx).view(np.int64)).cuda()
+        A = torch.from_numpy(wl.csr_to_packed(n, ai, ax).view(np.int64)).cuda()
+        out = torch.zeros_like(C)
+
+        def step():
+            return ctx.is_foreign(C, A, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant)
+        unit, units_per_step, name = "programs/s", 1, "geo_kg_n14541_f7991_isforeign"
     else:
         rels = wl.kg_relations()
         items, keep = [], []

@@ -175,6 +175,52 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
 bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt,
                          void* out, const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
 
+/*
+ * Boolean matrix operators that join BMLP algorithms into larger programs
+ * (paper Sec. 3.4, Fig. 3). All take n x n matrices in format fmt (device or
+ * host memory, like bmlp_rms) and run on the given stream.
+ *
+ * bmlp_transpose - TRANSP: out = R^T, i.e. the relation with its arguments
+ *     swapped (clauses such as p(X,Y) <- q(Y,X)).
+ * bmlp_union - the union of two relations (two clauses with one head):
+ *     out = A OR B.
+ * bmlp_negate - NEG with the type literals of a stratified negation
+ *     (p(X,Y) <- t(X), t(Y), not q(X,Y)): out[i][j] = rows(i) AND cols(j)
+ *     AND NOT R[i][j]. rows and cols are packed bit vectors of ceil(n/64)
+ *     uint64 words (the monadic type predicates, device or host memory); a
+ *     null vector admits every constant.
+ * out may alias an input for bmlp_union and bmlp_negate, not for
+ * bmlp_transpose.
+ */
+bmlp_status bmlp_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out,
+                           cudaStream_t stream);
+bmlp_status bmlp_union(bmlp_ctx* ctx, const void* A, const void* B, int64_t n, int32_t fmt, void* out,
+                       cudaStream_t stream);
+bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* rows,
+                        const uint64_t* cols, void* out, cudaStream_t stream);
+
+/*
+ * bmlp_is_foreign - the composed program P3 u P4 u P5 of paper Sec. 3.4
+ * (Fig. 3), in one call:
+ *
+ *     hasPlace          = contains+                          (BMLP-RMS)
+ *     indirectlyPartOf  = (I + hasPlace^T) (adjoins OR adjoins^T)
+ *                         (the recursion through hasPlace(Z,X) is a
+ *                          composition with the transposed closure, Thm. 1)
+ *     isForeign         = location x location AND NOT indirectlyPartOf
+ *
+ * contains, adjoins and out are n x n in format fmt; location is a packed
+ * bit vector (ceil(n/64) uint64 words) or null for "every constant is a
+ * location". The closure of contains runs with opts->variant (BMLP_AUTO: the
+ * learned dispatcher when trained, else tensor cores); the composition runs
+ * on the tensor cores for BMLP_RMS_TC / BMLP_SMP_TC and on packed rows
+ * otherwise. iters_out (2 entries, may be null) receives the products of the
+ * closure of contains and of the closure inside the composition.
+ */
+bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
+                            int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
+                            cudaStream_t stream);
+
 /* One problem of a grouped batch. */
 typedef enum bmlp_problem_kind {
     BMLP_PROBLEM_CLOSURE = 0,  /* out = R1+ (or I + R1+): program P2 of Sec. 3.3   */

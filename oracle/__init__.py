@@ -15,6 +15,7 @@ What it computes (paper Sec. 2 Eq. 1, Sec. 3.3 Eq. 4-5, Sec. 3.4 Thm. 1):
 * ``warshall``     Warshall triple loop (small n)
 * ``compose_rows`` rows of (I + R2+) R1 by search
 * ``rms_iterations`` number of products the squaring fixpoint issues
+* ``is_foreign``   rows of the composed program P3 u P4 u P5 of Sec. 3.4
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (paper examples, closed forms, invariants, brute force on tiny inputs).
@@ -173,3 +174,34 @@ def compose_rows(n, csr1, csr2, rows=None):
         _L().oracle_compose_rows(n, _p(ip1, _i64p), _p(ix1, _i32p), _p(ip2, _i64p), _p(ix2, _i32p),
                                  _p(rr, _i32p), len(rr), _p(out, _u8p))
     return out
+
+
+def _dense_to_csr(m):
+    r, c = np.nonzero(m)
+    ip = np.zeros(m.shape[0] + 1, np.int64)
+    np.add.at(ip, r + 1, 1)
+    return np.cumsum(ip), c.astype(np.int32)
+
+
+def is_foreign(n, contains, adjoins, location=None, rows=None):
+    """Rows of isForeign for the programs P3, P4, P5 of Sec. 3.4.
+
+    P3: hasPlace = contains+ (per-source BFS). P4: indirectlyPartOf(X,Y) holds
+    for adjoins(X,Y), adjoins(Y,X), or hasPlace(Z,X) with
+    indirectlyPartOf(Z,Y); its least model is p <- base ; p <- rec, p with
+    base = adjoins u adjoins^T and rec(X,Z) = hasPlace(Z,X), evaluated row by
+    row by ``compose_rows``. P5: isForeign(X,Y) = location(X), location(Y),
+    not indirectlyPartOf(X,Y). contains / adjoins are (indptr, indices);
+    location is a 0/1 vector of length n or None (every constant).
+    """
+    rr = np.arange(n, dtype=np.int32) if rows is None else np.ascontiguousarray(rows, np.int32)
+    has_place = closure(n, *contains)
+    rec = _dense_to_csr(np.ascontiguousarray(has_place.T))
+    a = np.zeros((n, n), np.uint8)
+    ip, ix = _csr(*adjoins)
+    for i in range(n):
+        a[i, ix[ip[i]:ip[i + 1]]] = 1
+    base = _dense_to_csr(a | a.T)
+    ipo = compose_rows(n, base, rec, rr)
+    loc = np.ones(n, np.uint8) if location is None else np.asarray(location, np.uint8)
+    return (loc[rr][:, None] & loc[None, :] & (1 - ipo)).astype(np.uint8)

@@ -117,6 +117,11 @@ def lib():
                                    ctypes.POINTER(i32), vp]
             L.bmlp_compose.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
                                        ctypes.POINTER(i32), vp]
+            L.bmlp_transpose.argtypes = [vp, vp, i64, i32, vp, vp]
+            L.bmlp_union.argtypes = [vp, vp, vp, i64, i32, vp, vp]
+            L.bmlp_negate.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+            L.bmlp_is_foreign.argtypes = [vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
+                                          ctypes.POINTER(i32), vp]
             L.bmlp_batch_run.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.POINTER(bmlp_options),
                                          ctypes.POINTER(i32), vp]
             L.bmlp_batch_autotune.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.c_char_p, vp]
@@ -133,7 +138,7 @@ def lib():
                          "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune", "bmlp_dispatch_features",
                          "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_loss_grad",
                          "bmlp_dispatch_set_params", "bmlp_dispatch_get_params", "bmlp_dispatch_save",
-                         "bmlp_dispatch_load"):
+                         "bmlp_dispatch_load", "bmlp_transpose", "bmlp_union", "bmlp_negate", "bmlp_is_foreign"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -351,6 +356,30 @@ class Context:
         self._check(self._L.bmlp_compose(self.handle, _ptr(R1), _ptr(R2), int(n), int(fmt), _ptr(out),
                                          ctypes.byref(o), ctypes.byref(it), _stream(stream, self.device)))
         return it.value
+
+    def transpose(self, R, n, out, fmt=BMLP_FMT_U8, stream=None):
+        """bmlp_transpose (TRANSP): out = R^T."""
+        self._check(self._L.bmlp_transpose(self.handle, _ptr(R), int(n), int(fmt), _ptr(out),
+                                           _stream(stream, self.device)))
+
+    def union(self, A, B, n, out, fmt=BMLP_FMT_U8, stream=None):
+        """bmlp_union: out = A OR B."""
+        self._check(self._L.bmlp_union(self.handle, _ptr(A), _ptr(B), int(n), int(fmt), _ptr(out),
+                                       _stream(stream, self.device)))
+
+    def negate(self, R, n, out, rows=None, cols=None, fmt=BMLP_FMT_U8, stream=None):
+        """bmlp_negate (NEG): out = rows x cols AND NOT R (None = every constant)."""
+        self._check(self._L.bmlp_negate(self.handle, _ptr(R), int(n), int(fmt), _ptr(rows), _ptr(cols), _ptr(out),
+                                        _stream(stream, self.device)))
+
+    def is_foreign(self, contains, adjoins, n, out, location=None, fmt=BMLP_FMT_U8, stream=None, **opt):
+        """bmlp_is_foreign: the composed program P3 u P4 u P5. Returns the
+        products of (closure of contains, closure inside the composition)."""
+        o = make_options(**opt)
+        it = (ctypes.c_int32 * 2)()
+        self._check(self._L.bmlp_is_foreign(self.handle, _ptr(contains), _ptr(adjoins), _ptr(location), int(n),
+                                            int(fmt), _ptr(out), ctypes.byref(o), it, _stream(stream, self.device)))
+        return it[0], it[1]
 
 
 def rms_tc_noalloc(R, n, out, fmt=BMLP_FMT_U8, reflexive=False, max_iters=0, stream=None, device=0):

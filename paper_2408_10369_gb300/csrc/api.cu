@@ -69,6 +69,8 @@ enum : int {
     WS_FEAT = 16, WS_PT = 17, WS_WPTRT = 18, WS_WIDXT = 19
 };
 constexpr int WS_WVALT = 20;
+// Relation operators and the composed isForeign program (packed buffers and type vectors).
+constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 
@@ -870,6 +872,152 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
     }
     ctx->stats.iterations = iters;
     if (iters_out) *iters_out = iters;
+    return finish_out(ctx, ov, s);
+}
+
+// ---- relation operators of Sec. 3.4 (Fig. 3) on packed rows of words_of(n) words
+static bmlp_status op_args(bmlp_ctx* ctx, int64_t n, int32_t fmt) {
+    if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    return BMLP_OK;
+}
+
+// A packed workspace copy of a caller matrix (staged through `stage_slot` when it is host memory).
+static bmlp_status packed_operand(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, int stage_slot, int slot,
+                                  cudaStream_t s, uint64_t** P) {
+    Operand in;
+    ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), stage_slot, s, &in));
+    void* p = nullptr;
+    ST(ws_get(ctx, slot, static_cast<size_t>(n * words_of(n) * 8), &p));
+    *P = static_cast<uint64_t*>(p);
+    return to_packed(ctx, in, fmt, n, *P, words_of(n), s);
+}
+
+bmlp_status bmlp_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    ST(op_args(ctx, n, fmt));
+    if (n == 0) return BMLP_OK;
+    if (!R || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    DeviceGuard g(ctx->device);
+    reset_stats(ctx, 0, n);
+    const int64_t ldw = words_of(n);
+    uint64_t *P = nullptr, *PT = nullptr;
+    ST(packed_operand(ctx, R, n, fmt, WS_IN0, WS_PIPE0, s, &P));
+    void* pt = nullptr;
+    ST(ws_get(ctx, WS_PIPE1, static_cast<size_t>(n * ldw * 8), &pt));
+    PT = static_cast<uint64_t*>(pt);
+    CK(launch_bit_transpose(P, PT, n, ldw, s), "transpose launch");
+    ctx->stats.launches++;
+    OutView ov;
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    ST(packed_out(ctx, PT, ldw, n, fmt, ov.dev, 0, s));
+    return finish_out(ctx, ov, s);
+}
+
+bmlp_status bmlp_union(bmlp_ctx* ctx, const void* A, const void* B, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    ST(op_args(ctx, n, fmt));
+    if (n == 0) return BMLP_OK;
+    if (!A || !B || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    DeviceGuard g(ctx->device);
+    reset_stats(ctx, 0, n);
+    const int64_t ldw = words_of(n);
+    uint64_t *PA = nullptr, *PB = nullptr;
+    ST(packed_operand(ctx, A, n, fmt, WS_IN0, WS_PIPE0, s, &PA));
+    ST(packed_operand(ctx, B, n, fmt, WS_IN1, WS_PIPE1, s, &PB));
+    launch_packed_or(PA, ldw, PB, ldw, n, n, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "union launch");
+    OutView ov;
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    ST(packed_out(ctx, PA, ldw, n, fmt, ov.dev, 0, s));
+    return finish_out(ctx, ov, s);
+}
+
+// Device view of an optional packed type vector (null = every constant).
+static bmlp_status type_vector(bmlp_ctx* ctx, const uint64_t* v, int64_t n, int slot, cudaStream_t s,
+                               const uint64_t** dv) {
+    *dv = nullptr;
+    if (!v) return BMLP_OK;
+    Operand o;
+    ST(stage_in(ctx, v, static_cast<size_t>(words_of(n) * 8), slot, s, &o));
+    *dv = static_cast<const uint64_t*>(o.dev);
+    return BMLP_OK;
+}
+
+bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* rows,
+                        const uint64_t* cols, void* out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    ST(op_args(ctx, n, fmt));
+    if (n == 0) return BMLP_OK;
+    if (!R || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    DeviceGuard g(ctx->device);
+    reset_stats(ctx, 0, n);
+    const int64_t ldw = words_of(n);
+    uint64_t* P = nullptr;
+    ST(packed_operand(ctx, R, n, fmt, WS_IN0, WS_PIPE0, s, &P));
+    const uint64_t *dr = nullptr, *dc = nullptr;
+    ST(type_vector(ctx, rows, n, WS_SRC, s, &dr));
+    ST(type_vector(ctx, cols, n, WS_VEC0, s, &dc));
+    launch_packed_negate(P, ldw, n, dr, dc, P, ldw, s);
+    ctx->stats.launches++;
+    CK(cudaGetLastError(), "negate launch");
+    OutView ov;
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    ST(packed_out(ctx, P, ldw, n, fmt, ov.dev, 0, s));
+    return finish_out(ctx, ov, s);
+}
+
+bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
+                            int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
+                            cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (iters_out) iters_out[0] = iters_out[1] = 0;
+    ST(op_args(ctx, n, fmt));
+    if (n == 0) return BMLP_OK;
+    if (!contains || !adjoins || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    DeviceGuard g(ctx->device);
+    const bmlp_options o = resolve(opts);
+    const int64_t ldw = words_of(n);
+    const size_t pbytes = static_cast<size_t>(n * ldw * 8);
+    // PA = adjoins, PC = contains (packed); PH receives hasPlace = contains+ (P3)
+    uint64_t *PA = nullptr, *PC = nullptr, *PH = nullptr;
+    ST(packed_operand(ctx, adjoins, n, fmt, WS_IN1, WS_PIPE0, s, &PA));
+    ST(packed_operand(ctx, contains, n, fmt, WS_IN0, WS_PIPE2, s, &PC));
+    void* ph = nullptr;
+    ST(ws_get(ctx, WS_PIPE1, pbytes, &ph));
+    PH = static_cast<uint64_t*>(ph);
+    bmlp_options oc = o;
+    oc.reflexive = 0;
+    int32_t it0 = 0, it1 = 0;
+    ST(bmlp_rms(ctx, PC, n, BMLP_FMT_PACKED64, PH, &oc, &it0, s));
+    bmlp_stats acc = ctx->stats;
+    // P4: indirectlyPartOf = adjoins u adjoins^T u hasPlace^T . indirectlyPartOf = (I + (hasPlace^T)+) B
+    CK(launch_bit_transpose(PH, PC, n, ldw, s), "transpose launch");  // PC := hasPlace^T
+    CK(launch_bit_transpose(PA, PH, n, ldw, s), "transpose launch");  // PH := adjoins^T
+    launch_packed_or(PH, ldw, PA, ldw, n, n, s);                     // PH := B = adjoins u adjoins^T
+    CK(cudaGetLastError(), "union launch");
+    oc.variant = (o.variant == BMLP_RMS_TC || o.variant == BMLP_SMP_TC) ? BMLP_RMS_TC : BMLP_RMS_PACKED;
+    ST(bmlp_compose(ctx, PH, PC, n, BMLP_FMT_PACKED64, PA, &oc, &it1, s));  // PA := indirectlyPartOf
+    // P5: isForeign = location x location AND NOT indirectlyPartOf
+    const uint64_t* loc = nullptr;
+    ST(type_vector(ctx, location, n, WS_VEC0, s, &loc));
+    launch_packed_negate(PA, ldw, n, loc, loc, PA, ldw, s);
+    CK(cudaGetLastError(), "negate launch");
+    OutView ov;
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    ST(packed_out(ctx, PA, ldw, n, fmt, ov.dev, 0, s));
+    acc.product_launches += ctx->stats.product_launches;
+    acc.launches += ctx->stats.launches + 5;
+    acc.product_ms += ctx->stats.product_ms;
+    acc.issued_ops += ctx->stats.issued_ops;
+    acc.iterations = it0 + it1;
+    ctx->stats = acc;
+    if (iters_out) {
+        iters_out[0] = it0;
+        iters_out[1] = it1;
+    }
     return finish_out(ctx, ov, s);
 }
 

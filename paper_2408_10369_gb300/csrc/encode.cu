@@ -214,6 +214,28 @@ __global__ void identity_packed_kernel(uint64_t* __restrict__ out, int64_t ldw, 
     }
 }
 
+// NEG of Fig. 3 with the type literals of a stratified negation: out[i][j] =
+// rows(i) AND cols(j) AND NOT in[i][j] for i, j < n; a null rows / cols
+// vector admits every constant. Bits at j >= n stay zero.
+__global__ void negate_restrict_kernel(const uint64_t* __restrict__ in, int64_t ldw_in, int64_t n,
+                                       const uint64_t* __restrict__ rows, const uint64_t* __restrict__ cols,
+                                       uint64_t* __restrict__ out, int64_t ldw_out) {
+    const int64_t wpr = (n + 63) / 64;
+    const int64_t total = n * ldw_out;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = t / ldw_out, w = t % ldw_out;
+        uint64_t v = 0;
+        if (w < wpr && (!rows || ((rows[r >> 6] >> (r & 63)) & 1ull))) {
+            v = ~in[r * ldw_in + w];
+            if (cols) v &= cols[w];
+            const int64_t valid = n - w * 64;
+            if (valid < 64) v &= (1ull << valid) - 1ull;
+        }
+        out[t] = v;
+    }
+}
+
 __global__ void set_diag_kernel(uint8_t* R, int64_t ld, int64_t n) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -289,6 +311,11 @@ void launch_packed_or(uint64_t* out, int64_t ldw_out, const uint64_t* src, int64
 
 void launch_identity_packed(uint64_t* out, int64_t ldw, int64_t n, cudaStream_t s) {
     identity_packed_kernel<<<grid_for(n * ldw, 256), 256, 0, s>>>(out, ldw, n);
+}
+
+void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const uint64_t* rows, const uint64_t* cols,
+                          uint64_t* out, int64_t ldw_out, cudaStream_t s) {
+    negate_restrict_kernel<<<grid_for(n * ldw_out, 256), 256, 0, s>>>(in, ldw_in, n, rows, cols, out, ldw_out);
 }
 
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s) {

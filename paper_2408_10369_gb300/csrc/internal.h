@@ -128,7 +128,7 @@ struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
     char err[512] = {0};
-    bmlp::DevBuf ws[24];
+    bmlp::DevBuf ws[28];
     void* batch = nullptr;       // cached grouped-batch graph (batch.cu)
     int tune[32];                // autotuned engine per size bucket (-1 = unknown)
     int* d_ctl = nullptr;        // device control words (see CTL_* below)
@@ -201,6 +201,9 @@ void launch_packed_or(uint64_t* out, int64_t ldw_out, const uint64_t* src, int64
                       cudaStream_t s);
 // identity as packed rows: row i has only bit i
 void launch_identity_packed(uint64_t* out, int64_t ldw, int64_t n, cudaStream_t s);
+// out = rows x cols AND NOT in over n x n packed rows (null vector = all constants)
+void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const uint64_t* rows, const uint64_t* cols,
+                          uint64_t* out, int64_t ldw_out, cudaStream_t s);
 // set the diagonal of an n x n byte matrix (ld) to E4M3 one
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s);
 // per (M block, K block) nonzero flags of a byte matrix rows_pad x n_pad

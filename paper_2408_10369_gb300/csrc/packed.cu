@@ -182,11 +182,14 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
 constexpr int PULL_RATIO = 4;
 
 // ---- selective product per query row
-// Per warp in shared memory: D, N (ldw words each) and FL, the list of the
-// frontier's nonzero words (ldw 16-bit word indices). The visited set V is
-// the query's own output row in global memory (only its warp touches it).
-// The stride is rounded up to 16 bytes so every warp's uint64 arrays stay aligned.
-__host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) { return (18 * ldw + 16 + 15) & ~int64_t(15); }
+// Per warp in shared memory: D, N (ldw words each), FL, the list of the
+// frontier's nonzero words (ldw 16-bit word indices), and GM, 64 bytes that
+// map a rank to the index of a touched word group. The visited set V is the
+// query's own output row in global memory (only its warp touches it). The
+// stride is rounded up to 16 bytes so every warp's uint64 arrays stay aligned.
+__host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) {
+    return (18 * ldw + 64 + 16 + 15) & ~int64_t(15);
+}
 
 __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
@@ -203,7 +206,13 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
     uint64_t* D = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw));
     uint64_t* N = D + ldw;
     uint16_t* FL = reinterpret_cast<uint16_t*>(N + ldw);
+    uint8_t* GM = reinterpret_cast<uint8_t*>(FL + ldw);
     const int64_t wpr = (n + 63) / 64;
+    // words of N form at most 64 groups of 2^gshift words; a push records the groups it wrote
+    int gshift = 0;
+    while ((int64_t(64) << gshift) < wpr) ++gshift;
+    const int ngroups = static_cast<int>((wpr + (int64_t(1) << gshift) - 1) >> gshift);
+    const uint64_t all_groups = ngroups >= 64 ? ~0ull : (1ull << ngroups) - 1ull;
     while (true) {
         unsigned long long qi = 0;
         if (lane == 0) qi = atomicAdd(qcounter, 1ull);
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
         int64_t nu = n;  // unvisited constants
         while (true) {
             if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
-            int nlo = 0, nhi = static_cast<int>(wpr);  // words of N that may be nonzero after this expansion
+            uint64_t gm = all_groups;  // groups of N that may be nonzero after this expansion
             if (pull) {
                 // pull: unvisited j joins the next frontier iff some word of column j (row j of R^T) meets D;
                 // each lane owns whole words of N (no atomics)
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
             } else {
                 // push: OR the nonzero words of every frontier row into N (no return values, so the
                 // atomics are reductions); track the range of words written
-                int tlo = static_cast<int>(wpr), thi = -1;
+                uint64_t tm = 0;
                 for (int i0 = 0; i0 < fcount; i0 += 32) {
                     const int i = i0 + lane;
                     const int64_t w = i < fcount ? FL[i] : 0;
@@ -286,8 +295,7 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
                                 const int x = widx[e];
                                 atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
                                          static_cast<unsigned long long>(wval[e]));
-                                tlo = x < tlo ? x : tlo;
-                                thi = x > thi ? x : thi;
+                                tm |= 1ull << (x >> gshift);
                             }
                         unsigned hm = __ballot_sync(FULL, k >= 0 && heavy);
                         while (hm) {
@@ -298,26 +306,32 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
                                 const int x = widx[e];
                                 atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
                                          static_cast<unsigned long long>(wval[e]));
-                                tlo = x < tlo ? x : tlo;
-                                thi = x > thi ? x : thi;
+                                tm |= 1ull << (x >> gshift);
                             }
                         }
                     }
                 }
-                nlo = __reduce_min_sync(FULL, tlo);
-                nhi = __reduce_max_sync(FULL, thi) + 1;
-                if (nhi <= nlo) nlo = nhi = 0;
+                gm = static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm))) |
+                     (static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm >> 32))) << 32);
             }
             __syncwarp();
-            // D := 0 on the old frontier words, then D := N & ~V on N's range (V |= D, N := 0);
+            // D := 0 on the old frontier words, then D := N & ~V on the touched groups (V |= D, N := 0);
             // the words that come out nonzero become the new frontier list FL
             for (int i = lane; i < fcount; i += 32) D[FL[i]] = 0;
             __syncwarp();
             int nf = 0, fnew = 0;
-            for (int w0 = nlo; w0 < nhi; w0 += 32) {
-                const int w = w0 + lane;
+            // GM[r] = index of the r-th set group of gm; candidates are the words of those groups
+            for (int b = lane; b < 64; b += 32)
+                if ((gm >> b) & 1ull) GM[__popcll(gm & ((1ull << b) - 1ull))] = static_cast<uint8_t>(b);
+            __syncwarp();
+            const int cand = __popcll(gm) << gshift;
+            const int gmask = (1 << gshift) - 1;
+            for (int c0 = 0; c0 < cand; c0 += 32) {
+                const int c = c0 + lane;
+                int w = static_cast<int>(wpr);
+                if (c < cand) w = (static_cast<int>(GM[c >> gshift]) << gshift) + (c & gmask);
                 uint64_t nw = 0;
-                if (w < nhi) {
+                if (w < wpr) {
                     nw = N[w] & ~V[w];
                     N[w] = 0;
                     if (nw) {

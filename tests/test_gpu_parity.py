@@ -165,6 +165,48 @@ def test_smp_powerlaw_packed_input(ctx, variant):
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
 
 
+# ------------------------------------------- long shortest paths --
+def shortcut_case(n, shape, seed):
+    """A chain (i -> i+1) or a right/down grid plus round(1 % of n) random
+    shortcuts: many frontier heads scattered over the row, hundreds of levels."""
+    if shape == "grid":
+        side = max(2, int(np.sqrt(n)))
+        idx = np.arange(n)
+        right = idx[(idx % side + 1 < side) & (idx + 1 < n)]
+        down = idx[idx + side < n]
+        src, dst = np.concatenate([right, down]), np.concatenate([right + 1, down + side])
+    else:
+        src = np.arange(n - 1)
+        dst = src + 1
+    a, b = wl.random_pairs(n, max(1, round(0.01 * n)), seed)
+    return wl.csr_from_pairs(n, np.concatenate([src, a]), np.concatenate([dst, b]))
+
+
+@pytest.mark.parametrize("variant", CLOSURE_VARIANTS)
+@pytest.mark.parametrize("n,shape,seed", [(3000, "chain", 1), (2500, "grid", 2), (4500, "chain", 3)])
+def test_closure_long_paths(ctx, variant, n, shape, seed):
+    ip, ix = shortcut_case(n, shape, seed)
+    want = oracle.closure(n, ip, ix)
+    got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), variant, fmt="packed")
+    np.testing.assert_array_equal(got, want)
+
+
+def test_smp_wide_rows_long_paths(ctx):
+    """n = 135,000 (2,110 words per row, so more than 32 words of the
+    touched-word bitmap per warp) on a chain with shortcuts."""
+    n, q = 135_000, 6
+    ip, ix = shortcut_case(n, "chain", 7)
+    src = wl.query_rows(n, q, 1, 4, 8)
+    want, levels = oracle.smp(n, ip, ix, src)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
+    it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=pkg.BMLP_FMT_PACKED64, variant="smp_packed")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
+    assert it == int(levels.max()) + 1
+    del P
+
+
 # ------------------------------------------------------------ compose --
 @pytest.mark.parametrize("variant", ["rms_tc", "rms_packed"])
 @pytest.mark.parametrize("n,seed", [(1, 0), (77, 1), (256, 2), (513, 3)])

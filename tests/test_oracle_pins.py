@@ -75,6 +75,55 @@ def test_p3_p5_isforeign_example():
     assert int(is_foreign.sum()) == n * n - 4
 
 
+def test_is_foreign_oracle_example():
+    """The composed-program oracle on the Sec. 3.4 example: 45 of 49 groundings,
+    the 4 false ones exactly as listed; a location subset restricts both
+    arguments."""
+    consts, facts = read_facts("p3p5_isforeign.txt")
+    n = len(consts)
+    c, a = csr(matrix(consts, facts["contains"])), csr(matrix(consts, facts["adjoins"]))
+    got = oracle.is_foreign(n, c, a)
+    np.testing.assert_array_equal(1 - got, matrix(consts, facts["not_isForeign"]))
+    assert int(got.sum()) == 45
+    loc = np.array([1, 1, 1, 1, 0, 0, 0], np.uint8)           # only g1..g4 are locations
+    got = oracle.is_foreign(n, c, a, loc)
+    assert int(got[4:].sum()) == 0 and int(got[:, 4:].sum()) == 0
+    assert int(got.sum()) == 16 - 3                            # (g2, g4), (g3, g4), (g4, g3) stay false
+    np.testing.assert_array_equal(oracle.is_foreign(n, c, a, loc, rows=[3, 0]), got[[3, 0]])
+
+
+def brute_is_foreign(n, contains, adjoins, loc):
+    """Naive bottom-up evaluation of P3, P4, P5 over sets of ground atoms."""
+    has_place = set(contains)
+    while True:
+        new = {(x, y) for (x, z) in contains for (z2, y) in has_place if z == z2} - has_place
+        if not new:
+            break
+        has_place |= new
+    ipo = set(adjoins) | {(y, x) for (x, y) in adjoins}
+    while True:
+        new = {(x, y) for (z, x) in has_place for (z2, y) in ipo if z == z2} - ipo
+        if not new:
+            break
+        ipo |= new
+    return {(x, y) for x in range(n) for y in range(n) if loc[x] and loc[y] and (x, y) not in ipo}
+
+
+def test_is_foreign_oracle_brute_force():
+    rng = np.random.default_rng(5)
+    for _ in range(150):
+        n = int(rng.integers(1, 7))
+        cm = (rng.random((n, n)) < rng.uniform(0.05, 0.4)).astype(np.uint8)
+        am = (rng.random((n, n)) < rng.uniform(0.0, 0.3)).astype(np.uint8)
+        loc = (rng.random(n) < 0.7).astype(np.uint8)
+        contains = list(zip(*np.nonzero(cm)))
+        adjoins = list(zip(*np.nonzero(am)))
+        want = np.zeros((n, n), np.uint8)
+        for x, y in brute_is_foreign(n, contains, adjoins, loc):
+            want[x, y] = 1
+        np.testing.assert_array_equal(oracle.is_foreign(n, csr(cm), csr(am), loc), want)
+
+
 # -------------------------------------------------------- brute force --
 def walk_closure(m):
     """(i, j) in R+ iff some walk i -> v1 -> ... -> j of 1..n edges exists,

@@ -68,3 +68,31 @@ def test_kg_relations_shape():
     assert 15000 < total <= 20000
     pairs = wl.kg_compose_pairs(rels, 20, 0)
     assert len(pairs) == 20 and all(a != b for a, b in pairs)
+
+
+def test_geo_kg_shape():
+    (ci, cx), (ai, ax) = wl.geo_kg()
+    assert len(cx) + len(ax) == 7991                      # 14,541 entities, 7,991 facts
+    assert len(ci) == len(ai) == 14542
+    child_parents = np.bincount(cx, minlength=14541)
+    assert child_parents.max() == 1                      # a forest: one parent per place
+    (ci2, cx2), _ = wl.geo_kg()
+    np.testing.assert_array_equal(cx, cx2)
+    n = 3000
+    (ci, cx), _ = wl.geo_kg(n=n, n_contains=1500, n_adjoins=300, n_roots=50, seed=3)
+    assert oracle_free_acyclic(n, ci, cx)
+
+
+def oracle_free_acyclic(n, ip, ix):
+    """Kahn's algorithm: the contains relation has no cycle."""
+    indeg = np.bincount(ix, minlength=n)
+    stack = [i for i in range(n) if indeg[i] == 0]
+    seen = 0
+    while stack:
+        v = stack.pop()
+        seen += 1
+        for w in ix[ip[v]:ip[v + 1]]:
+            indeg[w] -= 1
+            if indeg[w] == 0:
+                stack.append(w)
+    return seen == n

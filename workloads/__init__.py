@@ -300,6 +300,38 @@ def csr_to_packed(n: int, indptr, indices) -> np.ndarray:
     return rows[:n, :ld]
 
 
+def geo_kg(n: int = 14541, n_contains: int = 5993, n_adjoins: int = 1998, n_roots: int = 200, seed: int = 0):
+    """A place hierarchy with neighbours, the shape of the location subset of
+    FB15K-237 used for isForeign (14,541 entities, 7,991 facts).
+
+    contains(p, c): entities are put in a random order; the first n_roots are
+    top-level regions, each of the next n_contains entities gets one parent
+    among the entities before it, drawn from an urn holding every earlier
+    entity once plus one copy per child it already has (preferential
+    attachment, so a few regions contain many places). The hierarchy is a
+    forest, hence acyclic. adjoins(a, b): n_adjoins uniform pairs a != b,
+    deduplicated. Returns (contains CSR, adjoins CSR).
+    """
+    order = sorted(range(n), key=lambda i: draw(seed, 40, i))
+    urn = list(order[:n_roots])
+    src, dst = [], []
+    for t in range(n_roots, min(n, n_roots + n_contains)):
+        child = order[t]
+        parent = urn[draw(seed, 41, t) % len(urn)]
+        src.append(parent)
+        dst.append(child)
+        urn.append(child)
+        urn.append(parent)
+    contains = csr_from_pairs(n, np.array(src, np.int64), np.array(dst, np.int64))
+    a, b = random_pairs(n, n_adjoins, wl_seed(seed, 42))
+    return contains, csr_from_pairs(n, a, b)
+
+
+def wl_seed(seed: int, tag: int) -> int:
+    """A derived 63-bit seed for a sub-stream."""
+    return draw(seed, tag, 0) >> 1
+
+
 FAMILIES = ("er", "powerlaw", "chain_grid", "sbm")
 
 
