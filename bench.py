@@ -37,6 +37,7 @@ METRIC = "Boolean closure eff. TOPS & graphs/s vs plain RMS, same GB300, bit-exa
 UNIT = "eff. Boolean TOPS (iters*2n^3/s)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP8_PER_BF16 = 2.0          # nominal dense ratio fp8 / bf16 (4.5 / 2.25 PFLOP/s)
+FP4_PER_BF16 = 6.0          # nominal dense ratio fp4 / bf16 (13.5 / 2.25 PFLOP/s)
 FALLBACK_BF16_BURST = 1900.0
 
 
@@ -92,9 +93,9 @@ def peaks():
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)
-        return float(p["bf16_tflops"]) * FP8_PER_BF16, float(p.get("hbm_gbs", 0.0)), "measured"
+        return float(p["bf16_tflops"]), float(p.get("hbm_gbs", 0.0)), "measured"
     except Exception:
-        return FALLBACK_BF16_BURST * FP8_PER_BF16, 6800.0, "fallback"
+        return FALLBACK_BF16_BURST, 6800.0, "fallback"
 
 
 class ClockSampler:
@@ -149,9 +150,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_hash():
+KERNEL_SOURCES = {"tc_pair_kernel": "tc_product.cu", "tc_product_kernel": "tc_product.cu",
+                  "tc4_pair_kernel": "tc_fp4.cu"}
+
+
+def kernel_hash(kernel="tc_pair_kernel"):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2408_10369_gb300", "csrc", "tc_product.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2408_10369_gb300", "csrc", KERNEL_SOURCES[kernel]), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:12]
 
@@ -167,7 +172,7 @@ def profiled_traffic(kernel, n):
                 if ln.startswith("- ") and ":" in ln:
                     k, v = ln[2:].split(":", 1)
                     kv[k.strip()] = v.strip().strip("`")
-        if kv.get("kernel_source_sha256_12") != kernel_hash():
+        if kv.get("kernel_source_sha256_12") != kernel_hash(kernel):
             return None
         return float(kv["dram_bytes_per_launch"])
     except Exception:
@@ -333,7 +338,7 @@ def main():
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    prod_ms, prod_n, launches, issued = 0.0, 0, 0, 0.0
+    prod_ms, prod_n, launches, issued, e2m1_n = 0.0, 0, 0, 0.0, 0
     for _ in range(args.steps):
         iters = step(True)
         st = ctx.stats()
@@ -341,6 +346,7 @@ def main():
         prod_n += st["product_launches"]
         launches += st["launches"]
         issued += st["issued_ops"]
+        e2m1_n += st["e2m1_products"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -398,13 +404,21 @@ def main():
             variants["auto"] = {"ms": ta * 1e3, "chosen": chosen, "graphs_per_s": 1.0 / ta,
                                 "eff_tops": iters * 2.0 * n ** 3 / ta / 1e12,
                                 "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
-    peak, _, peak_src = peaks()
+    bf16, _, peak_src = peaks()
     avg_launch_s = prod_ms / max(prod_n, 1) / 1e3
     achieved = 2.0 * n ** 3 / avg_launch_s / 1e12 if avg_launch_s > 0 else None
-    kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
+    # every timed product on packed E2M1 operands (kind::mxf4), else E4M3 (kind::f8f6f4)
+    fp4 = prod_n > 0 and e2m1_n == prod_n
+    ratio, rname = (FP4_PER_BF16, "fp4/bf16") if fp4 else (FP8_PER_BF16, "fp8/bf16")
+    peak = bf16 * ratio
+    if fp4:
+        kname = "tc4_pair_kernel"
+    else:
+        kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
-            "peak_source": "%s bf16 burst x %g (fp8/bf16 nominal); the product runs unthrottled at max SM clock" % (peak_src, FP8_PER_BF16),
+            "peak_source": "%s bf16 burst x %g (%s nominal); the product runs unthrottled at max SM clock"
+                           % (peak_src, ratio, rname),
             "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None}
     if rank != 0:
         ctx.close()
@@ -421,7 +435,8 @@ def main():
                % (rows, n, tc)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3 0/1 operands, fp32 accumulate", "data": "synthetic",
+            "vs_baseline": None, "dtype": ("e2m1 0/1 operands (UE8M0 block scales of 1), fp32 accumulate" if fp4
+                                           else "e4m3 0/1 operands, fp32 accumulate"), "data": "synthetic",
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
                        "seed": "rank", "variant": args.variant, "iterations": iters, "nnz": int(len(ix)),
                        "graphs_per_s": args.steps * world / t, "l2": "inputs larger than L2 (1 GiB per matrix)",

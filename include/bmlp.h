@@ -65,7 +65,9 @@ typedef enum bmlp_format {
  * bits; they differ only in speed. */
 typedef enum bmlp_variant {
     BMLP_AUTO = 0,        /* library choice (learned dispatcher if trained)    */
-    BMLP_RMS_TC = 1,      /* repeated squaring, tcgen05 FP8 tensor-core product */
+    BMLP_RMS_TC = 1,      /* repeated squaring on the tcgen05 tensor cores: E4M3
+                             operands while R is block-sparse (empty K blocks
+                             skipped), packed E2M1 (kind::mxf4) once dense     */
     BMLP_RMS_PACKED = 2,  /* repeated squaring on uint64 row bitsets            */
     BMLP_SMP_TC = 3,      /* frontier expansion, tensor-core frontier product   */
     BMLP_SMP_PACKED = 4   /* frontier expansion on uint64 row bitsets           */
@@ -108,6 +110,8 @@ typedef struct bmlp_stats {
                                   (only with options.profile = 1)               */
     double issued_ops;         /* Boolean multiply-adds issued x 2 (tensor core
                                   path: 2 * M * N * K per tile actually run)    */
+    int32_t e2m1_products;     /* squarings run on packed E2M1 (4-bit) operands */
+    int32_t reserved;
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

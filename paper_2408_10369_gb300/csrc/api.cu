@@ -239,6 +239,15 @@ bool tc_pairs_enabled() {
     return on;
 }
 
+// Dense squarings on packed E2M1 operands (kind::mxf4) unless BMLP_TC_FP4=0.
+bool tc_fp4_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_TC_FP4");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // K-block skipping by the block-occupancy map of R, unless BMLP_TC_SKIP=0.
 bool tc_skip_enabled() {
     static const bool on = [] {
@@ -310,11 +319,73 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     ProductTimer tm{ctx, o.profile != 0, s};
     p.issued = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_ISSUED);
     CK(cudaMemsetAsync(p.issued, 0, sizeof(unsigned long long), s), "reset issued counter");
+    // Once R is dense, the squarings continue on packed E2M1 operands (half the bytes per Boolean operation):
+    // R, R^T are converted into the halves of the free E4M3 buffer pair (index sw ^ 1) and ping-pong there;
+    // the result is converted back into the E4M3 pair sw.
+    const bool fp4 = pair && tc_fp4_enabled();
+    bool on_f4 = false;
+    int sw = 0, qcur = 0;
+    uint8_t* Q[2] = {nullptr, nullptr};
+    uint8_t* QT[2] = {nullptr, nullptr};
+    CUtensorMap mapA4[2], mapB4[2];
+    const int64_t ld4 = n_pad / 2;
+    auto finish_f4 = [&](uint8_t** r, uint8_t** rt) -> bmlp_status {
+        launch_e2m1_to_e4m3(Q[qcur], M[sw], n_pad * n_pad, s);
+        launch_e2m1_to_e4m3(QT[qcur], T[sw], n_pad * n_pad, s);
+        CK(cudaGetLastError(), "E2M1 decode");
+        ctx->stats.launches += 2;
+        *r = M[sw];
+        *rt = T[sw];
+        return BMLP_OK;
+    };
     int cur = 0;
     *iters = 0;
     for (int it = 0; it < max_iters; ++it) {
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        if (fp4 && !use_maps && !on_f4) {
+            sw = cur;
+            const size_t half = static_cast<size_t>(n_pad) * static_cast<size_t>(ld4);
+            Q[0] = M[nxt];
+            Q[1] = M[nxt] + half;
+            QT[0] = T[nxt];
+            QT[1] = T[nxt] + half;
+            launch_e4m3_to_e2m1(M[cur], Q[0], n_pad * n_pad, s);
+            launch_e4m3_to_e2m1(T[cur], QT[0], n_pad * n_pad, s);
+            CK(cudaGetLastError(), "E2M1 encode");
+            ctx->stats.launches += 2;
+            for (int b = 0; b < 2; ++b) {
+                ST(make_tmap(ctx, &mapA4[b], Q[b], n_pad, ld4, ld4, TC_BM));
+                ST(make_tmap(ctx, &mapB4[b], QT[b], n_pad, ld4, ld4, TC_BN / 2));
+            }
+            on_f4 = true;
+            qcur = 0;
+        }
+        if (on_f4) {
+            TcParams p4 = p;
+            p4.ld = ld4;
+            p4.k_blocks = static_cast<int32_t>(n_pad / 256);
+            p4.fmap = p4.fmapT = p4.fmap_next = p4.fmapT_next = nullptr;
+            p4.old_r = Q[qcur];
+            p4.out_r = Q[qcur ^ 1];
+            p4.out_rt = QT[qcur ^ 1];
+            ST(tm.begin());
+            CK(launch_tc4_product_pair(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
+            ST(tm.end());
+            ctx->stats.product_launches++;
+            ctx->stats.e2m1_products++;
+            ctx->stats.launches += 2;
+            int changed = 0;
+            ST(read_ctl(ctx, s, &changed));
+            ST(tm.collect());
+            unsigned long long kbs = 0;
+            memcpy(&kbs, ctx->h_ctl + CTL_ISSUED, sizeof(kbs));
+            ctx->stats.issued_ops = 2.0 * TC_BM * TC_BN * TC_BK * static_cast<double>(kbs);
+            *iters = it + 1;
+            qcur ^= 1;
+            if (!changed) return finish_f4(res, res_t);
+            continue;
+        }
         if (use_maps) {
             CK(cudaMemsetAsync(F[nxt], 0, 2 * fbytes, s), "clear block map");
             p.fmap = F[cur];
@@ -352,8 +423,12 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         }
         if (use_maps) ST(sparse_map(F[cur], &use_maps));
     }
-    *res = M[cur];
-    *res_t = T[cur];
+    if (on_f4)
+        ST(finish_f4(res, res_t));
+    else {
+        *res = M[cur];
+        *res_t = T[cur];
+    }
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
 }
 

@@ -222,6 +222,14 @@ cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const 
 // a box of TC_BN / 2 rows; m_tiles must be even
 cudaError_t launch_tc_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
                                    cudaStream_t s);
+// squaring step (RMS mode only) on packed E2M1 operands (n_pad x n_pad / 2 bytes, p.ld = n_pad / 2,
+// p.k_blocks = n_pad / 256), 2-CTA clusters; maps: A box 128 rows, B box 128 rows (half a tile), 128 bytes wide
+cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                    cudaStream_t s);
+int tc4_smem_bytes();
+// E4M3 bytes <-> packed E2M1 nibbles (sizes multiples of 16 bytes)
+void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s);
+void launch_e2m1_to_e4m3(const uint8_t* in, uint8_t* out, int64_t bytes_out, cudaStream_t s);
 // grouped form: tc_group_kernel(const GroupProblem*, const GroupState*, int nprob, int phase, int* error,
 // long long wait_cycles); phase 0 = squaring step of every active problem, 1 = final products of compositions
 void* tc_group_kernel_ptr();

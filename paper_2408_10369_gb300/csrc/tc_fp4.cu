@@ -1,0 +1,395 @@
+// Squaring step of BMLP-RMS (Algorithm 1 / Eq. 4, form R <- R + R R) on
+// 4-bit tensor-core operands.
+//
+// The Boolean product is the integer count C_ij = sum_k R_ik R_kj
+// thresholded at zero (Sec. 2). Here the 0/1 operands are E2M1 values
+// (0 = 0b0000, 1.0 = 0b0010) packed two per byte, element k of a row in byte
+// k / 2 (low nibble for even k), and the MMA is tcgen05 kind::mxf4 with every
+// UE8M0 block scale equal to 2^0, so each product term is exactly 1.0 x 1.0
+// and the FP32 accumulator holds the exact count (<= n < 2^24). Compared with
+// the E4M3 kernel, a 128-byte K block carries 256 elements instead of 128:
+// half the operand bytes per Boolean operation.
+//
+// Structure (2-CTA clusters, one CTA per SM, persistent over tile pairs):
+//   warp 0      TMA producer: the CTA's 128 x 256 A tile (128 bytes) and one
+//               128-row half of the pair's shared 256 x 256 B^T tile,
+//               multicast to both CTAs; 4-stage ring, 128-byte swizzle;
+//   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=256, K=64) per stage
+//               into one TMEM accumulator (256 FP32 columns); the scale
+//               factors occupy further TMEM columns;
+//   warps 2..5  epilogue: drains the accumulator into registers as bits and
+//               frees it at once, then computes R' = R | [C > 0], writes R'
+//               and R'^T (transposed through warp ballots) and raises
+//               `changed` if R' != R.
+// Every mbarrier wait is bounded; on expiry the CTA records an error code,
+// waits (bounded) for its own copies and MMAs in flight, frees TMEM and exits.
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace bmlp {
+namespace {
+
+constexpr int F4_BK = 128;                     // bytes of K per stage (256 elements)
+constexpr int F4_A_BYTES = TC_BM * F4_BK;      // 16 KiB
+constexpr int F4_B_BYTES = TC_BN * F4_BK;      // 32 KiB
+constexpr int F4_STAGE_BYTES = F4_A_BYTES + F4_B_BYTES;
+constexpr int F4_STAGES = 4;
+constexpr int F4_UMMA_K_BYTES = 32;            // 64 E2M1 elements per MMA
+constexpr int F4_TMEM_COLS = 512;
+constexpr int F4_SFA_COL = 256;                // scale factors of A (all 2^0)
+constexpr int F4_SFB_COL = 384;                // scale factors of B (all 2^0)
+constexpr uint32_t F4_UE8M0_ONE4 = 0x7F7F7F7Fu;  // four UE8M0 scales of 2^0
+
+constexpr int F4_OFF_A = 0;
+constexpr int F4_OFF_B = F4_OFF_A + F4_STAGES * F4_A_BYTES;
+constexpr int F4_OFF_BAR = F4_OFF_B + F4_STAGES * F4_B_BYTES;
+constexpr int F4_NUM_BARS = 2 * F4_STAGES + 3;  // full[], empty[], tfull, tempty, done
+constexpr int F4_OFF_MISC = F4_OFF_BAR + F4_NUM_BARS * 8;
+constexpr int F4_SMEM_END = F4_OFF_MISC + 16;
+constexpr int F4_SMEM_BYTES = F4_SMEM_END + 1024;
+
+constexpr int ERR_F4_PRODUCER = 0x201;
+constexpr int ERR_F4_MMA = 0x202;
+constexpr int ERR_F4_EPILOGUE = 0x203;
+constexpr int F4_GROUP_M = 8;  // raster: 8 row-block pairs share B tiles in L2
+
+__device__ __forceinline__ long long f4_drain_cycles(long long limit) {
+    return limit > 2000000000LL ? limit : 2000000000LL;
+}
+
+__device__ __forceinline__ bool f4_wait_lane0(uint64_t* bar, uint32_t parity, volatile int* abort, long long limit,
+                                              int lane) {
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait_bounded(bar, parity, abort, limit) ? 1 : 0;
+    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+}
+
+// Pair t -> (row-block pair mp, column block nb), grouped so that F4_GROUP_M
+// pairs in a row share each B tile while it is in L2.
+__device__ __forceinline__ void f4_pair_coords(int t, int m_pairs, int n_tiles, int& mp, int& nb) {
+    const int per_group = F4_GROUP_M * n_tiles;
+    const int g = t / per_group;
+    const int first = g * F4_GROUP_M;
+    const int gsz = min(m_pairs - first, F4_GROUP_M);
+    const int r = t % per_group;
+    mp = first + r % gsz;
+    nb = r / gsz;
+}
+
+// 8 bits -> 8 nibbles of {0, E2M1 one}: bit k becomes nibble k.
+__device__ __forceinline__ uint32_t f4_spread8(uint32_t b) {
+    uint32_t t = b & 0xFFu;
+    t = (t | (t << 12)) & 0x000F000Fu;
+    t = (t | (t << 6)) & 0x03030303u;
+    t = (t | (t << 3)) & 0x11111111u;
+    return t << 1;
+}
+
+// 8 nibbles -> 8 bits: bit k = (nibble k != 0).
+__device__ __forceinline__ uint32_t f4_gather8(uint32_t w) {
+    uint32_t x = w | (w >> 1);
+    x |= x >> 2;
+    x &= 0x11111111u;
+    x = (x | (x >> 3)) & 0x03030303u;
+    x = (x | (x >> 6)) & 0x000F000Fu;
+    x = (x | (x >> 12)) & 0xFFu;
+    return x;
+}
+
+__device__ __forceinline__ uint4 f4_nibbles32(uint32_t bits) {
+    return make_uint4(f4_spread8(bits), f4_spread8(bits >> 8), f4_spread8(bits >> 16), f4_spread8(bits >> 24));
+}
+
+__device__ __forceinline__ uint32_t f4_bits32(const uint4& v) {
+    return f4_gather8(v.x) | (f4_gather8(v.y) << 8) | (f4_gather8(v.z) << 16) | (f4_gather8(v.w) << 24);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
+tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem + F4_OFF_A;
+    uint8_t* sB = smem + F4_OFF_B;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + F4_OFF_BAR);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + F4_STAGES;
+    uint64_t* tfull = bars + 2 * F4_STAGES;
+    uint64_t* tempty = tfull + 1;
+    uint64_t* done = tempty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + F4_OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + F4_OFF_MISC + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int m_pairs = p.m_tiles / 2;
+    const int num_pairs = m_pairs * p.n_tiles;
+    const int first = static_cast<int>(blockIdx.x >> 1);
+    const int step = static_cast<int>(gridDim.x >> 1);
+    const long long limit = p.wait_cycles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F4_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 2);  // both CTAs' MMAs must release a stage
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 128);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, F4_TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (warp >= 2) {
+        // every scale factor of A and B is 2^0: 8 columns each, all 128 lanes
+        const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        const uint32_t ones[8] = {F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4,
+                                  F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4};
+        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFA_COL, ones);
+        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFB_COL, ones);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // the peer's barriers exist before any multicast reaches them
+    tc_fence_after();
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_par[F4_STAGES];
+#pragma unroll
+            for (int s = 0; s < F4_STAGES; ++s) last_par[s] = -1;
+            bool ok = true;
+            for (int t = first; t < num_pairs && ok; t += step) {
+                int mp, nb;
+                f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
+                const int mb = 2 * mp + static_cast<int>(rank);
+                for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], F4_STAGE_BYTES);
+                    tma_load_2d(sA + stage * F4_A_BYTES, &tmA, kb * F4_BK, mb * TC_BM, &full[stage]);
+                    tma_load_2d_mcast(sB + stage * F4_B_BYTES + rank * (F4_B_BYTES / 2), &tmB, kb * F4_BK,
+                                      nb * TC_BN + static_cast<int>(rank) * (TC_BN / 2), &full[stage], 0x3);
+                    last_par[stage] = static_cast<int>(phase);
+                    if (++stage == F4_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicCAS(p.error, 0, ERR_F4_PRODUCER);
+                volatile int never = 0;
+                for (int s = 0; s < F4_STAGES; ++s)
+                    if (last_par[s] >= 0)
+                        mbar_wait_bounded(&full[s], static_cast<uint32_t>(last_par[s]), &never,
+                                          f4_drain_cycles(limit));
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_mxf4_ue8m0(TC_BM, TC_BN);
+        const uint32_t sfa = tmem_base + F4_SFA_COL, sfb = tmem_base + F4_SFB_COL;
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int t = first; t < num_pairs && ok; t += step) {
+            if (!f4_wait_lane0(tempty, acc_phase ^ 1u, abort_flag, limit, lane)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            uint32_t accumulate = 0;
+            for (int kb = 0; kb < p.k_blocks; ++kb) {
+                if (!f4_wait_lane0(&full[stage], phase, abort_flag, limit, lane)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t a0 = smem_u32(sA + stage * F4_A_BYTES);
+                    const uint32_t b0 = smem_u32(sB + stage * F4_B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < F4_BK / F4_UMMA_K_BYTES; ++k) {
+                        tc_mma_mxf4(tmem_base, smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES),
+                                    smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc, sfa, sfb, accumulate);
+                        accumulate = 1;
+                    }
+                    tc_commit_mcast(&empty[stage], 0x3);
+                }
+                __syncwarp();
+                accumulate = 1;
+                if (++stage == F4_STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (!ok) break;
+            // one 256-deep K block counts as two 128-deep ones in the issued-work counter
+            if (lane == 0 && p.issued != nullptr) atomicAdd(p.issued, 2ull * static_cast<unsigned long long>(p.k_blocks));
+            if (lane == 0) tc_commit(tfull);
+            __syncwarp();
+            acc_phase ^= 1u;
+        }
+        if (!ok && lane == 0) atomicCAS(p.error, 0, ERR_F4_MMA);
+        if (lane == 0) {
+            tc_commit(done);
+            volatile int never = 0;
+            mbar_wait_bounded(done, 0, &never, f4_drain_cycles(limit));
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+        uint32_t acc_phase = 0;
+        for (int t = first; t < num_pairs; t += step) {
+            int mp, nb;
+            f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
+            const int mb = 2 * mp + static_cast<int>(rank);
+            if (!f4_wait_lane0(tfull, acc_phase, abort_flag, limit, lane)) {
+                if (lane == 0) atomicCAS(p.error, 0, ERR_F4_EPILOGUE);
+                break;
+            }
+            tc_fence_after();
+            // drain: C > 0 as 8 x 32 bits of this thread's row, then free the accumulator
+            uint32_t cb[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + lanes + static_cast<uint32_t>(c * 32), v);
+                tmem_ld_wait();
+                uint32_t bits = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) bits |= (v[j] != 0u ? 1u : 0u) << j;
+                cb[c] = bits;
+            }
+            tc_fence_before();
+            mbar_arrive(tempty);
+            acc_phase ^= 1u;
+
+            const int64_t row = static_cast<int64_t>(mb) * TC_BM + row_in_tile;
+            const int64_t rt_col = static_cast<int64_t>(mb) * (TC_BM / 2) + quarter * 16;  // byte of row in R'^T
+            uint32_t any = 0;
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                const int64_t col0 = static_cast<int64_t>(nb) * TC_BN + c * 32;
+                const int64_t off = row * p.ld + col0 / 2;
+                const uint32_t obits = f4_bits32(*reinterpret_cast<const uint4*>(p.old_r + off));
+                // cb[c] by selects, so that cb stays in registers
+                const uint32_t cbits = c < 4 ? (c < 2 ? (c == 0 ? cb[0] : cb[1]) : (c == 2 ? cb[2] : cb[3]))
+                                             : (c < 6 ? (c == 4 ? cb[4] : cb[5]) : (c == 6 ? cb[6] : cb[7]));
+                const uint32_t nbits = obits | cbits;
+                any |= nbits ^ obits;
+                *reinterpret_cast<uint4*>(p.out_r + off) = f4_nibbles32(nbits);
+                // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
+                uint32_t mine = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (nbits >> j) & 1u);
+                    mine = (lane == j) ? b : mine;
+                }
+                *reinterpret_cast<uint4*>(p.out_rt + (col0 + lane) * p.ld + rt_col) = f4_nibbles32(mine);
+            }
+            if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // no multicast data or arrival is still headed for this CTA
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, F4_TMEM_COLS);
+    }
+}
+
+// E4M3 bytes (0 / nonzero) -> packed E2M1 nibbles, 16 bytes -> 8 bytes per thread.
+__global__ void e4m3_to_e2m1_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int64_t bytes_in) {
+    const int64_t chunks = bytes_in / 16;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < chunks;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4*>(in)[i];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        uint32_t bits = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bits |= (((w[q] >> (8 * b)) & 0xFFu) != 0 ? 1u : 0u) << (4 * q + b);
+        reinterpret_cast<uint2*>(out)[i] = make_uint2(f4_spread8(bits), f4_spread8(bits >> 8));
+    }
+}
+
+// Packed E2M1 nibbles -> E4M3 bytes (0 / one), 8 bytes -> 16 bytes per thread.
+__global__ void e2m1_to_e4m3_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int64_t bytes_out) {
+    const int64_t chunks = bytes_out / 16;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < chunks;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint2 v = reinterpret_cast<const uint2*>(in)[i];
+        const uint32_t bits = f4_gather8(v.x) | (f4_gather8(v.y) << 8);
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                x |= (((bits >> (4 * q + b)) & 1u) ? static_cast<uint32_t>(BMLP_E4M3_ONE) : 0u) << (8 * b);
+            w[q] = x;
+        }
+        reinterpret_cast<uint4*>(out)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+int f4_grid(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return static_cast<int>(g);
+}
+
+}  // namespace
+
+int tc4_smem_bytes() { return F4_SMEM_BYTES; }
+
+cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                    cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc4_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             F4_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int pairs = (p.m_tiles / 2) * p.n_tiles;
+    int clusters = sms / 2;
+    if (clusters > pairs) clusters = pairs;
+    if (clusters < 1) clusters = 1;
+    tc4_pair_kernel<<<2 * clusters, TC_THREADS, F4_SMEM_BYTES, s>>>(a, b_half, p);
+    return cudaGetLastError();
+}
+
+void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s) {
+    e4m3_to_e2m1_kernel<<<f4_grid(bytes_in / 16, 256), 256, 0, s>>>(in, out, bytes_in);
+}
+
+void launch_e2m1_to_e4m3(const uint8_t* in, uint8_t* out, int64_t bytes_out, cudaStream_t s) {
+    e2m1_to_e4m3_kernel<<<f4_grid(bytes_out / 16, 256), 256, 0, s>>>(in, out, bytes_out);
+}
+
+}  // namespace bmlp

@@ -191,6 +191,23 @@ def test_closure_long_paths(ctx, variant, n, shape, seed):
     np.testing.assert_array_equal(got, want)
 
 
+def test_squaring_operand_forms(ctx):
+    """Dense R: every squaring on packed E2M1 operands. Block-sparse R (a
+    chain with shortcuts): E4M3 squarings with skipped K blocks first, E2M1
+    once R is dense; the switch keeps the bits."""
+    ip, ix, m = er_case(1500, 3.0, 21)
+    got, it = run_rms(ctx, m, "rms_tc")
+    np.testing.assert_array_equal(got, oracle.closure(1500, ip, ix))
+    st = ctx.stats()
+    assert st["e2m1_products"] == st["product_launches"] == it
+    n = 4500
+    ip, ix = shortcut_case(n, "chain", 3)
+    got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), "rms_tc")
+    np.testing.assert_array_equal(got, oracle.closure(n, ip, ix))
+    st = ctx.stats()
+    assert 0 < st["e2m1_products"] < st["product_launches"] == it
+
+
 def test_smp_wide_rows_long_paths(ctx):
     """n = 135,000 (2,110 words per row, so more than 32 words of the
     touched-word bitmap per warp) on a chain with shortcuts."""
