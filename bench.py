@@ -151,7 +151,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"tc_pair_kernel": "tc_product.cu", "tc_product_kernel": "tc_product.cu",
-                  "tc4_pair_kernel": "tc_fp4.cu"}
+                  "tc4_pair_kernel": "tc_fp4.cu", "tc4_duo_kernel": "tc_fp4.cu"}
 
 
 def kernel_hash(kernel="tc_pair_kernel"):
@@ -412,7 +412,7 @@ def main():
     ratio, rname = (FP4_PER_BF16, "fp4/bf16") if fp4 else (FP8_PER_BF16, "fp8/bf16")
     peak = bf16 * ratio
     if fp4:
-        kname = "tc4_pair_kernel"
+        kname = "tc4_pair_kernel" if os.environ.get("BMLP_TC_DUO", "1") == "0" else "tc4_duo_kernel"
     else:
         kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
@@ -439,7 +439,9 @@ def main():
                                            else "e4m3 0/1 operands, fp32 accumulate"), "data": "synthetic",
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
                        "seed": "rank", "variant": args.variant, "iterations": iters, "nnz": int(len(ix)),
-                       "graphs_per_s": args.steps * world / t, "l2": "inputs larger than L2 (1 GiB per matrix)",
+                       "graphs_per_s": args.steps * world / t,
+                       "l2": ("inputs larger than L2 (%.2f GiB per matrix)" % (n * n / 2 ** 30)) if n * n > 129e6
+                       else "inputs fit in L2 (%.1f MB per matrix; not flushed)" % (n * n / 1e6),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "variants": variants}

@@ -248,6 +248,15 @@ bool tc_fp4_enabled() {
     return on;
 }
 
+// Dense squarings as one M = 256 MMA per CTA pair (2-SM form) unless BMLP_TC_DUO=0.
+bool tc_duo_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_TC_DUO");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // K-block skipping by the block-occupancy map of R, unless BMLP_TC_SKIP=0.
 bool tc_skip_enabled() {
     static const bool on = [] {
@@ -370,7 +379,11 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             p4.out_r = Q[qcur ^ 1];
             p4.out_rt = QT[qcur ^ 1];
             ST(tm.begin());
-            CK(launch_tc4_product_pair(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
+            if (tc_duo_enabled())
+                CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
+            else
+                CK(launch_tc4_product_pair(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s),
+                   "tensor-core product launch");
             ST(tm.end());
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;

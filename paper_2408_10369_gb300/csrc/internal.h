@@ -227,6 +227,9 @@ cudaError_t launch_tc_product_pair(const CUtensorMap& a, const CUtensorMap& b_ha
 cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
                                     cudaStream_t s);
 int tc4_smem_bytes();
+// the same step as one M = 256 MMA per CTA pair (tcgen05 .cta_group::2), 6 stages of 32 KB per CTA
+cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                   cudaStream_t s);
 // E4M3 bytes <-> packed E2M1 nibbles (sizes multiples of 16 bytes)
 void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s);
 void launch_e2m1_to_e4m3(const uint8_t* in, uint8_t* out, int64_t bytes_out, cudaStream_t s);

@@ -106,6 +106,52 @@ __device__ __forceinline__ uint32_t f4_bits32(const uint4& v) {
     return f4_gather8(v.x) | (f4_gather8(v.y) << 8) | (f4_gather8(v.z) << 16) | (f4_gather8(v.w) << 24);
 }
 
+// Epilogue, part 1: C > 0 for the 256 accumulator columns of this thread's
+// TMEM lane, as 8 x 32 bits.
+__device__ __forceinline__ void f4_drain(uint32_t taddr, uint32_t (&cb)[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c * 32), v);
+        tmem_ld_wait();
+        uint32_t bits = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bits |= (v[j] != 0u ? 1u : 0u) << j;
+        cb[c] = bits;
+    }
+}
+
+// Epilogue, part 2: R' = R | C for row (mb, quarter, lane) of output tile
+// (mb, nb): writes R' and, through warp ballots, R'^T; returns the bits that
+// changed (nonzero in some lane iff R' != R in this warp's 32 x 256 block).
+__device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int nb, int quarter, int lane,
+                                              const uint32_t (&cb)[8]) {
+    const int64_t row = static_cast<int64_t>(mb) * TC_BM + quarter * 32 + lane;
+    const int64_t rt_col = static_cast<int64_t>(mb) * (TC_BM / 2) + quarter * 16;  // byte of row in R'^T
+    uint32_t any = 0;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        const int64_t col0 = static_cast<int64_t>(nb) * TC_BN + c * 32;
+        const int64_t off = row * p.ld + col0 / 2;
+        const uint32_t obits = f4_bits32(*reinterpret_cast<const uint4*>(p.old_r + off));
+        // cb[c] by selects, so that cb stays in registers
+        const uint32_t cbits = c < 4 ? (c < 2 ? (c == 0 ? cb[0] : cb[1]) : (c == 2 ? cb[2] : cb[3]))
+                                     : (c < 6 ? (c == 4 ? cb[4] : cb[5]) : (c == 6 ? cb[6] : cb[7]));
+        const uint32_t nbits = obits | cbits;
+        any |= nbits ^ obits;
+        *reinterpret_cast<uint4*>(p.out_r + off) = f4_nibbles32(nbits);
+        // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
+        uint32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, (nbits >> j) & 1u);
+            mine = (lane == j) ? b : mine;
+        }
+        *reinterpret_cast<uint4*>(p.out_rt + (col0 + lane) * p.ld + rt_col) = f4_nibbles32(mine);
+    }
+    return any;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
 tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -256,7 +302,6 @@ tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     } else {
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;
-        const int row_in_tile = quarter * 32 + lane;
         const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
         uint32_t acc_phase = 0;
         for (int t = first; t < num_pairs; t += step) {
@@ -268,45 +313,13 @@ tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 break;
             }
             tc_fence_after();
-            // drain: C > 0 as 8 x 32 bits of this thread's row, then free the accumulator
+            // drain C > 0 into registers, then free the accumulator for the next tile's MMAs
             uint32_t cb[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                uint32_t v[32];
-                tmem_ld_32x32b_x32(tmem_base + lanes + static_cast<uint32_t>(c * 32), v);
-                tmem_ld_wait();
-                uint32_t bits = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) bits |= (v[j] != 0u ? 1u : 0u) << j;
-                cb[c] = bits;
-            }
+            f4_drain(tmem_base + lanes, cb);
             tc_fence_before();
             mbar_arrive(tempty);
             acc_phase ^= 1u;
-
-            const int64_t row = static_cast<int64_t>(mb) * TC_BM + row_in_tile;
-            const int64_t rt_col = static_cast<int64_t>(mb) * (TC_BM / 2) + quarter * 16;  // byte of row in R'^T
-            uint32_t any = 0;
-#pragma unroll 1
-            for (int c = 0; c < 8; ++c) {
-                const int64_t col0 = static_cast<int64_t>(nb) * TC_BN + c * 32;
-                const int64_t off = row * p.ld + col0 / 2;
-                const uint32_t obits = f4_bits32(*reinterpret_cast<const uint4*>(p.old_r + off));
-                // cb[c] by selects, so that cb stays in registers
-                const uint32_t cbits = c < 4 ? (c < 2 ? (c == 0 ? cb[0] : cb[1]) : (c == 2 ? cb[2] : cb[3]))
-                                             : (c < 6 ? (c == 4 ? cb[4] : cb[5]) : (c == 6 ? cb[6] : cb[7]));
-                const uint32_t nbits = obits | cbits;
-                any |= nbits ^ obits;
-                *reinterpret_cast<uint4*>(p.out_r + off) = f4_nibbles32(nbits);
-                // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
-                uint32_t mine = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (nbits >> j) & 1u);
-                    mine = (lane == j) ? b : mine;
-                }
-                *reinterpret_cast<uint4*>(p.out_rt + (col0 + lane) * p.ld + rt_col) = f4_nibbles32(mine);
-            }
+            const uint32_t any = f4_update(p, mb, nb, quarter, lane, cb);
             if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
         }
     }
@@ -317,6 +330,212 @@ tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, F4_TMEM_COLS);
+    }
+}
+
+// ---- 2-SM form: one MMA of M = 256 over a CTA pair (tcgen05 .cta_group::2).
+// Each CTA keeps only its own 128 rows of A and its half of the 256-row B
+// tile, so a stage is 32 KB instead of 48 KB and 6 stages fit: more operand
+// bytes in flight per unit of tensor work. The even CTA issues every MMA; the
+// accumulator rows land in each CTA's own TMEM (CTA r holds output rows
+// 128 r .. 128 r + 127 of the pair's 256 x 256 tile).
+constexpr int D_A_BYTES = TC_BM * F4_BK;           // 16 KiB
+constexpr int D_B_BYTES = (TC_BN / 2) * F4_BK;     // 16 KiB
+constexpr int D_STAGE_BYTES = D_A_BYTES + D_B_BYTES;
+constexpr int D_STAGES = 6;
+constexpr int D_OFF_A = 0;
+constexpr int D_OFF_B = D_OFF_A + D_STAGES * D_A_BYTES;
+constexpr int D_OFF_BAR = D_OFF_B + D_STAGES * D_B_BYTES;
+constexpr int D_NUM_BARS = 2 * D_STAGES + 3;       // full[], empty[], tfull, tempty, done
+constexpr int D_OFF_MISC = D_OFF_BAR + D_NUM_BARS * 8;
+constexpr int D_SMEM_END = D_OFF_MISC + 16;
+constexpr int D_SMEM_BYTES = D_SMEM_END + 1024;
+constexpr int ERR_D_PRODUCER = 0x211;
+constexpr int ERR_D_MMA = 0x212;
+constexpr int ERR_D_EPILOGUE = 0x213;
+
+__global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
+tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem + D_OFF_A;
+    uint8_t* sB = smem + D_OFF_B;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D_OFF_BAR);
+    uint64_t* full = bars;                 // even CTA: both CTAs' copies of a stage complete here
+    uint64_t* empty = bars + D_STAGES;     // each CTA: the even CTA's MMAs released the stage
+    uint64_t* tfull = bars + 2 * D_STAGES; // each CTA: the accumulator holds a finished tile
+    uint64_t* tempty = tfull + 1;          // even CTA: both CTAs' epilogues drained the accumulator
+    uint64_t* done = tempty + 1;           // even CTA: every MMA it issued has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + D_OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + D_OFF_MISC + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int m_pairs = p.m_tiles / 2;
+    const int num_pairs = m_pairs * p.n_tiles;
+    const int first = static_cast<int>(blockIdx.x >> 1);
+    const int step = static_cast<int>(gridDim.x >> 1);
+    const long long limit = p.wait_cycles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < D_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 256);
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc_2sm(tmem_slot, F4_TMEM_COLS);
+        tmem_relinquish_2sm();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (warp >= 2) {
+        // every scale factor of A and B is 2^0: 8 columns each, all 128 lanes of this CTA
+        const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        const uint32_t ones[8] = {F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4,
+                                  F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4};
+        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFA_COL, ones);
+        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFB_COL, ones);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // barriers and scale factors of both CTAs are in place
+    tc_fence_after();
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            bool issued = false;
+            for (int t = first; t < num_pairs && ok; t += step) {
+                int mp, nb;
+                f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
+                const int mb = 2 * mp + static_cast<int>(rank);
+                for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bar = mapa_shared(smem_u32(&full[stage]), 0);
+                    if (leader) mbar_arrive_expect_tx(&full[stage], 2 * D_STAGE_BYTES);
+                    tma_load_2d_2sm(sA + stage * D_A_BYTES, &tmA, kb * F4_BK, mb * TC_BM, bar);
+                    tma_load_2d_2sm(sB + stage * D_B_BYTES, &tmB, kb * F4_BK,
+                                    nb * TC_BN + static_cast<int>(rank) * (TC_BN / 2), bar);
+                    issued = true;
+                    if (++stage == D_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicCAS(p.error, 0, ERR_D_PRODUCER);
+                // copies complete on the even CTA's barriers: give the last ones time to land
+                if (issued) {
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < 2000000) __nanosleep(1000);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (even CTA)
+        if (leader) {
+            const uint32_t idesc = idesc_mxf4_ue8m0(2 * TC_BM, TC_BN);
+            const uint32_t sfa = tmem_base + F4_SFA_COL, sfb = tmem_base + F4_SFB_COL;
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int t = first; t < num_pairs && ok; t += step) {
+                if (!f4_wait_lane0(tempty, acc_phase ^ 1u, abort_flag, limit, lane)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t accumulate = 0;
+                for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    if (!f4_wait_lane0(&full[stage], phase, abort_flag, limit, lane)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (lane == 0) {
+                        const uint32_t a0 = smem_u32(sA + stage * D_A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + stage * D_B_BYTES);
+#pragma unroll
+                        for (int k = 0; k < F4_BK / F4_UMMA_K_BYTES; ++k) {
+                            tc_mma_mxf4_2sm(tmem_base, smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES),
+                                            smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc, sfa, sfb,
+                                            accumulate);
+                            accumulate = 1;
+                        }
+                        tc_commit_2sm_mcast(&empty[stage], 0x3);  // the stage is free in both CTAs
+                    }
+                    __syncwarp();
+                    accumulate = 1;
+                    if (++stage == D_STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                // two 128-row tiles of 256-deep K blocks: four 128-deep blocks per K block
+                if (lane == 0 && p.issued != nullptr)
+                    atomicAdd(p.issued, 4ull * static_cast<unsigned long long>(p.k_blocks));
+                if (lane == 0) tc_commit_2sm_mcast(tfull, 0x3);
+                __syncwarp();
+                acc_phase ^= 1u;
+            }
+            if (!ok && lane == 0) atomicCAS(p.error, 0, ERR_D_MMA);
+            if (lane == 0) {
+                tc_commit_2sm_mcast(done, 0x1);
+                volatile int never = 0;
+                mbar_wait_bounded(done, 0, &never, f4_drain_cycles(limit));
+            }
+            __syncwarp();
+        }
+    } else {
+        // ------------------------------------------------ epilogue (both CTAs)
+        const int quarter = warp & 3;
+        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
+        const uint32_t tempty_even = mapa_shared(smem_u32(tempty), 0);
+        uint32_t acc_phase = 0;
+        for (int t = first; t < num_pairs; t += step) {
+            int mp, nb;
+            f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
+            const int mb = 2 * mp + static_cast<int>(rank);
+            if (!f4_wait_lane0(tfull, acc_phase, abort_flag, limit, lane)) {
+                if (lane == 0) atomicCAS(p.error, 0, ERR_D_EPILOGUE);
+                break;
+            }
+            tc_fence_after();
+            uint32_t cb[8];
+            f4_drain(tmem_base + lanes, cb);
+            tc_fence_before();
+            mbar_arrive_cluster(tempty_even);
+            acc_phase ^= 1u;
+            const uint32_t any = f4_update(p, mb, nb, quarter, lane, cb);
+            if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // the even CTA's MMAs into this CTA's TMEM have completed
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_2sm(tmem_base, F4_TMEM_COLS);
     }
 }
 
@@ -381,6 +600,23 @@ cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_h
     if (clusters > pairs) clusters = pairs;
     if (clusters < 1) clusters = 1;
     tc4_pair_kernel<<<2 * clusters, TC_THREADS, F4_SMEM_BYTES, s>>>(a, b_half, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                   cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             D_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int pairs = (p.m_tiles / 2) * p.n_tiles;
+    int clusters = sms / 2;
+    if (clusters > pairs) clusters = pairs;
+    if (clusters < 1) clusters = 1;
+    tc4_duo_kernel<<<2 * clusters, TC_THREADS, D_SMEM_BYTES, s>>>(a, b_half, p);
     return cudaGetLastError();
 }
 
