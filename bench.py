@@ -415,11 +415,14 @@ def main():
         kname = "tc4_pair_kernel" if os.environ.get("BMLP_TC_DUO", "1") == "0" else "tc4_duo_kernel"
     else:
         kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
+    # what this GPU issues for the kernel's operand kind (back-to-back MMAs, no operand traffic)
+    issue = ctx.mma_issue_rate(1 if fp4 else 0)
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
             "peak_source": "%s bf16 burst x %g (%s nominal); the product runs unthrottled at max SM clock"
                            % (peak_src, ratio, rname),
-            "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None}
+            "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None,
+            "issue_rate_peak": issue, "issue_rate_frac": (achieved / issue) if achieved and issue else None}
     if rank != 0:
         ctx.close()
         if world > 1:

@@ -225,7 +225,20 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
                             int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
                             cudaStream_t stream);
 
-/* One problem of a grouped batch. */
+/*
+ * bmlp_mma_issue_rate - a measurement helper, not part of the paper's method:
+ * the tensor-core FLOP rate of back-to-back tcgen05.mma instructions issued
+ * by one CTA per SM from fixed shared-memory tiles (no operand traffic), so
+ * that the squaring kernels can be compared with what this GPU issues.
+ * kind 0: kind::f8f6f4, E4M3, M128 N256 K32 (the block-sparse squarings);
+ * kind 1: kind::mxf4, E2M1 with unit UE8M0 scales, M128 N256 K64 (the dense
+ * squarings). iters: MMA groups of 4 per CTA (e.g. 20000, about 5 ms).
+ * *tflops receives 2 M N K x MMAs / time. Runs on the legacy default stream
+ * and synchronises the device.
+ */
+bmlp_status bmlp_mma_issue_rate(bmlp_ctx* ctx, int32_t kind, int32_t iters, double* tflops);
+
+/* One problem of a grouped batch. *//* One problem of a grouped batch. */
 typedef enum bmlp_problem_kind {
     BMLP_PROBLEM_CLOSURE = 0,  /* out = R1+ (or I + R1+): program P2 of Sec. 3.3   */
     BMLP_PROBLEM_COMPOSE = 1   /* out = (I + R2+) R1: p <- r1 ; p <- r2, p (Thm. 1) */

@@ -122,6 +122,7 @@ def lib():
             L.bmlp_negate.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
             L.bmlp_is_foreign.argtypes = [vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
                                           ctypes.POINTER(i32), vp]
+            L.bmlp_mma_issue_rate.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_double)]
             L.bmlp_batch_run.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.POINTER(bmlp_options),
                                          ctypes.POINTER(i32), vp]
             L.bmlp_batch_autotune.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.c_char_p, vp]
@@ -138,7 +139,8 @@ def lib():
                          "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune", "bmlp_dispatch_features",
                          "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_loss_grad",
                          "bmlp_dispatch_set_params", "bmlp_dispatch_get_params", "bmlp_dispatch_save",
-                         "bmlp_dispatch_load", "bmlp_transpose", "bmlp_union", "bmlp_negate", "bmlp_is_foreign"):
+                         "bmlp_dispatch_load", "bmlp_transpose", "bmlp_union", "bmlp_negate", "bmlp_is_foreign",
+                         "bmlp_mma_issue_rate"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -371,6 +373,12 @@ class Context:
         """bmlp_negate (NEG): out = rows x cols AND NOT R (None = every constant)."""
         self._check(self._L.bmlp_negate(self.handle, _ptr(R), int(n), int(fmt), _ptr(rows), _ptr(cols), _ptr(out),
                                         _stream(stream, self.device)))
+
+    def mma_issue_rate(self, kind, iters=20000):
+        """bmlp_mma_issue_rate: TFLOP/s of back-to-back tcgen05.mma (kind 0: E4M3 K32, 1: E2M1 K64)."""
+        v = ctypes.c_double(0.0)
+        self._check(self._L.bmlp_mma_issue_rate(self.handle, int(kind), int(iters), ctypes.byref(v)))
+        return v.value
 
     def is_foreign(self, contains, adjoins, n, out, location=None, fmt=BMLP_FMT_U8, stream=None, **opt):
         """bmlp_is_foreign: the composed program P3 u P4 u P5. Returns the

@@ -252,3 +252,13 @@ def test_argument_errors(ctx):
         ctx.rms(dev(np.roll(np.eye(64, dtype=np.uint8), 1, axis=1)), 64,
                 torch.zeros((64, 64), dtype=torch.uint8, device="cuda"), variant="rms_tc", max_iters=2)
     assert e.value.status == 5                   # a 64-cycle needs 7 products
+
+
+def test_mma_issue_rate(ctx):
+    """The tensor-core issue-rate probe runs and reports a positive rate; the
+    4-bit kind carries twice the K per instruction, so it is never slower."""
+    r8 = ctx.mma_issue_rate(0, iters=2000)
+    r4 = ctx.mma_issue_rate(1, iters=2000)
+    assert r8 > 0 and r4 >= r8
+    with pytest.raises(pkg.BmlpError):
+        ctx.mma_issue_rate(2)
