@@ -54,11 +54,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
-    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch", "isforeign"],
+    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch", "isforeign", "insert"],
                     help="er: the closure benchmark (default); powerlaw_smp: 4,096 selective query rows on the "
                          "n = 65,536 power-law graph; kg_batch: every relation closure and 200 compositions of "
                          "the knowledge-graph workload in one grouped batch; isforeign: the composed program "
-                         "hasPlace / indirectlyPartOf / isForeign on a 14,541-entity, 7,991-fact place hierarchy")
+                         "hasPlace / indirectlyPartOf / isForeign on a 14,541-entity, 7,991-fact place hierarchy; insert: "
+                         "1,000 new contains facts added incrementally to hasPlace of that hierarchy")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
     args = ap.parse_args()
     if args.variant is None:
@@ -232,6 +233,7 @@ def run_aux(args):
     from paper_2408_10369_gb300 import bmlp
     ctx = pkg.Context(0)
     stream = torch.cuda.current_stream()
+    extra = {}
     if args.workload == "powerlaw_smp":
         n, q = 65536, 4096
         ip, ix = wl.powerlaw_csr(n, 2.1, 1000, 0)
@@ -242,6 +244,33 @@ def run_aux(args):
         def step():
             return ctx.smp(P, n, src, q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant, profile=True)
         unit, units_per_step, name = "queries/s", q, "powerlaw_n65536_q4096"
+    elif args.workload == "insert":
+        n, m = 14541, 1000
+        (ci, cx), _ = wl.geo_kg(n=n)
+        C = torch.from_numpy(wl.csr_to_packed(n, ci, cx).view(np.int64)).cuda()
+        H0 = torch.zeros_like(C)
+        ctx.rms(C, n, H0, fmt=bmlp.BMLP_FMT_PACKED64)
+        a, b = wl.random_pairs(n, m, 12345)
+        E = torch.from_numpy(np.stack([a, b], 1).astype(np.int32)).cuda()
+        H = torch.empty_like(H0)
+        # recomputing the closure of the grown relation instead, for comparison
+        src = np.repeat(np.arange(n), np.diff(ci))
+        gip, gix = wl.csr_from_pairs(n, np.concatenate([src, a]), np.concatenate([cx, b]))
+        G = torch.from_numpy(wl.csr_to_packed(n, gip, gix).view(np.int64)).cuda()
+        Gout = torch.zeros_like(G)
+        ctx.rms(G, n, Gout, fmt=bmlp.BMLP_FMT_PACKED64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ctx.rms(G, n, Gout, fmt=bmlp.BMLP_FMT_PACKED64)
+        torch.cuda.synchronize()
+        extra["recompute_ms"] = (time.perf_counter() - t0) / 3 * 1e3
+
+        def step():
+            H.copy_(H0)
+            ctx.insert(H, n, E, fmt=bmlp.BMLP_FMT_PACKED64)
+            return m
+        unit, units_per_step, name = "facts/s", m, "geo_kg_n14541_insert1000"
     elif args.workload == "isforeign":
         n = 14541
         (ci, cx), (ai, ax) = wl.geo_kg(n=n)
@@ -287,7 +316,7 @@ def run_aux(args):
     t = ev0.elapsed_time(ev1) / 1e3
     print(json.dumps({"workload": name, "variant": args.variant, "value": args.steps * units_per_step / t,
                       "unit": unit, "ms_per_step": t / args.steps * 1e3, "steps": args.steps,
-                      "warmup": args.warmup, "iterations": it, "gpu_launches": launches}), flush=True)
+                      "warmup": args.warmup, "iterations": it, "gpu_launches": launches, **extra}), flush=True)
     ctx.close()
 
 

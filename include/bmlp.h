@@ -166,6 +166,21 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
                      const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
 
 /*
+ * bmlp_insert - incremental closure for a growing database (the dynamic
+ * setting of paper Sec. 7): given closure = R1+ (any transitive relation,
+ * e.g. the output of bmlp_rms), add the facts r1(u_k, v_k) of `pairs` (m
+ * pairs of int32 constants, device or host memory) and update closure in
+ * place to (R1 + E)+. Each fact is one rank-1 update: every constant that
+ * reaches u_k (and u_k) gains v_k and everything v_k reaches. closure is
+ * n x n in format fmt (device or host memory). Facts already derivable cost
+ * one word read. Constants outside [0, n) give BMLP_ERR_INVALID_ARG before
+ * anything changes. Deleting facts is not incremental: recompute with
+ * bmlp_rms.
+ */
+bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
+                        cudaStream_t stream);
+
+/*
  * bmlp_compose - the general binary linear recursion of paper Sec. 3.4
  * (Thm. 1):
  *

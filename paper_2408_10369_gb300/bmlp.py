@@ -123,6 +123,7 @@ def lib():
             L.bmlp_is_foreign.argtypes = [vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
                                           ctypes.POINTER(i32), vp]
             L.bmlp_mma_issue_rate.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_double)]
+            L.bmlp_insert.argtypes = [vp, vp, i64, i32, vp, i64, vp]
             L.bmlp_batch_run.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.POINTER(bmlp_options),
                                          ctypes.POINTER(i32), vp]
             L.bmlp_batch_autotune.argtypes = [vp, ctypes.POINTER(bmlp_problem), i64, ctypes.c_char_p, vp]
@@ -140,7 +141,7 @@ def lib():
                          "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_loss_grad",
                          "bmlp_dispatch_set_params", "bmlp_dispatch_get_params", "bmlp_dispatch_save",
                          "bmlp_dispatch_load", "bmlp_transpose", "bmlp_union", "bmlp_negate", "bmlp_is_foreign",
-                         "bmlp_mma_issue_rate"):
+                         "bmlp_mma_issue_rate", "bmlp_insert"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -372,6 +373,13 @@ class Context:
     def negate(self, R, n, out, rows=None, cols=None, fmt=BMLP_FMT_U8, stream=None):
         """bmlp_negate (NEG): out = rows x cols AND NOT R (None = every constant)."""
         self._check(self._L.bmlp_negate(self.handle, _ptr(R), int(n), int(fmt), _ptr(rows), _ptr(cols), _ptr(out),
+                                        _stream(stream, self.device)))
+
+    def insert(self, closure, n, pairs, m=None, fmt=BMLP_FMT_U8, stream=None):
+        """bmlp_insert: closure := (closure + pairs)+ in place; pairs is m x 2 int32."""
+        if m is None:
+            m = len(pairs)
+        self._check(self._L.bmlp_insert(self.handle, _ptr(closure), int(n), int(fmt), _ptr(pairs), int(m),
                                         _stream(stream, self.device)))
 
     def mma_issue_rate(self, kind, iters=20000):

@@ -831,6 +831,54 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
     return finish_out(ctx, ov, s);
 }
 
+bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
+                        cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (n < 0 || m < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0 or m < 0");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n == 0 || m == 0) return BMLP_OK;
+    if (!closure || !pairs) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null pointer");
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    DeviceGuard g(ctx->device);
+    reset_stats(ctx, 0, n);
+    // the facts are read on the host (they steer one launch each) and checked there
+    std::vector<int32_t> hp(static_cast<size_t>(2 * m));
+    if (is_device_ptr(pairs)) {
+        CK(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read facts");
+        CK(cudaStreamSynchronize(s), "read facts");
+    } else {
+        memcpy(hp.data(), pairs, hp.size() * sizeof(int32_t));
+    }
+    for (int64_t k = 0; k < 2 * m; ++k)
+        if (hp[k] < 0 || hp[k] >= n) return set_err(ctx, BMLP_ERR_INVALID_ARG, "fact %lld names constant %d outside [0, n)",
+                                                    static_cast<long long>(k / 2), hp[k]);
+    const int64_t ldw = words_of(n);
+    const bool dev_packed = fmt == BMLP_FMT_PACKED64 && is_device_ptr(closure);
+    uint64_t* P = nullptr;
+    Operand in;
+    if (dev_packed) {
+        P = static_cast<uint64_t*>(closure);
+    } else {
+        ST(stage_in(ctx, closure, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
+        void* p = nullptr;
+        ST(ws_get(ctx, WS_PIPE0, static_cast<size_t>(n * ldw * 8), &p));
+        P = static_cast<uint64_t*>(p);
+        ST(to_packed(ctx, in, fmt, n, P, ldw, s));
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        CK(launch_insert_fact(P, n, ldw, hp[2 * k], hp[2 * k + 1], ctx->sm_count, s), "insert launch");
+        ctx->stats.launches++;
+    }
+    ctx->stats.iterations = static_cast<int32_t>(m);
+    if (!dev_packed) {
+        OutView ov;
+        ST(stage_out(ctx, closure, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+        ST(packed_out(ctx, P, ldw, n, fmt, ov.dev, 0, s));
+        return finish_out(ctx, ov, s);
+    }
+    return BMLP_OK;
+}
+
 bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
                      uint64_t* out_rows, const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
     if (!ctx) return BMLP_ERR_INVALID_ARG;

@@ -253,6 +253,8 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
                               int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s,
                               Deadline dl = Deadline{0, nullptr, nullptr}, const int64_t* wptrT = nullptr,
                               const int32_t* widxT = nullptr, const uint64_t* wvalT = nullptr);
+// (R+ + {(u, v)})+ in place on a transitive R+ (n packed rows of ldw words)
+cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, int64_t v, int sms, cudaStream_t s);
 // out = in^T on n x n packed rows of ldw words (out cleared first)
 cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s);
 int smp_packed_max_words();

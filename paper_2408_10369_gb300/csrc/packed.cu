@@ -365,6 +365,34 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
     }
 }
 
+// ---- incremental closure: one new fact r(u, v) on a transitive R+ (packed rows)
+// (R + E_uv)+ = R+ + X Y^T with X = {i : i = u or R+_iu} (the constants that
+// reach u) and Y = R+_v + e_v (what v reaches, and v): every row in X gains Y.
+// A warp owns each row it updates, so membership (bit u of its own row) is
+// read before that row changes; row v itself only gains bit v, which every
+// reader adds anyway. When R+_uv already holds, every member row already
+// contains Y (transitivity) and no word is written.
+__global__ void insert_fact_kernel(uint64_t* __restrict__ P, int64_t n, int64_t ldw, int64_t u, int64_t v) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wu = u >> 6, wv = v >> 6;
+    const uint64_t bu = 1ull << (u & 63), bv = 1ull << (v & 63);
+    const int64_t wpr = (n + 63) >> 6;
+    const uint64_t* Y = P + v * ldw;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        uint64_t* row = P + i * ldw;
+        const bool member = (i == u) || (row[wu] & bu) != 0ull;  // uniform across the warp
+        if (!member) continue;
+        __syncwarp();
+        for (int64_t w = lane; w < wpr; w += 32) {
+            uint64_t y = Y[w];
+            if (w == wv) y |= bv;
+            const uint64_t r = row[w];
+            if ((r | y) != r) row[w] = r | y;
+        }
+    }
+}
+
 inline int warps_grid(int64_t rows, int sms) {
     int64_t blocks = (rows + 7) / 8;  // 8 warps of 256 threads
     const int64_t cap = static_cast<int64_t>(sms) * 8;
@@ -384,6 +412,11 @@ cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t
         product_packed_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
     else
         product_packed_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, int64_t v, int sms, cudaStream_t s) {
+    insert_fact_kernel<<<warps_grid(n, sms), 256, 0, s>>>(P, n, ldw, u, v);
     return cudaGetLastError();
 }
 
