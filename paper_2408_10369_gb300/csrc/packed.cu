@@ -191,6 +191,85 @@ __host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) {
     return (18 * ldw + 64 + 16 + 15) & ~int64_t(15);
 }
 
+// One push step of a warp: each lane takes up to NQ constants of its frontier
+// word d and ORs their rows' nonzero words into N (shared-memory atomics
+// without return value). The row ranges and the first four entries of every
+// light row (<= 16 nonzero words) are loaded before the first atomic; heavy
+// rows are walked by the whole warp. tm collects the word groups written.
+template <int NQ>
+__device__ __forceinline__ void push_step(uint64_t& d, int64_t w, int lane, const int64_t* __restrict__ wptr,
+                                          const int32_t* __restrict__ widx, const uint64_t* __restrict__ wval,
+                                          uint64_t* N, int gshift, uint64_t& tm) {
+    int64_t k[NQ], e0[NQ], e1[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        k[q] = -1;
+        if (d) {
+            const int b = __ffsll(static_cast<long long>(d)) - 1;
+            d &= d - 1;
+            k[q] = w * 64 + b;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        e0[q] = k[q] >= 0 ? wptr[k[q]] : 0;
+        e1[q] = k[q] >= 0 ? wptr[k[q] + 1] : 0;
+    }
+    bool light[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) light[q] = k[q] >= 0 && (e1[q] - e0[q]) <= 16;
+    int x[NQ][4];
+    uint64_t val[NQ][4];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = light[q] && e0[q] + j < e1[q];
+            x[q][j] = in ? widx[e0[q] + j] : -1;
+            val[q][j] = in ? wval[e0[q] + j] : 0ull;
+        }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (x[q][j] >= 0) {
+                atomicOr(reinterpret_cast<unsigned long long*>(&N[x[q][j]]), static_cast<unsigned long long>(val[q][j]));
+                tm |= 1ull << (x[q][j] >> gshift);
+            }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        if (light[q])
+            for (int64_t e = e0[q] + 4; e < e1[q]; e += 4) {
+                int y[4];
+                uint64_t yv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    y[j] = e + j < e1[q] ? widx[e + j] : -1;
+                    yv[j] = e + j < e1[q] ? wval[e + j] : 0ull;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (y[j] >= 0) {
+                        atomicOr(reinterpret_cast<unsigned long long*>(&N[y[j]]), static_cast<unsigned long long>(yv[j]));
+                        tm |= 1ull << (y[j] >> gshift);
+                    }
+            }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        unsigned hm = __ballot_sync(FULL, k[q] >= 0 && !light[q]);
+        while (hm) {
+            const int sl = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int64_t h0 = __shfl_sync(FULL, e0[q], sl), h1 = __shfl_sync(FULL, e1[q], sl);
+            for (int64_t e = h0 + lane; e < h1; e += 32) {
+                const int xx = widx[e];
+                atomicOr(reinterpret_cast<unsigned long long*>(&N[xx]), static_cast<unsigned long long>(wval[e]));
+                tm |= 1ull << (xx >> gshift);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
                                                          const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
@@ -256,59 +335,60 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
                         const int64_t valid = n - w * 64;
                         if (valid < 64) u &= (1ull << valid) - 1ull;
                         while (u) {
-                            const int b = __ffsll(static_cast<long long>(u)) - 1;
-                            u &= u - 1;
-                            const int64_t j = w * 64 + b;
-                            const int64_t e1 = wptrT[j + 1];
-                            for (int64_t e = wptrT[j]; e < e1; ++e)
-                                if (wvalT[e] & D[widxT[e]]) {
-                                    nw |= 1ull << b;
-                                    break;
+                            // two unvisited constants at a time: their column ranges, then the first two
+                            // entries of each, all loads in flight before the first test
+                            int bs[2];
+                            int64_t s0[2], s1[2];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                bs[q] = -1;
+                                if (u) {
+                                    bs[q] = __ffsll(static_cast<long long>(u)) - 1;
+                                    u &= u - 1;
                                 }
+                            }
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int64_t j = w * 64 + (bs[q] < 0 ? 0 : bs[q]);
+                                s0[q] = bs[q] < 0 ? 0 : wptrT[j];
+                                s1[q] = bs[q] < 0 ? 0 : wptrT[j + 1];
+                            }
+                            int xi[2][2];
+                            uint64_t xv[2][2];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                                for (int r = 0; r < 2; ++r) {
+                                    const bool in = s0[q] + r < s1[q];
+                                    xi[q][r] = in ? widxT[s0[q] + r] : 0;
+                                    xv[q][r] = in ? wvalT[s0[q] + r] : 0ull;
+                                }
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                if (bs[q] < 0) continue;
+                                bool hit = (xv[q][0] & D[xi[q][0]]) != 0ull || (xv[q][1] & D[xi[q][1]]) != 0ull;
+                                for (int64_t e = s0[q] + 2; !hit && e < s1[q]; ++e) hit = (wvalT[e] & D[widxT[e]]) != 0ull;
+                                if (hit) nw |= 1ull << bs[q];
+                            }
                         }
                         N[w] = nw;
                     }
                 }
             } else {
                 // push: OR the nonzero words of every frontier row into N (no return values, so the
-                // atomics are reductions); track the range of words written
+                // atomics are reductions); each lane records the word groups it wrote
                 uint64_t tm = 0;
                 for (int i0 = 0; i0 < fcount; i0 += 32) {
                     const int i = i0 + lane;
                     const int64_t w = i < fcount ? FL[i] : 0;
                     uint64_t d = i < fcount ? D[w] : 0ull;
                     while (__any_sync(FULL, d != 0ull)) {
-                        int64_t k = -1;
-                        if (d) {
-                            const int b = __ffsll(static_cast<long long>(d)) - 1;
-                            d &= d - 1;
-                            k = w * 64 + b;
-                        }
-                        int64_t e0 = 0, e1 = 0;
-                        if (k >= 0) {
-                            e0 = wptr[k];
-                            e1 = wptr[k + 1];
-                        }
-                        const bool heavy = (e1 - e0) > 16;
-                        if (k >= 0 && !heavy)
-                            for (int64_t e = e0; e < e1; ++e) {
-                                const int x = widx[e];
-                                atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
-                                         static_cast<unsigned long long>(wval[e]));
-                                tm |= 1ull << (x >> gshift);
-                            }
-                        unsigned hm = __ballot_sync(FULL, k >= 0 && heavy);
-                        while (hm) {
-                            const int sl = __ffs(hm) - 1;
-                            hm &= hm - 1;
-                            const int64_t h0 = __shfl_sync(FULL, e0, sl), h1 = __shfl_sync(FULL, e1, sl);
-                            for (int64_t e = h0 + lane; e < h1; e += 32) {
-                                const int x = widx[e];
-                                atomicOr(reinterpret_cast<unsigned long long*>(&N[x]),
-                                         static_cast<unsigned long long>(wval[e]));
-                                tm |= 1ull << (x >> gshift);
-                            }
-                        }
+                        // two frontier constants per lane when some lane has two left (dense frontiers),
+                        // else one (long sparse paths): every load of a step is in flight before its atomics
+                        if (__any_sync(FULL, __popcll(d) >= 2))
+                            push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
+                        else
+                            push_step<1>(d, w, lane, wptr, widx, wval, N, gshift, tm);
                     }
                 }
                 gm = static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm))) |
