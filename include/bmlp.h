@@ -285,6 +285,11 @@ typedef struct bmlp_problem {
  * the tensor cores or on packed rows, chosen per size bucket by the autotuner
  * (bmlp_batch_autotune) or forced by opts->variant (BMLP_RMS_TC /
  * BMLP_RMS_PACKED; compositions always use the tensor cores).
+ * Problems large enough to fill the GPU alone (n >= 8192 by default, the
+ * environment variable BMLP_BATCH_SOLO_N changes it, 0 = never) that are not
+ * forced onto packed rows run one after another on the single-problem
+ * tensor-core path instead (bmlp_rms / bmlp_compose with BMLP_RMS_TC, whose
+ * squarings switch to 4-bit operands once R is dense), before the batch.
  * iters_out (count entries, may be null) receives each problem's products.
  * All matrix pointers must be device memory. The instantiated graph is cached
  * in the context and reused while the problem list is unchanged.

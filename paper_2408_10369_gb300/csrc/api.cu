@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/bmlp.h): argument checks,
 // host/device staging, the fixpoint drivers of BMLP-RMS (Algorithm 1),
 // BMLP-SMP (Algorithm 2) and composition (Thm. 1), and the workspace.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -255,6 +256,15 @@ bool tc_duo_enabled() {
         return !(v && v[0] == '0');
     }();
     return on;
+}
+
+// Smallest n that a grouped batch hands to the single-problem path (BMLP_BATCH_SOLO_N, 0 = never).
+int64_t batch_solo_n() {
+    static const int64_t v = [] {
+        const char* e = getenv("BMLP_BATCH_SOLO_N");
+        return e ? static_cast<int64_t>(atoll(e)) : int64_t(8192);
+    }();
+    return v;
 }
 
 // K-block skipping by the block-occupancy map of R, unless BMLP_TC_SKIP=0.
@@ -1166,16 +1176,83 @@ bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
     bmlp_options o = resolve(opts);
     if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC && o.variant != BMLP_RMS_PACKED)
         return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a batch variant", o.variant);
-    reset_stats(ctx, o.variant, 0);
-    ProductTimer tm{ctx, o.profile != 0, s};
-    ST(tm.begin());
-    bmlp_status st = batch_run_impl(ctx, probs, count, o.variant, wait_cycles(ctx, o), iters_out, s);
-    ST(tm.end());
-    if (o.profile) {
-        CK(cudaStreamSynchronize(s), "synchronise batch");
-        ST(tm.collect());
+    // Problems large enough to fill the GPU on their own (n >= batch_solo_n()) and not forced onto packed rows
+    // run one by one on the single-problem path, whose squarings switch to 4-bit operands once R is dense; the
+    // rest run together as one grouped batch.
+    std::vector<bmlp_problem> rest;
+    std::vector<int64_t> rest_idx, solo_idx;
+    const int64_t solo_n = batch_solo_n();
+    for (int64_t i = 0; i < count; ++i) {
+        const bmlp_problem& p = probs[i];
+        const int v = p.variant ? p.variant : o.variant;
+        const bool valid = (p.kind == BMLP_PROBLEM_CLOSURE || p.kind == BMLP_PROBLEM_COMPOSE) &&
+                           (p.fmt == BMLP_FMT_U8 || p.fmt == BMLP_FMT_PACKED64) && p.R1 && p.out &&
+                           (p.kind == BMLP_PROBLEM_CLOSURE || p.R2);
+        if (valid && solo_n > 0 && p.n >= solo_n && p.n <= (int64_t(1) << 17) && v != BMLP_RMS_PACKED) {
+            solo_idx.push_back(i);
+        } else {
+            rest.push_back(p);
+            rest_idx.push_back(i);
+        }
     }
-    return st;
+    reset_stats(ctx, o.variant, 0);
+    bmlp_stats acc = ctx->stats;
+    double solo_ms = 0.0;
+    bmlp_status first_err = BMLP_OK;
+    for (int64_t i : solo_idx) {
+        const bmlp_problem& p = probs[i];
+        if (!is_device_ptr(p.R1) || !is_device_ptr(p.out) || (p.kind == BMLP_PROBLEM_COMPOSE && !is_device_ptr(p.R2)))
+            return set_err(ctx, BMLP_ERR_INVALID_ARG, "problem %lld: matrices must be device memory",
+                           static_cast<long long>(i));
+    }
+    for (int64_t i : solo_idx) {
+        const bmlp_problem& p = probs[i];
+        bmlp_options po = o;
+        po.variant = BMLP_RMS_TC;
+        po.reflexive = p.kind == BMLP_PROBLEM_CLOSURE ? p.reflexive : 0;
+        int32_t it = 0;
+        const auto t0 = std::chrono::steady_clock::now();
+        bmlp_status st = p.kind == BMLP_PROBLEM_CLOSURE
+                             ? bmlp_rms(ctx, p.R1, p.n, p.fmt, p.out, &po, &it, s)
+                             : bmlp_compose(ctx, p.R1, p.R2, p.n, p.fmt, p.out, &po, &it, s);
+        if (o.profile) {
+            CK(cudaStreamSynchronize(s), "synchronise problem");
+            solo_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        if (iters_out) iters_out[i] = it;
+        acc.iterations = std::max(acc.iterations, it);
+        acc.launches += ctx->stats.launches;
+        acc.product_launches += ctx->stats.product_launches;
+        acc.e2m1_products += ctx->stats.e2m1_products;
+        if (st == BMLP_ERR_NOT_CONVERGED) {
+            if (first_err == BMLP_OK) first_err = st;
+        } else if (st != BMLP_OK) {
+            return st;
+        }
+    }
+    bmlp_status st = BMLP_OK;
+    if (!rest.empty()) {
+        std::vector<int32_t> rit(rest.size(), 0);
+        ctx->stats = acc;
+        ProductTimer tm{ctx, o.profile != 0, s};
+        ST(tm.begin());
+        st = batch_run_impl(ctx, rest.data(), static_cast<int64_t>(rest.size()), o.variant, wait_cycles(ctx, o),
+                            rit.data(), s);
+        ST(tm.end());
+        if (o.profile) {
+            CK(cudaStreamSynchronize(s), "synchronise batch");
+            ST(tm.collect());
+        }
+        if (iters_out)
+            for (size_t k = 0; k < rest.size(); ++k) iters_out[rest_idx[k]] = rit[k];
+        ctx->stats.iterations = std::max(ctx->stats.iterations, acc.iterations);
+    } else {
+        ctx->stats = acc;
+    }
+    ctx->stats.product_ms += solo_ms;
+    if (st != BMLP_OK) return st;
+    if (first_err != BMLP_OK) return set_err(ctx, first_err, "a problem did not converge within its cap");
+    return BMLP_OK;
 }
 
 bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const char* cache_path,

@@ -122,3 +122,35 @@ def test_single_problem_device_loop(ctx, variant, n, d, seed):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), oracle.closure(n, ip, ix))
     assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+
+
+@pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
+def test_batch_mixes_solo_and_grouped_problems(ctx, fmt):
+    """Problems with n >= 8192 run on the single-problem path (4-bit operands
+    once dense), the others in the grouped batch; every output and every
+    iteration count as for the problem alone."""
+    items, expect, keep = [], [], []
+    for n, d, seed in [(8300, 2.0, 1), (300, 1.5, 2), (8250, 0.7, 3), (900, 1.2, 4)]:
+        ip, ix = wl.er_graph(n, d, seed)
+        m = wl.dense_u8(n, ip, ix)
+        R = dev(m if fmt == bmlp.BMLP_FMT_U8 else wl.pack_rows(m).view(np.int64))
+        out = torch.zeros_like(R)
+        keep += [R, out]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_CLOSURE, n=n, R1=R, out=out, fmt=fmt))
+        expect.append(("closure", n, ip, ix))
+    n = 8400
+    c1, c2 = wl.er_graph(n, 1.0, 5), wl.er_graph(n, 1.1, 6)
+    m1, m2 = wl.dense_u8(n, *c1), wl.dense_u8(n, *c2)
+    if fmt != bmlp.BMLP_FMT_U8:
+        m1, m2 = wl.pack_rows(m1).view(np.int64), wl.pack_rows(m2).view(np.int64)
+    R1, R2 = dev(m1), dev(m2)
+    out = torch.zeros_like(R1)
+    keep += [R1, R2, out]
+    items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=out, fmt=fmt))
+    expect.append(("compose", n, c1, c2))
+    iters = ctx.batch_run(ctx.problems(items), variant="rms_tc")
+    torch.cuda.synchronize()
+    check(items, expect)
+    for k in range(4):
+        _, n, ip, ix = expect[k]
+        assert iters[k] == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
