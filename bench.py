@@ -172,7 +172,10 @@ def profiled_traffic(kernel, n):
             for ln in f:
                 if ln.startswith("- ") and ":" in ln:
                     k, v = ln[2:].split(":", 1)
-                    kv[k.strip()] = v.strip().strip("`")
+                    v = v.strip()
+                    if v.startswith("`"):  # the value is the first backquoted token
+                        v = v[1:].split("`", 1)[0]
+                    kv[k.strip()] = v
         if kv.get("kernel_source_sha256_12") != kernel_hash(kernel):
             return None
         return float(kv["dram_bytes_per_launch"])
