@@ -279,9 +279,12 @@ bool tc_skip_enabled() {
 // ------------------------------------------------------------------------
 // Tensor-core squaring fixpoint on E4M3 R / R^T buffers already encoded in
 // (M[0], T[0]). On return *res points at the buffer holding R1+ (and *res_t at
-// its transpose).
+// its transpose). With res_f4 set, the caller has instead encoded R / R^T as
+// packed E2M1 into the halves of M[1] / T[1]; every squaring then runs on
+// 4-bit operands and *res_f4 receives the E2M1 result (row stride n_pad / 2).
 bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
-                        const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t) {
+                        const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
+                        const uint8_t** res_f4 = nullptr) {
     const bool pair = tc_pairs_enabled();
     CUtensorMap mapA[2], mapB[2];
     for (int b = 0; b < 2; ++b) {
@@ -306,7 +309,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     uint8_t* FT[2] = {nullptr, nullptr};
     p.fm_ld = static_cast<int32_t>(round_up(p.k_blocks, 16));
     const size_t fbytes = static_cast<size_t>(p.k_blocks) * static_cast<size_t>(p.fm_ld);
-    if (tc_skip_enabled() && p.k_blocks <= 256) {
+    if (tc_skip_enabled() && p.k_blocks <= 256 && res_f4 == nullptr) {
         void* f0 = nullptr;
         void* f1 = nullptr;
         ST(ws_get(ctx, WS_F0, 2 * fbytes, &f0));
@@ -359,6 +362,21 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     };
     int cur = 0;
     *iters = 0;
+    if (res_f4 != nullptr) {
+        // the caller encoded R, R^T as packed E2M1 into the halves of M[1], T[1]: 4-bit squarings from the start
+        const size_t half = static_cast<size_t>(n_pad) * static_cast<size_t>(ld4);
+        sw = 0;
+        Q[0] = M[1];
+        Q[1] = M[1] + half;
+        QT[0] = T[1];
+        QT[1] = T[1] + half;
+        for (int b = 0; b < 2; ++b) {
+            ST(make_tmap(ctx, &mapA4[b], Q[b], n_pad, ld4, ld4, TC_BM));
+            ST(make_tmap(ctx, &mapB4[b], QT[b], n_pad, ld4, ld4, TC_BN / 2));
+        }
+        on_f4 = true;
+        qcur = 0;
+    }
     for (int it = 0; it < max_iters; ++it) {
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
@@ -406,7 +424,14 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             ctx->stats.issued_ops = 2.0 * TC_BM * TC_BN * TC_BK * static_cast<double>(kbs);
             *iters = it + 1;
             qcur ^= 1;
-            if (!changed) return finish_f4(res, res_t);
+            if (!changed) {
+                if (res_f4 != nullptr) {
+                    *res_f4 = Q[qcur];
+                    *res = *res_t = nullptr;
+                    return BMLP_OK;
+                }
+                return finish_f4(res, res_t);
+            }
             continue;
         }
         if (use_maps) {
@@ -446,9 +471,12 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         }
         if (use_maps) ST(sparse_map(F[cur], &use_maps));
     }
-    if (on_f4)
+    if (on_f4 && res_f4 != nullptr) {
+        *res_f4 = Q[qcur];
+        *res = *res_t = nullptr;
+    } else if (on_f4) {
         ST(finish_f4(res, res_t));
-    else {
+    } else {
         *res = M[cur];
         *res_t = T[cur];
     }
@@ -788,10 +816,50 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         ST(ws_get(ctx, WS_T1, bytes, &b[3]));
         uint8_t* M[2] = {static_cast<uint8_t*>(b[0]), static_cast<uint8_t*>(b[1])};
         uint8_t* T[2] = {static_cast<uint8_t*>(b[2]), static_cast<uint8_t*>(b[3])};
-        ST(to_e4m3(ctx, in, fmt, n, M[0], T[0], n_pad, s));
         uint8_t *res = nullptr, *res_t = nullptr;
-        st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
-        if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) ST(bytes_out(ctx, res, n_pad, n, fmt, ov.dev, o.reflexive, s));
+        bool direct = false;
+        if (tc_pairs_enabled() && tc_fp4_enabled()) {
+            // a dense input (by its 128 x 128 block map) starts on 4-bit operands and leaves from them
+            const int64_t kb = n_pad / 128;
+            direct = !tc_skip_enabled() || kb > 256;
+            if (!direct) {
+                void* f = nullptr;
+                ST(ws_get(ctx, WS_F0, static_cast<size_t>(kb * kb), &f));
+                launch_input_block_flags(in.dev, fmt, n, n_pad, static_cast<uint8_t*>(f), kb, s);
+                CK(cudaGetLastError(), "input block map");
+                ctx->stats.launches++;
+                std::vector<uint8_t> h(static_cast<size_t>(kb * kb));
+                CK(cudaMemcpyAsync(h.data(), f, h.size(), cudaMemcpyDeviceToHost, s), "read input block map");
+                CK(cudaStreamSynchronize(s), "read input block map");
+                size_t nz = 0;
+                for (uint8_t x : h) nz += x != 0;
+                direct = static_cast<double>(nz) >= kSkipMaxDensity * static_cast<double>(kb * kb);
+            }
+        }
+        if (direct) {
+            const int64_t ld4 = n_pad / 2;
+            if (fmt == BMLP_FMT_U8)
+                launch_u8_to_e2m1(static_cast<const uint8_t*>(in.dev), n, M[1], T[1], n_pad, s);
+            else
+                launch_packed_to_e2m1(static_cast<const uint64_t*>(in.dev), words_of(n), n, M[1], T[1], n_pad, s);
+            CK(cudaGetLastError(), "E2M1 encode");
+            ctx->stats.launches++;
+            const uint8_t* q = nullptr;
+            st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t, &q);
+            if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) {
+                if (fmt == BMLP_FMT_U8)
+                    launch_e2m1_to_u8(q, ld4, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
+                else
+                    launch_e2m1_to_packed(q, ld4, n, static_cast<uint64_t*>(ov.dev), words_of(n), o.reflexive, s);
+                CK(cudaGetLastError(), "E2M1 decode");
+                ctx->stats.launches++;
+            }
+        } else {
+            ST(to_e4m3(ctx, in, fmt, n, M[0], T[0], n_pad, s));
+            st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
+            if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED)
+                ST(bytes_out(ctx, res, n_pad, n, fmt, ov.dev, o.reflexive, s));
+        }
     } else if (variant == BMLP_RMS_PACKED) {
         const int64_t ldw = round_up(words_of(n), 2);
         ctx->stats.n_pad = ldw * 64;

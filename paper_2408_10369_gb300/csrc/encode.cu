@@ -86,6 +86,112 @@ __global__ void encode_e4m3_tile(Src src, int64_t rows, uint8_t* __restrict__ R,
     *reinterpret_cast<uint4*>(RT + (col0 + r) * rows_pad + row0 + cseg) = expand16(t);
 }
 
+// ---- packed E2M1 (4-bit) operands: element k of a row in byte k / 2, low
+// nibble first; 0b0010 = 1.0.
+// 8 bits -> 8 nibbles of {0, one}
+__device__ __forceinline__ uint32_t nib_spread8(uint32_t b) {
+    uint32_t t = b & 0xFFu;
+    t = (t | (t << 12)) & 0x000F000Fu;
+    t = (t | (t << 6)) & 0x03030303u;
+    t = (t | (t << 3)) & 0x11111111u;
+    return t << 1;
+}
+// 8 nibbles -> 8 bits (nonzero nibble = 1)
+__device__ __forceinline__ uint32_t nib_gather8(uint32_t w) {
+    uint32_t x = w | (w >> 1);
+    x |= x >> 2;
+    x &= 0x11111111u;
+    x = (x | (x >> 3)) & 0x03030303u;
+    x = (x | (x >> 6)) & 0x000F000Fu;
+    x = (x | (x >> 12)) & 0xFFu;
+    return x;
+}
+
+// One 64 x 64 tile per block (256 threads, 16 elements each): packed E2M1 R
+// (row stride ld4 bytes) and R^T, as encode_e4m3_tile.
+template <class Src>
+__global__ void encode_e2m1_tile(Src src, int64_t rows, uint8_t* __restrict__ R, uint8_t* __restrict__ RT, int64_t ld4) {
+    __shared__ uint16_t masks[T][T / 16 + 1];
+    const int tid = threadIdx.x;
+    const int r = tid >> 2, cseg = (tid & 3) * 16;
+    const int64_t row0 = static_cast<int64_t>(blockIdx.y) * T, col0 = static_cast<int64_t>(blockIdx.x) * T;
+    const uint32_t m = src.bits16(row0 + r, col0 + cseg, rows);
+    masks[r][tid & 3] = static_cast<uint16_t>(m);
+    *reinterpret_cast<uint2*>(R + (row0 + r) * ld4 + (col0 + cseg) / 2) = make_uint2(nib_spread8(m), nib_spread8(m >> 8));
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int x = 0; x < 16; ++x) t |= ((masks[cseg + x][r >> 4] >> (r & 15)) & 1u) << x;
+    *reinterpret_cast<uint2*>(RT + (col0 + r) * ld4 + (row0 + cseg) / 2) = make_uint2(nib_spread8(t), nib_spread8(t >> 8));
+}
+
+// Packed E2M1 rows -> u8 0/1 rows (n x n, + I if reflexive); 16 outputs per thread.
+__global__ void e2m1_to_u8_kernel(const uint8_t* __restrict__ Q, int64_t ld4, int64_t n, uint8_t* __restrict__ out,
+                                  int reflexive, bool vec_out) {
+    const int64_t segs = (n + 15) / 16;
+    const int64_t total = n * segs;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = t / segs, j0 = (t % segs) * 16;
+        const uint2 v = *reinterpret_cast<const uint2*>(Q + i * ld4 + j0 / 2);
+        uint32_t bits = nib_gather8(v.x) | (nib_gather8(v.y) << 8);
+        if (reflexive && i >= j0 && i < j0 + 16) bits |= 1u << (i - j0);
+        uint8_t* o = out + i * n + j0;
+        if (vec_out && j0 + 16 <= n) {
+            uint32_t q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                q[k] = ((bits >> (4 * k)) & 1u) | (((bits >> (4 * k + 1)) & 1u) << 8) |
+                       (((bits >> (4 * k + 2)) & 1u) << 16) | (((bits >> (4 * k + 3)) & 1u) << 24);
+            *reinterpret_cast<uint4*>(o) = make_uint4(q[0], q[1], q[2], q[3]);
+        } else {
+            for (int k = 0; k < 16 && j0 + k < n; ++k) o[k] = (bits >> k) & 1u;
+        }
+    }
+}
+
+// Packed E2M1 rows -> packed bit rows (ldw_out words, + I if reflexive); one output word per thread.
+__global__ void e2m1_to_packed_kernel(const uint8_t* __restrict__ Q, int64_t ld4, int64_t n,
+                                      uint64_t* __restrict__ out, int64_t ldw_out, int reflexive) {
+    const int64_t wpr = (n + 63) / 64;
+    const int64_t total = n * ldw_out;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = t / ldw_out, w = t % ldw_out;
+        uint64_t bits = 0;
+        if (w < wpr) {
+            const uint4* src = reinterpret_cast<const uint4*>(Q + r * ld4 + w * 32);  // 64 nibbles
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint4 v = src[q];
+                const uint64_t b = nib_gather8(v.x) | (nib_gather8(v.y) << 8) | (nib_gather8(v.z) << 16) |
+                                   (static_cast<uint64_t>(nib_gather8(v.w)) << 24);
+                bits |= b << (32 * q);
+            }
+            const int64_t valid = n - w * 64;
+            if (valid < 64) bits &= (1ull << valid) - 1ull;
+            if (reflexive && (r >> 6) == w) bits |= 1ull << (r & 63);
+        }
+        out[t] = bits;
+    }
+}
+
+// 1 per nonzero 128 x 128 block of an input matrix (rows x n, padded to the block grid); one block of
+// 256 threads per map entry, 16 elements per thread per pass.
+template <class Src>
+__global__ void input_block_flags_kernel(Src src, int64_t rows, int64_t flags_ld, uint8_t* __restrict__ flags) {
+    const int64_t br = blockIdx.y, bc = blockIdx.x;
+    const int tid = threadIdx.x;
+    uint32_t any = 0;
+#pragma unroll 4
+    for (int k = 0; k < 4; ++k) {
+        const int e = (k * 256 + tid) * 16;  // element offset inside the 128 x 128 block
+        any |= src.bits16(br * 128 + e / 128, bc * 128 + e % 128, rows);
+    }
+    any = __syncthreads_or(any != 0);
+    if (tid == 0) flags[br * flags_ld + bc] = any ? 1 : 0;
+}
+
 // out[i][j] = (R[i][j] != 0) | (reflexive && i == j); 16 outputs per thread.
 __global__ void bytes_to_u8_kernel(const uint8_t* __restrict__ R, int64_t ld, int64_t n, uint8_t* __restrict__ out,
                                    int reflexive, bool vec_out) {
@@ -278,6 +384,42 @@ void launch_packed_to_e4m3(const uint64_t* in, int64_t ldw_in, int64_t rows, int
     SrcPacked src{in, ldw_in, n};
     dim3 grid(static_cast<unsigned>(n_pad / T), static_cast<unsigned>(rows_pad / T));
     encode_e4m3_tile<SrcPacked><<<grid, 256, 0, s>>>(src, rows, R, RT, n_pad, rows_pad);
+}
+
+void launch_u8_to_e2m1(const uint8_t* in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad, cudaStream_t s) {
+    SrcU8 src{in, n, (n % 16 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0)};
+    dim3 grid(static_cast<unsigned>(n_pad / T), static_cast<unsigned>(n_pad / T));
+    encode_e2m1_tile<SrcU8><<<grid, 256, 0, s>>>(src, n, R, RT, n_pad / 2);
+}
+
+void launch_packed_to_e2m1(const uint64_t* in, int64_t ldw_in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad,
+                           cudaStream_t s) {
+    SrcPacked src{in, ldw_in, n};
+    dim3 grid(static_cast<unsigned>(n_pad / T), static_cast<unsigned>(n_pad / T));
+    encode_e2m1_tile<SrcPacked><<<grid, 256, 0, s>>>(src, n, R, RT, n_pad / 2);
+}
+
+void launch_e2m1_to_u8(const uint8_t* Q, int64_t ld4, int64_t n, uint8_t* out, int reflexive, cudaStream_t s) {
+    const bool vec = (n % 16 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+    e2m1_to_u8_kernel<<<grid_for(n * ((n + 15) / 16), 256), 256, 0, s>>>(Q, ld4, n, out, reflexive, vec);
+}
+
+void launch_e2m1_to_packed(const uint8_t* Q, int64_t ld4, int64_t n, uint64_t* out, int64_t ldw_out, int reflexive,
+                           cudaStream_t s) {
+    e2m1_to_packed_kernel<<<grid_for(n * ldw_out, 256), 256, 0, s>>>(Q, ld4, n, out, ldw_out, reflexive);
+}
+
+void launch_input_block_flags(const void* in, int32_t fmt, int64_t n, int64_t n_pad, uint8_t* flags,
+                              int64_t flags_ld, cudaStream_t s) {
+    dim3 grid(static_cast<unsigned>(n_pad / 128), static_cast<unsigned>(n_pad / 128));
+    if (fmt == BMLP_FMT_U8) {
+        SrcU8 src{static_cast<const uint8_t*>(in), n,
+                  (n % 16 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0)};
+        input_block_flags_kernel<SrcU8><<<grid, 256, 0, s>>>(src, n, flags_ld, flags);
+    } else {
+        SrcPacked src{static_cast<const uint64_t*>(in), (n + 63) / 64, n};
+        input_block_flags_kernel<SrcPacked><<<grid, 256, 0, s>>>(src, n, flags_ld, flags);
+    }
 }
 
 void launch_bytes_to_u8(const uint8_t* R, int64_t ld, int64_t n, uint8_t* out, int reflexive, cudaStream_t s) {

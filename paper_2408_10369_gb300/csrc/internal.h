@@ -201,6 +201,17 @@ void launch_packed_or(uint64_t* out, int64_t ldw_out, const uint64_t* src, int64
                       cudaStream_t s);
 // identity as packed rows: row i has only bit i
 void launch_identity_packed(uint64_t* out, int64_t ldw, int64_t n, cudaStream_t s);
+// caller matrix (u8 n x n or packed n x ceil(n/64)) -> packed E2M1 R and R^T (n_pad x n_pad / 2 bytes)
+void launch_u8_to_e2m1(const uint8_t* in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad, cudaStream_t s);
+void launch_packed_to_e2m1(const uint64_t* in, int64_t ldw_in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad,
+                           cudaStream_t s);
+// packed E2M1 rows (ld4 bytes) -> u8 n x n / packed rows of ldw_out words (+ I if reflexive)
+void launch_e2m1_to_u8(const uint8_t* Q, int64_t ld4, int64_t n, uint8_t* out, int reflexive, cudaStream_t s);
+void launch_e2m1_to_packed(const uint8_t* Q, int64_t ld4, int64_t n, uint64_t* out, int64_t ldw_out, int reflexive,
+                           cudaStream_t s);
+// 1 per nonzero 128 x 128 block of a caller matrix (fmt u8 or packed), n_pad / 128 blocks a side
+void launch_input_block_flags(const void* in, int32_t fmt, int64_t n, int64_t n_pad, uint8_t* flags,
+                              int64_t flags_ld, cudaStream_t s);
 // out = rows x cols AND NOT in over n x n packed rows (null vector = all constants)
 void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const uint64_t* rows, const uint64_t* cols,
                           uint64_t* out, int64_t ldw_out, cudaStream_t s);

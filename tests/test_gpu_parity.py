@@ -262,3 +262,19 @@ def test_mma_issue_rate(ctx):
     assert r8 > 0 and r4 >= r8
     with pytest.raises(pkg.BmlpError):
         ctx.mma_issue_rate(2)
+
+
+@pytest.mark.parametrize("variant", ["rms_tc", "rms_packed", "smp_packed"])
+def test_pinned_host_buffers(ctx, variant):
+    """Page-locked host input and output: read and written in place by the kernels."""
+    n = 1100
+    ip, ix, m = er_case(n, 1.7, 31)
+    want = oracle.closure(n, ip, ix)
+    hin = torch.from_numpy(m).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    ctx.rms(hin, n, hout, variant=variant)
+    np.testing.assert_array_equal(hout.numpy(), want)
+    P = torch.from_numpy(wl.pack_rows(m).view(np.int64)).pin_memory()
+    Pout = torch.zeros_like(P).pin_memory()
+    ctx.rms(P, n, Pout, fmt=pkg.BMLP_FMT_PACKED64, variant=variant)
+    np.testing.assert_array_equal(wl.unpack_rows(Pout.numpy().view(np.uint64), n), want)
