@@ -2,10 +2,12 @@
 
 Workload (default): one directed Erdos-Renyi graph with n = 32,768 nodes and
 mean out-degree 4 (each ordered pair i != j an edge with p = 4 / (n - 1),
-seeded), given as a dense n x n uint8 0/1 matrix resident in HBM. One step is
-one call of ``bmlp_rms`` through the C ABI: encode to E4M3 R / R^T, the
-squaring fixpoint R <- R + R R with the changed-flag early exit, and decode of
-R1+ into a uint8 output matrix. The metric is effective Boolean TOPS =
+seeded), given as packed bit rows (the bit code of Sec. 3.2: n rows of n / 64
+uint64 words, 128 MiB) resident in HBM; ``--fmt u8`` gives it as a dense n x n
+uint8 0/1 matrix (1 GiB) instead. One step is one call of ``bmlp_rms``
+through the C ABI: encode to the tensor-core operands R / R^T, the squaring
+fixpoint R <- R + R R with the changed-flag early exit, and decode of R1+
+into the caller's format. The metric is effective Boolean TOPS =
 iterations * 2 n^3 / time (n logical, every product counted as dense).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -49,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--degree", type=float, default=4.0)
+    ap.add_argument("--fmt", default="packed", choices=["packed", "u8"],
+                    help="format of the input and output matrices of the closure benchmark")
     ap.add_argument("--variant", default=None,
                     help="default: rms_tc (er), smp_packed (powerlaw_smp), auto (kg_batch, isforeign)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -346,8 +350,13 @@ def main():
     torch.cuda.set_device(device)
     n = args.n
     ip, ix = wl.er_graph(n, args.degree, rank)
-    dense = wl.dense_u8(n, ip, ix)
-    R = torch.from_numpy(dense).to(device)
+    if args.fmt == "packed":
+        host_in = wl.csr_to_packed(n, ip, ix).view(np.int64)
+        FMT = pkg.BMLP_FMT_PACKED64
+    else:
+        host_in = wl.dense_u8(n, ip, ix)
+        FMT = pkg.BMLP_FMT_U8
+    R = torch.from_numpy(host_in).to(device)
     out = torch.empty_like(R)
     ctx = pkg.Context(local)
     stream = torch.cuda.current_stream(device)
@@ -357,7 +366,7 @@ def main():
             torch.distributed.barrier()
 
     def step(profile):
-        return ctx.rms(R, n, out, variant=args.variant, profile=profile, stream=stream)
+        return ctx.rms(R, n, out, fmt=FMT, variant=args.variant, profile=profile, stream=stream)
 
     iters = 0
     for _ in range(args.warmup):
@@ -388,18 +397,19 @@ def main():
     # ---- end-to-end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hin = torch.from_numpy(dense).pin_memory()
+        hin = torch.from_numpy(host_in).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
-        ctx.rms(hin, n, hout, variant=args.variant, stream=stream)
+        ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ctx.rms(hin, n, hout, variant=args.variant, stream=stream)
+            ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream)
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world, device)
+        nbytes = int(hin.numel() * hin.element_size())
         e2e = {"value": args.steps * iters * 2.0 * n ** 3 * world / te / 1e12, "unit": UNIT,
-               "h2d_bytes_per_step": n * n, "d2h_bytes_per_step": n * n}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     # ---- the other closure variants and the learned choice on the same graph (same bits, other kernels)
     variants = None
     if not args.no_variants:
@@ -409,11 +419,11 @@ def main():
         for v in ("smp_packed", "smp_tc", "rms_packed"):
             o2 = torch.empty_like(R)
             try:
-                ctx.rms(R, n, o2, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
+                ctx.rms(R, n, o2, fmt=FMT, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                ctx.rms(R, n, o2, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
+                ctx.rms(R, n, o2, fmt=FMT, variant=v, stream=stream, budget_ns=int(8 * ms_tc * 1e6))
                 e1.record(stream)
                 torch.cuda.synchronize()
                 variants[v] = {"ms": e0.elapsed_time(e1), "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
@@ -425,11 +435,11 @@ def main():
         if os.path.exists(model):
             ctx.dispatch_load(model)
             o2 = torch.empty_like(R)
-            ctx.rms(R, n, o2, stream=stream)
+            ctx.rms(R, n, o2, fmt=FMT, stream=stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                ctx.rms(R, n, o2, stream=stream)
+                ctx.rms(R, n, o2, fmt=FMT, stream=stream)
             torch.cuda.synchronize()
             ta = (time.perf_counter() - t0) / args.steps
             chosen = pkg.bmlp.VARIANT_LIST[ctx.stats()["variant"]]
@@ -475,8 +485,10 @@ def main():
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
                        "seed": "rank", "variant": args.variant, "iterations": iters, "nnz": int(len(ix)),
                        "graphs_per_s": args.steps * world / t,
-                       "l2": ("inputs larger than L2 (%.2f GiB per matrix)" % (n * n / 2 ** 30)) if n * n > 129e6
-                       else "inputs fit in L2 (%.1f MB per matrix; not flushed)" % (n * n / 1e6),
+                       "fmt": args.fmt,
+                       "l2": ("operands larger than L2 (%.2f GiB per E2M1 matrix, %.0f MiB input)"
+                              % (n * n / 2 ** 31, host_in.nbytes / 2 ** 20)) if n * n / 2 > 129e6
+                       else "operands fit in L2 (%.1f MB per E2M1 matrix; not flushed)" % (n * n / 2e6),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "variants": variants}
