@@ -58,16 +58,19 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
-    ap.add_argument("--workload", default="er", choices=["er", "powerlaw_smp", "kg_batch", "isforeign", "insert"],
+    ap.add_argument("--workload", default="er",
+                    choices=["er", "powerlaw_smp", "kg_batch", "isforeign", "insert", "dg_partial"],
                     help="er: the closure benchmark (default); powerlaw_smp: 4,096 selective query rows on the "
                          "n = 65,536 power-law graph; kg_batch: every relation closure and 200 compositions of "
                          "the knowledge-graph workload in one grouped batch; isforeign: the composed program "
                          "hasPlace / indirectlyPartOf / isForeign on a 14,541-entity, 7,991-fact place hierarchy; insert: "
-                         "1,000 new contains facts added incrementally to hasPlace of that hierarchy")
+                         "1,000 new contains facts added incrementally to hasPlace of that hierarchy; dg_partial: one "
+                         "partially grounded query path(c, Y) on an ER graph of n = 5,000 with --degree (default 50)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
     args = ap.parse_args()
     if args.variant is None:
-        args.variant = {"er": "rms_tc", "powerlaw_smp": "smp_packed"}.get(args.workload, "auto")
+        args.variant = {"er": "rms_tc", "powerlaw_smp": "smp_packed", "dg_partial": "smp_packed"}.get(args.workload,
+                                                                                                     "auto")
     return args
 
 
@@ -251,6 +254,18 @@ def run_aux(args):
         def step():
             return ctx.smp(P, n, src, q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant, profile=True)
         unit, units_per_step, name = "queries/s", q, "powerlaw_n65536_q4096"
+    elif args.workload == "dg_partial":
+        n = 5000
+        d = args.degree if args.degree != 4.0 else 50.0
+        ip, ix = wl.er_graph(n, d, 0)
+        P = torch.from_numpy(wl.csr_to_packed(n, ip, ix).view(np.int64)).cuda()
+        src = torch.from_numpy(wl.query_rows(n, 1, 1, 1, 0).view(np.int64)).cuda()
+        out = torch.zeros_like(src)
+        extra["mean_out_degree"] = d
+
+        def step():
+            return ctx.smp(P, n, src, 1, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant)
+        unit, units_per_step, name = "queries/s", 1, "dg_partial_n5000"
     elif args.workload == "insert":
         n, m = 14541, 1000
         (ci, cx), _ = wl.geo_kg(n=n)

@@ -40,3 +40,39 @@ def test_wait_timeout_is_reported_and_context_recovers():
         np.testing.assert_array_equal(o2.cpu().numpy(), oracle.closure(n, ip, ix))
     finally:
         ctx.close()
+
+
+def _chain_with_shortcuts(n, seed):
+    src = np.arange(n - 1)
+    a, b = wl.random_pairs(n, max(1, n // 100), seed)
+    return wl.csr_from_pairs(n, np.concatenate([src, a]), np.concatenate([src + 1, b]))
+
+
+@pytest.mark.parametrize("case", ["dense_e2m1_pairs", "sparse_e4m3_clusters"])
+def test_squaring_wait_timeout_recovers(case):
+    """The 4-bit 2-SM squaring kernel (dense input) and the E4M3 cluster
+    kernel with block skipping (block-sparse input): a one-nanosecond wait
+    bound gives BMLP_ERR_TIMEOUT, and the same context then closes exactly."""
+    ctx = pkg.Context(0)
+    try:
+        if case == "dense_e2m1_pairs":
+            n = 1500
+            ip, ix = wl.er_graph(n, 3.0, 19)
+        else:
+            n = 3000
+            ip, ix = _chain_with_shortcuts(n, 20)
+        R = torch.from_numpy(wl.dense_u8(n, ip, ix)).cuda()
+        out = torch.zeros_like(R)
+        with pytest.raises(bmlp.BmlpError) as e:
+            ctx.rms(R, n, out, variant="rms_tc", timeout_ns=1)
+        assert e.value.status == bmlp.BMLP_ERR_TIMEOUT
+        ctx.rms(R, n, out, variant="rms_tc")
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.closure(n, ip, ix))
+        st = ctx.stats()
+        if case == "dense_e2m1_pairs":
+            assert st["e2m1_products"] == st["product_launches"]
+        else:
+            assert st["e2m1_products"] < st["product_launches"]
+    finally:
+        ctx.close()

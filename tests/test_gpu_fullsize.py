@@ -78,6 +78,28 @@ def test_config2_er_tensor_cores(ctx, n, d):
     np.testing.assert_array_equal(out8[torch.from_numpy(rows).long().cuda()].cpu().numpy(), want_rows)
 
 
+def test_largest_tensor_core_closure(ctx):
+    """n = 65,536 (beyond the block-map limit of 256 x 256 blocks, so every
+    squaring runs on 4-bit operands from the start): every row's population
+    count and 64 whole rows against the oracle."""
+    n = 65536
+    ip, ix = wl.er_graph(n, 1.5, 3)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros_like(P)
+    it = ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_tc")
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert st["e2m1_products"] == st["product_launches"] == it
+    got = out.cpu().numpy().view(np.uint64)
+    _, depth, count = oracle.reach_rows(n, ip, ix, np.arange(n, dtype=np.int32), want_rows=False)
+    np.testing.assert_array_equal(popcount_rows(got), count)
+    assert it == oracle.rms_iterations(int(depth.max()))
+    rows = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(7).integers(0, n, 62)])).astype(np.int32)
+    want_rows, _, _ = oracle.reach_rows(n, ip, ix, rows)
+    np.testing.assert_array_equal(wl.unpack_rows(got[rows], n), want_rows)
+    del P, out
+
+
 @pytest.mark.parametrize("d", [1.5, 4.0])
 def test_config2_er8192_packed_and_frontier(ctx, d):
     n = 8192
