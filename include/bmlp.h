@@ -111,7 +111,10 @@ typedef struct bmlp_stats {
     double issued_ops;         /* Boolean multiply-adds issued x 2 (tensor core
                                   path: 2 * M * N * K per tile actually run)    */
     int32_t e2m1_products;     /* squarings run on packed E2M1 (4-bit) operands */
-    int32_t reserved;
+    int32_t frontier_squarings; /* BMLP_SMP_PACKED closures (n >= 4096): steps
+                                  R <- R + R R taken before the frontier
+                                  expansion (path-like relations; same closure,
+                                  fewer levels)                                 */
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

@@ -72,6 +72,10 @@ enum : int {
 constexpr int WS_WVALT = 20;
 // Relation operators and the composed isForeign program (packed buffers and type vectors).
 constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
+// R + R R and its word index, before a frontier closure of a path-like R.
+constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
+constexpr int64_t kSquareMinN = 4096;
+constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 
@@ -579,7 +583,7 @@ int pick_variant_rms(int64_t) { return BMLP_RMS_TC; }
 // (device, q x ldw_src words). out: device, q x ldw_out words.
 bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t n, const uint64_t* src,
                            int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out, const bmlp_options& o,
-                           cudaStream_t s, int* levels) {
+                           cudaStream_t s, int* levels, bool square_first = false) {
     const int64_t ldw = round_up(words_of(n), 2);
     if (ldw > smp_packed_max_words())
         return set_err(ctx, BMLP_ERR_UNSUPPORTED, "packed frontier path supports n <= %d", smp_packed_max_words() * 64);
@@ -593,6 +597,43 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                          static_cast<uint64_t*>(wval), s),
        "word index build");
     ctx->stats.launches += 3;
+    if (square_first && n >= kSquareMinN && ldw <= 2048) {
+        // Long shortest paths make the frontier latency-bound (one level per path step). closure(R + R R) =
+        // closure(R) with half the levels, so R is squared while that keeps its rows within ~1.5x the nonzero
+        // words (path-like structure); once the words grow faster, the frontier would pay more per level than
+        // it saves in levels, and the last squaring is dropped.
+        void *P2 = nullptr, *wptr2 = nullptr, *widx2 = nullptr, *wval2 = nullptr;
+        ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &P2));
+        ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 1) * 8), &wptr2));
+        ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx2));
+        ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval2));
+        auto words = [&](const void* wp, int64_t* total) -> bmlp_status {
+            CK(cudaMemcpyAsync(total, static_cast<const int64_t*>(wp) + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+               "read word count");
+            CK(cudaStreamSynchronize(s), "read word count");
+            return BMLP_OK;
+        };
+        int64_t W = 0, W2 = 0;
+        ST(words(wptr, &W));
+        for (int k = 0; k < kSquareMaxSteps; ++k) {
+            CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                                  static_cast<uint64_t*>(wval), static_cast<uint64_t*>(P), n, ldw,
+                                  static_cast<uint64_t*>(P2), ctx->sm_count, s),
+               "squaring launch");
+            CK(launch_wcsr_build(static_cast<uint64_t*>(P2), n, ldw, static_cast<int64_t*>(wptr2),
+                                 static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s),
+               "word index build");
+            ctx->stats.launches += 4;
+            ST(words(wptr2, &W2));
+            if (W2 > W + W / 2) break;
+            std::swap(P, P2);
+            std::swap(wptr, wptr2);
+            std::swap(widx, widx2);
+            std::swap(wval, wval2);
+            W = W2;
+            ctx->stats.frontier_squarings++;
+        }
+    }
     // transposed word index for the pull direction (levels whose frontier is large)
     void *PT = nullptr, *wptrT = nullptr, *widxT = nullptr, *wvalT = nullptr;
     ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &PT));
@@ -889,7 +930,8 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         o2.reflexive = 0;
         o2.max_iters = 0;
         if (variant == BMLP_SMP_PACKED)
-            st = smp_packed_run(ctx, in, fmt, n, static_cast<uint64_t*>(src), ldw_src, n, outp, ldw_src, o2, s, &iters);
+            st = smp_packed_run(ctx, in, fmt, n, static_cast<uint64_t*>(src), ldw_src, n, outp, ldw_src, o2, s, &iters,
+                                true);
         else
             st = smp_tc_run(ctx, in, fmt, n, static_cast<uint64_t*>(src), ldw_src, n, outp, ldw_src, o2, s, &iters);
         if (st == BMLP_OK) {

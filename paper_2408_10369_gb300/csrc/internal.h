@@ -128,7 +128,7 @@ struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
     char err[512] = {0};
-    bmlp::DevBuf ws[28];
+    bmlp::DevBuf ws[32];
     void* batch = nullptr;       // cached grouped-batch graph (batch.cu)
     int tune[32];                // autotuned engine per size bucket (-1 = unknown)
     int* d_ctl = nullptr;        // device control words (see CTL_* below)
@@ -264,6 +264,9 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
                               int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s,
                               Deadline dl = Deadline{0, nullptr, nullptr}, const int64_t* wptrT = nullptr,
                               const int32_t* widxT = nullptr, const uint64_t* wvalT = nullptr);
+// C = P | P P on packed rows through the word index (wptr, widx, wval) of P
+cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, const uint64_t* P,
+                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s);
 // (R+ + {(u, v)})+ in place on a transitive R+ (n packed rows of ldw words)
 cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, int64_t v, int sms, cudaStream_t s);
 // out = in^T on n x n packed rows of ldw words (out cleared first)

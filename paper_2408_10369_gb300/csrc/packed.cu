@@ -197,19 +197,10 @@ __host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) {
 // light row (<= 16 nonzero words) are loaded before the first atomic; heavy
 // rows are walked by the whole warp. tm collects the word groups written.
 template <int NQ>
-__device__ __forceinline__ void push_step(uint64_t& d, int64_t w, int lane, const int64_t* __restrict__ wptr,
+__device__ __forceinline__ void push_rows(const int64_t (&k)[NQ], int lane, const int64_t* __restrict__ wptr,
                                           const int32_t* __restrict__ widx, const uint64_t* __restrict__ wval,
                                           uint64_t* N, int gshift, uint64_t& tm) {
-    int64_t k[NQ], e0[NQ], e1[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        k[q] = -1;
-        if (d) {
-            const int b = __ffsll(static_cast<long long>(d)) - 1;
-            d &= d - 1;
-            k[q] = w * 64 + b;
-        }
-    }
+    int64_t e0[NQ], e1[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         e0[q] = k[q] >= 0 ? wptr[k[q]] : 0;
@@ -267,6 +258,81 @@ __device__ __forceinline__ void push_step(uint64_t& d, int64_t w, int lane, cons
                 tm |= 1ull << (xx >> gshift);
             }
         }
+    }
+}
+
+// One push step of a lane on its own frontier word d (the constants of word w): up to NQ of its set bits.
+template <int NQ>
+__device__ __forceinline__ void push_step(uint64_t& d, int64_t w, int lane, const int64_t* __restrict__ wptr,
+                                          const int32_t* __restrict__ widx, const uint64_t* __restrict__ wval,
+                                          uint64_t* N, int gshift, uint64_t& tm) {
+    int64_t k[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        k[q] = -1;
+        if (d) {
+            const int b = __ffsll(static_cast<long long>(d)) - 1;
+            d &= d - 1;
+            k[q] = w * 64 + b;
+        }
+    }
+    push_rows<NQ>(k, lane, wptr, widx, wval, N, gshift, tm);
+}
+
+// Position of the set bit of rank r (r < popcount) in x.
+__device__ __forceinline__ int select_bit(uint64_t x, int r) {
+    int pos = 0;
+    int c = __popc(static_cast<unsigned>(x));
+    if (r >= c) {
+        r -= c;
+        x >>= 32;
+        pos = 32;
+    }
+    unsigned v = static_cast<unsigned>(x);
+    c = __popc(v & 0xFFFFu);
+    if (r >= c) { r -= c; v >>= 16; pos += 16; }
+    c = __popc(v & 0xFFu);
+    if (r >= c) { r -= c; v >>= 8; pos += 8; }
+    c = __popc(v & 0xFu);
+    if (r >= c) { r -= c; v >>= 4; pos += 4; }
+    c = __popc(v & 0x3u);
+    if (r >= c) { r -= c; v >>= 2; pos += 2; }
+    if (r >= static_cast<int>(v & 1u)) pos += 1;
+    return pos;
+}
+
+// Push of a chunk of frontier words (lane l holds word d of index w) with the set bits dealt out to the
+// lanes in rank order, two per lane per step: a word with many bits (a band of a squared path, a dense
+// frontier) is shared by the whole warp instead of being walked by one lane.
+__device__ __forceinline__ void push_balanced(uint64_t d, int64_t w, int lane, const int64_t* __restrict__ wptr,
+                                              const int32_t* __restrict__ widx, const uint64_t* __restrict__ wval,
+                                              uint64_t* N, int gshift, uint64_t& tm) {
+    const int c = __popcll(d);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - c;
+    for (int base = 0; base < total; base += 64) {
+        int64_t k[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = base + q * 32 + lane;
+            int owner = 0;  // the lane whose bits hold rank r: the first with inclusive count > r
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int v = __shfl_sync(FULL, incl, owner + st - 1);
+                if (v <= r) owner += st;
+            }
+            const uint64_t od = __shfl_sync(FULL, d, owner);
+            const int64_t ow = __shfl_sync(FULL, w, owner);
+            const int oex = __shfl_sync(FULL, excl, owner);
+            k[q] = r < total ? ow * 64 + select_bit(od, r - oex) : -1;
+        }
+        push_rows<2>(k, lane, wptr, widx, wval, N, gshift, tm);
     }
 }
 
@@ -382,14 +448,11 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
                     const int i = i0 + lane;
                     const int64_t w = i < fcount ? FL[i] : 0;
                     uint64_t d = i < fcount ? D[w] : 0ull;
-                    while (__any_sync(FULL, d != 0ull)) {
-                        // two frontier constants per lane when some lane has two left (dense frontiers),
-                        // else one (long sparse paths): every load of a step is in flight before its atomics
-                        if (__any_sync(FULL, __popcll(d) >= 2))
-                            push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
-                        else
-                            push_step<1>(d, w, lane, wptr, widx, wval, N, gshift, tm);
-                    }
+                    // at most two constants per word: each lane takes its own; else the bits are dealt out
+                    if (__reduce_max_sync(FULL, static_cast<unsigned>(__popcll(d))) <= 2u)
+                        push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
+                    else
+                        push_balanced(d, w, lane, wptr, widx, wval, N, gshift, tm);
                 }
                 gm = static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm))) |
                      (static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm >> 32))) << 32);
@@ -473,6 +536,36 @@ __global__ void insert_fact_kernel(uint64_t* __restrict__ P, int64_t n, int64_t 
     }
 }
 
+// ---- one squaring step on packed rows through the word index of R:
+// C_i = R_i | OR_{k in R_i} R_k, where row k contributes only its nonzero
+// words (push_step), so the cost follows the index, not n / 64 words per k.
+// Warp per row; the row is assembled in shared memory (ldw words per warp).
+__global__ void __launch_bounds__(256) square_rows_kernel(const int64_t* __restrict__ wptr,
+                                                          const int32_t* __restrict__ widx,
+                                                          const uint64_t* __restrict__ wval,
+                                                          const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
+                                                          uint64_t* __restrict__ C) {
+    extern __shared__ uint64_t sq_sm[];
+    const int lane = threadIdx.x & 31;
+    uint64_t* S = sq_sm + static_cast<int64_t>(threadIdx.x >> 5) * ldw;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        for (int64_t w = lane; w < ldw; w += 32) S[w] = P[i * ldw + w];
+        __syncwarp();
+        uint64_t tm = 0;  // word groups are not needed here
+        const int64_t e0 = wptr[i], e1 = wptr[i + 1];
+        for (int64_t b0 = e0; b0 < e1; b0 += 32) {
+            const int64_t e = b0 + lane;
+            const uint64_t d = e < e1 ? wval[e] : 0ull;
+            const int64_t w = e < e1 ? widx[e] : 0;
+            push_balanced(d, w, lane, wptr, widx, wval, S, 30, tm);
+        }
+        __syncwarp();
+        for (int64_t w = lane; w < ldw; w += 32) C[i * ldw + w] = S[w];
+        __syncwarp();
+    }
+}
+
 inline int warps_grid(int64_t rows, int sms) {
     int64_t blocks = (rows + 7) / 8;  // 8 warps of 256 threads
     const int64_t cap = static_cast<int64_t>(sms) * 8;
@@ -510,6 +603,24 @@ cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t
 }
 
 int smp_packed_max_words() { return 7168; }
+
+cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, const uint64_t* P,
+                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s) {
+    int warps = 8;
+    while (warps > 1 && warps * ldw * 8 > 32 * 1024) warps >>= 1;
+    const size_t smem = static_cast<size_t>(warps) * static_cast<size_t>(ldw) * 8;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(square_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    int64_t blocks = (n + warps - 1) / warps;
+    const int64_t cap = static_cast<int64_t>(sms) * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    square_rows_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(wptr, widx, wval, P, n, ldw, C);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n, int64_t ldw,
                               const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out,

@@ -189,6 +189,9 @@ def test_closure_long_paths(ctx, variant, n, shape, seed):
     want = oracle.closure(n, ip, ix)
     got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), variant, fmt="packed")
     np.testing.assert_array_equal(got, want)
+    if variant == "smp_packed" and n >= 4096:
+        # a path-like relation is squared before the frontier expansion (same closure, fewer levels)
+        assert ctx.stats()["frontier_squarings"] >= 1
 
 
 def test_squaring_operand_forms(ctx):
