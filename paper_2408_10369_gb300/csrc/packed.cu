@@ -12,11 +12,15 @@
 //  * smp_packed   the selective product of Eq. 5 / Algorithm 2 per query row:
 //                 D = v; V = 0; repeat N = (OR_{k in D} R_k) & ~V; V |= N;
 //                 D = N until D is empty; out = V = v R+.
-//                 One warp per query row, frontier / visited / next bitsets in
-//                 shared memory, all frontier levels of a query in one launch
+//                 One warp per query row, frontier and next bitsets in shared
+//                 memory, the visited set in the query's output row, all
+//                 frontier levels of a query in one launch
 //                 (queries are independent, so no grid-wide step is needed;
 //                 a warp takes the next query from a global counter when its
 //                 query has converged).
+//  * square_rows  R + R R through the word index, before the frontier closure
+//                 of a path-like relation (same closure, fewer levels).
+//  * insert_fact  one new fact into a transitive closure (rank-1 update).
 #include "internal.h"
 
 namespace bmlp {
@@ -191,11 +195,11 @@ __host__ __device__ __forceinline__ int64_t smp_warp_bytes(int64_t ldw) {
     return (18 * ldw + 64 + 16 + 15) & ~int64_t(15);
 }
 
-// One push step of a warp: each lane takes up to NQ constants of its frontier
-// word d and ORs their rows' nonzero words into N (shared-memory atomics
-// without return value). The row ranges and the first four entries of every
-// light row (<= 16 nonzero words) are loaded before the first atomic; heavy
-// rows are walked by the whole warp. tm collects the word groups written.
+// Rows of up to NQ frontier constants per lane (k < 0: none) ORed into N:
+// their nonzero words, by shared-memory atomics without return value. The row
+// ranges and the first four entries of every light row (<= 16 nonzero words)
+// are loaded before the first atomic; heavy rows are walked by the whole warp.
+// tm collects the word groups written (bit x >> gshift for word x).
 template <int NQ>
 __device__ __forceinline__ void push_rows(const int64_t (&k)[NQ], int lane, const int64_t* __restrict__ wptr,
                                           const int32_t* __restrict__ widx, const uint64_t* __restrict__ wval,
@@ -538,7 +542,7 @@ __global__ void insert_fact_kernel(uint64_t* __restrict__ P, int64_t n, int64_t 
 
 // ---- one squaring step on packed rows through the word index of R:
 // C_i = R_i | OR_{k in R_i} R_k, where row k contributes only its nonzero
-// words (push_step), so the cost follows the index, not n / 64 words per k.
+// words (push_balanced), so the cost follows the index, not n / 64 words per k.
 // Warp per row; the row is assembled in shared memory (ldw words per warp).
 __global__ void __launch_bounds__(256) square_rows_kernel(const int64_t* __restrict__ wptr,
                                                           const int32_t* __restrict__ widx,
