@@ -169,20 +169,27 @@ def kernel_hash(kernel="tc_pair_kernel"):
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(kernel, n):
+def summary_values(path):
+    """The "- key: value" lines of an ncu summary; a value that starts with a
+    backquoted token is that token."""
+    kv = {}
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("- ") and ":" in ln:
+                k, v = ln[2:].split(":", 1)
+                v = v.strip()
+                if v.startswith("`"):
+                    v = v[1:].split("`", 1)[0]
+                kv[k.strip()] = v
+    return kv
+
+
+def profiled_traffic(kernel, n, root=None):
     """DRAM bytes per product launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "%s_er%d.md" % (kernel, n))
+    path = os.path.join(root or ROOT, "profiles", "%s_er%d.md" % (kernel, n))
     try:
-        kv = {}
-        with open(path) as f:
-            for ln in f:
-                if ln.startswith("- ") and ":" in ln:
-                    k, v = ln[2:].split(":", 1)
-                    v = v.strip()
-                    if v.startswith("`"):  # the value is the first backquoted token
-                        v = v[1:].split("`", 1)[0]
-                    kv[k.strip()] = v
+        kv = summary_values(path)
         if kv.get("kernel_source_sha256_12") != kernel_hash(kernel):
             return None
         return float(kv["dram_bytes_per_launch"])

@@ -68,3 +68,20 @@ def test_aux_workload_flags_parse(w, monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", w, "--variant", "smp_packed"])
     a = bench.parse()
     assert a.workload == w
+
+
+def test_profile_summary_values(tmp_path):
+    """The per-launch DRAM bytes come from the committed summary only while its
+    kernel hash matches the current source."""
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "tc4_duo_kernel_er64.md").write_text(
+        "# title\n- kernel_source_sha256_12: `%s`\n- dram_bytes_per_launch: `1234`  (note)\n"
+        % bench.kernel_hash("tc4_duo_kernel"))
+    assert bench.profiled_traffic("tc4_duo_kernel", 64, root=str(tmp_path)) == 1234.0
+    (prof / "tc4_duo_kernel_er64.md").write_text("- kernel_source_sha256_12: `000000000000`\n"
+                                                 "- dram_bytes_per_launch: `1234`\n")
+    assert bench.profiled_traffic("tc4_duo_kernel", 64, root=str(tmp_path)) is None
+    assert bench.profiled_traffic("tc4_duo_kernel", 32768) is None or bench.profiled_traffic(
+        "tc4_duo_kernel", 32768) > 0
