@@ -207,8 +207,9 @@ __device__ __forceinline__ void push_rows(const int64_t (&k)[NQ], int lane, cons
     int64_t e0[NQ], e1[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        e0[q] = k[q] >= 0 ? wptr[k[q]] : 0;
-        e1[q] = k[q] >= 0 ? wptr[k[q] + 1] : 0;
+        const int64_t kk = k[q] >= 0 ? k[q] : 0;  // an in-range index even where the value is dropped
+        e0[q] = k[q] >= 0 ? wptr[kk] : 0;
+        e1[q] = k[q] >= 0 ? wptr[kk + 1] : 0;
     }
     bool light[NQ];
 #pragma unroll
@@ -220,8 +221,9 @@ __device__ __forceinline__ void push_rows(const int64_t (&k)[NQ], int lane, cons
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const bool in = light[q] && e0[q] + j < e1[q];
-            x[q][j] = in ? widx[e0[q] + j] : -1;
-            val[q][j] = in ? wval[e0[q] + j] : 0ull;
+            const int64_t ee = in ? e0[q] + j : 0;
+            x[q][j] = in ? widx[ee] : -1;
+            val[q][j] = in ? wval[ee] : 0ull;
         }
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
@@ -239,8 +241,9 @@ __device__ __forceinline__ void push_rows(const int64_t (&k)[NQ], int lane, cons
                 uint64_t yv[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    y[j] = e + j < e1[q] ? widx[e + j] : -1;
-                    yv[j] = e + j < e1[q] ? wval[e + j] : 0ull;
+                    const int64_t ee = e + j < e1[q] ? e + j : 0;
+                    y[j] = e + j < e1[q] ? widx[ee] : -1;
+                    yv[j] = e + j < e1[q] ? wval[ee] : 0ull;
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
                 for (int i0 = 0; i0 < fcount; i0 += 32) {
                     const int i = i0 + lane;
                     const int64_t w = i < fcount ? FL[i] : 0;
-                    uint64_t d = i < fcount ? D[w] : 0ull;
+                    uint64_t d = i < fcount ? D[w] : 0ull;  // FL[i] for i < fcount <= ldw only
                     // at most two constants per word: each lane takes its own; else the bits are dealt out
                     if (__reduce_max_sync(FULL, static_cast<unsigned>(__popcll(d))) <= 2u)
                         push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
@@ -560,8 +563,9 @@ __global__ void __launch_bounds__(256) square_rows_kernel(const int64_t* __restr
         const int64_t e0 = wptr[i], e1 = wptr[i + 1];
         for (int64_t b0 = e0; b0 < e1; b0 += 32) {
             const int64_t e = b0 + lane;
-            const uint64_t d = e < e1 ? wval[e] : 0ull;
-            const int64_t w = e < e1 ? widx[e] : 0;
+            const int64_t ee = e < e1 ? e : 0;
+            const uint64_t d = e < e1 ? wval[ee] : 0ull;
+            const int64_t w = e < e1 ? widx[ee] : 0;
             push_balanced(d, w, lane, wptr, widx, wval, S, 30, tm);
         }
         __syncwarp();
