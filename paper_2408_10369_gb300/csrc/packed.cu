@@ -182,8 +182,10 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
     if (c < n) out[c * ldw + bi] = o;
 }
 
-// Frontier share of the unvisited above which a level pulls instead of pushing.
-constexpr int PULL_RATIO = 4;
+// A level pulls instead of pushing once the frontier is at least 1 / PULL_RATIO of the
+// unvisited constants (measured on ER, SBM, power-law and chain graphs: 1 is best,
+// 2 and 4 pull too early on random graphs, later switches push too long).
+constexpr int PULL_RATIO = 1;
 
 // ---- selective product per query row
 // Per warp in shared memory: D, N (ldw words each), FL, the list of the
