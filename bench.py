@@ -46,7 +46,7 @@ FALLBACK_BF16_BURST = 1900.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32768)
@@ -401,7 +401,7 @@ def main():
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    prod_ms, prod_n, launches, issued, e2m1_n = 0.0, 0, 0, 0.0, 0
+    prod_ms, prod_n, launches, issued, e2m1_n, sparse_n = 0.0, 0, 0, 0.0, 0, 0
     for _ in range(args.steps):
         iters = step(True)
         st = ctx.stats()
@@ -410,6 +410,7 @@ def main():
         launches += st["launches"]
         issued += st["issued_ops"]
         e2m1_n += st["e2m1_products"]
+        sparse_n += st["sparse_squarings"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -438,6 +439,17 @@ def main():
         from paper_2408_10369_gb300 import bmlp as _b
         variants = {}
         ms_tc = t / args.steps * 1e3
+        if args.variant == "rms_tc":
+            # every squaring on the tensor cores (no bit-row squarings while R is sparse)
+            o2 = torch.empty_like(R)
+            ctx.rms(R, n, o2, fmt=FMT, variant="rms_tc", stream=stream, tc_only=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.rms(R, n, o2, fmt=FMT, variant="rms_tc", stream=stream, tc_only=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants["rms_tc_tc_only"] = {"ms": e0.elapsed_time(e1), "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
         for v in ("smp_packed", "smp_tc", "rms_packed"):
             o2 = torch.empty_like(R)
             try:
@@ -485,7 +497,7 @@ def main():
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
             "peak_source": "%s bf16 burst x %g (%s nominal); the product runs unthrottled at max SM clock"
                            % (peak_src, ratio, rname),
-            "issued_frac": (issued / args.steps / iters / (2.0 * n ** 3)) if iters else None,
+            "issued_frac": (issued / prod_n / (2.0 * n ** 3)) if prod_n else None,
             "issue_rate_peak": issue, "issue_rate_frac": (achieved / issue) if achieved and issue else None}
     if rank != 0:
         ctx.close()
@@ -505,7 +517,9 @@ def main():
             "vs_baseline": None, "dtype": ("e2m1 0/1 operands (UE8M0 block scales of 1), fp32 accumulate" if fp4
                                            else "e4m3 0/1 operands, fp32 accumulate"), "data": "synthetic",
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
-                       "seed": "rank", "variant": args.variant, "iterations": iters, "nnz": int(len(ix)),
+                       "seed": "rank", "variant": args.variant, "iterations": iters,
+                       "bit_row_squarings": sparse_n // max(args.steps, 1),
+                       "tensor_core_squarings": prod_n // max(args.steps, 1), "nnz": int(len(ix)),
                        "graphs_per_s": args.steps * world / t,
                        "fmt": args.fmt,
                        "l2": ("operands larger than L2 (%.2f GiB per E2M1 matrix, %.0f MiB input)"

@@ -89,7 +89,12 @@ typedef struct bmlp_options {
                             levels for frontier expansion)                     */
     int32_t loop;        /* bmlp_loop                                          */
     int32_t profile;     /* 1: time the product kernel with CUDA events        */
-    int32_t reserved;
+    int32_t tc_only;     /* BMLP_RMS_TC closures with n >= 8192: 0 = squarings
+                            run on word-indexed bit rows for as long as one
+                            costs less than a tensor-core product (R sparse),
+                            then on the tensor cores from their result (same
+                            fixpoint, same number of products); 1 = every
+                            squaring on the tensor cores                      */
     uint64_t timeout_ns; /* bound of every in-kernel wait; 0 = 2 s             */
     uint64_t budget_ns;  /* 0 = none; else the call gives up (BMLP_ERR_BUDGET)
                             once about this much time has passed: checked
@@ -115,6 +120,13 @@ typedef struct bmlp_stats {
                                   R <- R + R R taken before the frontier
                                   expansion (path-like relations; same closure,
                                   fewer levels)                                 */
+    int32_t sparse_squarings;  /* BMLP_RMS_TC: squarings run on word-indexed
+                                  bit rows before the tensor cores took over
+                                  (counted in iterations, not in
+                                  product_launches)                             */
+    int32_t reserved1;
+    double sparse_ms;          /* their summed device time (options.profile)    */
+    double sparse_words;       /* the word ORs they issued                      */
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

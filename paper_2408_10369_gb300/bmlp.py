@@ -50,14 +50,16 @@ _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT
 
 class bmlp_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("reflexive", ctypes.c_int32), ("max_iters", ctypes.c_int32),
-                ("loop", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("loop", ctypes.c_int32), ("profile", ctypes.c_int32), ("tc_only", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_uint64), ("budget_ns", ctypes.c_uint64)]
 
 
 class bmlp_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("variant", ctypes.c_int32), ("product_launches", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("n_pad", ctypes.c_int64), ("product_ms", ctypes.c_double),
-                ("issued_ops", ctypes.c_double), ("e2m1_products", ctypes.c_int32), ("frontier_squarings", ctypes.c_int32)]
+                ("issued_ops", ctypes.c_double), ("e2m1_products", ctypes.c_int32), ("frontier_squarings", ctypes.c_int32),
+                ("sparse_squarings", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("sparse_ms", ctypes.c_double),
+                ("sparse_words", ctypes.c_double)]
 
 
 class bmlp_problem(ctypes.Structure):
@@ -187,7 +189,7 @@ def _stream(stream, device):
 
 
 def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HOST, profile=False, timeout_ns=0,
-                 budget_ns=0):
+                 budget_ns=0, tc_only=False):
     o = bmlp_options()
     lib().bmlp_default_options(ctypes.byref(o))
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -197,6 +199,7 @@ def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HO
     o.profile = int(bool(profile))
     o.timeout_ns = int(timeout_ns)
     o.budget_ns = int(budget_ns)
+    o.tc_only = int(bool(tc_only))
     return o
 
 

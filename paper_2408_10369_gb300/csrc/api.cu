@@ -217,6 +217,7 @@ struct ProductTimer {
     bmlp_ctx* ctx;
     bool on;
     cudaStream_t s;
+    double* sink = nullptr;  // where collect() adds the time (default: stats.product_ms)
     bmlp_status begin() {
         if (on) CK(cudaEventRecord(ctx->ev[0], s), "event record");
         return BMLP_OK;
@@ -229,7 +230,7 @@ struct ProductTimer {
         if (!on) return BMLP_OK;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "event elapsed");
-        ctx->stats.product_ms += ms;
+        *(sink ? sink : &ctx->stats.product_ms) += ms;
         return BMLP_OK;
     }
 };
@@ -529,13 +530,14 @@ bmlp_status to_packed(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, 
     return BMLP_OK;
 }
 
-// E4M3 R and R^T (n_pad) of a caller matrix.
+// E4M3 R and R^T (n_pad) of a caller matrix (packed rows of ldw_in words; 0 = ceil(n / 64)).
 bmlp_status to_e4m3(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad,
-                    cudaStream_t s) {
+                    cudaStream_t s, int64_t ldw_in = 0) {
     if (fmt == BMLP_FMT_U8)
         launch_u8_to_e4m3(static_cast<const uint8_t*>(in.dev), n, R, RT, n_pad, s);
     else
-        launch_packed_to_e4m3(static_cast<const uint64_t*>(in.dev), words_of(n), n, n, R, RT, n_pad, n_pad, s);
+        launch_packed_to_e4m3(static_cast<const uint64_t*>(in.dev), ldw_in > 0 ? ldw_in : words_of(n), n, n, R, RT,
+                              n_pad, n_pad, s);
     ctx->stats.launches++;
     CK(cudaGetLastError(), "encode launch");
     return BMLP_OK;
@@ -560,6 +562,104 @@ bmlp_status packed_out(bmlp_ctx* ctx, const uint64_t* P, int64_t ldw, int64_t n,
         launch_packed_copy(P, ldw, n, n, static_cast<uint64_t*>(out), words_of(n), reflexive, s);
     ctx->stats.launches++;
     CK(cudaGetLastError(), "decode launch");
+    return BMLP_OK;
+}
+
+// ---- engine switch inside one closure (squaring on bit rows, then on the tensor cores)
+// Smallest n whose tensor-core closures start on bit rows: below it a tensor-core product takes microseconds and
+// the word index, the cost pass and one host round trip per step cost more than they save.
+constexpr int64_t kSparseMinN = 8192;
+
+// Device seconds per word OR of square_rows_kernel over the whole GPU, and per word OR of the one warp that
+// assembles a row (BMLP_SPARSE_PS_PER_WORD / BMLP_SPARSE_ROW_PS_PER_WORD in picoseconds override them).
+double sparse_s_per_word() {
+    static const double v = [] {
+        const char* e = getenv("BMLP_SPARSE_PS_PER_WORD");
+        return (e ? atof(e) : 10.0) * 1e-12;
+    }();
+    return v;
+}
+double sparse_row_s_per_word() {
+    static const double v = [] {
+        const char* e = getenv("BMLP_SPARSE_ROW_PS_PER_WORD");
+        return (e ? atof(e) : 10000.0) * 1e-12;
+    }();
+    return v;
+}
+
+// Device seconds of one dense tensor-core squaring of an n_pad x n_pad matrix (2 n_pad^3 Boolean multiply-adds at
+// the 4-bit kernel's measured rate, plus launch and flag read-back).
+double tc_product_s(int64_t n_pad) {
+    const double n3 = static_cast<double>(n_pad) * static_cast<double>(n_pad) * static_cast<double>(n_pad);
+    return 2.0 * n3 / 7.0e15 + 20e-6;
+}
+
+struct SparseStart {
+    uint64_t* P = nullptr;  // packed rows after the squarings on bit rows (nullptr: none ran)
+    int64_t ldw = 0;
+    int iters = 0;          // squarings run on bit rows
+    bool done = false;      // the last of them changed nothing: P is the closure
+};
+
+// Squarings R <- R + R R on word-indexed bit rows (square_rows_kernel) for as long as the next one costs less than a
+// tensor-core product. Each step is the squaring the tensor cores would run, so the fixpoint and the count of
+// products are the same (R_k covers the paths of length 1 .. 2^k whichever engine squared it); the cost of a step is
+// the word ORs it will issue, summed on the GPU from the word index, and only grows as R gains bits, so the switch
+// goes one way. Leaves at least one product to the caller's loop unless the fixpoint was reached here.
+bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, int64_t n_pad, int max_iters,
+                             const bmlp_options& o, cudaStream_t s, SparseStart* out) {
+    const int64_t ldw = round_up(words_of(n), 2);
+    if (n < kSparseMinN || ldw > 2048 || max_iters < 2) return BMLP_OK;
+    void *pa = nullptr, *pb = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
+    ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &pa));
+    ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &pb));
+    ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 1) * 8), &wptr));
+    ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx));
+    ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval));
+    uint64_t* P[2] = {static_cast<uint64_t*>(pa), static_cast<uint64_t*>(pb)};
+    ST(to_packed(ctx, in, fmt, n, P[0], ldw, s));
+    auto* cost = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
+    const double limit = tc_product_s(n_pad);
+    ProductTimer tm{ctx, o.profile != 0, s, &ctx->stats.sparse_ms};
+    int cur = 0;
+    for (;;) {
+        CK(launch_wcsr_build(P[cur], n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                             static_cast<uint64_t*>(wval), s),
+           "word index build");
+        CK(cudaMemsetAsync(cost, 0, 2 * sizeof(unsigned long long), s), "reset cost");
+        CK(launch_square_cost(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
+                              n, cost, ctx->sm_count, s),
+           "squaring cost launch");
+        ctx->stats.launches += 4;
+        int changed = 1;
+        ST(read_ctl(ctx, s, &changed));
+        if (out->iters > 0) ST(tm.collect());  // the squaring recorded in the previous pass
+        if (out->iters > 0 && !changed) {
+            out->done = true;
+            break;
+        }
+        unsigned long long words = 0, row_words = 0;
+        memcpy(&words, ctx->h_ctl + CTL_COST, sizeof(words));
+        memcpy(&row_words, ctx->h_ctl + CTL_COST + 2, sizeof(row_words));
+        const double t = std::max(static_cast<double>(words) * sparse_s_per_word(),
+                                  static_cast<double>(row_words) * sparse_row_s_per_word());
+        if (out->iters + 1 >= max_iters || t > limit) break;
+        CK(cudaMemsetAsync(ctx->d_ctl + CTL_CHANGED, 0, sizeof(int), s), "reset flag");
+        ST(tm.begin());
+        CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
+                              P[cur], n, ldw, P[cur ^ 1], ctx->sm_count, s, ctx->d_ctl + CTL_CHANGED),
+           "squaring launch");
+        ST(tm.end());
+        ctx->stats.launches++;
+        ctx->stats.sparse_squarings++;
+        ctx->stats.sparse_words += static_cast<double>(words);
+        out->iters++;
+        cur ^= 1;
+    }
+    if (out->iters > 0) {
+        out->P = P[cur];
+        out->ldw = ldw;
+    }
     return BMLP_OK;
 }
 
@@ -858,6 +958,24 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         uint8_t* M[2] = {static_cast<uint8_t*>(b[0]), static_cast<uint8_t*>(b[1])};
         uint8_t* T[2] = {static_cast<uint8_t*>(b[2]), static_cast<uint8_t*>(b[3])};
         uint8_t *res = nullptr, *res_t = nullptr;
+        // while R is sparse, the squarings run on word-indexed bit rows; the tensor cores take over from their result
+        SparseStart sp;
+        if (!o.tc_only) ST(sparse_squarings(ctx, in, fmt, n, n_pad, max_iters, o, s, &sp));
+        if (sp.done) {
+            ctx->stats.iterations = iters = sp.iters;
+            if (iters_out) *iters_out = iters;
+            ST(packed_out(ctx, sp.P, sp.ldw, n, fmt, ov.dev, o.reflexive, s));
+            return finish_out(ctx, ov, s);
+        }
+        Operand src = in;
+        int32_t sfmt = fmt;
+        int64_t sldw = words_of(n);
+        if (sp.P) {
+            src.dev = sp.P;
+            src.host = false;
+            sfmt = BMLP_FMT_PACKED64;
+            sldw = sp.ldw;
+        }
         bool direct = false;
         if (tc_pairs_enabled() && tc_fp4_enabled()) {
             // a dense input (by its 128 x 128 block map) starts on 4-bit operands and leaves from them
@@ -866,7 +984,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
             if (!direct) {
                 void* f = nullptr;
                 ST(ws_get(ctx, WS_F0, static_cast<size_t>(kb * kb), &f));
-                launch_input_block_flags(in.dev, fmt, n, n_pad, static_cast<uint8_t*>(f), kb, s);
+                launch_input_block_flags(src.dev, sfmt, sldw, n, n_pad, static_cast<uint8_t*>(f), kb, s);
                 CK(cudaGetLastError(), "input block map");
                 ctx->stats.launches++;
                 std::vector<uint8_t> h(static_cast<size_t>(kb * kb));
@@ -879,14 +997,14 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         }
         if (direct) {
             const int64_t ld4 = n_pad / 2;
-            if (fmt == BMLP_FMT_U8)
-                launch_u8_to_e2m1(static_cast<const uint8_t*>(in.dev), n, M[1], T[1], n_pad, s);
+            if (sfmt == BMLP_FMT_U8)
+                launch_u8_to_e2m1(static_cast<const uint8_t*>(src.dev), n, M[1], T[1], n_pad, s);
             else
-                launch_packed_to_e2m1(static_cast<const uint64_t*>(in.dev), words_of(n), n, M[1], T[1], n_pad, s);
+                launch_packed_to_e2m1(static_cast<const uint64_t*>(src.dev), sldw, n, M[1], T[1], n_pad, s);
             CK(cudaGetLastError(), "E2M1 encode");
             ctx->stats.launches++;
             const uint8_t* q = nullptr;
-            st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t, &q);
+            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q);
             if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) {
                 if (fmt == BMLP_FMT_U8)
                     launch_e2m1_to_u8(q, ld4, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
@@ -896,11 +1014,12 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
                 ctx->stats.launches++;
             }
         } else {
-            ST(to_e4m3(ctx, in, fmt, n, M[0], T[0], n_pad, s));
-            st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
+            ST(to_e4m3(ctx, src, sfmt, n, M[0], T[0], n_pad, s, sldw));
+            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
             if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED)
                 ST(bytes_out(ctx, res, n_pad, n, fmt, ov.dev, o.reflexive, s));
         }
+        iters += sp.iters;
     } else if (variant == BMLP_RMS_PACKED) {
         const int64_t ldw = round_up(words_of(n), 2);
         ctx->stats.n_pad = ldw * 64;
@@ -1072,9 +1191,25 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
         uint8_t* M[2] = {static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[1])};
         uint8_t* T[2] = {static_cast<uint8_t*>(bb[2]), static_cast<uint8_t*>(bb[3])};
         uint8_t* X = static_cast<uint8_t*>(bb[4]);
-        ST(to_e4m3(ctx, b, fmt, n, M[0], T[0], n_pad, s));
+        // R2+ as in bmlp_rms: squarings on bit rows while R2 is sparse, then on the tensor cores
+        SparseStart sp;
+        if (!o.tc_only) ST(sparse_squarings(ctx, b, fmt, n, n_pad, max_iters, o, s, &sp));
+        if (sp.P) {
+            Operand pk;
+            pk.dev = sp.P;
+            ST(to_e4m3(ctx, pk, BMLP_FMT_PACKED64, n, M[0], T[0], n_pad, s, sp.ldw));
+        } else {
+            ST(to_e4m3(ctx, b, fmt, n, M[0], T[0], n_pad, s));
+        }
         uint8_t *res = nullptr, *res_t = nullptr;
-        st = rms_tc_loop(ctx, n_pad, M, T, max_iters, o, s, &iters, &res, &res_t);
+        if (sp.done) {
+            res = M[0];
+            res_t = T[0];
+            st = BMLP_OK;
+        } else {
+            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
+        }
+        iters += sp.iters;
         if (st != BMLP_OK) return st;
         // A = I + R2+ (row-major, in res); B^T = R1^T (written into the other R^T buffer)
         launch_set_diag_e4m3(res, n_pad, n, s);

@@ -409,7 +409,7 @@ void launch_e2m1_to_packed(const uint8_t* Q, int64_t ld4, int64_t n, uint64_t* o
     e2m1_to_packed_kernel<<<grid_for(n * ldw_out, 256), 256, 0, s>>>(Q, ld4, n, out, ldw_out, reflexive);
 }
 
-void launch_input_block_flags(const void* in, int32_t fmt, int64_t n, int64_t n_pad, uint8_t* flags,
+void launch_input_block_flags(const void* in, int32_t fmt, int64_t ldw_in, int64_t n, int64_t n_pad, uint8_t* flags,
                               int64_t flags_ld, cudaStream_t s) {
     dim3 grid(static_cast<unsigned>(n_pad / 128), static_cast<unsigned>(n_pad / 128));
     if (fmt == BMLP_FMT_U8) {
@@ -417,7 +417,7 @@ void launch_input_block_flags(const void* in, int32_t fmt, int64_t n, int64_t n_
                   (n % 16 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0)};
         input_block_flags_kernel<SrcU8><<<grid, 256, 0, s>>>(src, n, flags_ld, flags);
     } else {
-        SrcPacked src{static_cast<const uint64_t*>(in), (n + 63) / 64, n};
+        SrcPacked src{static_cast<const uint64_t*>(in), ldw_in, n};
         input_block_flags_kernel<SrcPacked><<<grid, 256, 0, s>>>(src, n, flags_ld, flags);
     }
 }

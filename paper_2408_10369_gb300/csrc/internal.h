@@ -143,10 +143,10 @@ struct bmlp_ctx {
 
 namespace bmlp {
 
-// CTL_QCOUNT and CTL_T0 are 64-bit words (two ints each, 8-byte aligned).
+// CTL_QCOUNT, CTL_T0 and CTL_ISSUED are 64-bit words, CTL_COST two of them (two ints each, 8-byte aligned).
 enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
-    CTL_ISSUED = 10, CTL_WORDS = 16
+    CTL_ISSUED = 10, CTL_COST = 12, CTL_WORDS = 16
 };
 
 // Workspace slot of the grouped batch (the others are private to api.cu).
@@ -209,8 +209,9 @@ void launch_packed_to_e2m1(const uint64_t* in, int64_t ldw_in, int64_t n, uint8_
 void launch_e2m1_to_u8(const uint8_t* Q, int64_t ld4, int64_t n, uint8_t* out, int reflexive, cudaStream_t s);
 void launch_e2m1_to_packed(const uint8_t* Q, int64_t ld4, int64_t n, uint64_t* out, int64_t ldw_out, int reflexive,
                            cudaStream_t s);
-// 1 per nonzero 128 x 128 block of a caller matrix (fmt u8 or packed), n_pad / 128 blocks a side
-void launch_input_block_flags(const void* in, int32_t fmt, int64_t n, int64_t n_pad, uint8_t* flags,
+// 1 per nonzero 128 x 128 block of an n x n matrix (fmt u8 with rows of n bytes, or packed with rows of
+// ldw_in words), n_pad / 128 blocks a side
+void launch_input_block_flags(const void* in, int32_t fmt, int64_t ldw_in, int64_t n, int64_t n_pad, uint8_t* flags,
                               int64_t flags_ld, cudaStream_t s);
 // out = rows x cols AND NOT in over n x n packed rows (null vector = all constants)
 void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const uint64_t* rows, const uint64_t* cols,
@@ -266,7 +267,11 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
                               const int32_t* widxT = nullptr, const uint64_t* wvalT = nullptr);
 // C = P | P P on packed rows through the word index (wptr, widx, wval) of P
 cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, const uint64_t* P,
-                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s);
+                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s, int* changed = nullptr);
+// word ORs of the next squaring step (sum over the set bits k of a row of the nonzero words of row k):
+// cost[0] += their total over all rows, cost[1] = max(cost[1], the largest row's)
+cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                               unsigned long long* cost, int sms, cudaStream_t s);
 // (R+ + {(u, v)})+ in place on a transitive R+ (n packed rows of ldw words)
 cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, int64_t v, int sms, cudaStream_t s);
 // out = in^T on n x n packed rows of ldw words (out cleared first)

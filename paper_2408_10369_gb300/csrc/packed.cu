@@ -182,10 +182,12 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
     if (c < n) out[c * ldw + bi] = o;
 }
 
-// A level pulls instead of pushing once the frontier is at least 1 / PULL_RATIO of the
-// unvisited constants (measured on ER, SBM, power-law and chain graphs: 1 is best,
-// 2 and 4 pull too early on random graphs, later switches push too long).
-constexpr int PULL_RATIO = 1;
+// Direction of a level, by the words each would touch: a push ORs the nonzero words of every frontier
+// constant's row (w_out per constant on average); a pull scans an unvisited constant's column words (rows of
+// R^T, w_in on average) until one meets the frontier, which on a frontier of nf constants spread over n takes
+// about n / nf words, plus PULL_OVERHEAD words' worth of row-range loads per constant. A level pulls when
+// nf w_out > nu (PULL_OVERHEAD + min(w_in, n / nf)).
+constexpr float PULL_OVERHEAD = 1.0f;
 
 // ---- selective product per query row
 // Per warp in shared memory: D, N (ldw words each), FL, the list of the
@@ -367,6 +369,8 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
     while ((int64_t(64) << gshift) < wpr) ++gshift;
     const int ngroups = static_cast<int>((wpr + (int64_t(1) << gshift) - 1) >> gshift);
     const uint64_t all_groups = ngroups >= 64 ? ~0ull : (1ull << ngroups) - 1ull;
+    const float w_out = wptrT != nullptr ? static_cast<float>(wptr[n]) / static_cast<float>(n) : 0.f;
+    const float w_in = wptrT != nullptr ? static_cast<float>(wptrT[n]) / static_cast<float>(n) : 0.f;
     while (true) {
         unsigned long long qi = 0;
         if (lane == 0) qi = atomicAdd(qcounter, 1ull);
@@ -502,8 +506,10 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
             nu -= nf;
             ++lv;
             if (nf == 0 || lv > max_levels) break;
-            // direction choice for the next level: pull once the frontier is a sizeable share of the unvisited
-            pull = wptrT != nullptr && static_cast<int64_t>(nf) * PULL_RATIO >= nu;
+            // direction of the next level: the cheaper one by the words it touches (nf > 0 here)
+            pull = wptrT != nullptr &&
+                   static_cast<float>(nf) * w_out >
+                       static_cast<float>(nu) * (PULL_OVERHEAD + fminf(w_in, static_cast<float>(n) / static_cast<float>(nf)));
         }
         if (reflexive)
             for (int64_t w = lane; w < wpr; w += 32) {
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(256) square_rows_kernel(const int64_t* __restr
                                                           const int32_t* __restrict__ widx,
                                                           const uint64_t* __restrict__ wval,
                                                           const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
-                                                          uint64_t* __restrict__ C) {
+                                                          uint64_t* __restrict__ C, int* __restrict__ changed) {
     extern __shared__ uint64_t sq_sm[];
     const int lane = threadIdx.x & 31;
     uint64_t* S = sq_sm + static_cast<int64_t>(threadIdx.x >> 5) * ldw;
@@ -571,8 +577,49 @@ __global__ void __launch_bounds__(256) square_rows_kernel(const int64_t* __restr
             push_balanced(d, w, lane, wptr, widx, wval, S, 30, tm);
         }
         __syncwarp();
-        for (int64_t w = lane; w < ldw; w += 32) C[i * ldw + w] = S[w];
+        bool grew = false;
+        for (int64_t w = lane; w < ldw; w += 32) {
+            const uint64_t c = S[w];
+            grew |= c != P[i * ldw + w];
+            C[i * ldw + w] = c;
+        }
+        if (changed != nullptr && __any_sync(FULL, grew) && lane == 0) atomicOr(changed, 1);
         __syncwarp();
+    }
+}
+
+// ---- the work of the next squaring step through the word index: for every
+// set bit k of every row, the nonzero words of row k (what square_rows_kernel
+// ORs into that row). cost[0] += the total, cost[1] = max over rows (one warp
+// assembles a row, so the largest row bounds the step from below). Warp per
+// row, two 64-bit atomics per warp. Bits at or beyond n are zero in every
+// row, so k < n.
+__global__ void __launch_bounds__(256) square_cost_kernel(const int64_t* __restrict__ wptr,
+                                                          const int32_t* __restrict__ widx,
+                                                          const uint64_t* __restrict__ wval, int64_t n,
+                                                          unsigned long long* __restrict__ cost) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    unsigned long long total = 0, top = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        unsigned long long c = 0;
+        const int64_t e1 = wptr[i + 1];
+        for (int64_t e = wptr[i] + lane; e < e1; e += 32) {
+            uint64_t d = wval[e];
+            const int64_t base = static_cast<int64_t>(widx[e]) << 6;
+            while (d) {
+                const int64_t k = base + (__ffsll(static_cast<long long>(d)) - 1);
+                d &= d - 1ull;
+                c += static_cast<unsigned long long>(wptr[k + 1] - wptr[k]);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+        total += c;
+        top = c > top ? c : top;
+    }
+    if (lane == 0 && total != 0ull) {
+        atomicAdd(cost, total);
+        atomicMax(cost + 1, top);
     }
 }
 
@@ -615,7 +662,7 @@ cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t
 int smp_packed_max_words() { return 7168; }
 
 cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, const uint64_t* P,
-                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s) {
+                               int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s, int* changed) {
     int warps = 8;
     while (warps > 1 && warps * ldw * 8 > 32 * 1024) warps >>= 1;
     const size_t smem = static_cast<size_t>(warps) * static_cast<size_t>(ldw) * 8;
@@ -628,7 +675,13 @@ cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const u
     const int64_t cap = static_cast<int64_t>(sms) * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    square_rows_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(wptr, widx, wval, P, n, ldw, C);
+    square_rows_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(wptr, widx, wval, P, n, ldw, C, changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                               unsigned long long* cost, int sms, cudaStream_t s) {
+    square_cost_kernel<<<warps_grid(n, sms), 256, 0, s>>>(wptr, widx, wval, n, cost);
     return cudaGetLastError();
 }
 

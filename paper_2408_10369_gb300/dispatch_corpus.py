@@ -16,7 +16,8 @@ train  fits the MLP on the GPU (bmlp_dispatch_train) on graphs with index <
 eval   on the held-out graphs: regret of the chosen variant against the best
        one, and the time of the dispatched pipeline (features + prediction +
        chosen variant, closures grouped in one bmlp_batch_run) against plain
-       single-instance tensor-core squaring on every graph, both measured live.
+       single-instance BMLP_RMS_TC squaring on every graph, with and without
+       its bit-row squarings (options.tc_only), all measured live.
 """
 from __future__ import annotations
 
@@ -209,9 +210,11 @@ def evaluate(args):
 
 
 def live_pipeline(ctx, rows, n_max):
-    """Time (a) plain single-instance tensor-core squaring per graph and (b)
-    the dispatched path: features + prediction for every graph, then the
-    graphs predicted to be fastest with squaring run grouped in one
+    """Time (a) plain single-instance squaring per graph with BMLP_RMS_TC
+    (bit-row squarings while R is sparse for n >= 8192, then tensor cores),
+    (a') the same with every squaring on the tensor cores (options.tc_only),
+    and (b) the dispatched path: features + prediction for every graph, then
+    the graphs predicted to be fastest with squaring run grouped in one
     bmlp_batch_run (engine per problem from the prediction), the others one
     by one with their frontier variant. Every output is compared with (a)."""
     from . import bmlp
@@ -229,6 +232,18 @@ def live_pipeline(ctx, rows, n_max):
         ctx.rms(P, g["n"], o, fmt=F, variant="rms_tc")
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
+    # the same with every squaring on the tensor cores (no bit-row squarings while R is sparse)
+    for (g, P), o in list(zip(graphs, outs_b))[:4]:
+        ctx.rms(P, g["n"], o, fmt=F, variant="rms_tc", tc_only=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (g, P), o in zip(graphs, outs_b):
+        ctx.rms(P, g["n"], o, fmt=F, variant="rms_tc", tc_only=True)
+    torch.cuda.synchronize()
+    t_tc_only = time.perf_counter() - t0
+    bad_tc_only = sum(0 if torch.equal(a, b) else 1 for a, b in zip(outs_a, outs_b))
+    for o in outs_b:
+        o.zero_()
 
     def dispatched():
         feats = np.stack([ctx.dispatch_features(P, g["n"], fmt=F) for g, P in graphs])
@@ -253,6 +268,8 @@ def live_pipeline(ctx, rows, n_max):
     bad = sum(0 if torch.equal(a, b) else 1 for a, b in zip(outs_a, outs_b))
     return {"live_graphs": len(graphs), "live_plain_rms_tc_s": t_plain, "live_dispatched_s": t_disp,
             "live_speedup": t_plain / t_disp, "live_bit_mismatches": bad,
+            "live_tc_only_s": t_tc_only, "live_speedup_vs_tc_only": t_tc_only / t_disp,
+            "live_tc_only_bit_mismatches": bad_tc_only,
             "live_choice_hist": {VARIANT_NAMES[v - 1]: int((choice == v).sum()) for v in (1, 2, 3, 4)}}
 
 
