@@ -165,6 +165,23 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
                      const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
 
 /*
+ * bmlp_rms_alg1 - R1+ in the literal form of paper Algorithm 1 (Sec. 3.3):
+ *
+ *     R* = (I + R1)^(2^k)   squaring until a squaring changes nothing
+ *     out = R* R1           one more product
+ *
+ * Same result as bmlp_rms (the squaring form R <- R + R R from R1 saves the
+ * last product). *iters_out receives the squarings plus 1: ceil(log2 L0) + 2,
+ * with L0 the longest shortest path between two different constants (2 when
+ * L0 <= 1). The squarings run as bmlp_rms with BMLP_RMS_TC (bit-row start,
+ * operand forms, options.tc_only), the final product on the tensor cores
+ * with E4M3 operands. Variants: BMLP_RMS_TC or BMLP_AUTO (the same). R and
+ * out as in bmlp_rms; options.reflexive gives I + R1+.
+ */
+bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out,
+                          const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);
+
+/*
  * bmlp_smp - partially grounded queries r2(c, Y) (BMLP-SMP, paper Sec. 3.3
  * Eq. 5, Algorithm 2):
  *

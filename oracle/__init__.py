@@ -15,6 +15,7 @@ What it computes (paper Sec. 2 Eq. 1, Sec. 3.3 Eq. 4-5, Sec. 3.4 Thm. 1):
 * ``warshall``     Warshall triple loop (small n)
 * ``compose_rows`` rows of (I + R2+) R1 by search
 * ``rms_iterations`` number of products the squaring fixpoint issues
+* ``alg1_products`` number of products of Algorithm 1 as printed
 * ``is_foreign``   rows of the composed program P3 u P4 u P5 of Sec. 3.4
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
@@ -123,6 +124,21 @@ def rms_iterations(L: int) -> int:
     if L <= 1:
         return 1
     return int(math.ceil(math.log2(L))) + 1
+
+
+def alg1_products(L0: int) -> int:
+    """Products issued by Algorithm 1 as printed: squarings of I + R1 until
+    one changes nothing, then the product with R1.
+
+    After t squarings (I + R1)^(2^t) covers the paths of length 0..2^t (the
+    diagonal is there from I), so it equals I + R1+ once 2^t >= L0, the
+    longest shortest path between two different constants, and one more
+    squaring confirms it: ceil(log2 L0) + 1 squarings when L0 >= 2, one when
+    L0 <= 1; plus the final product.
+    """
+    if L0 <= 1:
+        return 2
+    return int(math.ceil(math.log2(L0))) + 2
 
 
 def smp(n, indptr, indices, src_rows):

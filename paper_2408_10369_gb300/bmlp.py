@@ -115,6 +115,7 @@ def lib():
             L.bmlp_default_options.restype = None
             L.bmlp_get_stats.argtypes = [vp, ctypes.POINTER(bmlp_stats)]
             L.bmlp_rms.argtypes = [vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options), ctypes.POINTER(i32), vp]
+            L.bmlp_rms_alg1.argtypes = [vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options), ctypes.POINTER(i32), vp]
             L.bmlp_smp.argtypes = [vp, vp, i64, i32, vp, i64, vp, ctypes.POINTER(bmlp_options),
                                    ctypes.POINTER(i32), vp]
             L.bmlp_compose.argtypes = [vp, vp, vp, i64, i32, vp, ctypes.POINTER(bmlp_options),
@@ -250,6 +251,15 @@ class Context:
         it = ctypes.c_int32(0)
         self._check(self._L.bmlp_rms(self.handle, _ptr(R), int(n), int(fmt), _ptr(out), ctypes.byref(o),
                                      ctypes.byref(it), _stream(stream, self.device)))
+        return it.value
+
+    def rms_alg1(self, R, n, out, fmt=BMLP_FMT_U8, stream=None, **opt):
+        """bmlp_rms_alg1: out = (I + R1)^(2^k) R1 = R1+ (Algorithm 1 as printed).
+        Returns the squarings plus the final product."""
+        o = make_options(**opt)
+        it = ctypes.c_int32(0)
+        self._check(self._L.bmlp_rms_alg1(self.handle, _ptr(R), int(n), int(fmt), _ptr(out), ctypes.byref(o),
+                                          ctypes.byref(it), _stream(stream, self.device)))
         return it.value
 
     def smp(self, R, n, src_rows, q, out_rows, fmt=BMLP_FMT_U8, stream=None, **opt):

@@ -663,6 +663,31 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
     return BMLP_OK;
 }
 
+// X = A B for E4M3 0/1 operands on the tensor cores: A row-major, B given as B^T (both n_pad x n_pad); one plain
+// product (no OR with an old R) with exact FP32 counts thresholded to 0/1.
+bmlp_status tc_plain_product(bmlp_ctx* ctx, const uint8_t* A, const uint8_t* BT, int64_t n_pad, uint8_t* X,
+                             const bmlp_options& o, cudaStream_t s) {
+    CUtensorMap mapA, mapB;
+    ST(make_tmap(ctx, &mapA, A, n_pad, n_pad, n_pad, TC_BM));
+    ST(make_tmap(ctx, &mapB, BT, n_pad, n_pad, n_pad, TC_BN));
+    TcParams p{};
+    p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+    p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+    p.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
+    p.mode = TC_MODE_PLAIN;
+    p.ld = n_pad;
+    p.out_r = X;
+    p.changed = ctx->d_ctl + CTL_CHANGED;
+    p.error = ctx->d_ctl + CTL_ERROR;
+    p.wait_cycles = wait_cycles(ctx, o);
+    const int tiles = p.m_tiles * p.n_tiles;
+    CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+    CK(launch_tc_product(mapA, mapB, p, tiles < ctx->sm_count ? tiles : ctx->sm_count, s), "product launch");
+    ctx->stats.product_launches++;
+    ctx->stats.launches += 2;
+    return read_ctl(ctx, s, nullptr);
+}
+
 bmlp_options resolve(const bmlp_options* o) {
     bmlp_options r;
     bmlp_default_options(&r);
@@ -1213,28 +1238,11 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
         if (st != BMLP_OK) return st;
         // A = I + R2+ (row-major, in res); B^T = R1^T (written into the other R^T buffer)
         launch_set_diag_e4m3(res, n_pad, n, s);
+        ctx->stats.launches++;
         uint8_t* r1t = (res_t == T[0]) ? T[1] : T[0];
         uint8_t* r1 = (res == M[0]) ? M[1] : M[0];
         ST(to_e4m3(ctx, a, fmt, n, r1, r1t, n_pad, s));
-        CUtensorMap mapA, mapB;
-        ST(make_tmap(ctx, &mapA, res, n_pad, n_pad, n_pad, TC_BM));
-        ST(make_tmap(ctx, &mapB, r1t, n_pad, n_pad, n_pad, TC_BN));
-        TcParams p{};
-        p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
-        p.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
-        p.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
-        p.mode = TC_MODE_PLAIN;
-        p.ld = n_pad;
-        p.out_r = X;
-        p.changed = ctx->d_ctl + CTL_CHANGED;
-        p.error = ctx->d_ctl + CTL_ERROR;
-        p.wait_cycles = wait_cycles(ctx, o);
-        const int tiles = p.m_tiles * p.n_tiles;
-        CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
-        CK(launch_tc_product(mapA, mapB, p, tiles < ctx->sm_count ? tiles : ctx->sm_count, s), "product launch");
-        ctx->stats.product_launches++;
-        ctx->stats.launches += 3;
-        ST(read_ctl(ctx, s, nullptr));
+        ST(tc_plain_product(ctx, res, r1t, n_pad, X, o, s));
         ST(bytes_out(ctx, X, n_pad, n, fmt, ov.dev, 0, s));
     } else {
         const int64_t ldw = round_up(words_of(n), 2);
@@ -1263,6 +1271,70 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
     }
     ctx->stats.iterations = iters;
     if (iters_out) *iters_out = iters;
+    return finish_out(ctx, ov, s);
+}
+
+// Algorithm 1 as printed: R* = (I + R1)^(2^k) by squaring until a squaring changes nothing, then one product
+// R* R1 = R1+. With I inside R the squaring step R <- R + R R is R <- R R, so the squaring loop of bmlp_rms run on
+// I + R1 is Algorithm 1's loop (same engines and switches); the last product runs on the tensor cores.
+bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+                          int32_t* iters_out, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (iters_out) *iters_out = 0;
+    if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
+    if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    if (n == 0) return BMLP_OK;
+    if (!R || !out) return set_err(ctx, BMLP_ERR_INVALID_ARG, "null matrix pointer");
+    if (n > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "n > 2^20");
+    DeviceGuard g(ctx->device);
+    bmlp_options o = resolve(opts);
+    if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "Algorithm 1 runs as tensor-core squaring (variant %d)", o.variant);
+    reset_stats(ctx, BMLP_RMS_TC, n);
+    ST(begin_call(ctx, o, s));
+    Operand a;
+    OutView ov;
+    ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &a));
+    ST(stage_out(ctx, out, fmt_bytes(fmt, n, n), WS_OUT, &ov));
+    // I + R1 as packed rows
+    const int64_t ldw = words_of(n);
+    void *p0 = nullptr, *q = nullptr;
+    ST(ws_get(ctx, WS_PIPE0, static_cast<size_t>(n * ldw * 8), &p0));
+    ST(ws_get(ctx, WS_PIPE1, static_cast<size_t>(n * ldw * 8), &q));
+    if (fmt == BMLP_FMT_U8) {
+        launch_u8_to_packed(static_cast<const uint8_t*>(a.dev), n, static_cast<uint64_t*>(p0), ldw, s);
+        launch_packed_copy(static_cast<uint64_t*>(p0), ldw, n, n, static_cast<uint64_t*>(p0), ldw, 1, s);
+    } else {
+        launch_packed_copy(static_cast<const uint64_t*>(a.dev), ldw, n, n, static_cast<uint64_t*>(p0), ldw, 1, s);
+    }
+    CK(cudaGetLastError(), "encode launch");
+    // squarings of I + R1 until one changes nothing: q = I + R1+
+    bmlp_options o2 = o;
+    o2.variant = BMLP_RMS_TC;
+    o2.reflexive = 0;
+    o2.loop = BMLP_LOOP_HOST;
+    int32_t squarings = 0;
+    ST(bmlp_rms(ctx, p0, n, BMLP_FMT_PACKED64, q, &o2, &squarings, s));
+    ctx->stats.launches += fmt == BMLP_FMT_U8 ? 2 : 1;
+    // R1+ = (I + R1+) R1 on the tensor cores
+    const int64_t n_pad = round_up(n, TC_PAD);
+    const size_t bytes = static_cast<size_t>(n_pad * n_pad);
+    void* bb[5];
+    ST(ws_get(ctx, WS_M0, bytes, &bb[0]));
+    ST(ws_get(ctx, WS_M1, bytes, &bb[1]));
+    ST(ws_get(ctx, WS_T0, bytes, &bb[2]));
+    ST(ws_get(ctx, WS_T1, bytes, &bb[3]));
+    ST(ws_get(ctx, WS_M2, bytes, &bb[4]));
+    Operand qs;
+    qs.dev = q;
+    ST(to_e4m3(ctx, qs, BMLP_FMT_PACKED64, n, static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[2]), n_pad, s,
+               ldw));
+    ST(to_e4m3(ctx, a, fmt, n, static_cast<uint8_t*>(bb[1]), static_cast<uint8_t*>(bb[3]), n_pad, s));
+    ST(tc_plain_product(ctx, static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[3]), n_pad,
+                        static_cast<uint8_t*>(bb[4]), o, s));
+    ST(bytes_out(ctx, static_cast<uint8_t*>(bb[4]), n_pad, n, fmt, ov.dev, o.reflexive, s));
+    ctx->stats.iterations = squarings + 1;
+    if (iters_out) *iters_out = squarings + 1;
     return finish_out(ctx, ov, s);
 }
 

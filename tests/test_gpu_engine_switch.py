@@ -154,3 +154,77 @@ def test_compose_switch(ctx, d2):
     assert ctx.stats()["sparse_squarings"] >= 1
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n),
                                   oracle.compose_rows(n, csr1, csr2))
+
+
+# ------------------------------------------------ Algorithm 1 as printed --
+def offdiag_L0(n, ip, ix):
+    """Longest shortest path between two different constants (BFS distances from scipy)."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    import scipy.sparse as sp
+    A = sp.csr_matrix((np.ones(len(ix)), ix, ip), shape=(n, n))
+    D = csgraph.shortest_path(A, method="D", unweighted=True)
+    np.fill_diagonal(D, 0)
+    fin = D[np.isfinite(D)]
+    return int(fin.max()) if fin.size else 0
+
+
+@pytest.mark.parametrize("fmt", ["u8", "packed"])
+@pytest.mark.parametrize("n,d,seed", [(1, 0.0, 0), (2, 1.0, 1), (65, 1.3, 2), (300, 1.1, 3), (1000, 2.0, 4),
+                                      (2500, 1.2, 5)])
+def test_alg1_literal_form(ctx, fmt, n, d, seed):
+    """(I + R1)^(2^k) R1 through bmlp_rms_alg1: the closure's bits, and
+    squarings + 1 products with the squarings fixed by L0."""
+    ip, ix = wl.er_graph(n, d, seed)
+    want = oracle.closure(n, ip, ix)
+    if fmt == "u8":
+        R = dev(wl.dense_u8(n, ip, ix))
+        out = torch.zeros_like(R)
+        it = ctx.rms_alg1(R, n, out, fmt=bmlp.BMLP_FMT_U8)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+    else:
+        R = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+        out = torch.zeros_like(R)
+        it = ctx.rms_alg1(R, n, out, fmt=bmlp.BMLP_FMT_PACKED64)
+        torch.cuda.synchronize()
+        got = wl.unpack_rows(out.cpu().numpy().view(np.uint64), n)
+    np.testing.assert_array_equal(got, want)
+    assert it == oracle.alg1_products(offdiag_L0(n, ip, ix))
+
+
+def test_alg1_self_loop_and_reflexive(ctx):
+    for loop in (0, 1):
+        R = torch.tensor([[loop]], dtype=torch.uint8, device="cuda")
+        out = torch.zeros_like(R)
+        assert ctx.rms_alg1(R, 1, out) == 2
+        assert int(out.item()) == loop
+    n = 700
+    ip, ix = wl.er_graph(n, 1.4, 12)
+    R = dev(wl.dense_u8(n, ip, ix))
+    out = torch.zeros_like(R)
+    ctx.rms_alg1(R, n, out, reflexive=True)
+    want = oracle.closure(n, ip, ix)
+    np.fill_diagonal(want, 1)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    with pytest.raises(bmlp.BmlpError) as e:
+        ctx.rms_alg1(R, n, out, variant="smp_packed")
+    assert e.value.status == bmlp.BMLP_ERR_INVALID_ARG
+
+
+def test_alg1_large_dag_with_bit_row_start(ctx):
+    """n = 9,000 DAG (forward chain plus forward shortcuts, so L0 = L): the
+    squarings start on bit rows; bits and the product count against the oracle."""
+    n = 9000
+    a, b = wl.random_pairs(n, 90, 13)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keep = lo != hi
+    src = np.concatenate([np.arange(n - 1), lo[keep]])
+    dst = np.concatenate([np.arange(1, n), hi[keep]])
+    ip, ix = wl.csr_from_pairs(n, src, dst)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros_like(P)
+    it = ctx.rms_alg1(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64)
+    torch.cuda.synchronize()
+    assert ctx.stats()["sparse_squarings"] >= 1
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), oracle.closure(n, ip, ix))
+    assert it == oracle.alg1_products(oracle.longest_shortest_path(n, ip, ix))

@@ -336,6 +336,58 @@ def test_rms_iterations_chain_and_cycle():
         assert k == oracle.rms_iterations(n)
 
 
+def offdiag_longest_shortest(m):
+    """L0, the longest shortest path between two different constants, by
+    Boolean powers: the largest k at which some pair i != j is first reached."""
+    n = m.shape[0]
+    reach = np.eye(n, dtype=np.uint8)
+    p = np.eye(n, dtype=np.uint8)
+    L0 = 0
+    for k in range(1, n + 1):
+        p = bool_mm(p, m)
+        if (p & (1 - reach)).any():
+            L0 = k
+        reach |= p
+    return L0
+
+
+def alg1_literal(m):
+    """Algorithm 1 as printed, with numpy matmul: R* = I + R1 squared until a
+    squaring changes nothing, then R* R1. Returns (R1+, products)."""
+    n = m.shape[0]
+    r = m | np.eye(n, dtype=np.uint8)
+    k = 0
+    while True:
+        k += 1
+        nr = bool_mm(r, r)
+        if np.array_equal(nr, r):
+            break
+        r = nr
+    return bool_mm(r, m), k + 1
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_alg1_literal_form_matches_closure_and_count(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 70))
+    d = float(rng.uniform(0.3, 3.0))
+    ip, ix = wl.er_graph(n, d, 100 + seed)
+    m = wl.dense_u8(n, ip, ix)
+    got, k = alg1_literal(m)
+    np.testing.assert_array_equal(got, oracle.closure(n, ip, ix))
+    assert k == oracle.alg1_products(offdiag_longest_shortest(m))
+
+
+def test_alg1_products_chain_and_cycle():
+    """A chain or a cycle on n constants has L0 = n - 1."""
+    for n in (2, 3, 4, 5, 9, 17, 40):
+        for dst in (np.arange(1, n), (np.arange(n) + 1) % n):
+            src = np.arange(len(dst))
+            m = wl.dense_u8(n, *wl.csr_from_pairs(n, src, dst))
+            _, k = alg1_literal(m)
+            assert k == oracle.alg1_products(n - 1)
+
+
 # --------------------------------------------------------------- SMP --
 @pytest.mark.parametrize("n,d,q,seed", [(64, 1.2, 5, 0), (200, 2.0, 9, 1), (130, 0.7, 16, 2)])
 def test_smp_is_union_of_closure_rows(n, d, q, seed):
