@@ -89,7 +89,7 @@ typedef struct bmlp_options {
                             levels for frontier expansion)                     */
     int32_t loop;        /* bmlp_loop                                          */
     int32_t profile;     /* 1: time the product kernel with CUDA events        */
-    int32_t tc_only;     /* BMLP_RMS_TC closures with n >= 8192: 0 = squarings
+    int32_t tc_only;     /* BMLP_RMS_TC closures with n >= 4096: 0 = squarings
                             run on word-indexed bit rows for as long as one
                             costs less than a tensor-core product (R sparse),
                             then on the tensor cores from their result (same
@@ -317,7 +317,7 @@ typedef struct bmlp_problem {
  * the tensor cores or on packed rows, chosen per size bucket by the autotuner
  * (bmlp_batch_autotune) or forced by opts->variant (BMLP_RMS_TC /
  * BMLP_RMS_PACKED; compositions always use the tensor cores).
- * Problems large enough to fill the GPU alone (n >= 8192 by default, the
+ * Problems large enough to fill the GPU alone (n >= 4096 by default, the
  * environment variable BMLP_BATCH_SOLO_N changes it, 0 = never) that are not
  * forced onto packed rows run one after another on the single-problem
  * tensor-core path instead (bmlp_rms / bmlp_compose with BMLP_RMS_TC, whose

@@ -267,7 +267,7 @@ bool tc_duo_enabled() {
 int64_t batch_solo_n() {
     static const int64_t v = [] {
         const char* e = getenv("BMLP_BATCH_SOLO_N");
-        return e ? static_cast<int64_t>(atoll(e)) : int64_t(8192);
+        return e ? static_cast<int64_t>(atoll(e)) : int64_t(4096);
     }();
     return v;
 }
@@ -568,7 +568,9 @@ bmlp_status packed_out(bmlp_ctx* ctx, const uint64_t* P, int64_t ldw, int64_t n,
 // ---- engine switch inside one closure (squaring on bit rows, then on the tensor cores)
 // Smallest n whose tensor-core closures start on bit rows: below it a tensor-core product takes microseconds and
 // the word index, the cost pass and one host round trip per step cost more than they save.
-constexpr int64_t kSparseMinN = 8192;
+constexpr int64_t kSparseMinN = 4096;
+// Fixed device and host time of one bit-row step besides its word ORs: word index, cost pass, flag read-back.
+constexpr double kSparseStepS = 20e-6;
 
 // Device seconds per word OR of square_rows_kernel over the whole GPU, and per word OR of the one warp that
 // assembles a row (BMLP_SPARSE_PS_PER_WORD / BMLP_SPARSE_ROW_PS_PER_WORD in picoseconds override them).
@@ -641,8 +643,8 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
         unsigned long long words = 0, row_words = 0;
         memcpy(&words, ctx->h_ctl + CTL_COST, sizeof(words));
         memcpy(&row_words, ctx->h_ctl + CTL_COST + 2, sizeof(row_words));
-        const double t = std::max(static_cast<double>(words) * sparse_s_per_word(),
-                                  static_cast<double>(row_words) * sparse_row_s_per_word());
+        const double t = kSparseStepS + std::max(static_cast<double>(words) * sparse_s_per_word(),
+                                                 static_cast<double>(row_words) * sparse_row_s_per_word());
         if (out->iters + 1 >= max_iters || t > limit) break;
         CK(cudaMemsetAsync(ctx->d_ctl + CTL_CHANGED, 0, sizeof(int), s), "reset flag");
         ST(tm.begin());

@@ -126,7 +126,7 @@ def test_single_problem_device_loop(ctx, variant, n, d, seed):
 
 @pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
 def test_batch_mixes_solo_and_grouped_problems(ctx, fmt):
-    """Problems with n >= 8192 run on the single-problem path (4-bit operands
+    """Problems with n >= 4096 run on the single-problem path (4-bit operands
     once dense), the others in the grouped batch; every output and every
     iteration count as for the problem alone."""
     items, expect, keep = [], [], []

@@ -1,6 +1,6 @@
 """Squarings on bit rows before the tensor cores: the engine switch inside one closure.
 
-For n >= 8192 a tensor-core closure first squares R on word-indexed bit rows
+For n >= 4096 a tensor-core closure first squares R on word-indexed bit rows
 for as long as one such step is predicted to cost less than a tensor-core
 product, then hands the squared R to the tensor cores (or stops there when a
 step changed nothing). Every step is the same R <- R + R R whichever engine

@@ -205,10 +205,16 @@ def test_squaring_operand_forms(ctx):
     assert st["e2m1_products"] == st["product_launches"] == it
     n = 4500
     ip, ix = shortcut_case(n, "chain", 3)
-    got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), "rms_tc")
-    np.testing.assert_array_equal(got, oracle.closure(n, ip, ix))
+    want = oracle.closure(n, ip, ix)
+    got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), "rms_tc", tc_only=True)
+    np.testing.assert_array_equal(got, want)
     st = ctx.stats()
     assert 0 < st["e2m1_products"] < st["product_launches"] == it
+    # by default the sparse first squarings run on bit rows; the tensor cores finish
+    got, it2 = run_rms(ctx, wl.dense_u8(n, ip, ix), "rms_tc")
+    np.testing.assert_array_equal(got, want)
+    st = ctx.stats()
+    assert st["sparse_squarings"] >= 1 and st["sparse_squarings"] + st["product_launches"] == it2 == it
 
 
 def test_smp_wide_rows_long_paths(ctx):
