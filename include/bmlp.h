@@ -124,7 +124,9 @@ typedef struct bmlp_stats {
                                   bit rows before the tensor cores took over
                                   (counted in iterations, not in
                                   product_launches)                             */
-    int32_t reserved1;
+    int32_t sliced_closures;   /* BMLP_SMP_PACKED closures whose first squaring
+                                  widened the rows: every row expanded 64
+                                  sources at a time (bit-sliced frontiers)      */
     double sparse_ms;          /* their summed device time (options.profile)    */
     double sparse_words;       /* the word ORs they issued                      */
 } bmlp_stats;

@@ -76,6 +76,11 @@ constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
 constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
+// A full frontier closure expands 64 sources at a time when R + R R has more than this many times the nonzero
+// words of R (rows that widen fast reach most constants within a few levels).
+constexpr double kSlicedMinGrowth = 3.0;
+// ... and when no column of R has more than this many times the mean nonzero words of a column.
+constexpr double kSlicedMaxSkew = 8.0;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 
@@ -249,6 +254,16 @@ bool tc_pairs_enabled() {
 bool tc_fp4_enabled() {
     static const bool on = [] {
         const char* v = getenv("BMLP_TC_FP4");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+// Full frontier closures whose first squaring widens the rows run 64 sources per CTA (bit-sliced) unless
+// BMLP_SMP_SLICED=0.
+bool smp_sliced_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_SMP_SLICED");
         return !(v && v[0] == '0');
     }();
     return on;
@@ -615,7 +630,7 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
     void *pa = nullptr, *pb = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
     ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &pa));
     ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &pb));
-    ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 1) * 8), &wptr));
+    ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 2) * 8), &wptr));
     ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx));
     ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval));
     uint64_t* P[2] = {static_cast<uint64_t*>(pa), static_cast<uint64_t*>(pb)};
@@ -707,7 +722,9 @@ void reset_stats(bmlp_ctx* ctx, int variant, int64_t n_pad) {
 int pick_variant_rms(int64_t) { return BMLP_RMS_TC; }
 
 // Frontier expansion (Algorithm 2) on packed rows for the sources `src`
-// (device, q x ldw_src words). out: device, q x ldw_out words.
+// (device, q x ldw_src words). out: device, q x ldw_out words. square_first:
+// a full closure (src = the identity, q = n), which may square R first
+// (path-like R) or expand 64 sources at a time (rows that widen fast).
 bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t n, const uint64_t* src,
                            int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out, const bmlp_options& o,
                            cudaStream_t s, int* levels, bool square_first = false) {
@@ -716,7 +733,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         return set_err(ctx, BMLP_ERR_UNSUPPORTED, "packed frontier path supports n <= %d", smp_packed_max_words() * 64);
     void *P = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
     ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &P));
-    ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 1) * 8), &wptr));
+    ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 2) * 8), &wptr));
     ST(ws_get(ctx, WS_WIDX, static_cast<size_t>(n * ldw * 4), &widx));
     ST(ws_get(ctx, WS_WVAL, static_cast<size_t>(n * ldw * 8), &wval));
     ST(to_packed(ctx, R, fmt, n, static_cast<uint64_t*>(P), ldw, s));
@@ -724,6 +741,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                          static_cast<uint64_t*>(wval), s),
        "word index build");
     ctx->stats.launches += 3;
+    bool dense_reach = false;
     if (square_first && n >= kSquareMinN && ldw <= 2048) {
         // Long shortest paths make the frontier latency-bound (one level per path step). closure(R + R R) =
         // closure(R) with half the levels, so R is squared while that keeps its rows within ~1.5x the nonzero
@@ -731,7 +749,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         // it saves in levels, and the last squaring is dropped.
         void *P2 = nullptr, *wptr2 = nullptr, *widx2 = nullptr, *wval2 = nullptr;
         ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &P2));
-        ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 1) * 8), &wptr2));
+        ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 2) * 8), &wptr2));
         ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx2));
         ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval2));
         auto words = [&](const void* wp, int64_t* total) -> bmlp_status {
@@ -752,7 +770,11 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                "word index build");
             ctx->stats.launches += 4;
             ST(words(wptr2, &W2));
-            if (W2 > W + W / 2) break;
+            if (W2 > W + W / 2) {
+                // the first squaring widens the rows fast: closure rows fill up within a few levels
+                dense_reach = k == 0 && static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
+                break;
+            }
             std::swap(P, P2);
             std::swap(wptr, wptr2);
             std::swap(widx, widx2);
@@ -764,7 +786,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     // transposed word index for the pull direction (levels whose frontier is large)
     void *PT = nullptr, *wptrT = nullptr, *widxT = nullptr, *wvalT = nullptr;
     ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &PT));
-    ST(ws_get(ctx, WS_WPTRT, static_cast<size_t>((n + 1) * 8), &wptrT));
+    ST(ws_get(ctx, WS_WPTRT, static_cast<size_t>((n + 2) * 8), &wptrT));
     ST(ws_get(ctx, WS_WIDXT, static_cast<size_t>(n * ldw * 4), &widxT));
     ST(ws_get(ctx, WS_WVALT, static_cast<size_t>(n * ldw * 8), &wvalT));
     CK(launch_bit_transpose(static_cast<uint64_t*>(P), static_cast<uint64_t*>(PT), n, ldw, s), "bit transpose");
@@ -774,6 +796,35 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     ctx->stats.launches += 4;
     CK(cudaMemsetAsync(ctx->d_ctl + CTL_LEVELS, 0, 3 * sizeof(int), s), "reset level and query counters");
     ProductTimer tm{ctx, o.profile != 0, s};
+    if (dense_reach && smp_sliced_enabled()) {
+        // no hubs among the columns: a pull scans a hub's whole in-list at every level until all active sources
+        // reach it (power-law targets), which the one-query-per-warp kernel avoids
+        int64_t wt[2] = {0, 0};
+        CK(cudaMemcpyAsync(wt, static_cast<const int64_t*>(wptrT) + n, sizeof(wt), cudaMemcpyDeviceToHost, s),
+           "read column word counts");
+        CK(cudaStreamSynchronize(s), "read column word counts");
+        dense_reach = static_cast<double>(wt[1]) * static_cast<double>(n) <= kSlicedMaxSkew * static_cast<double>(wt[0]);
+    }
+    if (dense_reach && smp_sliced_enabled()) {
+        // every row of the closure (src = the identity), 64 sources per CTA over the word index of R^T
+        void* scratch = nullptr;
+        ST(ws_get(ctx, WS_V, static_cast<size_t>(smp_sliced_grid(n, ctx->sm_count) * 3 * n * 8), &scratch));
+        ST(tm.begin());
+        CK(launch_smp_sliced(static_cast<int64_t*>(wptrT), static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT),
+                             n, static_cast<uint64_t*>(scratch), out, ldw_out,
+                             reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_QCOUNT), ctx->d_ctl + CTL_LEVELS,
+                             static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF), ctx->sm_count, s,
+                             deadline_of(ctx)),
+           "sliced frontier kernel launch");
+        ST(tm.end());
+        ctx->stats.product_launches++;
+        ctx->stats.launches++;
+        ctx->stats.sliced_closures++;
+        ST(read_ctl(ctx, s, nullptr));
+        ST(tm.collect());
+        *levels = ctx->h_ctl[CTL_LEVELS];
+        return BMLP_OK;
+    }
     ST(tm.begin());
     CK(launch_smp_packed(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval), n, ldw,
                          src, ldw_src, q, out, ldw_out, ctx->d_ctl + CTL_LEVELS, ctx->d_ctl + CTL_QCOUNT, o.reflexive,

@@ -257,7 +257,8 @@ cudaError_t prepare_tc_group();
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
                                   int or_a, int* changed, int sms, cudaStream_t s, Deadline dl = Deadline{0, nullptr, nullptr});
 // word-CSR of packed rows: counts -> (exclusive scan by caller kernel) -> fill
-// (widx / wval must hold n * ldw entries: the dense worst case)
+// (widx / wval must hold n * ldw entries: the dense worst case; wptr holds n + 2 entries, wptr[n + 1] receives
+// the largest row's count)
 cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx,
                               uint64_t* wval, cudaStream_t s);
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
@@ -268,6 +269,12 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
 // C = P | P P on packed rows through the word index (wptr, widx, wval) of P
 cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, const uint64_t* P,
                                int64_t n, int64_t ldw, uint64_t* C, int sms, cudaStream_t s, int* changed = nullptr);
+// Full closure rows by 64-source bit-sliced frontier expansion over the word index of R^T (rows 0 .. n-1 of out,
+// ldw_out words each). scratch: smp_sliced_grid(n, sms) x 3 n words; *bcounter = 0 and *levels = 0 beforehand.
+int64_t smp_sliced_grid(int64_t n, int sms);
+cudaError_t launch_smp_sliced(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
+                              uint64_t* scratch, uint64_t* out, int64_t ldw_out, unsigned long long* bcounter,
+                              int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl);
 // word ORs of the next squaring step (sum over the set bits k of a row of the nonzero words of row k):
 // cost[0] += their total over all rows, cost[1] = max(cost[1], the largest row's)
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,

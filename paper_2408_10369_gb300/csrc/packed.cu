@@ -122,16 +122,22 @@ __global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int
     }
 }
 
-// In-place inclusive scan of wptr[1..n] by one block of 1024 threads.
+// In-place inclusive scan of wptr[1..n] by one block of 1024 threads; wptr[n + 1] = the largest count.
 __global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) {
     __shared__ int64_t part[1024];
+    __shared__ unsigned long long top;
     const int t = threadIdx.x;
     const int64_t per = (n + 1023) / 1024;
     const int64_t a = 1 + t * per, b = (a + per < n + 1) ? a + per : n + 1;
-    int64_t s = 0;
-    for (int64_t x = a; x < b; ++x) s += wptr[x];
+    int64_t s = 0, mx = 0;
+    for (int64_t x = a; x < b; ++x) {
+        s += wptr[x];
+        mx = wptr[x] > mx ? wptr[x] : mx;
+    }
+    if (t == 0) top = 0ull;
     part[t] = s;
     __syncthreads();
+    atomicMax(&top, static_cast<unsigned long long>(mx));
     for (int off = 1; off < 1024; off <<= 1) {
         int64_t v = (t >= off) ? part[t - off] : 0;
         __syncthreads();
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, 
         run += wptr[x];
         wptr[x] = run;
     }
+    if (t == 0) wptr[n + 1] = static_cast<int64_t>(top);
 }
 
 __global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, const int64_t* __restrict__ wptr,
@@ -623,6 +630,110 @@ __global__ void __launch_bounds__(256) square_cost_kernel(const int64_t* __restr
     }
 }
 
+// ---- frontier expansion of 64 sources at once (closures whose rows reach most constants)
+// Algorithm 2 for the 64 query rows e_s0 .. e_s0+63 together, bit-sliced: word w of V, D and Dn holds, in bit j,
+// whether constant w is visited by / in the frontier of / in the next frontier of source s0 + j. A level pulls:
+// Dn[w] = (OR of D[v] over the in-neighbours v of w, i.e. the set bits of row w of R^T) AND NOT V[w], skipping every
+// w already reached from all sources whose frontier is not empty (A, the OR of all D words). One traversal of R^T
+// serves 64 sources, and no word is written by two threads. V, D and Dn live in the CTA's slice of `scratch` (3 n words); the CTA takes batches from
+// a global counter and, after the last level, writes its 64 output rows through 64 x 64 bit transposes (ballots).
+__global__ void __launch_bounds__(256) smp_sliced_kernel(const int64_t* __restrict__ wptrT,
+                                                         const int32_t* __restrict__ widxT,
+                                                         const uint64_t* __restrict__ wvalT, int64_t n, int64_t nbatch,
+                                                         uint64_t* __restrict__ scratch, uint64_t* __restrict__ out,
+                                                         int64_t ldw_out, unsigned long long* bcounter,
+                                                         int* levels_max, int max_levels, Deadline dl) {
+    __shared__ unsigned long long s_batch;
+    __shared__ unsigned long long s_active;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    uint64_t* const V = scratch + static_cast<int64_t>(blockIdx.x) * 3 * n;
+    while (true) {
+        if (tid == 0) s_batch = atomicAdd(bcounter, 1ull);
+        __syncthreads();
+        const int64_t b = static_cast<int64_t>(s_batch);
+        __syncthreads();
+        if (b >= nbatch) break;
+        const int64_t s0 = b * 64;
+        const int cnt = static_cast<int>(n - s0 < 64 ? n - s0 : 64);
+        const uint64_t full = cnt == 64 ? ~0ull : (1ull << cnt) - 1ull;
+        uint64_t* D = V + n;
+        uint64_t* Dn = V + 2 * n;
+        for (int64_t w = tid; w < n; w += blockDim.x) {
+            V[w] = 0ull;
+            D[w] = (w >= s0 && w < s0 + cnt) ? (1ull << (w - s0)) : 0ull;
+        }
+        if (tid == 0) s_active = 0ull;
+        uint64_t act = full;  // sources whose frontier is not empty
+        __syncthreads();
+        int lv = 0;
+        while (true) {
+            int stop = 0;
+            if (tid == 0 && dl.budget_ns) stop = dl.past() ? 1 : 0;
+            if (__syncthreads_or(stop)) break;
+            uint64_t grown = 0ull;
+            for (int64_t w = tid; w < n; w += blockDim.x) {
+                const uint64_t vw = V[w];
+                const uint64_t need = act & ~vw;  // active sources that have not reached w
+                uint64_t acc = 0ull;
+                if (need) {
+                    const int64_t e1 = wptrT[w + 1];
+                    for (int64_t e = wptrT[w]; e < e1 && (acc & need) != need; ++e) {
+                        uint64_t bits = wvalT[e];
+                        const int64_t base = static_cast<int64_t>(widxT[e]) << 6;
+                        while (bits) {
+                            const int64_t v = base + (__ffsll(static_cast<long long>(bits)) - 1);
+                            bits &= bits - 1ull;
+                            acc |= D[v];
+                        }
+                    }
+                }
+                const uint64_t nn = acc & need;
+                Dn[w] = nn;
+                if (nn) V[w] = vw | nn;
+                grown |= nn;
+            }
+            const unsigned glo = __reduce_or_sync(FULL, static_cast<unsigned>(grown));
+            const unsigned ghi = __reduce_or_sync(FULL, static_cast<unsigned>(grown >> 32));
+            if (lane == 0 && (glo | ghi)) atomicOr(&s_active, static_cast<unsigned long long>(glo) |
+                                                                (static_cast<unsigned long long>(ghi) << 32));
+            __syncthreads();
+            act = s_active;
+            __syncthreads();
+            if (tid == 0) s_active = 0ull;
+            ++lv;
+            uint64_t* t = D;
+            D = Dn;
+            Dn = t;
+            if (act == 0ull || lv > max_levels) break;
+        }
+        if (tid == 0) atomicMax(levels_max, lv);
+        // rows s0 .. s0 + cnt - 1 of the output: word wd of row s0 + j = bit j of V[64 wd .. 64 wd + 63]
+        const int64_t wpr = (n + 63) >> 6;
+        for (int64_t wd = tid >> 5; wd < wpr; wd += blockDim.x >> 5) {
+            const int64_t w0 = wd * 64 + lane, w1 = w0 + 32;
+            const uint64_t v0 = w0 < n ? V[w0] : 0ull;
+            const uint64_t v1 = w1 < n ? V[w1] : 0ull;
+            uint64_t mine0 = 0ull, mine1 = 0ull;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const unsigned lo = __ballot_sync(FULL, ((v0 >> j) & 1ull) != 0ull);
+                const unsigned hi = __ballot_sync(FULL, ((v1 >> j) & 1ull) != 0ull);
+                if (j == lane) mine0 = static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+            }
+#pragma unroll 8
+            for (int j = 32; j < 64; ++j) {
+                const unsigned lo = __ballot_sync(FULL, ((v0 >> j) & 1ull) != 0ull);
+                const unsigned hi = __ballot_sync(FULL, ((v1 >> j) & 1ull) != 0ull);
+                if (j - 32 == lane) mine1 = static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+            }
+            if (lane < cnt) out[(s0 + lane) * ldw_out + wd] = mine0;
+            if (lane + 32 < cnt) out[(s0 + lane + 32) * ldw_out + wd] = mine1;
+        }
+        __syncthreads();
+    }
+}
+
 inline int warps_grid(int64_t rows, int sms) {
     int64_t blocks = (rows + 7) / 8;  // 8 warps of 256 threads
     const int64_t cap = static_cast<int64_t>(sms) * 8;
@@ -676,6 +787,21 @@ cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const u
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     square_rows_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(wptr, widx, wval, P, n, ldw, C, changed);
+    return cudaGetLastError();
+}
+
+int64_t smp_sliced_grid(int64_t n, int sms) {
+    const int64_t nbatch = (n + 63) / 64;
+    const int64_t cap = static_cast<int64_t>(sms) * 4;
+    return nbatch < cap ? nbatch : cap;
+}
+
+cudaError_t launch_smp_sliced(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
+                              uint64_t* scratch, uint64_t* out, int64_t ldw_out, unsigned long long* bcounter,
+                              int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl) {
+    const int64_t grid = smp_sliced_grid(n, sms);
+    smp_sliced_kernel<<<static_cast<int>(grid), 256, 0, s>>>(wptrT, widxT, wvalT, n, (n + 63) / 64, scratch, out,
+                                                             ldw_out, bcounter, levels, max_levels, dl);
     return cudaGetLastError();
 }
 
