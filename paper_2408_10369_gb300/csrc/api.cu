@@ -77,10 +77,12 @@ constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // A full frontier closure expands 64 sources at a time when R + R R has more than this many times the nonzero
-// words of R (rows that widen fast reach most constants within a few levels).
-constexpr double kSlicedMinGrowth = 3.0;
-// ... and when no column of R has more than this many times the mean nonzero words of a column.
-constexpr double kSlicedMaxSkew = 8.0;
+// words of R (rows that widen fast reach most constants within a few levels; measured on ER, SBM, power-law and
+// grid graphs: the sliced kernel wins above about 2.8, the one-query-per-warp kernel below) ...
+constexpr double kSlicedMinGrowth = 2.8;
+// ... and no column of R has more than this many times the mean nonzero words of a column (a pull rescans a hub's
+// in-list at every level until every active source reaches it).
+constexpr double kSlicedMaxSkew = 16.0;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 

@@ -637,7 +637,12 @@ __global__ void __launch_bounds__(256) square_cost_kernel(const int64_t* __restr
 // w already reached from all sources whose frontier is not empty (A, the OR of all D words). One traversal of R^T
 // serves 64 sources, and no word is written by two threads. V, D and Dn live in the CTA's slice of `scratch` (3 n words); the CTA takes batches from
 // a global counter and, after the last level, writes its 64 output rows through 64 x 64 bit transposes (ballots).
-__global__ void __launch_bounds__(256) smp_sliced_kernel(const int64_t* __restrict__ wptrT,
+// Threads per CTA and CTAs per SM of the sliced kernel: each CTA holds 3 n words of state, so the number of CTAs
+// in flight sets the working set that has to stay in L2.
+constexpr int kSlicedThreads = 1024;
+constexpr int kSlicedPerSm = 1;
+
+__global__ void __launch_bounds__(kSlicedThreads) smp_sliced_kernel(const int64_t* __restrict__ wptrT,
                                                          const int32_t* __restrict__ widxT,
                                                          const uint64_t* __restrict__ wvalT, int64_t n, int64_t nbatch,
                                                          uint64_t* __restrict__ scratch, uint64_t* __restrict__ out,
@@ -792,7 +797,7 @@ cudaError_t launch_square_rows(const int64_t* wptr, const int32_t* widx, const u
 
 int64_t smp_sliced_grid(int64_t n, int sms) {
     const int64_t nbatch = (n + 63) / 64;
-    const int64_t cap = static_cast<int64_t>(sms) * 4;
+    const int64_t cap = static_cast<int64_t>(sms) * kSlicedPerSm;
     return nbatch < cap ? nbatch : cap;
 }
 
@@ -800,7 +805,7 @@ cudaError_t launch_smp_sliced(const int64_t* wptrT, const int32_t* widxT, const 
                               uint64_t* scratch, uint64_t* out, int64_t ldw_out, unsigned long long* bcounter,
                               int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl) {
     const int64_t grid = smp_sliced_grid(n, sms);
-    smp_sliced_kernel<<<static_cast<int>(grid), 256, 0, s>>>(wptrT, widxT, wvalT, n, (n + 63) / 64, scratch, out,
+    smp_sliced_kernel<<<static_cast<int>(grid), kSlicedThreads, 0, s>>>(wptrT, widxT, wvalT, n, (n + 63) / 64, scratch, out,
                                                              ldw_out, bcounter, levels, max_levels, dl);
     return cudaGetLastError();
 }

@@ -1,7 +1,7 @@
 """Full frontier closures expanded 64 sources at a time (bit-sliced frontiers).
 
 BMLP_SMP_PACKED closures with n >= 4096 whose first squaring widens the rows
-(not path-like) run Algorithm 2 for 64 source rows per CTA, with bit j of the
+fast (not path-like, no hub columns) run Algorithm 2 for 64 source rows per CTA, with bit j of the
 state word of constant w standing for source s0 + j, pulling over the word
 index of R^T. Bits against the oracle, the reported level count (deepest BFS
 level + 1, as for the one-query-per-warp kernel), ragged batches (n not a
