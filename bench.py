@@ -197,14 +197,19 @@ def profiled_traffic(kernel, n, root=None):
         return None
 
 
-def cpu_oracle_closure(n, ip, ix, rows):
-    """Time the oracle's BFS closure on `rows` source rows (materialised)."""
+def cpu_oracle_closure(n, ip, ix, rows, threads=0):
+    """Time the oracle's BFS closure on `rows` source rows (materialised), on `threads` cores (0: all)."""
     import numpy as np
     import oracle
     src = np.arange(rows, dtype=np.int32) * (n // rows)
-    t0 = time.perf_counter()
-    oracle.reach_rows(n, ip, ix, src)
-    return time.perf_counter() - t0
+    prev = oracle.set_threads(threads) if threads else None
+    try:
+        t0 = time.perf_counter()
+        oracle.reach_rows(n, ip, ix, src)
+        return time.perf_counter() - t0
+    finally:
+        if prev is not None:
+            oracle.set_threads(prev)
 
 
 def oracle_threads():
@@ -506,12 +511,19 @@ def main():
         return
     cpu = None
     if not args.no_cpu:
+        # the oracle on all host cores (median of 3 samples of rows) and on one core (median of 3 smaller samples)
         rows = args.cpu_rows or max(64, n // 4)
-        tc = cpu_oracle_closure(n, ip, ix, rows)
+        tc = statistics.median(cpu_oracle_closure(n, ip, ix, rows) for _ in range(3))
         t_full = tc * n / rows
+        rows1 = max(16, rows // 16)
+        t1 = statistics.median(cpu_oracle_closure(n, ip, ix, rows1, threads=1) for _ in range(3))
+        t1_full = t1 * n / rows1
         cpu = {"value": iters * 2.0 * n ** 3 / t_full / 1e12, "unit": UNIT, "cores": oracle_threads(),
-               "kind": "oracle", "sample": "BFS closure rows for %d of %d sources (%.1f s), scaled to the full closure"
-               % (rows, n, tc)}
+               "kind": "oracle", "sample": "BFS closure rows for %d of %d sources (median of 3: %.2f s), scaled to the "
+               "full closure" % (rows, n, tc),
+               "value_1_thread": iters * 2.0 * n ** 3 / t1_full / 1e12,
+               "sample_1_thread": "%d rows on one core (median of 3: %.2f s), scaled" % (rows1, t1),
+               "closure_s": t_full, "closure_s_1_thread": t1_full}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": ("e2m1 0/1 operands (UE8M0 block scales of 1), fp32 accumulate" if fp4

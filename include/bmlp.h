@@ -158,10 +158,14 @@ bmlp_status bmlp_get_stats(const bmlp_ctx* ctx, bmlp_stats* out);
  * computed by the fixpoint R <- R + R.R started from R1 (same result as
  * Algorithm 1's (I + R1)^(2^k) followed by one product with R1). R and out
  * are n x n in format fmt. *iters_out (if not null) receives the number of
- * products issued (ceil(log2 L) + 1, L the longest shortest path). n = 0 is
- * a no-op that returns BMLP_OK.
- * Variants: BMLP_RMS_TC, BMLP_RMS_PACKED, BMLP_SMP_PACKED (all n rows as
- * frontiers), BMLP_AUTO.
+ * products issued (ceil(log2 L) + 1, L the longest shortest path), or for
+ * the frontier variants the deepest level + 1. n = 0 is a no-op that returns
+ * BMLP_OK.
+ * Variants: BMLP_RMS_TC (n >= 4096: bit-row squarings while R is sparse,
+ * see options.tc_only; then tensor cores), BMLP_RMS_PACKED, BMLP_SMP_PACKED
+ * (all n rows as frontiers: path-like R is squared first and expanded one
+ * row per warp, R whose rows widen fast is expanded 64 rows per CTA), BMLP_SMP_TC,
+ * BMLP_AUTO (the learned dispatcher once trained or loaded, else BMLP_RMS_TC).
  */
 bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out,
                      const bmlp_options* opts, int32_t* iters_out, cudaStream_t stream);

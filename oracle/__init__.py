@@ -66,8 +66,15 @@ def _L():
             lib.oracle_seminaive.argtypes = [ctypes.c_int64, _u8p, _u8p, _u8p]
             lib.oracle_warshall.argtypes = [ctypes.c_int64, _u8p, _u8p]
             lib.oracle_compose_rows.argtypes = [ctypes.c_int64, _i64p, _i32p, _i64p, _i32p, _i32p, ctypes.c_int64, _u8p]
+            lib.oracle_set_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's parallel loops (t <= 0 keeps them); returns the previous setting."""
+    return int(_L().oracle_set_threads(int(t)))
 
 
 def _p(a, t):

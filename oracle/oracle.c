@@ -25,6 +25,15 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <omp.h>
+
+/* Threads of the parallel loops below (t <= 0: keep); returns the previous
+ * setting. Used to time the oracle on one core and on all cores. */
+int oracle_set_threads(int t) {
+    const int prev = omp_get_max_threads();
+    if (t > 0) omp_set_num_threads(t);
+    return prev;
+}
 
 /* Reach rows from a list of sources by BFS that starts at the successors of
  * each source (paths of length >= 1, so a source is in its own row only if

@@ -424,3 +424,17 @@ def test_compose_matches_definition(n, seed):
     np.testing.assert_array_equal(sn, want)
     # with r1 = r2 = R the composition is the closure itself
     np.testing.assert_array_equal(oracle.compose_rows(n, (ip1, ix1), (ip1, ix1)), closure_by_powers(r1))
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's parallel loops give the same rows on one core as on all."""
+    n = 700
+    ip, ix = wl.er_graph(n, 1.7, 31)
+    many = oracle.closure(n, ip, ix)
+    prev = oracle.set_threads(1)
+    try:
+        one = oracle.closure(n, ip, ix)
+        assert oracle.set_threads(0) == 1
+    finally:
+        oracle.set_threads(prev)
+    np.testing.assert_array_equal(one, many)
