@@ -122,33 +122,58 @@ __global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int
     }
 }
 
-// In-place inclusive scan of wptr[1..n] by one block of 1024 threads; wptr[n + 1] = the largest count.
+// In-place inclusive scan of wptr[1..n] by one block of 1024 threads, in tiles of 4,096 counts (4 consecutive
+// counts per thread, so a warp reads 1 KB contiguously); wptr[n + 1] = the largest count.
 __global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) {
-    __shared__ int64_t part[1024];
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
     __shared__ unsigned long long top;
-    const int t = threadIdx.x;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t a = 1 + t * per, b = (a + per < n + 1) ? a + per : n + 1;
-    int64_t s = 0, mx = 0;
-    for (int64_t x = a; x < b; ++x) {
-        s += wptr[x];
-        mx = wptr[x] > mx ? wptr[x] : mx;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) {
+        carry = 0;
+        top = 0ull;
     }
-    if (t == 0) top = 0ull;
-    part[t] = s;
     __syncthreads();
+    int64_t mx = 0;
+    for (int64_t base = 1; base <= n; base += 4096) {
+        int64_t v[4];
+        int64_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t x = base + 4 * t + k;
+            const int64_t c = x <= n ? wptr[x] : 0;
+            mx = c > mx ? c : mx;
+            s += c;
+            v[k] = s;  // inclusive within the thread
+        }
+        int64_t ws = s;  // inclusive over the warp's threads
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, ws, off);
+            if (lane >= off) ws += y;
+        }
+        if (lane == 31) warp_tot[wid] = ws;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t x = warp_tot[lane];  // inclusive over the block's warps
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL, x, off);
+                if (lane >= off) x += y;
+            }
+            warp_tot[lane] = x;
+        }
+        __syncthreads();
+        const int64_t before = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + (ws - s);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t x = base + 4 * t + k;
+            if (x <= n) wptr[x] = before + v[k];
+        }
+        __syncthreads();  // every thread has read carry and warp_tot
+        if (t == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
     atomicMax(&top, static_cast<unsigned long long>(mx));
-    for (int off = 1; off < 1024; off <<= 1) {
-        int64_t v = (t >= off) ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int64_t run = (t > 0) ? part[t - 1] : 0;
-    for (int64_t x = a; x < b; ++x) {
-        run += wptr[x];
-        wptr[x] = run;
-    }
+    __syncthreads();
     if (t == 0) wptr[n + 1] = static_cast<int64_t>(top);
 }
 
