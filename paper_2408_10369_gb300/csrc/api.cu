@@ -76,6 +76,8 @@ constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
 constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
+// A squaring is kept while it grows the rows' nonzero words by at most this factor (path-like relations).
+constexpr double kSquareMaxGrowth = 1.5;
 // A full frontier closure expands 64 sources at a time when R + R R has more than this many times the nonzero
 // words of R (rows that widen fast reach most constants within a few levels; measured on ER, SBM, power-law and
 // grid graphs: the sliced kernel wins above about 2.8, the one-query-per-warp kernel below) ...
@@ -772,7 +774,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                "word index build");
             ctx->stats.launches += 4;
             ST(words(wptr2, &W2));
-            if (W2 > W + W / 2) {
+            if (static_cast<double>(W2) > kSquareMaxGrowth * static_cast<double>(W)) {
                 // the first squaring widens the rows fast: closure rows fill up within a few levels
                 dense_reach = k == 0 && static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
                 break;
