@@ -14,6 +14,11 @@
 
 #include "internal.h"
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define BMLP_HAVE_NVTX 1
+#endif
+
 using namespace bmlp;
 
 namespace bmlp {
@@ -61,6 +66,19 @@ bmlp_status ws_get(bmlp_ctx* ctx, int slot, size_t bytes, void** out) {
 }  // namespace bmlp
 
 namespace {
+
+// A named range around a call or a phase of it, for profilers that read NVTX (ncu --nvtx, nsys); without a tool
+// attached a push and a pop cost a few nanoseconds.
+struct NvtxRange {
+#ifdef BMLP_HAVE_NVTX
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char*) {}
+#endif
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Workspace slots.
 enum : int {
@@ -309,6 +327,7 @@ bool tc_skip_enabled() {
 bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
                         const uint8_t** res_f4 = nullptr) {
+    NvtxRange nvtx_("tensor-core squarings");
     const bool pair = tc_pairs_enabled();
     CUtensorMap mapA[2], mapB[2];
     for (int b = 0; b < 2; ++b) {
@@ -629,6 +648,7 @@ struct SparseStart {
 // goes one way. Leaves at least one product to the caller's loop unless the fixpoint was reached here.
 bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, int64_t n_pad, int max_iters,
                              const bmlp_options& o, cudaStream_t s, SparseStart* out) {
+    NvtxRange nvtx_("bit-row squarings");
     const int64_t ldw = round_up(words_of(n), 2);
     if (n < kSparseMinN || ldw > 2048 || max_iters < 2) return BMLP_OK;
     void *pa = nullptr, *pb = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
@@ -732,6 +752,7 @@ int pick_variant_rms(int64_t) { return BMLP_RMS_TC; }
 bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t n, const uint64_t* src,
                            int64_t ldw_src, int64_t q, uint64_t* out, int64_t ldw_out, const bmlp_options& o,
                            cudaStream_t s, int* levels, bool square_first = false) {
+    NvtxRange nvtx_("frontier expansion");
     const int64_t ldw = round_up(words_of(n), 2);
     if (ldw > smp_packed_max_words())
         return set_err(ctx, BMLP_ERR_UNSUPPORTED, "packed frontier path supports n <= %d", smp_packed_max_words() * 64);
@@ -984,6 +1005,7 @@ bmlp_status bmlp_get_stats(const bmlp_ctx* ctx, bmlp_stats* out) {
 
 bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
                      int32_t* iters_out, cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_rms");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (iters_out) *iters_out = 0;
     if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
@@ -1154,6 +1176,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
 
 bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
                         cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_insert");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (n < 0 || m < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0 or m < 0");
     if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
@@ -1202,6 +1225,7 @@ bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, co
 
 bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
                      uint64_t* out_rows, const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_smp");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (iters_out) *iters_out = 0;
     if (n < 0 || q < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "negative size");
@@ -1238,6 +1262,7 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const
 
 bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt, void* out,
                          const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_compose");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (iters_out) *iters_out = 0;
     if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
@@ -1336,6 +1361,7 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
 // I + R1 is Algorithm 1's loop (same engines and switches); the last product runs on the tensor cores.
 bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
                           int32_t* iters_out, cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_rms_alg1");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (iters_out) *iters_out = 0;
     if (n < 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "n < 0");
@@ -1492,6 +1518,7 @@ bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, co
 bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
                             int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
                             cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_is_foreign");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (iters_out) iters_out[0] = iters_out[1] = 0;
     ST(op_args(ctx, n, fmt));
@@ -1543,6 +1570,7 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
 
 bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const bmlp_options* opts,
                            int32_t* iters_out, cudaStream_t s) {
+    NvtxRange nvtx_("bmlp_batch_run");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     if (count < 0 || (count > 0 && !probs)) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad problem list");
     if (count == 0) return BMLP_OK;
