@@ -55,6 +55,8 @@ def parse():
                     help="format of the input and output matrices of the closure benchmark")
     ap.add_argument("--variant", default=None,
                     help="default: rms_tc (er), smp_packed (powerlaw_smp), auto (kg_batch, isforeign)")
+    ap.add_argument("--e4m3-only", action="store_true",
+                    help="every tensor-core squaring on E4M3 operands (kind::f8f6f4) instead of packed E2M1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
@@ -158,11 +160,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"tc_pair_kernel": "tc_product.cu", "tc_product_kernel": "tc_product.cu",
-                  "tc4_pair_kernel": "tc_fp4.cu", "tc4_duo_kernel": "tc_fp4.cu"}
+KERNEL_SOURCES = {"tc_product_kernel": "tc_product.cu", "tc4_duo_kernel": "tc_fp4.cu"}
 
 
-def kernel_hash(kernel="tc_pair_kernel"):
+def kernel_hash(kernel="tc4_duo_kernel"):
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2408_10369_gb300", "csrc", KERNEL_SOURCES[kernel]), "rb") as f:
         h.update(f.read())
@@ -393,7 +394,8 @@ def main():
             torch.distributed.barrier()
 
     def step(profile):
-        return ctx.rms(R, n, out, fmt=FMT, variant=args.variant, profile=profile, stream=stream)
+        return ctx.rms(R, n, out, fmt=FMT, variant=args.variant, profile=profile, stream=stream,
+                       e4m3_only=args.e4m3_only)
 
     iters = 0
     for _ in range(args.warmup):
@@ -427,12 +429,12 @@ def main():
     if not args.no_e2e:
         hin = torch.from_numpy(host_in).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
-        ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream)
+        ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream, e4m3_only=args.e4m3_only)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream)
+            ctx.rms(hin, n, hout, fmt=FMT, variant=args.variant, stream=stream, e4m3_only=args.e4m3_only)
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world, device)
         nbytes = int(hin.numel() * hin.element_size())
@@ -492,10 +494,7 @@ def main():
     fp4 = prod_n > 0 and e2m1_n == prod_n
     ratio, rname = (FP4_PER_BF16, "fp4/bf16") if fp4 else (FP8_PER_BF16, "fp8/bf16")
     peak = bf16 * ratio
-    if fp4:
-        kname = "tc4_pair_kernel" if os.environ.get("BMLP_TC_DUO", "1") == "0" else "tc4_duo_kernel"
-    else:
-        kname = "tc_product_kernel" if os.environ.get("BMLP_TC_PAIR", "1") == "0" else "tc_pair_kernel"
+    kname = "tc4_duo_kernel" if fp4 else "tc_product_kernel"
     # what this GPU issues for the kernel's operand kind (back-to-back MMAs, no operand traffic)
     issue = ctx.mma_issue_rate(1 if fp4 else 0)
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,

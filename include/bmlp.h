@@ -102,6 +102,11 @@ typedef struct bmlp_options {
                             every warp before each row / query (used to time
                             variants with a cap, e.g. by the dispatcher's
                             training sweep)                                    */
+    int32_t e4m3_only;   /* BMLP_RMS_TC: 0 = dense squarings run on packed E2M1
+                            operands (tcgen05 kind::mxf4, half the bytes per
+                            Boolean operation); 1 = every tensor-core squaring
+                            on E4M3 operands (kind::f8f6f4). Same bits.       */
+    int32_t reserved;    /* 0                                                  */
 } bmlp_options;
 
 /* Per-call statistics of the last call on a context. */
@@ -291,7 +296,7 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
  */
 bmlp_status bmlp_mma_issue_rate(bmlp_ctx* ctx, int32_t kind, int32_t iters, double* tflops);
 
-/* One problem of a grouped batch. *//* One problem of a grouped batch. */
+/* One problem of a grouped batch. */
 typedef enum bmlp_problem_kind {
     BMLP_PROBLEM_CLOSURE = 0,  /* out = R1+ (or I + R1+): program P2 of Sec. 3.3   */
     BMLP_PROBLEM_COMPOSE = 1   /* out = (I + R2+) R1: p <- r1 ; p <- r2, p (Thm. 1) */
@@ -435,15 +440,20 @@ bmlp_status bmlp_dispatch_load(bmlp_ctx* ctx, const char* path);
  * routine.
  *
  * Arguments: as bmlp_rms, on the calling thread's current CUDA device. R and
- * out must be device memory (host pointers give BMLP_ERR_INVALID_ARG, since
+ * out must be device memory of that device, or managed memory (host
+ * pointers and other devices' memory give BMLP_ERR_INVALID_ARG, since
  * staging them would need an allocation). reflexive: 0 gives R1+, 1 gives
  * I + R1+. max_iters: 0 = ceil(log2 n) + 2. Sizes n > BMLP_NOALLOC_MAX_N give
  * BMLP_ERR_UNSUPPORTED. Errors are status codes only (there is no context to
  * hold a message).
  *
- * Set-up: the first call on a device looks up the scratch's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture on the device.
+ * Set-up: each call looks up the scratch's device address
+ * (cudaGetSymbolAddress, with the device current), so a context that was
+ * torn down and recreated is followed. The first call on a device does the
+ * set-up there (it loads the library's device code, which places the
+ * scratch); make that first call before any stream capture on the device.
+ * After each squaring the call copies the changed flag to the host and
+ * synchronises `stream`.
  *
  * Sharing: every call on a device uses the same scratch, which keeps the last
  * call's contents (each call rewrites all of it that it reads). Calls whose

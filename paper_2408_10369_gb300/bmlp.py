@@ -51,7 +51,8 @@ _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NOT
 class bmlp_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("reflexive", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("loop", ctypes.c_int32), ("profile", ctypes.c_int32), ("tc_only", ctypes.c_int32),
-                ("timeout_ns", ctypes.c_uint64), ("budget_ns", ctypes.c_uint64)]
+                ("timeout_ns", ctypes.c_uint64), ("budget_ns", ctypes.c_uint64), ("e4m3_only", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class bmlp_stats(ctypes.Structure):
@@ -190,7 +191,7 @@ def _stream(stream, device):
 
 
 def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HOST, profile=False, timeout_ns=0,
-                 budget_ns=0, tc_only=False):
+                 budget_ns=0, tc_only=False, e4m3_only=False):
     o = bmlp_options()
     lib().bmlp_default_options(ctypes.byref(o))
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -201,6 +202,7 @@ def make_options(variant="auto", reflexive=False, max_iters=0, loop=BMLP_LOOP_HO
     o.timeout_ns = int(timeout_ns)
     o.budget_ns = int(budget_ns)
     o.tc_only = int(bool(tc_only))
+    o.e4m3_only = int(bool(e4m3_only))
     return o
 
 

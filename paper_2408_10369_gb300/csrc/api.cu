@@ -262,39 +262,11 @@ struct ProductTimer {
     }
 };
 
-// The squaring product runs as 2-CTA clusters sharing each B tile by TMA
-// multicast unless BMLP_TC_PAIR=0 is set in the environment.
-bool tc_pairs_enabled() {
-    static const bool on = [] {
-        const char* v = getenv("BMLP_TC_PAIR");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
-
-// Dense squarings on packed E2M1 operands (kind::mxf4) unless BMLP_TC_FP4=0.
-bool tc_fp4_enabled() {
-    static const bool on = [] {
-        const char* v = getenv("BMLP_TC_FP4");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
-
 // Full frontier closures whose first squaring widens the rows run 64 sources per CTA (bit-sliced) unless
 // BMLP_SMP_SLICED=0.
 bool smp_sliced_enabled() {
     static const bool on = [] {
         const char* v = getenv("BMLP_SMP_SLICED");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
-
-// Dense squarings as one M = 256 MMA per CTA pair (2-SM form) unless BMLP_TC_DUO=0.
-bool tc_duo_enabled() {
-    static const bool on = [] {
-        const char* v = getenv("BMLP_TC_DUO");
         return !(v && v[0] == '0');
     }();
     return on;
@@ -328,11 +300,10 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
                         const uint8_t** res_f4 = nullptr) {
     NvtxRange nvtx_("tensor-core squarings");
-    const bool pair = tc_pairs_enabled();
     CUtensorMap mapA[2], mapB[2];
     for (int b = 0; b < 2; ++b) {
         ST(make_tmap(ctx, &mapA[b], M[b], n_pad, n_pad, n_pad, TC_BM));
-        ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, pair ? TC_BN / 2 : TC_BN));
+        ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, TC_BN));
     }
     TcParams p{};
     p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
@@ -387,7 +358,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     // Once R is dense, the squarings continue on packed E2M1 operands (half the bytes per Boolean operation):
     // R, R^T are converted into the halves of the free E4M3 buffer pair (index sw ^ 1) and ping-pong there;
     // the result is converted back into the E4M3 pair sw.
-    const bool fp4 = pair && tc_fp4_enabled();
+    const bool fp4 = o.e4m3_only == 0;
     bool on_f4 = false;
     int sw = 0, qcur = 0;
     uint8_t* Q[2] = {nullptr, nullptr};
@@ -450,11 +421,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             p4.out_r = Q[qcur ^ 1];
             p4.out_rt = QT[qcur ^ 1];
             ST(tm.begin());
-            if (tc_duo_enabled())
-                CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
-            else
-                CK(launch_tc4_product_pair(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s),
-                   "tensor-core product launch");
+            CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
             ST(tm.end());
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;
@@ -491,10 +458,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         p.out_r = M[nxt];
         p.out_rt = T[nxt];
         ST(tm.begin());
-        if (pair)
-            CK(launch_tc_product_pair(mapA[cur], mapB[cur], p, ctx->sm_count, s), "tensor-core product launch");
-        else
-            CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
+        CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
         ST(tm.end());
         ctx->stats.product_launches++;
         ctx->stats.launches += 2;
@@ -1081,7 +1045,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
             sldw = sp.ldw;
         }
         bool direct = false;
-        if (tc_pairs_enabled() && tc_fp4_enabled()) {
+        if (o.e4m3_only == 0) {
             // a dense input (by its 128 x 128 block map) starts on 4-bit operands and leaves from them
             const int64_t kb = n_pad / 128;
             direct = !tc_skip_enabled() || kb > 256;

@@ -230,16 +230,9 @@ bmlp_status make_tmap(bmlp_ctx* ctx, CUtensorMap* map, const void* base, int64_t
 int tc_smem_bytes();
 cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int grid,
                               cudaStream_t s);
-// 2-CTA-cluster form (RMS / PLAIN modes): b_half is a tensor map of B^T with
-// a box of TC_BN / 2 rows; m_tiles must be even
-cudaError_t launch_tc_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                   cudaStream_t s);
 // squaring step (RMS mode only) on packed E2M1 operands (n_pad x n_pad / 2 bytes, p.ld = n_pad / 2,
-// p.k_blocks = n_pad / 256), 2-CTA clusters; maps: A box 128 rows, B box 128 rows (half a tile), 128 bytes wide
-cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                    cudaStream_t s);
-int tc4_smem_bytes();
-// the same step as one M = 256 MMA per CTA pair (tcgen05 .cta_group::2), 6 stages of 32 KB per CTA
+// p.k_blocks = n_pad / 256) as one M = 256 MMA per CTA pair (tcgen05 .cta_group::2, 2-CTA clusters);
+// maps: A box 128 rows, B box 128 rows (half a tile), 128 bytes wide
 cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
                                    cudaStream_t s);
 // E4M3 bytes <-> packed E2M1 nibbles (sizes multiples of 16 bytes)

@@ -20,29 +20,28 @@ constexpr size_t NA_BYTES = 4 * NA_MAT + NA_CTL;                // 16 MiB + 256 
 // holds it until the process exits.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
 
-constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_mu;
-uint8_t* g_addr[NA_MAX_DEVICES] = {nullptr};   // device address of the scratch, per device
 void* g_encode = nullptr;                      // cuTensorMapEncodeTiled
 
-// Device address of the scratch on the current device (looked up once per
-// device, with that device current; the host-side symbol is only a handle).
+// Device address of the scratch on the current device. In host code the
+// array's name is only a handle, so the address comes from
+// cudaGetSymbolAddress with the device current. It is looked up on every
+// call: the lookup allocates nothing once the module is loaded (the first
+// call on a device loads it), and an address kept from an earlier call would
+// be stale if the caller had torn down and recreated the device's context.
 bmlp_status scratch_on_current_device(int* dev_out, uint8_t** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return BMLP_ERR_CUDA;
+    }
+    void* addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || addr == nullptr) {
         cudaGetLastError();
         return BMLP_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_addr[dev] == nullptr) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return BMLP_ERR_CUDA;
-        }
-        g_addr[dev] = static_cast<uint8_t*>(p);
-    }
     if (g_encode == nullptr) {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
@@ -54,7 +53,7 @@ bmlp_status scratch_on_current_device(int* dev_out, uint8_t** out) {
         g_encode = fn;
     }
     *dev_out = dev;
-    *out = g_addr[dev];
+    *out = static_cast<uint8_t*>(addr);
     return BMLP_OK;
 }
 
@@ -69,13 +68,16 @@ bool tmap(CUtensorMap* map, const void* base, int64_t n_pad, int box_rows) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (or managed memory): the kernels read and
+// write it directly, so host memory and another GPU's memory are refused.
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -90,11 +92,11 @@ extern "C" bmlp_status bmlp_rms_tc_noalloc(const void* R, int64_t n, int32_t fmt
     if (n == 0) return BMLP_OK;
     if (R == nullptr || out == nullptr) return BMLP_ERR_INVALID_ARG;
     if (n > NA_MAX_N) return BMLP_ERR_UNSUPPORTED;
-    if (!on_device(R) || !on_device(out)) return BMLP_ERR_INVALID_ARG;
     int dev = 0;
     uint8_t* base = nullptr;
     bmlp_status st = scratch_on_current_device(&dev, &base);
     if (st != BMLP_OK) return st;
+    if (!on_device(R, dev) || !on_device(out, dev)) return BMLP_ERR_INVALID_ARG;
     int sms = 0, khz = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);

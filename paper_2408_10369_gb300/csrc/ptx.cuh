@@ -71,19 +71,6 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
-// The same box loaded once and written to the same shared-memory offset of
-// every CTA in cta_mask (this GPU's memory only), completing `bytes` on the
-// mbarrier at `bar`'s offset in each of those CTAs.
-__device__ __forceinline__ void tma_load_2d_mcast(void* smem_dst, const CUtensorMap* map, int32_t x, int32_t y,
-                                                  uint64_t* bar, uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)),
-          "h"(cta_mask)
-        : "memory");
-}
-
 // 2-SM form (.cta_group::2): the box lands in this CTA's shared memory and its
 // transaction bytes complete on the mbarrier at shared::cluster address
 // `bar_cluster`, which may belong to the peer CTA of the pair.
@@ -185,7 +172,8 @@ __device__ __forceinline__ void tc_mma_mxf4_2sm(uint32_t d_tmem, uint64_t a_desc
         : "memory");
 }
 // Arrive once on the mbarrier at `bar`'s offset in every CTA of cta_mask when
-// the 2-SM MMAs issued so far by this thread have completed.
+// the 2-SM MMAs issued so far by this thread have completed (a completion
+// signal to the pair's barriers; it moves no data).
 __device__ __forceinline__ void tc_commit_2sm_mcast(uint64_t* bar, uint16_t cta_mask) {
     asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
                  ::"r"(smem_u32(bar)), "h"(cta_mask) : "memory");
@@ -196,13 +184,6 @@ __device__ __forceinline__ void tc_commit_2sm_mcast(uint64_t* bar, uint16_t cta_
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(smem_u32(bar)) : "memory");
-}
-
-// As tc_commit, arriving on the mbarrier at `bar`'s offset in every CTA of
-// cta_mask.
-__device__ __forceinline__ void tc_commit_mcast(uint64_t* bar, uint16_t cta_mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(smem_u32(bar)), "h"(cta_mask) : "memory");
 }
 
 // 32 lanes x 32 bits, repeated 32 times along columns: thread t receives

@@ -11,13 +11,15 @@
 // half the operand bytes per Boolean operation.
 //
 // Structure (2-CTA clusters, one CTA per SM, persistent over tile pairs):
-//   warp 0      TMA producer: the CTA's 128 x 256 A tile (128 bytes) and one
-//               128-row half of the pair's shared 256 x 256 B^T tile,
-//               multicast to both CTAs; 4-stage ring, 128-byte swizzle;
-//   warp 1      MMA issuer: 4 x tcgen05.mma (M=128, N=256, K=64) per stage
-//               into one TMEM accumulator (256 FP32 columns); the scale
-//               factors occupy further TMEM columns;
-//   warps 2..5  epilogue: drains the accumulator into registers as bits and
+//   warp 0      TMA producer (both CTAs): the CTA's own 128 rows of A and
+//               its 128-row half of the pair's 256-row B^T tile, 128 bytes of
+//               K per stage, 128-byte swizzle; both CTAs' copies complete on
+//               the even CTA's barrier (no multicast loads);
+//   warp 1      MMA issuer (even CTA): 4 x tcgen05.mma.cta_group::2
+//               (M=256, N=256, K=64) per stage into one TMEM accumulator
+//               (256 FP32 columns in each CTA); the scale factors occupy
+//               further TMEM columns;
+//   warps 2..5  epilogue (both CTAs): drains the accumulator into registers as bits and
 //               frees it at once, then computes R' = R | [C > 0], writes R'
 //               and R'^T (transposed through warp ballots) and raises
 //               `changed` if R' != R.
@@ -32,27 +34,12 @@ namespace bmlp {
 namespace {
 
 constexpr int F4_BK = 128;                     // bytes of K per stage (256 elements)
-constexpr int F4_A_BYTES = TC_BM * F4_BK;      // 16 KiB
-constexpr int F4_B_BYTES = TC_BN * F4_BK;      // 32 KiB
-constexpr int F4_STAGE_BYTES = F4_A_BYTES + F4_B_BYTES;
-constexpr int F4_STAGES = 4;
 constexpr int F4_UMMA_K_BYTES = 32;            // 64 E2M1 elements per MMA
 constexpr int F4_TMEM_COLS = 512;
 constexpr int F4_SFA_COL = 256;                // scale factors of A (all 2^0)
 constexpr int F4_SFB_COL = 384;                // scale factors of B (all 2^0)
 constexpr uint32_t F4_UE8M0_ONE4 = 0x7F7F7F7Fu;  // four UE8M0 scales of 2^0
 
-constexpr int F4_OFF_A = 0;
-constexpr int F4_OFF_B = F4_OFF_A + F4_STAGES * F4_A_BYTES;
-constexpr int F4_OFF_BAR = F4_OFF_B + F4_STAGES * F4_B_BYTES;
-constexpr int F4_NUM_BARS = 2 * F4_STAGES + 3;  // full[], empty[], tfull, tempty, done
-constexpr int F4_OFF_MISC = F4_OFF_BAR + F4_NUM_BARS * 8;
-constexpr int F4_SMEM_END = F4_OFF_MISC + 16;
-constexpr int F4_SMEM_BYTES = F4_SMEM_END + 1024;
-
-constexpr int ERR_F4_PRODUCER = 0x201;
-constexpr int ERR_F4_MMA = 0x202;
-constexpr int ERR_F4_EPILOGUE = 0x203;
 constexpr int F4_GROUP_M = 8;  // raster: 8 row-block pairs share B tiles in L2
 
 __device__ __forceinline__ long long f4_drain_cycles(long long limit) {
@@ -150,187 +137,6 @@ __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int nb,
         *reinterpret_cast<uint4*>(p.out_rt + (col0 + lane) * p.ld + rt_col) = f4_nibbles32(mine);
     }
     return any;
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
-tc4_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem + F4_OFF_A;
-    uint8_t* sB = smem + F4_OFF_B;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + F4_OFF_BAR);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + F4_STAGES;
-    uint64_t* tfull = bars + 2 * F4_STAGES;
-    uint64_t* tempty = tfull + 1;
-    uint64_t* done = tempty + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + F4_OFF_MISC);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + F4_OFF_MISC + 4);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_ctarank();
-    const int m_pairs = p.m_tiles / 2;
-    const int num_pairs = m_pairs * p.n_tiles;
-    const int first = static_cast<int>(blockIdx.x >> 1);
-    const int step = static_cast<int>(gridDim.x >> 1);
-    const long long limit = p.wait_cycles;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < F4_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);  // both CTAs' MMAs must release a stage
-        }
-        mbar_init(tfull, 1);
-        mbar_init(tempty, 128);
-        mbar_init(done, 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, F4_TMEM_COLS);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem_base = *tmem_slot;
-    if (warp >= 2) {
-        // every scale factor of A and B is 2^0: 8 columns each, all 128 lanes
-        const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
-        const uint32_t ones[8] = {F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4,
-                                  F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4};
-        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFA_COL, ones);
-        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFB_COL, ones);
-        tmem_st_wait();
-    }
-    tc_fence_before();
-    __syncthreads();
-    cluster_sync();  // the peer's barriers exist before any multicast reaches them
-    tc_fence_after();
-
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int last_par[F4_STAGES];
-#pragma unroll
-            for (int s = 0; s < F4_STAGES; ++s) last_par[s] = -1;
-            bool ok = true;
-            for (int t = first; t < num_pairs && ok; t += step) {
-                int mp, nb;
-                f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
-                const int mb = 2 * mp + static_cast<int>(rank);
-                for (int kb = 0; kb < p.k_blocks; ++kb) {
-                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&full[stage], F4_STAGE_BYTES);
-                    tma_load_2d(sA + stage * F4_A_BYTES, &tmA, kb * F4_BK, mb * TC_BM, &full[stage]);
-                    tma_load_2d_mcast(sB + stage * F4_B_BYTES + rank * (F4_B_BYTES / 2), &tmB, kb * F4_BK,
-                                      nb * TC_BN + static_cast<int>(rank) * (TC_BN / 2), &full[stage], 0x3);
-                    last_par[stage] = static_cast<int>(phase);
-                    if (++stage == F4_STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
-                }
-            }
-            if (!ok) {
-                atomicCAS(p.error, 0, ERR_F4_PRODUCER);
-                volatile int never = 0;
-                for (int s = 0; s < F4_STAGES; ++s)
-                    if (last_par[s] >= 0)
-                        mbar_wait_bounded(&full[s], static_cast<uint32_t>(last_par[s]), &never,
-                                          f4_drain_cycles(limit));
-            }
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_mxf4_ue8m0(TC_BM, TC_BN);
-        const uint32_t sfa = tmem_base + F4_SFA_COL, sfb = tmem_base + F4_SFB_COL;
-        int stage = 0;
-        uint32_t phase = 0;
-        uint32_t acc_phase = 0;
-        bool ok = true;
-        for (int t = first; t < num_pairs && ok; t += step) {
-            if (!f4_wait_lane0(tempty, acc_phase ^ 1u, abort_flag, limit, lane)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            uint32_t accumulate = 0;
-            for (int kb = 0; kb < p.k_blocks; ++kb) {
-                if (!f4_wait_lane0(&full[stage], phase, abort_flag, limit, lane)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                if (lane == 0) {
-                    const uint32_t a0 = smem_u32(sA + stage * F4_A_BYTES);
-                    const uint32_t b0 = smem_u32(sB + stage * F4_B_BYTES);
-#pragma unroll
-                    for (int k = 0; k < F4_BK / F4_UMMA_K_BYTES; ++k) {
-                        tc_mma_mxf4(tmem_base, smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES),
-                                    smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc, sfa, sfb, accumulate);
-                        accumulate = 1;
-                    }
-                    tc_commit_mcast(&empty[stage], 0x3);
-                }
-                __syncwarp();
-                accumulate = 1;
-                if (++stage == F4_STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
-                }
-            }
-            if (!ok) break;
-            // one 256-deep K block counts as two 128-deep ones in the issued-work counter
-            if (lane == 0 && p.issued != nullptr) atomicAdd(p.issued, 2ull * static_cast<unsigned long long>(p.k_blocks));
-            if (lane == 0) tc_commit(tfull);
-            __syncwarp();
-            acc_phase ^= 1u;
-        }
-        if (!ok && lane == 0) atomicCAS(p.error, 0, ERR_F4_MMA);
-        if (lane == 0) {
-            tc_commit(done);
-            volatile int never = 0;
-            mbar_wait_bounded(done, 0, &never, f4_drain_cycles(limit));
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------ epilogue
-        const int quarter = warp & 3;
-        const uint32_t lanes = static_cast<uint32_t>(quarter * 32) << 16;
-        uint32_t acc_phase = 0;
-        for (int t = first; t < num_pairs; t += step) {
-            int mp, nb;
-            f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
-            const int mb = 2 * mp + static_cast<int>(rank);
-            if (!f4_wait_lane0(tfull, acc_phase, abort_flag, limit, lane)) {
-                if (lane == 0) atomicCAS(p.error, 0, ERR_F4_EPILOGUE);
-                break;
-            }
-            tc_fence_after();
-            // drain C > 0 into registers, then free the accumulator for the next tile's MMAs
-            uint32_t cb[8];
-            f4_drain(tmem_base + lanes, cb);
-            tc_fence_before();
-            mbar_arrive(tempty);
-            acc_phase ^= 1u;
-            const uint32_t any = f4_update(p, mb, nb, quarter, lane, cb);
-            if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    cluster_sync();  // no multicast data or arrival is still headed for this CTA
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem_base, F4_TMEM_COLS);
-    }
 }
 
 // ---- 2-SM form: one MMA of M = 256 over a CTA pair (tcgen05 .cta_group::2).
@@ -584,34 +390,11 @@ int f4_grid(int64_t work, int threads) {
 
 }  // namespace
 
-int tc4_smem_bytes() { return F4_SMEM_BYTES; }
-
-cudaError_t launch_tc4_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                    cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc4_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             F4_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int pairs = (p.m_tiles / 2) * p.n_tiles;
-    int clusters = sms / 2;
-    if (clusters > pairs) clusters = pairs;
-    if (clusters < 1) clusters = 1;
-    tc4_pair_kernel<<<2 * clusters, TC_THREADS, F4_SMEM_BYTES, s>>>(a, b_half, p);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
                                    cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             D_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current device, and a call costs well under a microsecond
+    cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     const int pairs = (p.m_tiles / 2) * p.n_tiles;
     int clusters = sms / 2;
     if (clusters > pairs) clusters = pairs;

@@ -200,40 +200,6 @@ struct SingleSource {
     }
 };
 
-// One problem, CTA pairs (2-CTA clusters): pair t covers row blocks 2 mp and
-// 2 mp + 1 of the same column block; the CTA of cluster rank r takes row
-// block 2 mp + r. Both CTAs need the same 256 x 128 B tile per stage, so
-// each loads one 128-row half and multicasts it to both.
-struct PairSource {
-    const CUtensorMap* a;
-    const CUtensorMap* b;   // box of 128 rows (half a B tile)
-    const TcParams* p;
-    int rank;
-    __device__ int count() const { return (p->m_tiles / 2) * p->n_tiles; }
-    __device__ void get(int t, Tile& x) const {
-        int mp;
-        tile_coords(t, p->m_tiles / 2, p->n_tiles, mp, x.nb);
-        x.mb = 2 * mp + rank;
-        x.mapA = a;
-        x.mapB = b;
-        x.k_blocks = p->k_blocks;
-        x.mode = p->mode;
-        x.ld = p->ld;
-        x.old_r = p->old_r;
-        x.out_r = p->out_r;
-        x.out_rt = p->out_rt;
-        x.visited = nullptr;
-        x.kflags = nullptr;
-        x.kflags_next = nullptr;
-        x.changed = p->changed;
-        x.masked = p->fmap != nullptr;
-        if (x.masked) build_kmask(p, 2 * mp, 2 * mp + 1, x.nb, x.kmask);
-        x.fmap_next = p->fmap_next;
-        x.fmapT_next = p->fmapT_next;
-        x.fm_ld = p->fm_ld;
-    }
-};
-
 // Many problems: items are numbered problem by problem; offs[p] is the first
 // item of problem p (exclusive prefix of its active tile count).
 struct GroupSource {
@@ -281,7 +247,7 @@ struct GroupSource {
     }
 };
 
-template <class Src, bool kPair = false>
+template <class Src>
 __device__ __forceinline__ void tc_body(const Src& src, int* error, long long limit,
                                         unsigned long long* issued = nullptr) {
     extern __shared__ uint8_t smem_raw[];
@@ -299,15 +265,13 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_tiles = src.count();
-    // CTA pairs walk the pair list together; single CTAs walk the tile list
-    const int first = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
-    const int step = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
-    const uint32_t rank = kPair ? cluster_ctarank() : 0u;
+    const int first = static_cast<int>(blockIdx.x);
+    const int step = static_cast<int>(gridDim.x);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kPair ? 2 : 1);  // pairs: both CTAs' MMAs must release a stage
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -323,7 +287,6 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
     }
     tc_fence_before();
     __syncthreads();
-    if (kPair) cluster_sync();  // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -347,11 +310,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                     }
                     mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
                     tma_load_2d(sA + stage * A_BYTES, x.mapA, kb * TC_BK, x.mb * TC_BM, &full[stage]);
-                    if (kPair)
-                        tma_load_2d_mcast(sB + stage * B_BYTES + rank * (B_BYTES / 2), x.mapB, kb * TC_BK,
-                                          x.nb * TC_BN + static_cast<int>(rank) * (TC_BN / 2), &full[stage], 0x3);
-                    else
-                        tma_load_2d(sB + stage * B_BYTES, x.mapB, kb * TC_BK, x.nb * TC_BN, &full[stage]);
+                    tma_load_2d(sB + stage * B_BYTES, x.mapB, kb * TC_BK, x.nb * TC_BN, &full[stage]);
                     last_par[stage] = static_cast<int>(phase);
                     if (++stage == TC_STAGES) {
                         stage = 0;
@@ -404,10 +363,7 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                                   smem_desc_kmajor_sw128(b0 + k * UMMA_K), idesc, accumulate);
                         accumulate = 1;
                     }
-                    if (kPair)
-                        tc_commit_mcast(&empty[stage], 0x3);  // the stage is free in both CTAs' views
-                    else
-                        tc_commit(&empty[stage]);
+                    tc_commit(&empty[stage]);
                 }
                 __syncwarp();
                 accumulate = 1;
@@ -518,7 +474,6 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
 
     tc_fence_before();
     __syncthreads();
-    if (kPair) cluster_sync();  // no multicast data or arrival is still headed for this CTA
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, TMEM_COLS);
@@ -533,17 +488,6 @@ tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     }
     SingleSource src{&tmA, &tmB, &p};
     tc_body(src, p.error, p.wait_cycles, p.issued);
-}
-
-// Launched as 2-CTA clusters (RMS and PLAIN modes; no K-block skipping).
-__global__ void __launch_bounds__(TC_THREADS, 1)
-tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh, const TcParams p) {
-    if (threadIdx.x == 0) {
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmBh);
-    }
-    PairSource src{&tmA, &tmBh, &p, static_cast<int>(cluster_ctarank())};
-    tc_body<PairSource, true>(src, p.error, p.wait_cycles, p.issued);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -584,30 +528,6 @@ cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const 
     if (e != cudaSuccess) return e;
     tc_product_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(a, b, p);
     return cudaGetLastError();
-}
-
-cudaError_t launch_tc_product_pair(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                   cudaStream_t s) {
-    if (p.kflags != nullptr || (p.m_tiles & 1) != 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    const int pairs = (p.m_tiles / 2) * p.n_tiles;
-    int clusters = sms / 2;
-    if (clusters > pairs) clusters = pairs;
-    if (clusters < 1) clusters = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
-    cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tc_pair_kernel, a, b_half, p);
 }
 
 void* tc_group_kernel_ptr() { return reinterpret_cast<void*>(&tc_group_kernel); }

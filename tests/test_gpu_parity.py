@@ -217,6 +217,18 @@ def test_squaring_operand_forms(ctx):
     assert st["sparse_squarings"] >= 1 and st["sparse_squarings"] + st["product_launches"] == it2 == it
 
 
+@pytest.mark.parametrize("n,d,seed,fmt", [(1500, 3.0, 21, "u8"), (1000, 1.4, 22, "packed"), (777, 2.5, 23, "u8")])
+def test_e4m3_only_option(ctx, n, d, seed, fmt):
+    """options.e4m3_only keeps every tensor-core squaring on E4M3 operands
+    (kind::f8f6f4, the single-CTA kernel): same bits, same product count."""
+    ip, ix, m = er_case(n, d, seed)
+    got, it = run_rms(ctx, m, "rms_tc", fmt=fmt, e4m3_only=True)
+    np.testing.assert_array_equal(got, oracle.closure(n, ip, ix))
+    assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+    st = ctx.stats()
+    assert st["e2m1_products"] == 0 and st["product_launches"] == it
+
+
 def test_smp_wide_rows_long_paths(ctx):
     """n = 135,000 (2,110 words per row, so more than 32 words of the
     touched-word bitmap per warp) on a chain with shortcuts."""
