@@ -289,10 +289,14 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
  * by one CTA per SM from fixed shared-memory tiles (no operand traffic), so
  * that the squaring kernels can be compared with what this GPU issues.
  * kind 0: kind::f8f6f4, E4M3, M128 N256 K32 (the block-sparse squarings);
- * kind 1: kind::mxf4, E2M1 with unit UE8M0 scales, M128 N256 K64 (the dense
- * squarings). iters: MMA groups of 4 per CTA (e.g. 20000, about 5 ms).
- * *tflops receives 2 M N K x MMAs / time. Runs on the legacy default stream
- * and synchronises the device.
+ * kind 1: kind::mxf4, E2M1 with unit UE8M0 scales, M128 N256 K64;
+ * kind 2: the same as one M256 N256 K64 .cta_group::2 MMA per CTA pair (the
+ * form of the dense squaring kernel). iters: MMA groups of 4 per CTA or pair
+ * (e.g. 20000, about 5 ms). *tflops receives 2 M N K x MMAs / time.
+ * kind 3: the integer ALU instead: 64-bit word ORs from registers by 8
+ * warps per SM scheduler (the operation of the bit-row kernels); iters: 128
+ * ORs per thread each (e.g. 20000); *tflops receives tera word-ORs per
+ * second. Runs on the legacy default stream and synchronises the device.
  */
 bmlp_status bmlp_mma_issue_rate(bmlp_ctx* ctx, int32_t kind, int32_t iters, double* tflops);
 

@@ -10,6 +10,7 @@ What it computes (paper Sec. 2 Eq. 1, Sec. 3.3 Eq. 4-5, Sec. 3.4 Thm. 1):
 
 * ``closure``      R1+ = sum_{k>=1} R1^k by per-source BFS from successors
 * ``reach_rows``   selected rows of R1+ with shortest-path depths
+* ``reach_rows_bits`` the same rows as LSB-first uint64 bit rows
 * ``smp``          v R1+ for packed source rows (Eq. 5)
 * ``seminaive``    semi-naive bottom-up evaluation of p <- base ; p <- rec, p
 * ``warshall``     Warshall triple loop (small n)
@@ -61,6 +62,8 @@ def _L():
         if _lib is None:
             lib = ctypes.CDLL(build())
             lib.oracle_reach_rows.argtypes = [ctypes.c_int64, _i64p, _i32p, _i32p, ctypes.c_int64, _u8p, _i32p, _i64p]
+            lib.oracle_reach_rows_bits.argtypes = [ctypes.c_int64, _i64p, _i32p, _i32p, ctypes.c_int64, _u64p,
+                                                   ctypes.c_int64]
             lib.oracle_smp.argtypes = [ctypes.c_int64, _i64p, _i32p, _u64p, ctypes.c_int64, ctypes.c_int64, _u8p, _i32p]
             lib.oracle_seminaive.restype = ctypes.c_int32
             lib.oracle_seminaive.argtypes = [ctypes.c_int64, _u8p, _u8p, _u8p]
@@ -106,6 +109,26 @@ def reach_rows(n, indptr, indices, sources, want_rows=True):
         _L().oracle_reach_rows(n, _p(ip, _i64p), _p(ix, _i32p), _p(src, _i32p), m,
                                _p(out, _u8p) if want_rows else None, _p(depth, _i32p), _p(count, _i64p))
     return out, depth[:m], count[:m]
+
+
+def reach_rows_bits(n, indptr, indices, sources, ldw=None):
+    """Rows of R1+ for ``sources`` as bit rows (uint64 [len(sources), ldw],
+    bit j % 64 of word j / 64 least significant first; ldw defaults to
+    ceil(n / 64)), by the same BFS as ``reach_rows``."""
+    ip, ix = _csr(indptr, indices)
+    src = np.ascontiguousarray(sources, np.int32)
+    ldw = (n + 63) // 64 if ldw is None else int(ldw)
+    out = np.zeros((len(src), ldw), np.uint64)
+    if len(src) and n:
+        _L().oracle_reach_rows_bits(n, _p(ip, _i64p), _p(ix, _i32p), _p(src, _i32p), len(src), _p(out, _u64p), ldw)
+    return out
+
+
+def closure_bits_chunks(n, indptr, indices, rows_per_chunk=4096):
+    """R1+ as bit rows, ``rows_per_chunk`` rows at a time: yields (first row, uint64 block)."""
+    for r0 in range(0, n, rows_per_chunk):
+        r1 = min(n, r0 + rows_per_chunk)
+        yield r0, reach_rows_bits(n, indptr, indices, np.arange(r0, r1, dtype=np.int32))
 
 
 def closure(n, indptr, indices):

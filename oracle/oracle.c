@@ -35,6 +35,31 @@ int oracle_set_threads(int t) {
     return prev;
 }
 
+/* BFS over paths of length >= 1 from source s: dist[j] = shortest path
+ * length s -> j (>= 1), -1 if j is not reached. The search starts at the
+ * successors of s, so s is reached only if it lies on a cycle. queue holds
+ * the reached nodes in BFS order; returns their count, *dmax the deepest. */
+static int64_t bfs_from_successors(int64_t n, const int64_t* indptr, const int32_t* indices, int32_t s,
+                                   int32_t* dist, int32_t* queue, int32_t* dmax_out) {
+    for (int64_t j = 0; j < n; ++j) dist[j] = -1;
+    int64_t head = 0, tail = 0;
+    for (int64_t e = indptr[s]; e < indptr[s + 1]; ++e) {
+        int32_t j = indices[e];
+        if (dist[j] < 0) { dist[j] = 1; queue[tail++] = j; }
+    }
+    int32_t dmax = 0;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        if (dist[u] > dmax) dmax = dist[u];
+        for (int64_t e = indptr[u]; e < indptr[u + 1]; ++e) {
+            int32_t j = indices[e];
+            if (dist[j] < 0) { dist[j] = dist[u] + 1; queue[tail++] = j; }
+        }
+    }
+    *dmax_out = dmax;
+    return tail;
+}
+
 /* Reach rows from a list of sources by BFS that starts at the successors of
  * each source (paths of length >= 1, so a source is in its own row only if
  * it lies on a cycle). For each requested source s:
@@ -51,28 +76,40 @@ void oracle_reach_rows(int64_t n, const int64_t* indptr, const int32_t* indices,
         int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
         #pragma omp for schedule(dynamic, 16)
         for (int64_t r = 0; r < nsrc; ++r) {
-            int32_t s = src[r];
-            for (int64_t j = 0; j < n; ++j) dist[j] = -1;
-            int64_t head = 0, tail = 0;
-            for (int64_t e = indptr[s]; e < indptr[s + 1]; ++e) {
-                int32_t j = indices[e];
-                if (dist[j] < 0) { dist[j] = 1; queue[tail++] = j; }
-            }
             int32_t dmax = 0;
-            while (head < tail) {
-                int32_t u = queue[head++];
-                if (dist[u] > dmax) dmax = dist[u];
-                for (int64_t e = indptr[u]; e < indptr[u + 1]; ++e) {
-                    int32_t j = indices[e];
-                    if (dist[j] < 0) { dist[j] = dist[u] + 1; queue[tail++] = j; }
-                }
-            }
+            const int64_t reached = bfs_from_successors(n, indptr, indices, src[r], dist, queue, &dmax);
             if (out) {
                 uint8_t* row = out + r * n;
                 for (int64_t j = 0; j < n; ++j) row[j] = (uint8_t)(dist[j] > 0);
             }
             if (depth) depth[r] = dmax;
-            if (count) count[r] = tail;
+            if (count) count[r] = reached;
+        }
+        free(dist);
+        free(queue);
+    }
+}
+
+/* The same rows of R1+ as bit rows: bit j % 64 of word j / 64 of row r
+ * (ldw words per row, least significant bit first) is 1 iff j is reachable
+ * from src[r] by >= 1 edge; padding bits stay 0. Lets large closures be
+ * compared word by word without an n x n byte matrix. */
+void oracle_reach_rows_bits(int64_t n, const int64_t* indptr, const int32_t* indices,
+                            const int32_t* src, int64_t nsrc, uint64_t* out, int64_t ldw) {
+    #pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < nsrc; ++r) {
+            int32_t dmax = 0;
+            const int64_t reached = bfs_from_successors(n, indptr, indices, src[r], dist, queue, &dmax);
+            uint64_t* row = out + r * ldw;
+            memset(row, 0, sizeof(uint64_t) * (size_t)ldw);
+            for (int64_t x = 0; x < reached; ++x) {
+                const int32_t j = queue[x];
+                row[j / 64] |= (uint64_t)1 << (j % 64);
+            }
         }
         free(dist);
         free(queue);

@@ -363,7 +363,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     int sw = 0, qcur = 0;
     uint8_t* Q[2] = {nullptr, nullptr};
     uint8_t* QT[2] = {nullptr, nullptr};
-    CUtensorMap mapA4[2], mapB4[2];
+    CUtensorMap mapA4[2], mapB4[2], mapB4x[2];
     const int64_t ld4 = n_pad / 2;
     auto finish_f4 = [&](uint8_t** r, uint8_t** rt) -> bmlp_status {
         launch_e2m1_to_e4m3(Q[qcur], M[sw], n_pad * n_pad, s);
@@ -387,6 +387,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         for (int b = 0; b < 2; ++b) {
             ST(make_tmap(ctx, &mapA4[b], Q[b], n_pad, ld4, ld4, TC_BM));
             ST(make_tmap(ctx, &mapB4[b], QT[b], n_pad, ld4, ld4, TC_BN / 2));
+            ST(make_tmap(ctx, &mapB4x[b], QT[b], n_pad, ld4, ld4, tc4_b1_rows()));
         }
         on_f4 = true;
         qcur = 0;
@@ -408,6 +409,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             for (int b = 0; b < 2; ++b) {
                 ST(make_tmap(ctx, &mapA4[b], Q[b], n_pad, ld4, ld4, TC_BM));
                 ST(make_tmap(ctx, &mapB4[b], QT[b], n_pad, ld4, ld4, TC_BN / 2));
+                ST(make_tmap(ctx, &mapB4x[b], QT[b], n_pad, ld4, ld4, tc4_b1_rows()));
             }
             on_f4 = true;
             qcur = 0;
@@ -416,12 +418,14 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             TcParams p4 = p;
             p4.ld = ld4;
             p4.k_blocks = static_cast<int32_t>(n_pad / 256);
+            p4.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
             p4.fmap = p4.fmapT = p4.fmap_next = p4.fmapT_next = nullptr;
             p4.old_r = Q[qcur];
             p4.out_r = Q[qcur ^ 1];
             p4.out_rt = QT[qcur ^ 1];
             ST(tm.begin());
-            CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], p4, ctx->sm_count, s), "tensor-core product launch");
+            CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], mapB4x[qcur], p4, ctx->sm_count, s),
+               "tensor-core product launch");
             ST(tm.end());
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;
@@ -431,7 +435,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             ST(tm.collect());
             unsigned long long kbs = 0;
             memcpy(&kbs, ctx->h_ctl + CTL_ISSUED, sizeof(kbs));
-            ctx->stats.issued_ops = 2.0 * TC_BM * TC_BN * TC_BK * static_cast<double>(kbs);
+            ctx->stats.issued_ops = 2.0 * TC_BM * 32.0 * TC_BK * static_cast<double>(kbs);
             *iters = it + 1;
             qcur ^= 1;
             if (!changed) {
@@ -465,10 +469,10 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         int changed = 0;
         ST(read_ctl(ctx, s, &changed));
         ST(tm.collect());
-        // multiply-adds actually issued: K blocks run x (128 x 256 x 128) each, times 2
+        // multiply-adds actually issued (units of 128 x 32 x 128), times 2
         unsigned long long kbs = 0;
         memcpy(&kbs, ctx->h_ctl + CTL_ISSUED, sizeof(kbs));
-        ctx->stats.issued_ops = 2.0 * TC_BM * TC_BN * TC_BK * static_cast<double>(kbs);
+        ctx->stats.issued_ops = 2.0 * TC_BM * 32.0 * TC_BK * static_cast<double>(kbs);
         *iters = it + 1;
         cur = nxt;
         if (!changed) {

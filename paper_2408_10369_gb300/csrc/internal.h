@@ -50,7 +50,7 @@ struct TcParams {
     uint8_t* fmap_next;
     uint8_t* fmapT_next;
     int32_t fm_ld;
-    unsigned long long* issued; // K blocks actually multiplied (one MMA group each), or null
+    unsigned long long* issued; // multiply-adds issued in units of 128 x 32 x 128 (rows x columns x K), or null
 };
 
 // One problem of a grouped batch (device copy; built on the host).
@@ -231,10 +231,14 @@ int tc_smem_bytes();
 cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, int grid,
                               cudaStream_t s);
 // squaring step (RMS mode only) on packed E2M1 operands (n_pad x n_pad / 2 bytes, p.ld = n_pad / 2,
-// p.k_blocks = n_pad / 256) as one M = 256 MMA per CTA pair (tcgen05 .cta_group::2, 2-CTA clusters);
-// maps: A box 128 rows, B box 128 rows (half a tile), 128 bytes wide
-cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                   cudaStream_t s);
+// p.k_blocks = n_pad / 256) as M = 256 MMAs per CTA pair (tcgen05 .cta_group::2, 2-CTA clusters) on pair tiles
+// of 256 rows x tc4_tile_n() columns (p.n_tiles = ceil(n_pad / tc4_tile_n())); maps over R (A, box 128 rows)
+// and R^T (b0: box 128 rows; b1: box tc4_b1_rows() rows), 128 bytes wide. p.issued counts 128 x 32 x 128
+// multiply-add units.
+int tc4_tile_n();
+int tc4_b1_rows();
+cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1,
+                                   const TcParams& p, int sms, cudaStream_t s);
 // E4M3 bytes <-> packed E2M1 nibbles (sizes multiples of 16 bytes)
 void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s);
 void launch_e2m1_to_e4m3(const uint8_t* in, uint8_t* out, int64_t bytes_out, cudaStream_t s);

@@ -10,19 +10,21 @@
 // the E4M3 kernel, a 128-byte K block carries 256 elements instead of 128:
 // half the operand bytes per Boolean operation.
 //
-// Structure (2-CTA clusters, one CTA per SM, persistent over tile pairs):
-//   warp 0      TMA producer (both CTAs): the CTA's own 128 rows of A and
-//               its 128-row half of the pair's 256-row B^T tile, 128 bytes of
-//               K per stage, 128-byte swizzle; both CTAs' copies complete on
-//               the even CTA's barrier (no multicast loads);
-//   warp 1      MMA issuer (even CTA): 4 x tcgen05.mma.cta_group::2
-//               (M=256, N=256, K=64) per stage into one TMEM accumulator
-//               (256 FP32 columns in each CTA); the scale factors occupy
-//               further TMEM columns;
-//   warps 2..5  epilogue (both CTAs): drains the accumulator into registers as bits and
-//               frees it at once, then computes R' = R | [C > 0], writes R'
-//               and R'^T (transposed through warp ballots) and raises
-//               `changed` if R' != R.
+// Structure (2-CTA clusters, one CTA per SM, persistent over pair tiles of
+// 256 rows x 480 columns):
+//   warp 0      TMA producer (both CTAs): the CTA's own 128 rows of A and its
+//               240 of the tile's 480 B^T rows (128 of the first 256, 112 of
+//               the last 224), 128 bytes of K per stage, 4 stages of 46 KB,
+//               128-byte swizzle; both CTAs' copies complete on the even
+//               CTA's barrier (no multicast loads);
+//   warp 1      MMA issuer (even CTA): per 64-deep K step one
+//               tcgen05.mma.cta_group::2 kind::mxf4 of M=256, N=256 into TMEM
+//               columns 0..255 and one of M=256, N=224 into columns 256..479
+//               (in each CTA); the unit scale factors fill columns 480..511;
+//   warps 2..5  epilogue (both CTAs): drains the accumulator into registers as
+//               bits and frees it at once, then computes R' = R | [C > 0],
+//               writes R' and R'^T (transposed through warp ballots) and
+//               raises `changed` if R' != R.
 // Every mbarrier wait is bounded; on expiry the CTA records an error code,
 // waits (bounded) for its own copies and MMAs in flight, frees TMEM and exits.
 #include <cudaTypedefs.h>
@@ -36,8 +38,6 @@ namespace {
 constexpr int F4_BK = 128;                     // bytes of K per stage (256 elements)
 constexpr int F4_UMMA_K_BYTES = 32;            // 64 E2M1 elements per MMA
 constexpr int F4_TMEM_COLS = 512;
-constexpr int F4_SFA_COL = 256;                // scale factors of A (all 2^0)
-constexpr int F4_SFB_COL = 384;                // scale factors of B (all 2^0)
 constexpr uint32_t F4_UE8M0_ONE4 = 0x7F7F7F7Fu;  // four UE8M0 scales of 2^0
 
 constexpr int F4_GROUP_M = 8;  // raster: 8 row-block pairs share B tiles in L2
@@ -93,11 +93,59 @@ __device__ __forceinline__ uint32_t f4_bits32(const uint4& v) {
     return f4_gather8(v.x) | (f4_gather8(v.y) << 8) | (f4_gather8(v.z) << 16) | (f4_gather8(v.w) << 24);
 }
 
-// Epilogue, part 1: C > 0 for the 256 accumulator columns of this thread's
-// TMEM lane, as 8 x 32 bits.
-__device__ __forceinline__ void f4_drain(uint32_t taddr, uint32_t (&cb)[8]) {
+// ---- The squaring kernel: one M = 256 MMA per CTA pair (tcgen05
+// .cta_group::2) per 64-deep K step, on a pair tile of 256 rows x BN columns.
+// Each CTA keeps only its own 128 rows of A and its half of the B rows the
+// pair needs, and the even CTA issues every MMA; the accumulator rows land in
+// each CTA's own TMEM (CTA r holds output rows 128 r .. 128 r + 127 of the
+// pair's tile). A wider tile reads fewer operand bytes per Boolean operation
+// from L2: per 256-deep K block a CTA stages 16 KB of A and 128 (N1 = 0) or
+// 240 (N1 = 224) rows of B for 256 x BN x 256 multiply-adds.
+//
+// N1 = 0:   BN = 256, one N = 256 MMA per K step, 6 stages of 32 KB.
+// N1 = 224: BN = 480, an N = 256 MMA into TMEM columns 0..255 and an N = 224
+//           MMA into columns 256..479 per K step (the scale factors take
+//           columns 480..511), 4 stages of 46 KB; a tile whose columns from
+//           256 on all lie beyond n_pad issues only the first MMA.
+template <int N1>
+struct Duo {
+    static constexpr int BN = TC_BN + N1;               // output columns of a pair tile
+    static constexpr int B0_ROWS = TC_BN / 2;           // this CTA's rows of the N = 256 part
+    static constexpr int B1_ROWS = N1 / 2;              // and of the N1 part
+    static constexpr int A_BYTES = TC_BM * F4_BK;       // 16 KiB
+    static constexpr int B0_BYTES = B0_ROWS * F4_BK;    // 16 KiB
+    static constexpr int B1_BYTES = B1_ROWS * F4_BK;
+    static constexpr int B_BYTES = B0_BYTES + B1_BYTES;
+    static constexpr int STAGES = N1 ? 4 : 6;
+    static constexpr int CHUNKS = BN / 32;              // 32-column chunks of the epilogue
+    static constexpr int SFA_COL = N1 ? 480 : 256;      // scale factors (all 2^0; with N1 both operands
+    static constexpr int SFB_COL = N1 ? 480 : 384;      // read the same filled columns)
+    static constexpr int SF_FILL = N1 ? 32 : 0;         // N1: columns 480..511 hold 2^0 scales
+    static constexpr int OFF_A = 0;
+    static constexpr int OFF_B = OFF_A + STAGES * A_BYTES;
+    static constexpr int OFF_BAR = OFF_B + STAGES * B_BYTES;
+    static constexpr int NUM_BARS = 2 * STAGES + 3;     // full[], empty[], tfull, tempty, done
+    static constexpr int OFF_MISC = OFF_BAR + NUM_BARS * 8;
+    static constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;
+    static_assert(N1 == 0 || (N1 % 32 == 0 && N1 <= 224), "second MMA width");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+    static_assert(B_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
+};
+
+// Second MMA width of the squaring kernel's pair tile (BN = 480). Measured on GB300 at n = 32,768: 8.88 PFLOP/s
+// against 7.33 for the 256-column tile (N1 = 0), which reads a third more operand bytes per Boolean operation.
+constexpr int TC4_N1 = 224;
+
+constexpr int ERR_D_PRODUCER = 0x211;
+constexpr int ERR_D_MMA = 0x212;
+constexpr int ERR_D_EPILOGUE = 0x213;
+
+// Epilogue, part 1: C > 0 for the accumulator columns of this thread's TMEM
+// lane, as CHUNKS x 32 bits.
+template <int CHUNKS>
+__device__ __forceinline__ void f4_drain(uint32_t taddr, uint32_t (&cb)[CHUNKS]) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < CHUNKS; ++c) {
         uint32_t v[32];
         tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c * 32), v);
         tmem_ld_wait();
@@ -108,23 +156,32 @@ __device__ __forceinline__ void f4_drain(uint32_t taddr, uint32_t (&cb)[8]) {
     }
 }
 
-// Epilogue, part 2: R' = R | C for row (mb, quarter, lane) of output tile
-// (mb, nb): writes R' and, through warp ballots, R'^T; returns the bits that
-// changed (nonzero in some lane iff R' != R in this warp's 32 x 256 block).
-__device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int nb, int quarter, int lane,
-                                              const uint32_t (&cb)[8]) {
+// cb[c] for a run-time c through selects, so that cb stays in registers.
+template <int CHUNKS>
+__device__ __forceinline__ uint32_t f4_pick(const uint32_t (&cb)[CHUNKS], int c) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < CHUNKS; ++j) v = (j == c) ? cb[j] : v;
+    return v;
+}
+
+// Epilogue, part 2: R' = R | C for row (mb, quarter, lane) of the pair tile
+// whose first column is col_base: writes R' and, through warp ballots, R'^T
+// for every 32-column chunk below n_pad; returns the bits that changed
+// (nonzero in some lane iff R' != R in this warp's rows).
+template <int CHUNKS>
+__device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int64_t col_base, int64_t n_pad, int quarter,
+                                              int lane, const uint32_t (&cb)[CHUNKS]) {
     const int64_t row = static_cast<int64_t>(mb) * TC_BM + quarter * 32 + lane;
     const int64_t rt_col = static_cast<int64_t>(mb) * (TC_BM / 2) + quarter * 16;  // byte of row in R'^T
     uint32_t any = 0;
 #pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
-        const int64_t col0 = static_cast<int64_t>(nb) * TC_BN + c * 32;
+    for (int c = 0; c < CHUNKS; ++c) {
+        const int64_t col0 = col_base + c * 32;
+        if (col0 >= n_pad) break;
         const int64_t off = row * p.ld + col0 / 2;
         const uint32_t obits = f4_bits32(*reinterpret_cast<const uint4*>(p.old_r + off));
-        // cb[c] by selects, so that cb stays in registers
-        const uint32_t cbits = c < 4 ? (c < 2 ? (c == 0 ? cb[0] : cb[1]) : (c == 2 ? cb[2] : cb[3]))
-                                     : (c < 6 ? (c == 4 ? cb[4] : cb[5]) : (c == 6 ? cb[6] : cb[7]));
-        const uint32_t nbits = obits | cbits;
+        const uint32_t nbits = obits | f4_pick(cb, c);
         any |= nbits ^ obits;
         *reinterpret_cast<uint4*>(p.out_r + off) = f4_nibbles32(nbits);
         // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
@@ -139,41 +196,25 @@ __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int nb,
     return any;
 }
 
-// ---- 2-SM form: one MMA of M = 256 over a CTA pair (tcgen05 .cta_group::2).
-// Each CTA keeps only its own 128 rows of A and its half of the 256-row B
-// tile, so a stage is 32 KB instead of 48 KB and 6 stages fit: more operand
-// bytes in flight per unit of tensor work. The even CTA issues every MMA; the
-// accumulator rows land in each CTA's own TMEM (CTA r holds output rows
-// 128 r .. 128 r + 127 of the pair's 256 x 256 tile).
-constexpr int D_A_BYTES = TC_BM * F4_BK;           // 16 KiB
-constexpr int D_B_BYTES = (TC_BN / 2) * F4_BK;     // 16 KiB
-constexpr int D_STAGE_BYTES = D_A_BYTES + D_B_BYTES;
-constexpr int D_STAGES = 6;
-constexpr int D_OFF_A = 0;
-constexpr int D_OFF_B = D_OFF_A + D_STAGES * D_A_BYTES;
-constexpr int D_OFF_BAR = D_OFF_B + D_STAGES * D_B_BYTES;
-constexpr int D_NUM_BARS = 2 * D_STAGES + 3;       // full[], empty[], tfull, tempty, done
-constexpr int D_OFF_MISC = D_OFF_BAR + D_NUM_BARS * 8;
-constexpr int D_SMEM_END = D_OFF_MISC + 16;
-constexpr int D_SMEM_BYTES = D_SMEM_END + 1024;
-constexpr int ERR_D_PRODUCER = 0x211;
-constexpr int ERR_D_MMA = 0x212;
-constexpr int ERR_D_EPILOGUE = 0x213;
-
+// tmA: A = R (box 128 rows x 128 bytes); tmB0 / tmB1: B^T = R^T (boxes of
+// B0_ROWS / B1_ROWS rows x 128 bytes; tmB1 unused when N1 = 0).
+template <int N1>
 __global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
-tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+               const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
+    using C = Duo<N1>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem + D_OFF_A;
-    uint8_t* sB = smem + D_OFF_B;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + D_OFF_BAR);
-    uint64_t* full = bars;                 // even CTA: both CTAs' copies of a stage complete here
-    uint64_t* empty = bars + D_STAGES;     // each CTA: the even CTA's MMAs released the stage
-    uint64_t* tfull = bars + 2 * D_STAGES; // each CTA: the accumulator holds a finished tile
-    uint64_t* tempty = tfull + 1;          // even CTA: both CTAs' epilogues drained the accumulator
-    uint64_t* done = tempty + 1;           // even CTA: every MMA it issued has completed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + D_OFF_MISC);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + D_OFF_MISC + 4);
+    uint8_t* sA = smem + C::OFF_A;
+    uint8_t* sB = smem + C::OFF_B;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    uint64_t* full = bars;                  // even CTA: both CTAs' copies of a stage complete here
+    uint64_t* empty = bars + C::STAGES;     // each CTA: the even CTA's MMAs released the stage
+    uint64_t* tfull = bars + 2 * C::STAGES; // each CTA: the accumulator holds a finished tile
+    uint64_t* tempty = tfull + 1;           // even CTA: both CTAs' epilogues drained the accumulator
+    uint64_t* done = tempty + 1;            // even CTA: every MMA it issued has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::OFF_MISC + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
@@ -183,9 +224,13 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int first = static_cast<int>(blockIdx.x >> 1);
     const int step = static_cast<int>(gridDim.x >> 1);
     const long long limit = p.wait_cycles;
+    const int64_t n_pad = static_cast<int64_t>(p.m_tiles) * TC_BM;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < D_STAGES; ++s) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB0);
+        if (N1) tma_prefetch_desc(&tmB1);
+        for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -204,12 +249,18 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     if (warp >= 2) {
-        // every scale factor of A and B is 2^0: 8 columns each, all 128 lanes of this CTA
+        // every scale factor of A and B is 2^0, in all 128 lanes of this CTA
         const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
         const uint32_t ones[8] = {F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4,
                                   F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4};
-        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFA_COL, ones);
-        tmem_st_32x32b_x8(tmem_base + lanes + F4_SFB_COL, ones);
+        if (C::SF_FILL) {
+#pragma unroll
+            for (int c = 0; c < C::SF_FILL; c += 8)
+                tmem_st_32x32b_x8(tmem_base + lanes + static_cast<uint32_t>(C::SFA_COL + c), ones);
+        } else {
+            tmem_st_32x32b_x8(tmem_base + lanes + C::SFA_COL, ones);
+            tmem_st_32x32b_x8(tmem_base + lanes + C::SFB_COL, ones);
+        }
         tmem_st_wait();
     }
     tc_fence_before();
@@ -228,18 +279,26 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int mp, nb;
                 f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
                 const int mb = 2 * mp + static_cast<int>(rank);
+                const int64_t col_base = static_cast<int64_t>(nb) * C::BN;
+                const bool has1 = N1 != 0 && col_base + TC_BN < n_pad;
+                const uint32_t tx = 2u * static_cast<uint32_t>(C::A_BYTES + C::B0_BYTES + (has1 ? C::B1_BYTES : 0));
                 for (int kb = 0; kb < p.k_blocks; ++kb) {
                     if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, limit)) {
                         ok = false;
                         break;
                     }
                     const uint32_t bar = mapa_shared(smem_u32(&full[stage]), 0);
-                    if (leader) mbar_arrive_expect_tx(&full[stage], 2 * D_STAGE_BYTES);
-                    tma_load_2d_2sm(sA + stage * D_A_BYTES, &tmA, kb * F4_BK, mb * TC_BM, bar);
-                    tma_load_2d_2sm(sB + stage * D_B_BYTES, &tmB, kb * F4_BK,
-                                    nb * TC_BN + static_cast<int>(rank) * (TC_BN / 2), bar);
+                    if (leader) mbar_arrive_expect_tx(&full[stage], tx);
+                    uint8_t* sb = sB + stage * C::B_BYTES;
+                    tma_load_2d_2sm(sA + stage * C::A_BYTES, &tmA, kb * F4_BK, mb * TC_BM, bar);
+                    tma_load_2d_2sm(sb, &tmB0, kb * F4_BK,
+                                    static_cast<int>(col_base) + static_cast<int>(rank) * C::B0_ROWS, bar);
+                    if (has1)
+                        tma_load_2d_2sm(sb + C::B0_BYTES, &tmB1, kb * F4_BK,
+                                        static_cast<int>(col_base) + TC_BN + static_cast<int>(rank) * C::B1_ROWS,
+                                        bar);
                     issued = true;
-                    if (++stage == D_STAGES) {
+                    if (++stage == C::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -257,13 +316,17 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (even CTA)
         if (leader) {
-            const uint32_t idesc = idesc_mxf4_ue8m0(2 * TC_BM, TC_BN);
-            const uint32_t sfa = tmem_base + F4_SFA_COL, sfb = tmem_base + F4_SFB_COL;
+            const uint32_t idesc0 = idesc_mxf4_ue8m0(2 * TC_BM, TC_BN);
+            const uint32_t idesc1 = idesc_mxf4_ue8m0(2 * TC_BM, N1 ? N1 : TC_BN);
+            const uint32_t sfa = tmem_base + C::SFA_COL, sfb = tmem_base + C::SFB_COL;
             int stage = 0;
             uint32_t phase = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
             for (int t = first; t < num_pairs && ok; t += step) {
+                int mp, nb;
+                f4_pair_coords(t, m_pairs, p.n_tiles, mp, nb);
+                const bool has1 = N1 != 0 && static_cast<int64_t>(nb) * C::BN + TC_BN < n_pad;
                 if (!f4_wait_lane0(tempty, acc_phase ^ 1u, abort_flag, limit, lane)) {
                     ok = false;
                     break;
@@ -277,28 +340,34 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     tc_fence_after();
                     if (lane == 0) {
-                        const uint32_t a0 = smem_u32(sA + stage * D_A_BYTES);
-                        const uint32_t b0 = smem_u32(sB + stage * D_B_BYTES);
+                        const uint32_t a0 = smem_u32(sA + stage * C::A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + stage * C::B_BYTES);
 #pragma unroll
                         for (int k = 0; k < F4_BK / F4_UMMA_K_BYTES; ++k) {
-                            tc_mma_mxf4_2sm(tmem_base, smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES),
-                                            smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc, sfa, sfb,
-                                            accumulate);
+                            const uint64_t ad = smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES);
+                            tc_mma_mxf4_2sm(tmem_base, ad, smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc0,
+                                            sfa, sfb, accumulate);
+                            if (has1)
+                                tc_mma_mxf4_2sm(tmem_base + TC_BN, ad,
+                                                smem_desc_kmajor_sw128(b0 + C::B0_BYTES + k * F4_UMMA_K_BYTES),
+                                                idesc1, sfa, sfb, accumulate);
                             accumulate = 1;
                         }
                         tc_commit_2sm_mcast(&empty[stage], 0x3);  // the stage is free in both CTAs
                     }
                     __syncwarp();
                     accumulate = 1;
-                    if (++stage == D_STAGES) {
+                    if (++stage == C::STAGES) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
                 if (!ok) break;
-                // two 128-row tiles of 256-deep K blocks: four 128-deep blocks per K block
+                // multiply-adds issued, in units of 128 x 32 x 128: per 256-deep K block two 128-row halves,
+                // two 128-deep halves and 8 (+ N1 / 32) column chunks
                 if (lane == 0 && p.issued != nullptr)
-                    atomicAdd(p.issued, 4ull * static_cast<unsigned long long>(p.k_blocks));
+                    atomicAdd(p.issued, 4ull * static_cast<unsigned long long>(TC_BN / 32 + (has1 ? N1 / 32 : 0)) *
+                                            static_cast<unsigned long long>(p.k_blocks));
                 if (lane == 0) tc_commit_2sm_mcast(tfull, 0x3);
                 __syncwarp();
                 acc_phase ^= 1u;
@@ -326,12 +395,15 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 break;
             }
             tc_fence_after();
-            uint32_t cb[8];
-            f4_drain(tmem_base + lanes, cb);
+            // drain C > 0 into registers, then free the accumulator for the next tile's MMAs (columns of a
+            // tile that got no second MMA hold stale counts; f4_update stops before them)
+            uint32_t cb[C::CHUNKS];
+            f4_drain<C::CHUNKS>(tmem_base + lanes, cb);
             tc_fence_before();
             mbar_arrive_cluster(tempty_even);
             acc_phase ^= 1u;
-            const uint32_t any = f4_update(p, mb, nb, quarter, lane, cb);
+            const uint32_t any =
+                f4_update<C::CHUNKS>(p, mb, static_cast<int64_t>(nb) * C::BN, n_pad, quarter, lane, cb);
             if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
         }
     }
@@ -390,17 +462,27 @@ int f4_grid(int64_t work, int threads) {
 
 }  // namespace
 
-cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
-                                   cudaStream_t s) {
+template <int N1>
+cudaError_t launch_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1, const TcParams& p, int sms,
+                       cudaStream_t s) {
     // set on every launch: the attribute belongs to the current device, and a call costs well under a microsecond
-    cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Duo<N1>::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int pairs = (p.m_tiles / 2) * p.n_tiles;
     int clusters = sms / 2;
     if (clusters > pairs) clusters = pairs;
     if (clusters < 1) clusters = 1;
-    tc4_duo_kernel<<<2 * clusters, TC_THREADS, D_SMEM_BYTES, s>>>(a, b_half, p);
+    tc4_duo_kernel<N1><<<2 * clusters, TC_THREADS, Duo<N1>::SMEM_BYTES, s>>>(a, b0, b1, p);
     return cudaGetLastError();
+}
+
+int tc4_tile_n() { return Duo<TC4_N1>::BN; }
+int tc4_b1_rows() { return Duo<TC4_N1>::B1_ROWS; }
+
+cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1,
+                                   const TcParams& p, int sms, cudaStream_t s) {
+    return launch_duo<TC4_N1>(a, b0, b1, p, sms, s);
 }
 
 void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s) {

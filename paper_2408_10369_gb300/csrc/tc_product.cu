@@ -373,7 +373,8 @@ __device__ __forceinline__ void tc_body(const Src& src, int* error, long long li
                 }
             }
             if (!ok) break;
-            if (lane == 0 && issued != nullptr) atomicAdd(issued, nk);
+            // 128 x 256 x 128 multiply-adds per K block run = 8 units of 128 x 32 x 128
+            if (lane == 0 && issued != nullptr) atomicAdd(issued, 8ull * nk);
             if (lane == 0) tc_commit(&tfull[acc]);
             __syncwarp();
             acc ^= 1;

@@ -438,3 +438,21 @@ def test_thread_count_does_not_change_results():
     finally:
         oracle.set_threads(prev)
     np.testing.assert_array_equal(one, many)
+
+
+@pytest.mark.parametrize("n,d,seed", [(1, 0.0, 0), (63, 1.5, 1), (64, 2.0, 2), (200, 1.3, 3), (333, 1.1, 4)])
+def test_reach_rows_bits_against_matrix_powers(n, d, seed):
+    """The bit-row output, unpacked with numpy (LSB first), is the closure by
+    matrix powers; padding bits past n are zero; a wider row stride only adds
+    zero words."""
+    ip, ix = wl.er_graph(n, d, seed)
+    m = wl.dense_u8(n, ip, ix)
+    want = closure_by_powers(m)
+    bits = oracle.reach_rows_bits(n, ip, ix, np.arange(n, dtype=np.int32))
+    assert bits.shape == (n, (n + 63) // 64)
+    full = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")
+    assert np.array_equal(full[:, :n], want) and not full[:, n:].any()
+    wide = oracle.reach_rows_bits(n, ip, ix, np.arange(n, dtype=np.int32), ldw=bits.shape[1] + 2)
+    assert np.array_equal(wide[:, :bits.shape[1]], bits) and not wide[:, bits.shape[1]:].any()
+    chunks = np.concatenate([blk for _, blk in oracle.closure_bits_chunks(n, ip, ix, rows_per_chunk=50)]) if n else bits
+    assert np.array_equal(chunks, bits)
