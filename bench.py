@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other variants and the learned choice")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (E4M3-only closure, probes, bit-row product, query batch, "
+                         "knowledge-graph batch, dispatcher on held-out graphs)")
     ap.add_argument("--workload", default="er",
                     choices=["er", "powerlaw_smp", "kg_batch", "isforeign", "insert", "dg_partial"],
                     help="er: the closure benchmark (default); powerlaw_smp: 4,096 selective query rows on the "
@@ -69,6 +72,9 @@ def parse():
                          "1,000 new contains facts added incrementally to hasPlace of that hierarchy; dg_partial: one "
                          "partially grounded query path(c, Y) on an ER graph of n = 5,000 with --degree (default 50)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
+    ap.add_argument("--sharded", action="store_true",
+                    help="powerlaw_smp / kg_batch: the multi-rank path (cost partition + all-gather) even on one "
+                         "rank; under torchrun with N > 1 it is the default")
     args = ap.parse_args()
     if args.variant is None:
         args.variant = {"er": "rms_tc", "powerlaw_smp": "smp_packed", "dg_partial": "smp_packed"}.get(args.workload,
@@ -217,6 +223,30 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def oracle_parity(n, ip, ix, got, fmt):
+    """The closure the GPU returned (device tensor: packed bit rows, or n x n
+    bytes for fmt "u8") against the oracle's closure of the same graph, every
+    one of the n^2 bits, compared as LSB-first 64-bit words in blocks of 4,096
+    rows. Part of the CPU (oracle) leg; runs after the timed regions."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    g = got.cpu().numpy()
+    ldw = (n + 63) // 64
+    bad = 0
+    for r0, blk in oracle.closure_bits_chunks(n, ip, ix, 4096):
+        part = g[r0:r0 + blk.shape[0]]
+        if fmt == "u8":
+            pk = np.packbits(part != 0, axis=1, bitorder="little")
+            pk = np.pad(pk, ((0, 0), (0, ldw * 8 - pk.shape[1])))
+            words = np.ascontiguousarray(pk).view(np.uint64)
+        else:
+            words = np.ascontiguousarray(part).view(np.uint64)[:, :ldw]
+        bad += int((words != blk).any(axis=1).sum())
+    return {"result": "bit-exact vs oracle, n^2 bits" if bad == 0 else "MISMATCH",
+            "bits_compared": n * n, "mismatched_rows": bad, "check_s": time.perf_counter() - t0}
+
+
 def run_reference(args, rank, world):
     import workloads as wl
     import oracle
@@ -245,6 +275,271 @@ def run_reference(args, rank, world):
                              "sample": "BFS closure rows for %d of %d sources per step, scaled to the full closure" % (rows, n)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def kg_items():
+    """The knowledge-graph workload on the device: every relation's closure
+    over its active entities (1,345) and 200 two-relation compositions, as
+    bmlp_batch_run problem dicts (packed bit rows) plus the tensors to keep."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2408_10369_gb300 import bmlp
+    rels = wl.kg_relations()
+    items, keep = [], []
+    for r in rels:
+        R = torch.from_numpy(wl.csr_to_packed(r["n"], r["indptr"], r["indices"]).view(np.int64)).cuda()
+        o = torch.zeros_like(R)
+        keep += [R, o]
+        items.append(dict(n=r["n"], R1=R, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
+    for a, b in wl.kg_compose_pairs(rels, 200, 0):
+        n, ents, c1, c2 = wl.union_space(rels[a], rels[b])
+        R1 = torch.from_numpy(wl.csr_to_packed(n, *c1).view(np.int64)).cuda()
+        R2 = torch.from_numpy(wl.csr_to_packed(n, *c2).view(np.int64)).cuda()
+        o = torch.zeros_like(R1)
+        keep += [R1, R2, o]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
+    return items, keep
+
+
+def ev_time(stream, fn, steps):
+    """Mean milliseconds of fn() over `steps` calls, CUDA events on `stream`."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check):
+    """Secondary measurements on the same GPU after the headline, each bounded
+    to seconds: the E4M3-only closure, the issue-rate probes, the bit-row
+    product and the frontier kernels against their rooflines, the selective
+    query batch (4,096 rows on the n = 65,536 power-law graph), the grouped
+    knowledge-graph batch (1,545 programs) and the learned dispatcher on 200
+    held-out corpus graphs. With `check`, the CPU (oracle) leg afterwards
+    compares the query rows and every dispatched closure with the oracle."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2408_10369_gb300 import bmlp
+    from paper_2408_10369_gb300 import dispatch_corpus as dc
+    PK = bmlp.BMLP_FMT_PACKED64
+    ex = {}
+    probes = {"e4m3_m128n256k32": ctx.mma_issue_rate(0), "e2m1_m128n256k64": ctx.mma_issue_rate(1),
+              "e2m1_2sm_m256n256k64": ctx.mma_issue_rate(2), "word_or_tera_per_s": ctx.mma_issue_rate(3)}
+    ex["issue_rate_probes_tflops"] = probes
+
+    # -- every tensor-core squaring on E4M3 operands (options.e4m3_only), same graph
+    o2 = torch.empty_like(R)
+    ctx.rms(R, n, o2, fmt=FMT, variant="rms_tc", stream=stream, e4m3_only=True)
+    acc = {"pm": 0.0, "pn": 0}
+
+    def e4():
+        ctx.rms(R, n, o2, fmt=FMT, variant="rms_tc", stream=stream, e4m3_only=True, profile=True)
+        st = ctx.stats()
+        acc["pm"] += st["product_ms"]
+        acc["pn"] += st["product_launches"]
+    ms = ev_time(stream, e4, 3)
+    it4 = ctx.stats()["iterations"]
+    kt = 2.0 * n ** 3 / (acc["pm"] / max(acc["pn"], 1) / 1e3) / 1e12 if acc["pn"] else None
+    ex["e4m3_only"] = {"ms_per_closure": ms, "eff_tops": it4 * 2.0 * n ** 3 / ms / 1e9,
+                       "kernel": "tc_product_kernel", "kernel_tflops": kt, "peak": bf16 * FP8_PER_BF16,
+                       "frac": kt / (bf16 * FP8_PER_BF16) if kt else None,
+                       "issue_rate_frac": kt / probes["e4m3_m128n256k32"] if kt else None,
+                       "bit_exact_vs_headline": bool(torch.equal(o2, out_main))}
+    del o2
+
+    # -- one bit-row product R <- R + R R (product_packed_kernel) on the sparse input: ER mean out-degree 4
+    pk = {}
+    for nn in (8192, n):
+        if nn == n and FMT == PK:
+            Pn, nnz = R, len(ix)
+        else:
+            pip, pix = wl.er_graph(nn, args.degree, 0)
+            Pn, nnz = torch.from_numpy(wl.csr_to_packed(nn, pip, pix).view(np.int64)).cuda(), len(pix)
+        on = torch.zeros_like(Pn)
+        tms = []
+        for _ in range(4):
+            try:
+                ctx.rms(Pn, nn, on, fmt=PK, variant="rms_packed", stream=stream, max_iters=1, profile=True)
+            except bmlp.BmlpError as e:
+                if e.status != bmlp.BMLP_ERR_NOT_CONVERGED:
+                    raise
+            tms.append(ctx.stats()["product_ms"])
+        t = statistics.median(tms[1:]) / 1e3
+        words = (nn + 63) // 64
+        hbm_bytes = 2.0 * nn * words * 8          # read R (A operand and old R), write R' (compulsory)
+        gathered = float(nnz) * words * 8         # the B rows named by A's bits
+        ors = float(nnz) * words
+        pk["n%d" % nn] = {"ms": t * 1e3, "nnz": nnz, "compulsory_hbm_bytes": hbm_bytes,
+                          "hbm_gbs": hbm_bytes / t / 1e9, "hbm_frac": hbm_bytes / t / 1e9 / hbm,
+                          "gathered_bytes": gathered, "gathered_gbs": gathered / t / 1e9,
+                          "word_or_tera_per_s": ors / t / 1e12,
+                          "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"]}
+        del on
+    ex["packed_product"] = pk
+
+    # -- selective queries: 4,096 rows of 1-64 sources on the n = 65,536 power-law graph (Zipf 2.1 out-degrees)
+    nq, q = 65536, 4096
+    pip, pix = wl.powerlaw_csr(nq, 2.1, 1000, 0)
+    Ph = wl.csr_to_packed(nq, pip, pix)
+    P = torch.from_numpy(Ph.view(np.int64)).cuda()
+    srch = wl.query_rows(nq, q, 1, 64, 0)
+    src = torch.from_numpy(srch.view(np.int64)).cuda()
+    qo = torch.zeros_like(src)
+    ctx.smp(P, nq, src, q, qo, fmt=PK, variant="smp_packed", stream=stream)
+    kacc = {"pm": 0.0}
+
+    def smp():
+        ctx.smp(P, nq, src, q, qo, fmt=PK, variant="smp_packed", stream=stream, profile=True)
+        kacc["pm"] += ctx.stats()["product_ms"]
+    ms = ev_time(stream, smp, 5)
+    kms = kacc["pm"] / 5
+    got = qo.cpu().numpy().view(np.uint64)
+    # algorithmic bytes: every constant a query expands (its sources and everything it reaches) once, read as
+    # the (4-byte index, 8-byte word) entries of its row's nonzero words
+    nzw = (Ph != 0).sum(1).astype(np.int64)
+    expanded = np.unpackbits((got | srch).view(np.uint8), axis=1, bitorder="little")[:, :nq]
+    alg_bytes = float(12 * (expanded.astype(np.int64) @ nzw).sum())
+    del expanded
+    ex["powerlaw_smp"] = {"queries_per_s": q / ms * 1e3, "ms_per_batch": ms, "kernel": "smp_packed_kernel",
+                          "kernel_ms": kms, "algorithmic_bytes": alg_bytes, "gbs": alg_bytes / kms / 1e6,
+                          "hbm_frac": alg_bytes / kms / 1e6 / hbm,
+                          "note": "the word indexes of R and R^T (L2-resident) are read, not HBM"}
+    pl = (nq, pip, pix, srch, got)
+    del P, src, qo
+
+    # -- grouped batch of the knowledge-graph workload: 1,345 closures + 200 compositions
+    items, keep = kg_items()
+    arr = ctx.problems(items)
+    ctx.batch_run(arr, stream=stream)
+    ms = ev_time(stream, lambda: ctx.batch_run(arr, stream=stream), 3)
+    ex["kg_batch"] = {"programs_per_s": len(items) / ms * 1e3, "ms_per_batch": ms, "programs": len(items)}
+    del items, keep, arr
+
+    # -- learned dispatcher on 200 held-out corpus graphs (seeds 9,000-9,199)
+    model = os.path.join(ROOT, "paper_2408_10369_gb300", "dispatch_model.bin")
+    disp = None
+    if os.path.exists(model):
+        ctx.dispatch_load(model)
+        rows = [{"index": i} for i in range(9000, 9200)]
+        rep, graphs, outs = dc.live_pipeline(ctx, rows, 32768, return_outputs=True)
+        ex["dispatch_heldout200"] = {k: v for k, v in rep.items()}
+        disp = (graphs, outs)
+    if check:
+        ex.update(extras_oracle_check(pl, disp))
+    return ex
+
+
+def extras_oracle_check(pl, disp):
+    """The CPU (oracle) leg for the secondary workloads: the 4,096 query rows
+    and every dispatched closure of the held-out graphs against the oracle."""
+    import numpy as np
+    import oracle
+    res = {}
+    t0 = time.perf_counter()
+    nq, pip, pix, srch, got = pl
+    want, _ = oracle.smp(nq, pip, pix, srch)
+    gb = np.unpackbits(got.view(np.uint8), axis=1, bitorder="little")[:, :nq]
+    res["powerlaw_smp_parity"] = {"result": "bit-exact vs oracle" if np.array_equal(gb, want) else "MISMATCH",
+                                  "bits_compared": int(want.size), "check_s": time.perf_counter() - t0}
+    if disp is not None:
+        t0 = time.perf_counter()
+        graphs, outs = disp
+        bad, bits = 0, 0
+        for (g, _), o in zip(graphs, outs):
+            n = g["n"]
+            h = o.cpu().numpy().view(np.uint64)
+            for r0, blk in oracle.closure_bits_chunks(n, g["indptr"], g["indices"], 4096):
+                bad += int((h[r0:r0 + blk.shape[0], :blk.shape[1]] != blk).any(axis=1).sum())
+            bits += n * n
+        res["dispatch_heldout200_parity"] = {"result": "bit-exact vs oracle" if bad == 0 else "MISMATCH",
+                                             "graphs": len(graphs), "bits_compared": bits, "mismatched_rows": bad,
+                                             "check_s": time.perf_counter() - t0}
+    return res
+
+
+def run_sharded_aux(args, rank, world, local):
+    """The selective query batch or the knowledge-graph batch split across
+    ranks (one GPU each): units assigned by predicted cost (longest processing
+    time first), each rank runs its share through the library, and one
+    all-gather (NCCL) returns every output to every rank. The gather is inside
+    the timed region; value = all units of all ranks / the slowest rank's time."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import workloads as wl
+    import paper_2408_10369_gb300 as pkg
+    from paper_2408_10369_gb300 import bmlp, shard
+    torch.cuda.set_device(local)
+    if world == 1:  # --sharded on one GPU without torchrun: a process group of one rank
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29533")
+        os.environ.setdefault("RANK", "0")
+        os.environ.setdefault("WORLD_SIZE", "1")
+    dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    ctx = pkg.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    PK = bmlp.BMLP_FMT_PACKED64
+    if args.workload == "powerlaw_smp":
+        n, q = 65536, 4096
+        ip, ix = wl.powerlaw_csr(n, 2.1, 1000, 0)
+        P = torch.from_numpy(wl.csr_to_packed(n, ip, ix).view(np.int64)).to(dev)
+        srch = wl.query_rows(n, q, 1, 64, 0)
+        parts = shard.lpt_partition(shard.query_costs(srch), world)
+        mine = parts[rank]
+        src = torch.from_numpy(np.ascontiguousarray(srch[mine]).view(np.int64)).to(dev)
+        out = torch.zeros_like(src)
+
+        def step():
+            if mine:
+                ctx.smp(P, n, src, len(mine), out, fmt=PK, variant=args.variant, stream=stream)
+            return shard.gather_rows(out, parts, rank, q)
+        units, unit, name = q, "queries/s", "powerlaw_n65536_q4096"
+    else:
+        items, keep = kg_items()
+        ns = [it["n"] for it in items]
+        kinds = [it.get("kind", 0) for it in items]
+        parts = shard.lpt_partition(shard.problem_costs(ns, kinds), world)
+        mine = [items[i] for i in parts[rank]]
+        arr = ctx.problems(mine) if mine else None
+        numel = [n_ * wl.words(n_) for n_ in ns]
+
+        def step():
+            if mine:
+                ctx.batch_run(arr, stream=stream)
+            return shard.gather_outputs([it["out"] for it in mine], parts, rank, numel, device=dev)
+        units, unit, name = len(items), "programs/s", "kg15000_r1345_t483000_plus200"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, dev)
+    loads = shard.part_loads(shard.query_costs(srch) if args.workload == "powerlaw_smp"
+                             else shard.problem_costs(ns, kinds), parts)
+    if rank == 0:
+        print(json.dumps({"workload": name, "variant": args.variant, "value": args.steps * units / t, "unit": unit,
+                          "n_gpus": world, "ms_per_step": t / args.steps * 1e3, "steps": args.steps,
+                          "warmup": args.warmup, "scaling": "strong",
+                          "parallelism": "units split by predicted cost (LPT), one all-gather of the outputs",
+                          "units_per_rank": [len(p) for p in parts],
+                          "cost_share_per_rank": [x / max(sum(loads), 1e-30) for x in loads]}), flush=True)
+    ctx.close()
+    dist.destroy_process_group()
 
 
 def run_aux(args):
@@ -317,20 +612,7 @@ def run_aux(args):
             return ctx.is_foreign(C, A, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant=args.variant)
         unit, units_per_step, name = "programs/s", 1, "geo_kg_n14541_f7991_isforeign"
     else:
-        rels = wl.kg_relations()
-        items, keep = [], []
-        for r in rels:
-            R = torch.from_numpy(wl.csr_to_packed(r["n"], r["indptr"], r["indices"]).view(np.int64)).cuda()
-            o = torch.zeros_like(R)
-            keep += [R, o]
-            items.append(dict(n=r["n"], R1=R, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
-        for a, b in wl.kg_compose_pairs(rels, 200, 0):
-            n, ents, c1, c2 = wl.union_space(rels[a], rels[b])
-            R1 = torch.from_numpy(wl.csr_to_packed(n, *c1).view(np.int64)).cuda()
-            R2 = torch.from_numpy(wl.csr_to_packed(n, *c2).view(np.int64)).cuda()
-            o = torch.zeros_like(R1)
-            keep += [R1, R2, o]
-            items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=o, fmt=bmlp.BMLP_FMT_PACKED64))
+        items, keep = kg_items()
         arr = ctx.problems(items)
         variant = args.variant if args.variant in ("rms_tc", "rms_packed") else "auto"
 
@@ -362,7 +644,9 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload != "er":
-        if rank == 0:
+        if (world > 1 or args.sharded) and args.workload in ("powerlaw_smp", "kg_batch"):
+            run_sharded_aux(args, rank, world, local)
+        elif rank == 0:
             run_aux(args)
         return
     import numpy as np
@@ -487,7 +771,7 @@ def main():
             variants["auto"] = {"ms": ta * 1e3, "chosen": chosen, "graphs_per_s": 1.0 / ta,
                                 "eff_tops": iters * 2.0 * n ** 3 / ta / 1e12,
                                 "bit_exact_vs_rms_tc": bool(torch.equal(o2, out))}
-    bf16, _, peak_src = peaks()
+    bf16, hbm, peak_src = peaks()
     avg_launch_s = prod_ms / max(prod_n, 1) / 1e3
     achieved = 2.0 * n ** 3 / avg_launch_s / 1e12 if avg_launch_s > 0 else None
     # every timed product on packed E2M1 operands (kind::mxf4), else E4M3 (kind::f8f6f4)
@@ -495,21 +779,30 @@ def main():
     ratio, rname = (FP4_PER_BF16, "fp4/bf16") if fp4 else (FP8_PER_BF16, "fp8/bf16")
     peak = bf16 * ratio
     kname = "tc4_duo_kernel" if fp4 else "tc_product_kernel"
-    # what this GPU issues for the kernel's operand kind (back-to-back MMAs, no operand traffic)
-    issue = ctx.mma_issue_rate(1 if fp4 else 0)
+    # what this GPU issues for the kernel's operand kind and form (back-to-back MMAs, no operand traffic):
+    # one M256 N256 K64 MMA per CTA pair for the 4-bit kernel, M128 N256 K32 per CTA for the E4M3 one
+    issue = ctx.mma_issue_rate(2 if fp4 else 0)
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
             "peak_source": "%s bf16 burst x %g (%s nominal); the product runs unthrottled at max SM clock"
                            % (peak_src, ratio, rname),
             "issued_frac": (issued / prod_n / (2.0 * n ** 3)) if prod_n else None,
+            "issue_rate_kind": "tcgen05 kind::mxf4 M256 N256 K64 .cta_group::2" if fp4
+                               else "tcgen05 kind::f8f6f4 M128 N256 K32",
             "issue_rate_peak": issue, "issue_rate_frac": (achieved / issue) if achieved and issue else None}
     if rank != 0:
         ctx.close()
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    extras = None
+    if not args.no_extras:
+        extras = run_extras(args, ctx, stream, n, ip, ix, R, FMT, out, bf16, hbm, check=not args.no_cpu)
     cpu = None
+    parity = None
     if not args.no_cpu:
+        # the oracle's full closure of the benchmark graph against the last timed output, every bit
+        parity = oracle_parity(n, ip, ix, out, args.fmt)
         # the oracle on all host cores (median of 3 samples of rows) and on one core (median of 3 smaller samples)
         rows = args.cpu_rows or max(64, n // 4)
         tc = statistics.median(cpu_oracle_closure(n, ip, ix, rows) for _ in range(3))
@@ -537,8 +830,9 @@ def main():
                               % (n * n / 2 ** 31, host_in.nbytes / 2 ** 20)) if n * n / 2 > 129e6
                        else "operands fit in L2 (%.1f MB per E2M1 matrix; not flushed)" % (n * n / 2e6),
                        "parallelism": "independent replicas" if world > 1 else "single GPU"},
+            "graphs_per_s": args.steps * world / t, "parity": parity,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "variants": variants}
+            "gpu_launches": launches, "variants": variants, "extras": extras}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -200,14 +200,16 @@ def evaluate(args):
             json.dump(report, f, indent=1)
 
 
-def live_pipeline(ctx, rows, n_max):
+def live_pipeline(ctx, rows, n_max, return_outputs=False):
     """Time (a) plain single-instance squaring per graph with BMLP_RMS_TC
     (bit-row squarings while R is sparse for n >= 8192, then tensor cores),
     (a') the same with every squaring on the tensor cores (options.tc_only),
     and (b) the dispatched path: features + prediction for every graph, then
     the graphs predicted to be fastest with squaring run grouped in one
     bmlp_batch_run (engine per problem from the prediction), the others one
-    by one with their frontier variant. Every output is compared with (a)."""
+    by one with their frontier variant. Every output is compared with (a).
+    With return_outputs, also returns the graphs (corpus dict, device input)
+    and the dispatched outputs (packed bit rows on the device)."""
     from . import bmlp
     torch = _torch()
     graphs = [graph_on_device(r["index"], n_max) for r in rows]
@@ -257,11 +259,15 @@ def live_pipeline(ctx, rows, n_max):
     torch.cuda.synchronize()
     t_disp = time.perf_counter() - t0
     bad = sum(0 if torch.equal(a, b) else 1 for a, b in zip(outs_a, outs_b))
-    return {"live_graphs": len(graphs), "live_plain_rms_tc_s": t_plain, "live_dispatched_s": t_disp,
+    rep = {"live_graphs": len(graphs), "live_plain_rms_tc_s": t_plain, "live_dispatched_s": t_disp,
             "live_speedup": t_plain / t_disp, "live_bit_mismatches": bad,
             "live_tc_only_s": t_tc_only, "live_speedup_vs_tc_only": t_tc_only / t_disp,
             "live_tc_only_bit_mismatches": bad_tc_only,
             "live_choice_hist": {VARIANT_NAMES[v - 1]: int((choice == v).sum()) for v in (1, 2, 3, 4)}}
+    if return_outputs:
+        del outs_a
+        return rep, graphs, outs_b
+    return rep
 
 
 def main():

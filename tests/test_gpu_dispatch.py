@@ -102,3 +102,23 @@ def test_budget_censors_a_long_run(ctx):
         ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_packed", budget_ns=200_000)
     assert e.value.status == bmlp.BMLP_ERR_BUDGET
     ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_packed")   # the context is still usable
+
+
+def test_dispatched_heldout_corpus_matches_oracle(ctx):
+    """The committed model on 40 held-out corpus graphs (seeds 9,000-9,039,
+    n up to 8,192): the dispatched pipeline (features, prediction, small
+    squaring problems grouped in one batch, the rest one by one with their
+    predicted variant) returns the oracle's closure for every graph, every bit."""
+    import os
+
+    from paper_2408_10369_gb300 import dispatch_corpus as dc
+    model = os.path.join(os.path.dirname(pkg.__file__), "dispatch_model.bin")
+    ctx.dispatch_load(model)
+    rows = [{"index": i} for i in range(9000, 9040)]
+    rep, graphs, outs = dc.live_pipeline(ctx, rows, 8192, return_outputs=True)
+    assert rep["live_bit_mismatches"] == 0 and rep["live_tc_only_bit_mismatches"] == 0
+    for (g, _), o in zip(graphs, outs):
+        n = g["n"]
+        got = o.cpu().numpy().view(np.uint64)
+        for r0, blk in oracle.closure_bits_chunks(n, g["indptr"], g["indices"], 4096):
+            np.testing.assert_array_equal(got[r0:r0 + blk.shape[0], :blk.shape[1]], blk)

@@ -276,13 +276,18 @@ def test_argument_errors(ctx):
 
 
 def test_mma_issue_rate(ctx):
-    """The tensor-core issue-rate probe runs and reports a positive rate; the
-    4-bit kind carries twice the K per instruction, so it is never slower."""
+    """The issue-rate probes run and report positive rates; the 4-bit kind
+    carries twice the K per instruction, so it is never slower than E4M3, and
+    the 2-SM form does the work of two 1-SM MMAs per instruction pair; the
+    word-OR probe reports a rate too. Unknown kinds are refused."""
     r8 = ctx.mma_issue_rate(0, iters=2000)
     r4 = ctx.mma_issue_rate(1, iters=2000)
-    assert r8 > 0 and r4 >= r8
-    with pytest.raises(pkg.BmlpError):
-        ctx.mma_issue_rate(2)
+    r4x2 = ctx.mma_issue_rate(2, iters=2000)
+    ors = ctx.mma_issue_rate(3, iters=2000)
+    assert r8 > 0 and r4 >= r8 and r4x2 > 0.5 * r4 and ors > 0
+    for bad in (-1, 4):
+        with pytest.raises(pkg.BmlpError):
+            ctx.mma_issue_rate(bad)
 
 
 @pytest.mark.parametrize("variant", ["rms_tc", "rms_packed", "smp_packed"])
