@@ -482,8 +482,8 @@ def run_sharded_aux(args, rank, world, local):
         os.environ.setdefault("MASTER_PORT", "29533")
         os.environ.setdefault("RANK", "0")
         os.environ.setdefault("WORLD_SIZE", "1")
-    dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
     ctx = pkg.Context(local)
     stream = torch.cuda.current_stream(dev)
     PK = bmlp.BMLP_FMT_PACKED64
@@ -507,14 +507,21 @@ def run_sharded_aux(args, rank, world, local):
         ns = [it["n"] for it in items]
         kinds = [it.get("kind", 0) for it in items]
         parts = shard.lpt_partition(shard.problem_costs(ns, kinds), world)
-        mine = [items[i] for i in parts[rank]]
-        arr = ctx.problems(mine) if mine else None
         numel = [n_ * wl.words(n_) for n_ in ns]
+        # this rank's outputs live in one contiguous buffer, so the gather is a single all_gather with no copy
+        offs, cap = shard.share_layout(parts, rank, numel)
+        flat = torch.zeros(cap, dtype=torch.int64, device=dev)
+        mine = []
+        for i in parts[rank]:
+            it = dict(items[i])
+            it["out"] = flat[offs[i]:offs[i] + numel[i]].view(ns[i], wl.words(ns[i]))
+            mine.append(it)
+        arr = ctx.problems(mine) if mine else None
 
         def step():
             if mine:
                 ctx.batch_run(arr, stream=stream)
-            return shard.gather_outputs([it["out"] for it in mine], parts, rank, numel, device=dev)
+            return shard.gather_flat(flat, parts, numel)
         units, unit, name = len(items), "programs/s", "kg15000_r1345_t483000_plus200"
     for _ in range(args.warmup):
         step()

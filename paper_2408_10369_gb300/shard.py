@@ -108,6 +108,39 @@ def gather_outputs(local: list, parts: List[List[int]], rank: int, numel: Sequen
     return out
 
 
+def share_layout(parts: List[List[int]], rank: int, numel: Sequence[int]):
+    """Word offsets of this rank's units inside one contiguous buffer (the
+    order of parts[rank]) and the buffer size every rank pads to, so that the
+    units' outputs can be written in place and gathered with no copy."""
+    sizes = [int(sum(numel[i] for i in p)) for p in parts]
+    offs, o = {}, 0
+    for i in parts[rank]:
+        offs[i] = o
+        o += int(numel[i])
+    return offs, max(max(sizes), 1)
+
+
+def gather_flat(buf, parts: List[List[int]], numel: Sequence[int]):
+    """All-gather of per-rank contiguous buffers laid out by ``share_layout``
+    (``buf``: 1-D int64 tensor of the padded size, this rank's outputs at
+    their offsets). Returns a list, indexed by unit, of 1-D views."""
+    import torch
+    dist = _dist()
+    world = len(parts)
+    if world == 1:
+        blocks = [buf]
+    else:
+        blocks = [torch.empty_like(buf) for _ in range(world)]
+        dist.all_gather(blocks, buf)
+    out: list = [None] * len(numel)
+    for r, p in enumerate(parts):
+        o = 0
+        for i in p:
+            out[i] = blocks[r][o:o + int(numel[i])]
+            o += int(numel[i])
+    return out
+
+
 def query_costs(src_rows: np.ndarray) -> np.ndarray:
     """Predicted cost of each selective query row: its number of sources
     (each one starts a frontier of its own), at least 1."""

@@ -112,3 +112,30 @@ def test_problems_sharded_over_two_gloo_ranks():
             assert len(res[r]) == len(graphs)
             for got, w in zip(res[r], want):
                 np.testing.assert_array_equal(got, w)
+
+
+def _flat_worker(rank, world, port, numel, parts_costs, res):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        parts = shard.lpt_partition(parts_costs, world)
+        offs, cap = shard.share_layout(parts, rank, numel)
+        buf = torch.zeros(cap, dtype=torch.int64)
+        for i in parts[rank]:  # unit i's output: numel[i] words of value 1000 * i + k
+            buf[offs[i]:offs[i] + numel[i]] = 1000 * i + torch.arange(numel[i])
+        out = shard.gather_flat(buf, parts, numel)
+        res[rank] = [o.numpy().copy() for o in out]
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gather_flat_over_two_gloo_ranks():
+    numel = [5, 1, 17, 3, 8, 2, 11]
+    costs = [3.0, 9.0, 1.0, 4.0, 4.0, 7.0, 2.0]
+    with mp.get_context("spawn").Manager() as man:
+        res = man.dict()
+        mp.spawn(_flat_worker, args=(2, _free_port(), numel, costs, res), nprocs=2, join=True)
+        for r in range(2):
+            for i, w in enumerate(numel):
+                np.testing.assert_array_equal(res[r][i], 1000 * i + np.arange(w))
