@@ -134,6 +134,11 @@ typedef struct bmlp_stats {
                                   sources at a time (bit-sliced frontiers)      */
     double sparse_ms;          /* their summed device time (options.profile)    */
     double sparse_words;       /* the word ORs they issued                      */
+    int32_t host_syncs;        /* times the host waited for the device during
+                                  the call to read back a flag, a decision or
+                                  the results (1 for a batch that ran as one
+                                  device-driven graph: the final read)          */
+    int32_t reserved;
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

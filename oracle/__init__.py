@@ -84,9 +84,12 @@ def _p(a, t):
     return a.ctypes.data_as(t)
 
 
-def _csr(indptr, indices):
+def _csr(indptr, indices, n=None):
     ip = np.ascontiguousarray(indptr, np.int64)
     ix = np.ascontiguousarray(indices, np.int32)
+    if n is not None:  # the C code trusts its inputs: a row or column index outside [0, n) is refused here
+        if len(ip) < n + 1 or (ix.size and (int(ix.min()) < 0 or int(ix.max()) >= n)):
+            raise ValueError("CSR does not describe an n = %d relation" % n)
     if ix.size == 0:
         ix = np.zeros(1, np.int32)
     return ip, ix
@@ -99,7 +102,7 @@ def reach_rows(n, indptr, indices, sources, want_rows=True):
     depth[r] is the longest shortest path (>= 1 edge) from sources[r] to any
     node it reaches; count[r] the number of nodes reached.
     """
-    ip, ix = _csr(indptr, indices)
+    ip, ix = _csr(indptr, indices, n)
     src = np.ascontiguousarray(sources, np.int32)
     m = len(src)
     out = np.zeros((m, n), np.uint8) if want_rows else None
@@ -115,7 +118,7 @@ def reach_rows_bits(n, indptr, indices, sources, ldw=None):
     """Rows of R1+ for ``sources`` as bit rows (uint64 [len(sources), ldw],
     bit j % 64 of word j / 64 least significant first; ldw defaults to
     ceil(n / 64)), by the same BFS as ``reach_rows``."""
-    ip, ix = _csr(indptr, indices)
+    ip, ix = _csr(indptr, indices, n)
     src = np.ascontiguousarray(sources, np.int32)
     ldw = (n + 63) // 64 if ldw is None else int(ldw)
     out = np.zeros((len(src), ldw), np.uint64)
@@ -173,7 +176,7 @@ def alg1_products(L0: int) -> int:
 
 def smp(n, indptr, indices, src_rows):
     """v R1+ for each packed (LSB-first uint64) source row; returns (out, levels)."""
-    ip, ix = _csr(indptr, indices)
+    ip, ix = _csr(indptr, indices, n)
     rows = np.ascontiguousarray(src_rows, np.uint64)
     q = rows.shape[0]
     ld = rows.shape[1] if rows.ndim == 2 else 0
@@ -212,8 +215,8 @@ def warshall(m):
 
 def compose_rows(n, csr1, csr2, rows=None):
     """Rows of P = (I + R2+) R1, the least model of p <- r1 ; p <- r2, p."""
-    ip1, ix1 = _csr(*csr1)
-    ip2, ix2 = _csr(*csr2)
+    ip1, ix1 = _csr(*csr1, n)
+    ip2, ix2 = _csr(*csr2, n)
     rr = np.arange(n, dtype=np.int32) if rows is None else np.ascontiguousarray(rows, np.int32)
     out = np.zeros((len(rr), n), np.uint8)
     if len(rr) and n:

@@ -63,6 +63,11 @@ bmlp_status ws_get(bmlp_ctx* ctx, int slot, size_t bytes, void** out) {
     return BMLP_OK;
 }
 
+cudaError_t host_sync(bmlp_ctx* ctx, cudaStream_t s) {
+    ctx->stats.host_syncs++;
+    return cudaStreamSynchronize(s);
+}
+
 }  // namespace bmlp
 
 namespace {
@@ -191,7 +196,7 @@ bmlp_status stage_out(bmlp_ctx* ctx, void* p, size_t bytes, int slot, OutView* o
 bmlp_status finish_out(bmlp_ctx* ctx, const OutView& o, cudaStream_t s) {
     if (o.host) {
         CK(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, s), "copy output to host");
-        CK(cudaStreamSynchronize(s), "synchronise output copy");
+        CK(host_sync(ctx, s), "synchronise output copy");
     }
     return BMLP_OK;
 }
@@ -230,7 +235,7 @@ Deadline deadline_of(bmlp_ctx* ctx) {
 
 bmlp_status read_ctl(bmlp_ctx* ctx, cudaStream_t s, int* changed) {
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, CTL_WORDS * sizeof(int), cudaMemcpyDeviceToHost, s), "read flags");
-    CK(cudaStreamSynchronize(s), "synchronise iteration");
+    CK(host_sync(ctx, s), "synchronise iteration");
     if (ctx->h_ctl[CTL_ERROR] != 0)
         return set_err(ctx, BMLP_ERR_TIMEOUT, "in-kernel wait timed out (code 0x%x)", ctx->h_ctl[CTL_ERROR]);
     if (ctx->budget_ns &&
@@ -344,7 +349,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     auto sparse_map = [&](const uint8_t* dmap, bool* sparse) -> bmlp_status {
         hmap.resize(fbytes);
         CK(cudaMemcpyAsync(hmap.data(), dmap, fbytes, cudaMemcpyDeviceToHost, s), "read block map");
-        CK(cudaStreamSynchronize(s), "read block map");
+        CK(host_sync(ctx, s), "read block map");
         size_t nz = 0;
         for (size_t i = 0; i < fbytes; ++i) nz += hmap[i] != 0;
         *sparse = static_cast<double>(nz) < kSkipMaxDensity * double(p.k_blocks) * double(p.k_blocks);
@@ -748,7 +753,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         auto words = [&](const void* wp, int64_t* total) -> bmlp_status {
             CK(cudaMemcpyAsync(total, static_cast<const int64_t*>(wp) + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
                "read word count");
-            CK(cudaStreamSynchronize(s), "read word count");
+            CK(host_sync(ctx, s), "read word count");
             return BMLP_OK;
         };
         int64_t W = 0, W2 = 0;
@@ -795,7 +800,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         int64_t wt[2] = {0, 0};
         CK(cudaMemcpyAsync(wt, static_cast<const int64_t*>(wptrT) + n, sizeof(wt), cudaMemcpyDeviceToHost, s),
            "read column word counts");
-        CK(cudaStreamSynchronize(s), "read column word counts");
+        CK(host_sync(ctx, s), "read column word counts");
         dense_reach = static_cast<double>(wt[1]) * static_cast<double>(n) <= kSlicedMaxSkew * static_cast<double>(wt[0]);
     }
     if (dense_reach && smp_sliced_enabled()) {
@@ -1016,7 +1021,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         pr.R1 = in.dev;
         pr.out = ov.dev;
         int32_t it = 0;
-        st = batch_run_impl(ctx, &pr, 1, variant, wait_cycles(ctx, o), &it, s);
+        st = batch_run_impl(ctx, &pr, 1, variant, wait_cycles(ctx, o), &it, s, batch_solo_n());
         iters = it;
     } else if (variant == BMLP_RMS_TC) {
         const int64_t n_pad = round_up(n, TC_PAD);
@@ -1061,7 +1066,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
                 ctx->stats.launches++;
                 std::vector<uint8_t> h(static_cast<size_t>(kb * kb));
                 CK(cudaMemcpyAsync(h.data(), f, h.size(), cudaMemcpyDeviceToHost, s), "read input block map");
-                CK(cudaStreamSynchronize(s), "read input block map");
+                CK(host_sync(ctx, s), "read input block map");
                 size_t nz = 0;
                 for (uint8_t x : h) nz += x != 0;
                 direct = static_cast<double>(nz) >= kSkipMaxDensity * static_cast<double>(kb * kb);
@@ -1157,7 +1162,7 @@ bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, co
     std::vector<int32_t> hp(static_cast<size_t>(2 * m));
     if (is_device_ptr(pairs)) {
         CK(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read facts");
-        CK(cudaStreamSynchronize(s), "read facts");
+        CK(host_sync(ctx, s), "read facts");
     } else {
         memcpy(hp.data(), pairs, hp.size() * sizeof(int32_t));
     }
@@ -1546,83 +1551,20 @@ bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
     bmlp_options o = resolve(opts);
     if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC && o.variant != BMLP_RMS_PACKED)
         return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a batch variant", o.variant);
-    // Problems large enough to fill the GPU on their own (n >= batch_solo_n()) and not forced onto packed rows
-    // run one by one on the single-problem path, whose squarings switch to 4-bit operands once R is dense; the
-    // rest run together as one grouped batch.
-    std::vector<bmlp_problem> rest;
-    std::vector<int64_t> rest_idx, solo_idx;
-    const int64_t solo_n = batch_solo_n();
-    for (int64_t i = 0; i < count; ++i) {
-        const bmlp_problem& p = probs[i];
-        const int v = p.variant ? p.variant : o.variant;
-        const bool valid = (p.kind == BMLP_PROBLEM_CLOSURE || p.kind == BMLP_PROBLEM_COMPOSE) &&
-                           (p.fmt == BMLP_FMT_U8 || p.fmt == BMLP_FMT_PACKED64) && p.R1 && p.out &&
-                           (p.kind == BMLP_PROBLEM_CLOSURE || p.R2);
-        if (valid && solo_n > 0 && p.n >= solo_n && p.n <= (int64_t(1) << 17) && v != BMLP_RMS_PACKED) {
-            solo_idx.push_back(i);
-        } else {
-            rest.push_back(p);
-            rest_idx.push_back(i);
-        }
-    }
+    // Problems large enough to fill the GPU on their own (n >= batch_solo_n()) and not forced onto packed rows run
+    // inside the same graph as device-driven single-problem pipelines (squarings on bit rows while R is sparse, then
+    // on 4-bit operands on the tensor cores); the rest run together as one grouped batch. One graph launch, one
+    // read of the results.
     reset_stats(ctx, o.variant, 0);
-    bmlp_stats acc = ctx->stats;
-    double solo_ms = 0.0;
-    bmlp_status first_err = BMLP_OK;
-    for (int64_t i : solo_idx) {
-        const bmlp_problem& p = probs[i];
-        if (!is_device_ptr(p.R1) || !is_device_ptr(p.out) || (p.kind == BMLP_PROBLEM_COMPOSE && !is_device_ptr(p.R2)))
-            return set_err(ctx, BMLP_ERR_INVALID_ARG, "problem %lld: matrices must be device memory",
-                           static_cast<long long>(i));
+    ProductTimer tm{ctx, o.profile != 0, s};
+    ST(tm.begin());
+    bmlp_status st = batch_run_impl(ctx, probs, count, o.variant, wait_cycles(ctx, o), iters_out, s, batch_solo_n());
+    ST(tm.end());
+    if (o.profile) {
+        CK(cudaEventSynchronize(ctx->ev[1]), "synchronise batch timer");
+        ST(tm.collect());
     }
-    for (int64_t i : solo_idx) {
-        const bmlp_problem& p = probs[i];
-        bmlp_options po = o;
-        po.variant = BMLP_RMS_TC;
-        po.reflexive = p.kind == BMLP_PROBLEM_CLOSURE ? p.reflexive : 0;
-        int32_t it = 0;
-        const auto t0 = std::chrono::steady_clock::now();
-        bmlp_status st = p.kind == BMLP_PROBLEM_CLOSURE
-                             ? bmlp_rms(ctx, p.R1, p.n, p.fmt, p.out, &po, &it, s)
-                             : bmlp_compose(ctx, p.R1, p.R2, p.n, p.fmt, p.out, &po, &it, s);
-        if (o.profile) {
-            CK(cudaStreamSynchronize(s), "synchronise problem");
-            solo_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        }
-        if (iters_out) iters_out[i] = it;
-        acc.iterations = std::max(acc.iterations, it);
-        acc.launches += ctx->stats.launches;
-        acc.product_launches += ctx->stats.product_launches;
-        acc.e2m1_products += ctx->stats.e2m1_products;
-        if (st == BMLP_ERR_NOT_CONVERGED) {
-            if (first_err == BMLP_OK) first_err = st;
-        } else if (st != BMLP_OK) {
-            return st;
-        }
-    }
-    bmlp_status st = BMLP_OK;
-    if (!rest.empty()) {
-        std::vector<int32_t> rit(rest.size(), 0);
-        ctx->stats = acc;
-        ProductTimer tm{ctx, o.profile != 0, s};
-        ST(tm.begin());
-        st = batch_run_impl(ctx, rest.data(), static_cast<int64_t>(rest.size()), o.variant, wait_cycles(ctx, o),
-                            rit.data(), s);
-        ST(tm.end());
-        if (o.profile) {
-            CK(cudaStreamSynchronize(s), "synchronise batch");
-            ST(tm.collect());
-        }
-        if (iters_out)
-            for (size_t k = 0; k < rest.size(); ++k) iters_out[rest_idx[k]] = rit[k];
-        ctx->stats.iterations = std::max(ctx->stats.iterations, acc.iterations);
-    } else {
-        ctx->stats = acc;
-    }
-    ctx->stats.product_ms += solo_ms;
-    if (st != BMLP_OK) return st;
-    if (first_err != BMLP_OK) return set_err(ctx, first_err, "a problem did not converge within its cap");
-    return BMLP_OK;
+    return st;
 }
 
 bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, const char* cache_path,
@@ -1756,3 +1698,11 @@ bmlp_status bmlp_dispatch_load(bmlp_ctx* ctx, const char* path) {
 }
 
 }  // extern "C"
+
+namespace bmlp {
+// The bit-row step-cost model, for the device-driven large problems of a grouped batch.
+double bitrow_s_per_word() { return sparse_s_per_word(); }
+double bitrow_row_s_per_word() { return sparse_row_s_per_word(); }
+double bitrow_step_s() { return kSparseStepS; }
+double tc4_product_s(int64_t n_pad) { return tc_product_s(n_pad); }
+}  // namespace bmlp

@@ -12,6 +12,17 @@
 // iteration. Encoding, the iteration, the final products of compositions and
 // decoding are one graph launch; the host reads back the per-problem
 // iteration counts once at the end.
+//
+// Problems large enough to fill the GPU on their own (n >= solo_n) run in the
+// same graph as device-driven single-problem pipelines, one after another:
+// squarings on word-indexed bit rows while the next one costs less than a
+// tensor-core product (the same cost model and the same switch as the
+// single-problem path, decided by a one-thread kernel that sets the
+// condition of a WHILE node), then squarings on packed E2M1 operands on the
+// tensor cores in a second WHILE node, two products per iteration with a
+// guard word so that the second is skipped once the first changed nothing,
+// then the decode (closures) or I + R2+ and the final product with R1
+// (compositions). No host round trip per squaring.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -310,6 +321,88 @@ __global__ void __launch_bounds__(256) batch_decode_kernel(const GroupProblem* p
     }
 }
 
+// ------------------------------------------- device-driven large problems --
+// Control words of one large problem (ints; the two 64-bit cost words at SW_COST).
+enum SoloWord : int {
+    SW_ITERS = 0,    // squarings issued so far
+    SW_NOTDONE = 1,  // 1 while the closure is not finished on bit rows
+    SW_NOTCONV = 2,  // stopped at the cap while still changing
+    SW_CHANGED = 3,  // set by the squaring kernels
+    SW_GC = 4,       // guard of the first tensor-core product of a loop iteration
+    SW_G1 = 5,       // guard of the second
+    SW_COST = 8,     // word ORs of the next bit-row squaring: total, largest row (2 x u64)
+    SW_WORDS = 16
+};
+
+// dst = src, 16 bytes per thread and step (sizes are multiples of 16 bytes).
+__global__ void solo_copy_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src, int64_t n16) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n16;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = src[i];
+}
+
+__global__ void solo_init_kernel(int* w) {
+    for (int i = 0; i < SW_WORDS; ++i) w[i] = 0;
+    w[SW_NOTDONE] = 1;
+}
+
+// After the cost pass on the current bit rows: stop if the last squaring changed nothing (the closure is done),
+// hand over to the tensor cores if the next squaring is predicted dearer than a tensor-core product or would use
+// the last product the cap allows, else run it (same rule as the single-problem path).
+__global__ void solo_rows_decide_kernel(int* w, int cap, int first, double step_s, double s_word, double s_row,
+                                        double limit, cudaGraphConditionalHandle h) {
+    unsigned long long* cost = reinterpret_cast<unsigned long long*>(w + SW_COST);
+    if (!first) {
+        w[SW_ITERS] += 1;
+        if (!w[SW_CHANGED]) {
+            w[SW_NOTDONE] = 0;
+            cudaGraphSetConditional(h, 0u);
+            return;
+        }
+    }
+    const double t = step_s + fmax(static_cast<double>(cost[0]) * s_word, static_cast<double>(cost[1]) * s_row);
+    if (w[SW_ITERS] + 1 >= cap || t > limit) {
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    w[SW_CHANGED] = 0;
+    cost[0] = 0;
+    cost[1] = 0;
+    cudaGraphSetConditional(h, 1u);
+}
+
+__global__ void solo_mid_kernel(int* w, cudaGraphConditionalHandle h) {
+    const int go = w[SW_NOTDONE];
+    w[SW_GC] = go;
+    w[SW_G1] = 0;
+    w[SW_CHANGED] = 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// After tensor-core product `half` (0: Q0 -> Q1, 1: Q1 -> Q0) of a loop iteration. A product that changed nothing
+// wrote R' = R, so both buffers hold the closure and either may be decoded.
+__global__ void solo_tc_decide_kernel(int* w, int cap, int half, cudaGraphConditionalHandle h) {
+    if (!w[half == 0 ? SW_GC : SW_G1]) return;  // that product was skipped
+    w[SW_ITERS] += 1;
+    bool go = w[SW_CHANGED] != 0;
+    w[SW_CHANGED] = 0;
+    if (go && w[SW_ITERS] >= cap) {
+        w[SW_NOTCONV] = 1;
+        go = false;
+    }
+    if (half == 0) {
+        w[SW_G1] = go ? 1 : 0;
+        if (!go) {
+            w[SW_GC] = 0;
+            cudaGraphSetConditional(h, 0u);
+        }
+    } else {
+        w[SW_G1] = 0;
+        if (!go) w[SW_GC] = 0;
+        cudaGraphSetConditional(h, go ? 1u : 0u);
+    }
+}
+
 // --------------------------------------------------------------- host --
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -357,6 +450,9 @@ struct BatchCache {
     cudaGraphExec_t exec = nullptr;
     size_t ws_bytes = 0;
     std::vector<int> h_iters, h_notconv;
+    std::vector<int> solo;           // caller indices of the device-driven large problems, in run order
+    int* d_solo = nullptr;           // SW_WORDS control words per large problem
+    std::vector<int> h_solo;
 };
 
 void batch_cache_free(bmlp_ctx* ctx) {
@@ -367,6 +463,7 @@ void batch_cache_free(bmlp_ctx* ctx) {
     if (c->d_probs) cudaFree(c->d_probs);
     if (c->d_st) cudaFree(c->d_st);
     if (c->d_ints) cudaFree(c->d_ints);
+    if (c->d_solo) cudaFree(c->d_solo);
     delete c;
     ctx->batch = nullptr;
 }
@@ -409,17 +506,30 @@ int engine_for(bmlp_ctx* ctx, const bmlp_problem& p, int variant) {
     return 0;
 }
 
+bool is_solo(const bmlp_problem& p, int variant, int64_t solo_n) {
+    if (solo_n <= 0 || p.n < solo_n) return false;
+    if (p.kind == BMLP_PROBLEM_COMPOSE) return true;
+    const int v = p.variant ? p.variant : variant;
+    return v != BMLP_RMS_PACKED;
+}
+
+bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, long long wait_cycles,
+                       const cudaGraphNode_t* after, size_t nafter);
+
 bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, int variant, long long wait_cycles,
-                        uint64_t key, BatchCache** out) {
+                        uint64_t key, int64_t solo_n, BatchCache** out) {
     batch_cache_free(ctx);
     BatchCache* c = new BatchCache();
     ctx->batch = c;
     c->key = key;
-    c->nprob = static_cast<int>(count);
+    // large problems first, as device-driven pipelines after the grouped part; the rest grouped, most expensive
+    // first (the work lists are then longest-first)
+    for (int64_t i = 0; i < count; ++i)
+        if (is_solo(probs[i], variant, solo_n)) c->solo.push_back(static_cast<int>(i));
+        else c->order.push_back(static_cast<int>(i));
+    std::stable_sort(c->solo.begin(), c->solo.end(), [&](int a, int b) { return probs[a].n > probs[b].n; });
+    c->nprob = static_cast<int>(c->order.size());
     const int np = c->nprob;
-    // order: most expensive first (the work lists are then longest-first)
-    c->order.resize(np);
-    for (int i = 0; i < np; ++i) c->order[i] = i;
     std::stable_sort(c->order.begin(), c->order.end(),
                      [&](int a, int b) { return probs[a].n > probs[b].n; });
     std::vector<GroupProblem> hp(np);
@@ -517,6 +627,12 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
     // ---- graph
     BCK(prepare_tc_group(), "tensor-core group kernel attributes");
     BCK(cudaGraphCreate(&c->graph, 0), "cudaGraphCreate");
+    if (np == 0) {
+        BST(build_solo(ctx, c, probs, wait_cycles, nullptr, 0));
+        BCK(cudaGraphInstantiate(&c->exec, c->graph, 0), "cudaGraphInstantiate");
+        *out = c;
+        return BMLP_OK;
+    }
     cudaGraphConditionalHandle h;
     BCK(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault), "conditional handle");
     GroupProblem* dp = c->d_probs;
@@ -578,15 +694,254 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
         BST(add_kernel(ctx, c->graph, &n_dec, &n_final, 1, reinterpret_cast<void*>(&batch_decode_kernel),
                        dim3(64, gy), dim3(256), 0, a));
     }
+    if (!c->solo.empty()) BST(build_solo(ctx, c, probs, wait_cycles, &n_dec, 1));
     BCK(cudaGraphInstantiate(&c->exec, c->graph, 0), "cudaGraphInstantiate");
     *out = c;
     return BMLP_OK;
 }
 
-uint64_t batch_key(const bmlp_problem* probs, int64_t count, int variant, const int* tune) {
+// Adds a conditional WHILE node after the current capture dependencies of `cs` and returns its body graph; the
+// capture of `cs` continues after the node.
+bmlp_status add_while(bmlp_ctx* ctx, cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    BCK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, nullptr, &nd), "capture info");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    BCK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp), "while node");
+    BCK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+        "capture dependencies");
+    *body = cp.conditional.phGraph_out[0];
+    return BMLP_OK;
+}
+
+// The large problems as device-driven single-problem pipelines, one after another (they share one scratch sized
+// for the largest), captured into the batch graph after `after`.
+bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, long long wait_cycles,
+                       const cudaGraphNode_t* after, size_t nafter) {
+    const int ns = static_cast<int>(c->solo.size());
+    int64_t nmax = 0;
+    bool any_compose = false;
+    for (int i : c->solo) {
+        nmax = std::max(nmax, probs[i].n);
+        any_compose |= probs[i].kind == BMLP_PROBLEM_COMPOSE;
+    }
+    const int64_t ldw_max = round_up((nmax + 63) / 64, 2);
+    const int64_t np_max = round_up(nmax, TC_PAD);
+    const size_t pk = static_cast<size_t>(nmax * ldw_max * 8);
+    const size_t q = static_cast<size_t>(np_max * np_max / 2);
+    const size_t e8 = static_cast<size_t>(np_max * np_max);
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = total;
+        total += round_up(static_cast<int64_t>(bytes), 1024);
+        return o;
+    };
+    const size_t oP0 = take(pk), oP1 = take(pk), oPtr = take(static_cast<size_t>((nmax + 2) * 8)),
+                 oIdx = take(static_cast<size_t>(nmax * ldw_max * 4)), oVal = take(pk);
+    size_t oQ[2], oQT[2];
+    for (int k = 0; k < 2; ++k) {
+        oQ[k] = take(q);
+        oQT[k] = take(q);
+    }
+    size_t oM0 = 0, oM1 = 0, oT1 = 0, oX = 0;
+    if (any_compose) {
+        oM0 = take(e8);
+        oM1 = take(e8);
+        oT1 = take(e8);
+        oX = take(e8);
+    }
+    void* base = nullptr;
+    BST(ws_get(ctx, WS_SOLO, total, &base));
+    uint8_t* b8 = static_cast<uint8_t*>(base);
+    uint64_t* P0 = reinterpret_cast<uint64_t*>(b8 + oP0);
+    uint64_t* P1 = reinterpret_cast<uint64_t*>(b8 + oP1);
+    int64_t* wptr = reinterpret_cast<int64_t*>(b8 + oPtr);
+    int32_t* widx = reinterpret_cast<int32_t*>(b8 + oIdx);
+    uint64_t* wval = reinterpret_cast<uint64_t*>(b8 + oVal);
+    uint8_t* Q[2] = {b8 + oQ[0], b8 + oQ[1]};
+    uint8_t* QT[2] = {b8 + oQT[0], b8 + oQT[1]};
+    uint8_t* M0 = b8 + oM0;
+    uint8_t* M1 = b8 + oM1;
+    uint8_t* T1 = b8 + oT1;
+    uint8_t* X = b8 + oX;
+    BCK(cudaMalloc(&c->d_solo, sizeof(int) * SW_WORDS * ns), "cudaMalloc(large-problem state)");
+    BCK(cudaMemset(c->d_solo, 0, sizeof(int) * SW_WORDS * ns), "clear large-problem state");
+    c->h_solo.assign(static_cast<size_t>(SW_WORDS * ns), 0);
+
+    cudaStream_t cs = nullptr, cb = nullptr;
+    BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaError_t ce = cudaStreamCreateWithFlags(&cb, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_err(ctx, ce, "capture stream");
+    }
+    struct Streams {
+        cudaStream_t a, b;
+        ~Streams() {
+            cudaStreamDestroy(a);
+            cudaStreamDestroy(b);
+        }
+    } guard_streams{cs, cb};
+    BCK(cudaStreamBeginCaptureToGraph(cs, c->graph, after, nullptr, nafter, cudaStreamCaptureModeRelaxed),
+        "begin capture of the large problems");
+    bmlp_status status = BMLP_OK;
+    auto fail = [&](bmlp_status st) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        cudaGetLastError();
+        return st;
+    };
+#define SCK(call, what)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return fail(cuda_err(ctx, e_, what));      \
+    } while (0)
+#define SST(call)                                  \
+    do {                                           \
+        bmlp_status s_ = (call);                   \
+        if (s_ != BMLP_OK) return fail(s_);        \
+    } while (0)
+    const int sms = ctx->sm_count;
+    const double s_word = bitrow_s_per_word(), s_row = bitrow_row_s_per_word(), step_s = bitrow_step_s();
+    for (int k = 0; k < ns; ++k) {
+        const bmlp_problem& p = probs[c->solo[k]];
+        int* w = c->d_solo + SW_WORDS * k;
+        const int64_t n = p.n, ldw = round_up((n + 63) / 64, 2), n_pad = round_up(n, TC_PAD), ld4 = n_pad / 2;
+        const int cap = log2_ceil(n > 1 ? n : 2) + 2;
+        const void* src = p.kind == BMLP_PROBLEM_COMPOSE ? p.R2 : p.R1;
+        const double limit = tc4_product_s(n_pad);
+        // ---- squarings on word-indexed bit rows while they are cheaper than a tensor-core product
+        solo_init_kernel<<<1, 1, 0, cs>>>(w);
+        if (p.fmt == BMLP_FMT_U8)
+            launch_u8_to_packed(static_cast<const uint8_t*>(src), n, P0, ldw, cs);
+        else
+            launch_packed_copy(static_cast<const uint64_t*>(src), (n + 63) / 64, n, n, P0, ldw, 0, cs);
+        SCK(launch_wcsr_build(P0, n, ldw, wptr, widx, wval, cs), "word index build");
+        auto* cost = reinterpret_cast<unsigned long long*>(w + SW_COST);
+        SCK(launch_square_cost(wptr, widx, wval, n, cost, sms, cs), "squaring cost");
+        cudaGraph_t g = nullptr;
+        cudaStreamCaptureStatus cst;
+        SCK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+        cudaGraphConditionalHandle hA, hC;
+        SCK(cudaGraphConditionalHandleCreate(&hA, g, 0, cudaGraphCondAssignDefault), "conditional handle");
+        SCK(cudaGraphConditionalHandleCreate(&hC, g, 0, cudaGraphCondAssignDefault), "conditional handle");
+        solo_rows_decide_kernel<<<1, 1, 0, cs>>>(w, cap, 1, step_s, s_word, s_row, limit, hA);
+        cudaGraph_t body = nullptr;
+        SST(add_while(ctx, cs, hA, &body));
+        SCK(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+            "begin capture of the bit-row loop");
+        {
+            cudaError_t e = launch_square_rows(wptr, widx, wval, P0, n, ldw, P1, sms, cb, w + SW_CHANGED);
+            if (e == cudaSuccess) {  // the next step reads P0 (ldw is even: rows are whole 16-byte units)
+                solo_copy_kernel<<<sms * 4, 256, 0, cb>>>(reinterpret_cast<uint4*>(P0),
+                                                           reinterpret_cast<const uint4*>(P1), n * ldw / 2);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = launch_wcsr_build(P0, n, ldw, wptr, widx, wval, cb);
+            if (e == cudaSuccess) e = launch_square_cost(wptr, widx, wval, n, cost, sms, cb);
+            if (e == cudaSuccess) {
+                solo_rows_decide_kernel<<<1, 1, 0, cb>>>(w, cap, 0, step_s, s_word, s_row, limit, hA);
+                e = cudaGetLastError();
+            }
+            cudaGraph_t tmp = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cb, &tmp);
+            if (e != cudaSuccess || e2 != cudaSuccess) return fail(cuda_err(ctx, e != cudaSuccess ? e : e2, "bit-row loop"));
+        }
+        // ---- squarings on packed E2M1 operands (R^T as the B operand), two per loop iteration
+        launch_packed_to_e2m1(P0, ldw, n, Q[0], QT[0], n_pad, cs);
+        solo_mid_kernel<<<1, 1, 0, cs>>>(w, hC);
+        CUtensorMap mA[2], mB0[2], mB1[2];
+        for (int b = 0; b < 2; ++b) {
+            SST(make_tmap(ctx, &mA[b], Q[b], n_pad, ld4, ld4, TC_BM));
+            SST(make_tmap(ctx, &mB0[b], QT[b], n_pad, ld4, ld4, TC_BN / 2));
+            SST(make_tmap(ctx, &mB1[b], QT[b], n_pad, ld4, ld4, tc4_b1_rows()));
+        }
+        SST(add_while(ctx, cs, hC, &body));
+        SCK(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+            "begin capture of the tensor-core loop");
+        {
+            cudaError_t e = cudaSuccess;
+            for (int half = 0; half < 2 && e == cudaSuccess; ++half) {
+                TcParams p4{};
+                p4.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+                p4.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
+                p4.k_blocks = static_cast<int32_t>(n_pad / 256);
+                p4.mode = TC_MODE_RMS;
+                p4.ld = ld4;
+                p4.old_r = Q[half];
+                p4.out_r = Q[half ^ 1];
+                p4.out_rt = QT[half ^ 1];
+                p4.changed = w + SW_CHANGED;
+                p4.error = ctx->d_ctl + CTL_ERROR;
+                p4.wait_cycles = wait_cycles;
+                p4.guard = w + (half == 0 ? SW_GC : SW_G1);
+                e = launch_tc4_product_duo(mA[half], mB0[half], mB1[half], p4, sms, cb);
+                if (e == cudaSuccess) {
+                    solo_tc_decide_kernel<<<1, 1, 0, cb>>>(w, cap, half, hC);
+                    e = cudaGetLastError();
+                }
+            }
+            cudaGraph_t tmp = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cb, &tmp);
+            if (e != cudaSuccess || e2 != cudaSuccess)
+                return fail(cuda_err(ctx, e != cudaSuccess ? e : e2, "tensor-core loop"));
+        }
+        // ---- results: Q[0] holds the closure (a product that changed nothing left both buffers equal)
+        if (p.kind == BMLP_PROBLEM_CLOSURE) {
+            if (p.fmt == BMLP_FMT_U8)
+                launch_e2m1_to_u8(Q[0], ld4, n, static_cast<uint8_t*>(p.out), p.reflexive, cs);
+            else
+                launch_e2m1_to_packed(Q[0], ld4, n, static_cast<uint64_t*>(p.out), (n + 63) / 64, p.reflexive, cs);
+        } else {
+            // out = (I + R2+) R1 on E4M3 operands: A = I + R2+, B^T = R1^T
+            launch_e2m1_to_e4m3(Q[0], M0, n_pad * n_pad, cs);
+            launch_set_diag_e4m3(M0, n_pad, n, cs);
+            if (p.fmt == BMLP_FMT_U8)
+                launch_u8_to_e4m3(static_cast<const uint8_t*>(p.R1), n, M1, T1, n_pad, cs);
+            else
+                launch_packed_to_e4m3(static_cast<const uint64_t*>(p.R1), (n + 63) / 64, n, n, M1, T1, n_pad, n_pad,
+                                      cs);
+            CUtensorMap fa, fb;
+            SST(make_tmap(ctx, &fa, M0, n_pad, n_pad, n_pad, TC_BM));
+            SST(make_tmap(ctx, &fb, T1, n_pad, n_pad, n_pad, TC_BN));
+            TcParams pp{};
+            pp.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+            pp.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
+            pp.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
+            pp.mode = TC_MODE_PLAIN;
+            pp.ld = n_pad;
+            pp.out_r = X;
+            pp.changed = w + SW_CHANGED;
+            pp.error = ctx->d_ctl + CTL_ERROR;
+            pp.wait_cycles = wait_cycles;
+            const int tiles = pp.m_tiles * pp.n_tiles;
+            SCK(launch_tc_product(fa, fb, pp, tiles < sms ? tiles : sms, cs), "final product");
+            if (p.fmt == BMLP_FMT_U8)
+                launch_bytes_to_u8(X, n_pad, n, static_cast<uint8_t*>(p.out), 0, cs);
+            else
+                launch_bytes_to_packed(X, n_pad, n, n, static_cast<uint64_t*>(p.out), (n + 63) / 64, 0, cs);
+        }
+        SCK(cudaGetLastError(), "large-problem launches");
+    }
+#undef SCK
+#undef SST
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamEndCapture(cs, &g), "end capture of the large problems");
+    return status;
+}
+
+uint64_t batch_key(const bmlp_problem* probs, int64_t count, int variant, const int* tune, int64_t solo_n) {
     uint64_t h = 1469598103934665603ull;
     h = fnv(h, &count, sizeof(count));
     h = fnv(h, &variant, sizeof(variant));
+    h = fnv(h, &solo_n, sizeof(solo_n));
     h = fnv(h, tune, sizeof(int) * 32);
     for (int64_t i = 0; i < count; ++i) h = fnv(h, &probs[i], sizeof(bmlp_problem));
     return h;
@@ -595,7 +950,7 @@ uint64_t batch_key(const bmlp_problem* probs, int64_t count, int variant, const 
 }  // namespace
 
 bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, int variant,
-                           long long wait_cycles, int32_t* iters_out, cudaStream_t s) {
+                           long long wait_cycles, int32_t* iters_out, cudaStream_t s, int64_t solo_n) {
     for (int64_t i = 0; i < count; ++i) {
         const bmlp_problem& p = probs[i];
         if (p.kind != BMLP_PROBLEM_CLOSURE && p.kind != BMLP_PROBLEM_COMPOSE)
@@ -611,9 +966,9 @@ bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
             return set_err(ctx, BMLP_ERR_INVALID_ARG, "problem %lld: matrices must be device memory", (long long)i);
     }
     if (count > (int64_t(1) << 20)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "more than 2^20 problems");
-    const uint64_t key = batch_key(probs, count, variant, ctx->tune);
+    const uint64_t key = batch_key(probs, count, variant, ctx->tune, solo_n);
     BatchCache* c = static_cast<BatchCache*>(ctx->batch);
-    if (c == nullptr || c->key != key) BST(build_batch(ctx, probs, count, variant, wait_cycles, key, &c));
+    if (c == nullptr || c->key != key) BST(build_batch(ctx, probs, count, variant, wait_cycles, key, solo_n, &c));
     BCK(cudaMemsetAsync(ctx->d_ctl, 0, CTL_WORDS * sizeof(int), s), "reset flags");
     ctx->stats.n_pad = static_cast<int64_t>(c->ws_bytes);
     BCK(cudaGraphLaunch(c->exec, s), "cudaGraphLaunch");
@@ -622,8 +977,12 @@ bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
         "read iterations");
     BCK(cudaMemcpyAsync(c->h_notconv.data(), c->d_ints + 4 * np, sizeof(int) * np, cudaMemcpyDeviceToHost, s),
         "read convergence");
+    const int ns = static_cast<int>(c->solo.size());
+    if (ns > 0)
+        BCK(cudaMemcpyAsync(c->h_solo.data(), c->d_solo, sizeof(int) * SW_WORDS * ns, cudaMemcpyDeviceToHost, s),
+            "read large-problem state");
     BCK(cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, CTL_WORDS * sizeof(int), cudaMemcpyDeviceToHost, s), "read flags");
-    BCK(cudaStreamSynchronize(s), "synchronise batch");
+    BCK(host_sync(ctx, s), "synchronise batch");
     if (ctx->h_ctl[CTL_ERROR] != 0)
         return set_err(ctx, BMLP_ERR_TIMEOUT, "in-kernel wait timed out (code 0x%x)", ctx->h_ctl[CTL_ERROR]);
     int maxit = 0, bad = 0;
@@ -632,6 +991,14 @@ bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
         if (iters_out) iters_out[i] = c->h_iters[sl];
         maxit = std::max(maxit, c->h_iters[sl]);
         bad |= c->h_notconv[sl];
+    }
+    for (int k = 0; k < ns; ++k) {
+        const int* w = c->h_solo.data() + SW_WORDS * k;
+        if (iters_out) iters_out[c->solo[k]] = w[SW_ITERS];
+        maxit = std::max(maxit, w[SW_ITERS]);
+        bad |= w[SW_NOTCONV];
+        ctx->stats.launches += 6 + 6 * w[SW_ITERS];
+        ctx->stats.product_launches += w[SW_ITERS];
     }
     ctx->stats.iterations = maxit;
     ctx->stats.launches += 4 + 3 * maxit;

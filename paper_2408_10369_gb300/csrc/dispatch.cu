@@ -528,7 +528,7 @@ bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n
     DCK(cudaGetLastError(), "feature kernels");
     ctx->stats.launches += 4;
     DCK(cudaMemcpyAsync(feat_host, d->d_feat, NF * sizeof(float), cudaMemcpyDeviceToHost, s), "read features");
-    DCK(cudaStreamSynchronize(s), "synchronise features");
+    DCK(host_sync(ctx, s), "synchronise features");
     return BMLP_OK;
 }
 
@@ -557,7 +557,7 @@ bmlp_status dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float
     std::vector<float> y(m * NV);
     DCK(cudaMemcpyAsync(y.data(), dY, m * NV * sizeof(float), cudaMemcpyDeviceToHost, s), "read predictions");
     DCK(cudaMemcpyAsync(c.data(), dC, m * sizeof(int), cudaMemcpyDeviceToHost, s), "read choices");
-    DCK(cudaStreamSynchronize(s), "synchronise predict");
+    DCK(host_sync(ctx, s), "synchronise predict");
     cudaFree(dX);
     cudaFree(dY);
     cudaFree(dC);

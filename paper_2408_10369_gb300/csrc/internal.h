@@ -51,6 +51,8 @@ struct TcParams {
     uint8_t* fmapT_next;
     int32_t fm_ld;
     unsigned long long* issued; // multiply-adds issued in units of 128 x 32 x 128 (rows x columns x K), or null
+    const int* guard;           // 4-bit squaring kernel: if not null and *guard == 0 the launch does nothing (a step
+                                // of a device-side loop that a decision kernel switched off)
 };
 
 // One problem of a grouped batch (device copy; built on the host).
@@ -149,12 +151,23 @@ enum CtlWord : int {
     CTL_ISSUED = 10, CTL_COST = 12, CTL_WORDS = 16
 };
 
-// Workspace slot of the grouped batch (the others are private to api.cu).
+// Workspace slots of the grouped batch and of its device-driven large problems (the others are private to api.cu).
 constexpr int WS_BATCH = 15;
+constexpr int WS_SOLO = 25;
 
 // ---- grouped batch (batch.cu)
+// Problems with n >= solo_n (0: none) that may use the tensor cores run as device-driven single-problem pipelines
+// (bit-row squarings, then 4-bit tensor-core squarings) inside the same graph; the rest are grouped.
 bmlp_status batch_run_impl(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count, int variant, long long wait_cycles,
-                           int32_t* iters_out, cudaStream_t s);
+                           int32_t* iters_out, cudaStream_t s, int64_t solo_n = 0);
+// The step-cost model of the bit-row squarings (api.cu): seconds of a step from its word ORs, and of a dense 4-bit
+// tensor-core product of n_pad.
+double bitrow_s_per_word();
+double bitrow_row_s_per_word();
+double bitrow_step_s();
+double tc4_product_s(int64_t n_pad);
+// Synchronise s on behalf of the current call (counted in bmlp_stats.host_syncs).
+cudaError_t host_sync(bmlp_ctx* ctx, cudaStream_t s);
 void batch_cache_free(bmlp_ctx* ctx);
 
 // ---- learned dispatcher (dispatch.cu)

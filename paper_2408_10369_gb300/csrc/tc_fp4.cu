@@ -203,6 +203,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
 tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
     using C = Duo<N1>;
+    // a step of a device-side loop that was switched off: every CTA of every pair leaves before it allocates TMEM or
+    // touches a barrier (they all read the same word, written by an earlier kernel in stream order)
+    if (p.guard != nullptr && *reinterpret_cast<const volatile int*>(p.guard) == 0) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem + C::OFF_A;

@@ -126,9 +126,10 @@ def test_single_problem_device_loop(ctx, variant, n, d, seed):
 
 @pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
 def test_batch_mixes_solo_and_grouped_problems(ctx, fmt):
-    """Problems with n >= 4096 run on the single-problem path (4-bit operands
-    once dense), the others in the grouped batch; every output and every
-    iteration count as for the problem alone."""
+    """Problems with n >= 4096 run as device-driven single-problem pipelines
+    (bit rows, then 4-bit operands) inside the batch graph, the others in the
+    grouped batch; every output and every iteration count as for the problem
+    alone."""
     items, expect, keep = [], [], []
     for n, d, seed in [(8300, 2.0, 1), (300, 1.5, 2), (8250, 0.7, 3), (900, 1.2, 4)]:
         ip, ix = wl.er_graph(n, d, seed)
@@ -154,3 +155,72 @@ def test_batch_mixes_solo_and_grouped_problems(ctx, fmt):
     for k in range(4):
         _, n, ip, ix = expect[k]
         assert iters[k] == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+    # one graph launch: the host waits once, for the results
+    assert ctx.stats()["host_syncs"] == 1
+
+
+@pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
+def test_batch_of_large_problems_only(ctx, fmt):
+    """Only problems with n >= 4096 (no grouped part): a path-like relation
+    (many squarings on bit rows before the tensor cores take over), a sparse
+    one that finishes on bit rows, a dense one that goes straight to the
+    tensor cores, a reflexive closure and a composition, all in one graph."""
+    items, expect, keep = [], [], []
+    cases = [("chain", 5000, 0.01, 11), ("er", 4100, 0.6, 12), ("er", 4500, 6.0, 13), ("refl", 4200, 1.3, 14)]
+    for kind, n, p, seed in cases:
+        if kind == "chain":
+            src = np.arange(n - 1)
+            dst = src + 1
+            a, b = wl.random_pairs(n, int(p * n), seed)
+            ip, ix = wl.csr_from_pairs(n, np.concatenate([src, a]), np.concatenate([dst, b]))
+        else:
+            ip, ix = wl.er_graph(n, p, seed)
+        m = wl.dense_u8(n, ip, ix)
+        R = dev(m if fmt == bmlp.BMLP_FMT_U8 else wl.pack_rows(m).view(np.int64))
+        out = torch.zeros_like(R)
+        keep += [R, out]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_CLOSURE, n=n, R1=R, out=out, fmt=fmt, reflexive=kind == "refl"))
+        expect.append((kind, n, ip, ix))
+    nc = 4300
+    c1, c2 = wl.er_graph(nc, 1.2, 15), wl.er_graph(nc, 0.9, 16)
+    m1, m2 = wl.dense_u8(nc, *c1), wl.dense_u8(nc, *c2)
+    if fmt != bmlp.BMLP_FMT_U8:
+        m1, m2 = wl.pack_rows(m1).view(np.int64), wl.pack_rows(m2).view(np.int64)
+    R1, R2 = dev(m1), dev(m2)
+    out = torch.zeros_like(R1)
+    keep += [R1, R2, out]
+    items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=nc, R1=R1, R2=R2, out=out, fmt=fmt))
+    iters = ctx.batch_run(items)
+    torch.cuda.synchronize()
+    assert ctx.stats()["host_syncs"] == 1
+    for it, (kind, n, ip, ix), k in zip(items, expect, iters):
+        got = it["out"].cpu().numpy()
+        if fmt == bmlp.BMLP_FMT_PACKED64:
+            got = wl.unpack_rows(got.view(np.uint64), n)
+        want = oracle.closure(n, ip, ix)
+        if kind == "refl":
+            want = want | np.eye(n, dtype=np.uint8)
+        np.testing.assert_array_equal(got, want)
+        assert k == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+    got = items[-1]["out"].cpu().numpy()
+    if fmt == bmlp.BMLP_FMT_PACKED64:
+        got = wl.unpack_rows(got.view(np.uint64), nc)
+    np.testing.assert_array_equal(got, oracle.compose_rows(nc, c1, c2))
+    # the same problems again reuse the cached graph
+    for it in items:
+        it["out"].zero_()
+    assert ctx.batch_run(items) == iters
+
+
+def test_single_problem_device_loop_large(ctx):
+    """loop = BMLP_LOOP_GRAPH with n >= 4096: the device-driven pipeline
+    (bit rows, then 4-bit tensor-core squarings) as a batch of one."""
+    n = 6000
+    ip, ix = wl.er_graph(n, 1.7, 21)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros_like(P)
+    it = ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="rms_tc", loop=bmlp.BMLP_LOOP_GRAPH)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), oracle.closure(n, ip, ix))
+    assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+    assert ctx.stats()["host_syncs"] == 1

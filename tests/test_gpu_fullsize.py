@@ -162,6 +162,8 @@ def test_config4_kg_batch(ctx):
         expect.append(("compose", n, c1, c2))
     iters = ctx.batch_run(items)
     torch.cuda.synchronize()
+    # one graph launch for all 1,545 programs (the large ones as device-driven pipelines): one host wait
+    assert ctx.stats()["host_syncs"] == 1
     for it, ex, k in zip(items, expect, iters):
         n = ex[1]
         got = it["out"].cpu().numpy().view(np.uint64)
