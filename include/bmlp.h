@@ -339,9 +339,14 @@ typedef struct bmlp_problem {
  * BMLP_RMS_PACKED; compositions always use the tensor cores).
  * Problems large enough to fill the GPU alone (n >= 4096 by default, the
  * environment variable BMLP_BATCH_SOLO_N changes it, 0 = never) that are not
- * forced onto packed rows run one after another on the single-problem
- * tensor-core path instead (bmlp_rms / bmlp_compose with BMLP_RMS_TC, whose
- * squarings switch to 4-bit operands once R is dense), before the batch.
+ * forced onto packed rows run in the same graph, one after another, as
+ * device-driven single-problem pipelines: squarings on word-indexed bit rows
+ * while the next one is predicted cheaper than a tensor-core product (a
+ * one-thread decision kernel sets the condition of a WHILE node), then
+ * squarings on packed E2M1 operands on the tensor cores (a second WHILE
+ * node), then the decode or, for a composition, I + R2+ and the product with
+ * R1. The whole batch is one graph launch and one read of the results
+ * (bmlp_stats.host_syncs = 1).
  * iters_out (count entries, may be null) receives each problem's products.
  * All matrix pointers must be device memory. The instantiated graph is cached
  * in the context and reused while the problem list is unchanged.
