@@ -305,10 +305,11 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
                         const uint8_t** res_f4 = nullptr) {
     NvtxRange nvtx_("tensor-core squarings");
-    CUtensorMap mapA[2], mapB[2];
+    CUtensorMap mapA[2], mapB[2], mapBh[2];
     for (int b = 0; b < 2; ++b) {
         ST(make_tmap(ctx, &mapA[b], M[b], n_pad, n_pad, n_pad, TC_BM));
         ST(make_tmap(ctx, &mapB[b], T[b], n_pad, n_pad, n_pad, TC_BN));
+        ST(make_tmap(ctx, &mapBh[b], T[b], n_pad, n_pad, n_pad, TC_BN / 2));
     }
     TcParams p{};
     p.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
@@ -467,7 +468,15 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         p.out_r = M[nxt];
         p.out_rt = T[nxt];
         ST(tm.begin());
-        CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
+        if (use_maps) {
+            // block-sparse R: one CTA per SM, empty K blocks skipped, block maps of the new R
+            CK(launch_tc_product(mapA[cur], mapB[cur], p, grid, s), "tensor-core product launch");
+        } else {
+            // dense R on E4M3 operands: M = 256 MMAs per CTA pair on 256 x 512 pair tiles
+            TcParams p8 = p;
+            p8.n_tiles = static_cast<int32_t>((n_pad + tc8_tile_n() - 1) / tc8_tile_n());
+            CK(launch_tc8_product_duo(mapA[cur], mapBh[cur], p8, ctx->sm_count, s), "tensor-core product launch");
+        }
         ST(tm.end());
         ctx->stats.product_launches++;
         ctx->stats.launches += 2;

@@ -250,6 +250,12 @@ cudaError_t launch_tc_product(const CUtensorMap& a, const CUtensorMap& b, const 
 // multiply-add units.
 int tc4_tile_n();
 int tc4_b1_rows();
+// the same squaring step on E4M3 operands (n_pad x n_pad bytes, p.ld = n_pad, p.k_blocks = n_pad / 128) as
+// kind::f8f6f4 M = 256 MMAs per CTA pair on pair tiles of 256 x tc8_tile_n() (p.n_tiles = ceil(n_pad / that));
+// no block maps (p.fmap must be null): A box 128 rows, b_half box 128 rows of R^T
+int tc8_tile_n();
+cudaError_t launch_tc8_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                   cudaStream_t s);
 cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1,
                                    const TcParams& p, int sms, cudaStream_t s);
 // E4M3 bytes <-> packed E2M1 nibbles (sizes multiples of 16 bytes)

@@ -159,6 +159,16 @@ __device__ __forceinline__ void tmem_relinquish_2sm() {
 __device__ __forceinline__ void tmem_dealloc_2sm(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// kind::f8f6f4 (E4M3) over a CTA pair: M = 256 rows split over the pair as for tc_mma_mxf4_2sm, no scale factors.
+__device__ __forceinline__ void tc_mma_f8_2sm(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // D (+)= A * B^T with M = 256 rows split over the pair (128 per CTA, same
 // shared-memory offset and TMEM columns in both) and B's N rows split in halves
 // the same way; kind::mxf4 as tc_mma_mxf4.

@@ -107,7 +107,10 @@ __device__ __forceinline__ uint32_t f4_bits32(const uint4& v) {
 //           MMA into columns 256..479 per K step (the scale factors take
 //           columns 480..511), 4 stages of 46 KB; a tile whose columns from
 //           256 on all lie beyond n_pad issues only the first MMA.
-template <int N1>
+// KIND 1: packed E2M1 operands, kind::mxf4 with unit scale factors (256 elements per 128-byte K block);
+// KIND 0: E4M3 operands, kind::f8f6f4 (128 elements per 128-byte K block, no scale factors, so the second MMA can
+// be N = 256 and all 512 TMEM columns hold accumulators).
+template <int KIND, int N1>
 struct Duo {
     static constexpr int BN = TC_BN + N1;               // output columns of a pair tile
     static constexpr int B0_ROWS = TC_BN / 2;           // this CTA's rows of the N = 256 part
@@ -118,7 +121,7 @@ struct Duo {
     static constexpr int B_BYTES = B0_BYTES + B1_BYTES;
     static constexpr int STAGES = N1 ? 4 : 6;
     static constexpr int CHUNKS = BN / 32;              // 32-column chunks of the epilogue
-    static constexpr int SFA_COL = N1 ? 480 : 256;      // scale factors (all 2^0; with N1 both operands
+    static constexpr int SFA_COL = N1 ? 480 : 256;      // E2M1 scale factors (all 2^0; with N1 both operands
     static constexpr int SFB_COL = N1 ? 480 : 384;      // read the same filled columns)
     static constexpr int SF_FILL = N1 ? 32 : 0;         // N1: columns 480..511 hold 2^0 scales
     static constexpr int OFF_A = 0;
@@ -127,7 +130,7 @@ struct Duo {
     static constexpr int NUM_BARS = 2 * STAGES + 3;     // full[], empty[], tfull, tempty, done
     static constexpr int OFF_MISC = OFF_BAR + NUM_BARS * 8;
     static constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;
-    static_assert(N1 == 0 || (N1 % 32 == 0 && N1 <= 224), "second MMA width");
+    static_assert(N1 == 0 || (N1 % 32 == 0 && N1 <= (KIND ? 224 : 256)), "second MMA width");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
     static_assert(B_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
 };
@@ -135,6 +138,8 @@ struct Duo {
 // Second MMA width of the squaring kernel's pair tile (BN = 480). Measured on GB300 at n = 32,768: 8.88 PFLOP/s
 // against 7.33 for the 256-column tile (N1 = 0), which reads a third more operand bytes per Boolean operation.
 constexpr int TC4_N1 = 224;
+// The E4M3 form has no scale factors in TMEM, so its pair tile is 256 x 512 (two N = 256 MMAs per K step).
+constexpr int TC8_N1 = 256;
 
 constexpr int ERR_D_PRODUCER = 0x211;
 constexpr int ERR_D_MMA = 0x212;
@@ -169,21 +174,55 @@ __device__ __forceinline__ uint32_t f4_pick(const uint32_t (&cb)[CHUNKS], int c)
 // whose first column is col_base: writes R' and, through warp ballots, R'^T
 // for every 32-column chunk below n_pad; returns the bits that changed
 // (nonzero in some lane iff R' != R in this warp's rows).
-template <int CHUNKS>
+// E4M3 bytes: 4 bytes -> 4 bits (bit k = byte k nonzero), and back (0 / one).
+__device__ __forceinline__ uint32_t e4_bits4(uint32_t w) {
+    const uint32_t x = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+    return ((x >> 7) & 1u) | ((x >> 14) & 2u) | ((x >> 21) & 4u) | ((x >> 28) & 8u);
+}
+__device__ __forceinline__ uint32_t e4_bits16(const uint4& v) {
+    return e4_bits4(v.x) | (e4_bits4(v.y) << 4) | (e4_bits4(v.z) << 8) | (e4_bits4(v.w) << 12);
+}
+__device__ __forceinline__ uint32_t e4_bytes4(uint32_t b) {
+    const uint32_t t = b & 0xFu;
+    return ((t | (t << 7) | (t << 14) | (t << 21)) & 0x01010101u) * static_cast<uint32_t>(BMLP_E4M3_ONE);
+}
+__device__ __forceinline__ uint4 e4_bytes16(uint32_t m) {
+    return make_uint4(e4_bytes4(m), e4_bytes4(m >> 4), e4_bytes4(m >> 8), e4_bytes4(m >> 12));
+}
+
+// 32 columns of a row as bits, and back, in the operand form of KIND.
+template <int KIND>
+__device__ __forceinline__ uint32_t load_bits32(const uint8_t* p) {
+    if (KIND) return f4_bits32(*reinterpret_cast<const uint4*>(p));
+    return e4_bits16(reinterpret_cast<const uint4*>(p)[0]) | (e4_bits16(reinterpret_cast<const uint4*>(p)[1]) << 16);
+}
+template <int KIND>
+__device__ __forceinline__ void store_bits32(uint8_t* p, uint32_t bits) {
+    if (KIND) {
+        *reinterpret_cast<uint4*>(p) = f4_nibbles32(bits);
+    } else {
+        reinterpret_cast<uint4*>(p)[0] = e4_bytes16(bits & 0xFFFFu);
+        reinterpret_cast<uint4*>(p)[1] = e4_bytes16(bits >> 16);
+    }
+}
+
+template <int KIND, int CHUNKS>
 __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int64_t col_base, int64_t n_pad, int quarter,
                                               int lane, const uint32_t (&cb)[CHUNKS]) {
+    constexpr int CB = KIND ? 16 : 32;  // bytes of 32 columns
     const int64_t row = static_cast<int64_t>(mb) * TC_BM + quarter * 32 + lane;
-    const int64_t rt_col = static_cast<int64_t>(mb) * (TC_BM / 2) + quarter * 16;  // byte of row in R'^T
+    // byte of this warp's 32 rows inside a row of R'^T
+    const int64_t rt_col = (static_cast<int64_t>(mb) * TC_BM + quarter * 32) / 32 * CB;
     uint32_t any = 0;
 #pragma unroll 1
     for (int c = 0; c < CHUNKS; ++c) {
         const int64_t col0 = col_base + c * 32;
         if (col0 >= n_pad) break;
-        const int64_t off = row * p.ld + col0 / 2;
-        const uint32_t obits = f4_bits32(*reinterpret_cast<const uint4*>(p.old_r + off));
+        const int64_t off = row * p.ld + col0 / 32 * CB;
+        const uint32_t obits = load_bits32<KIND>(p.old_r + off);
         const uint32_t nbits = obits | f4_pick(cb, c);
         any |= nbits ^ obits;
-        *reinterpret_cast<uint4*>(p.out_r + off) = f4_nibbles32(nbits);
+        store_bits32<KIND>(p.out_r + off, nbits);
         // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
         uint32_t mine = 0;
 #pragma unroll
@@ -191,18 +230,18 @@ __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int64_t
             const uint32_t b = __ballot_sync(0xFFFFFFFFu, (nbits >> j) & 1u);
             mine = (lane == j) ? b : mine;
         }
-        *reinterpret_cast<uint4*>(p.out_rt + (col0 + lane) * p.ld + rt_col) = f4_nibbles32(mine);
+        store_bits32<KIND>(p.out_rt + (col0 + lane) * p.ld + rt_col, mine);
     }
     return any;
 }
 
 // tmA: A = R (box 128 rows x 128 bytes); tmB0 / tmB1: B^T = R^T (boxes of
 // B0_ROWS / B1_ROWS rows x 128 bytes; tmB1 unused when N1 = 0).
-template <int N1>
+template <int KIND, int N1>
 __global__ void __launch_bounds__(TC_THREADS, 1) __cluster_dims__(2, 1, 1)
-tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+tc_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
-    using C = Duo<N1>;
+    using C = Duo<KIND, N1>;
     // a step of a device-side loop that was switched off: every CTA of every pair leaves before it allocates TMEM or
     // touches a barrier (they all read the same word, written by an earlier kernel in stream order)
     if (p.guard != nullptr && *reinterpret_cast<const volatile int*>(p.guard) == 0) return;
@@ -251,7 +290,7 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    if (warp >= 2) {
+    if (KIND == 1 && warp >= 2) {
         // every scale factor of A and B is 2^0, in all 128 lanes of this CTA
         const uint32_t lanes = static_cast<uint32_t>((warp & 3) * 32) << 16;
         const uint32_t ones[8] = {F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4, F4_UE8M0_ONE4,
@@ -319,8 +358,9 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (even CTA)
         if (leader) {
-            const uint32_t idesc0 = idesc_mxf4_ue8m0(2 * TC_BM, TC_BN);
-            const uint32_t idesc1 = idesc_mxf4_ue8m0(2 * TC_BM, N1 ? N1 : TC_BN);
+            const uint32_t idesc0 = KIND ? idesc_mxf4_ue8m0(2 * TC_BM, TC_BN) : idesc_e4m3_f32(2 * TC_BM, TC_BN);
+            const uint32_t idesc1 = KIND ? idesc_mxf4_ue8m0(2 * TC_BM, N1 ? N1 : TC_BN)
+                                         : idesc_e4m3_f32(2 * TC_BM, N1 ? N1 : TC_BN);
             const uint32_t sfa = tmem_base + C::SFA_COL, sfb = tmem_base + C::SFB_COL;
             int stage = 0;
             uint32_t phase = 0;
@@ -348,12 +388,15 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                         for (int k = 0; k < F4_BK / F4_UMMA_K_BYTES; ++k) {
                             const uint64_t ad = smem_desc_kmajor_sw128(a0 + k * F4_UMMA_K_BYTES);
-                            tc_mma_mxf4_2sm(tmem_base, ad, smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES), idesc0,
-                                            sfa, sfb, accumulate);
-                            if (has1)
-                                tc_mma_mxf4_2sm(tmem_base + TC_BN, ad,
-                                                smem_desc_kmajor_sw128(b0 + C::B0_BYTES + k * F4_UMMA_K_BYTES),
-                                                idesc1, sfa, sfb, accumulate);
+                            const uint64_t bd0 = smem_desc_kmajor_sw128(b0 + k * F4_UMMA_K_BYTES);
+                            const uint64_t bd1 = smem_desc_kmajor_sw128(b0 + C::B0_BYTES + k * F4_UMMA_K_BYTES);
+                            if (KIND) {
+                                tc_mma_mxf4_2sm(tmem_base, ad, bd0, idesc0, sfa, sfb, accumulate);
+                                if (has1) tc_mma_mxf4_2sm(tmem_base + TC_BN, ad, bd1, idesc1, sfa, sfb, accumulate);
+                            } else {
+                                tc_mma_f8_2sm(tmem_base, ad, bd0, idesc0, accumulate);
+                                if (has1) tc_mma_f8_2sm(tmem_base + TC_BN, ad, bd1, idesc1, accumulate);
+                            }
                             accumulate = 1;
                         }
                         tc_commit_2sm_mcast(&empty[stage], 0x3);  // the stage is free in both CTAs
@@ -366,10 +409,11 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                 }
                 if (!ok) break;
-                // multiply-adds issued, in units of 128 x 32 x 128: per 256-deep K block two 128-row halves,
-                // two 128-deep halves and 8 (+ N1 / 32) column chunks
+                // multiply-adds issued, in units of 128 x 32 x 128: per K block two 128-row halves, one (E4M3) or
+                // two (E2M1) 128-deep parts and 8 (+ N1 / 32) column chunks
                 if (lane == 0 && p.issued != nullptr)
-                    atomicAdd(p.issued, 4ull * static_cast<unsigned long long>(TC_BN / 32 + (has1 ? N1 / 32 : 0)) *
+                    atomicAdd(p.issued, (KIND ? 4ull : 2ull) *
+                                            static_cast<unsigned long long>(TC_BN / 32 + (has1 ? N1 / 32 : 0)) *
                                             static_cast<unsigned long long>(p.k_blocks));
                 if (lane == 0) tc_commit_2sm_mcast(tfull, 0x3);
                 __syncwarp();
@@ -406,7 +450,7 @@ tc4_duo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_arrive_cluster(tempty_even);
             acc_phase ^= 1u;
             const uint32_t any =
-                f4_update<C::CHUNKS>(p, mb, static_cast<int64_t>(nb) * C::BN, n_pad, quarter, lane, cb);
+                f4_update<KIND, C::CHUNKS>(p, mb, static_cast<int64_t>(nb) * C::BN, n_pad, quarter, lane, cb);
             if (__any_sync(0xFFFFFFFFu, any != 0) && lane == 0) atomicOr(p.changed, 1);
         }
     }
@@ -465,27 +509,33 @@ int f4_grid(int64_t work, int threads) {
 
 }  // namespace
 
-template <int N1>
+template <int KIND, int N1>
 cudaError_t launch_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1, const TcParams& p, int sms,
                        cudaStream_t s) {
     // set on every launch: the attribute belongs to the current device, and a call costs well under a microsecond
-    cudaError_t e = cudaFuncSetAttribute(tc4_duo_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Duo<N1>::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc_duo_kernel<KIND, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Duo<KIND, N1>::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int pairs = (p.m_tiles / 2) * p.n_tiles;
     int clusters = sms / 2;
     if (clusters > pairs) clusters = pairs;
     if (clusters < 1) clusters = 1;
-    tc4_duo_kernel<N1><<<2 * clusters, TC_THREADS, Duo<N1>::SMEM_BYTES, s>>>(a, b0, b1, p);
+    tc_duo_kernel<KIND, N1><<<2 * clusters, TC_THREADS, Duo<KIND, N1>::SMEM_BYTES, s>>>(a, b0, b1, p);
     return cudaGetLastError();
 }
 
-int tc4_tile_n() { return Duo<TC4_N1>::BN; }
-int tc4_b1_rows() { return Duo<TC4_N1>::B1_ROWS; }
+int tc4_tile_n() { return Duo<1, TC4_N1>::BN; }
+int tc4_b1_rows() { return Duo<1, TC4_N1>::B1_ROWS; }
+int tc8_tile_n() { return Duo<0, TC8_N1>::BN; }
 
 cudaError_t launch_tc4_product_duo(const CUtensorMap& a, const CUtensorMap& b0, const CUtensorMap& b1,
                                    const TcParams& p, int sms, cudaStream_t s) {
-    return launch_duo<TC4_N1>(a, b0, b1, p, sms, s);
+    return launch_duo<1, TC4_N1>(a, b0, b1, p, sms, s);
+}
+
+cudaError_t launch_tc8_product_duo(const CUtensorMap& a, const CUtensorMap& b_half, const TcParams& p, int sms,
+                                   cudaStream_t s) {
+    return launch_duo<0, TC8_N1>(a, b_half, b_half, p, sms, s);
 }
 
 void launch_e4m3_to_e2m1(const uint8_t* in, uint8_t* out, int64_t bytes_in, cudaStream_t s) {

@@ -76,12 +76,12 @@ def test_profile_summary_values(tmp_path):
     import bench
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "tc4_duo_kernel_er64.md").write_text(
+    (prof / "tc_duo_kernel_er64.md").write_text(
         "# title\n- kernel_source_sha256_12: `%s`\n- dram_bytes_per_launch: `1234`  (note)\n"
-        % bench.kernel_hash("tc4_duo_kernel"))
-    assert bench.profiled_traffic("tc4_duo_kernel", 64, root=str(tmp_path)) == 1234.0
-    (prof / "tc4_duo_kernel_er64.md").write_text("- kernel_source_sha256_12: `000000000000`\n"
+        % bench.kernel_hash("tc_duo_kernel"))
+    assert bench.profiled_traffic("tc_duo_kernel", 64, root=str(tmp_path)) == 1234.0
+    (prof / "tc_duo_kernel_er64.md").write_text("- kernel_source_sha256_12: `000000000000`\n"
                                                  "- dram_bytes_per_launch: `1234`\n")
-    assert bench.profiled_traffic("tc4_duo_kernel", 64, root=str(tmp_path)) is None
-    assert bench.profiled_traffic("tc4_duo_kernel", 32768) is None or bench.profiled_traffic(
-        "tc4_duo_kernel", 32768) > 0
+    assert bench.profiled_traffic("tc_duo_kernel", 64, root=str(tmp_path)) is None
+    assert bench.profiled_traffic("tc_duo_kernel", 32768) is None or bench.profiled_traffic(
+        "tc_duo_kernel", 32768) > 0
