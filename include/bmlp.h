@@ -316,7 +316,8 @@ typedef struct bmlp_problem {
     int32_t fmt;        /* bmlp_format of R1, R2 and out                          */
     int32_t reflexive;  /* closures only: 1 gives I + R1+                         */
     int32_t variant;    /* closures only: 0 = the batch's choice, else
-                           BMLP_RMS_TC or BMLP_RMS_PACKED for this problem       */
+                           BMLP_RMS_TC, BMLP_RMS_PACKED or BMLP_SMP_PACKED
+                           (every row by frontier expansion) for this problem */
     int64_t n;          /* matrix size (0 = nothing to do)                        */
     const void* R1;     /* device memory                                          */
     const void* R2;     /* device memory, compositions only                       */
@@ -336,7 +337,12 @@ typedef struct bmlp_problem {
  * not take part until the whole batch has converged. Each problem runs on
  * the tensor cores or on packed rows, chosen per size bucket by the autotuner
  * (bmlp_batch_autotune) or forced by opts->variant (BMLP_RMS_TC /
- * BMLP_RMS_PACKED; compositions always use the tensor cores).
+ * BMLP_RMS_PACKED; compositions always use the tensor cores). Closures with
+ * variant BMLP_SMP_PACKED (the problem's or the batch's) take no part in the
+ * squaring loop: every row of every such closure is one query of a single
+ * grouped frontier launch (Algorithm 2 from each constant), after grouped
+ * launches that build their transposes and word indexes; their iteration
+ * count is the deepest level + 1.
  * Problems large enough to fill the GPU alone (n >= 4096 by default, the
  * environment variable BMLP_BATCH_SOLO_N changes it, 0 = never) that are not
  * forced onto packed rows run in the same graph, one after another, as

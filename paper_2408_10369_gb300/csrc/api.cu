@@ -1011,10 +1011,8 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
         void* P = nullptr;
         ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
         ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
-        float feats[BMLP_NFEAT];
-        ST(dispatch_features_packed(ctx, static_cast<uint64_t*>(P), n, ldw, feats, s));
         int32_t choice = BMLP_RMS_TC;
-        ST(dispatch_predict(ctx, feats, 1, nullptr, &choice, s));
+        ST(dispatch_choose_packed(ctx, static_cast<uint64_t*>(P), n, ldw, &choice, s));
         variant = choice;
         ctx->stats.variant = variant;
     }
@@ -1558,8 +1556,13 @@ bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
     if (count == 0) return BMLP_OK;
     DeviceGuard g(ctx->device);
     bmlp_options o = resolve(opts);
-    if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC && o.variant != BMLP_RMS_PACKED)
+    if (o.variant != BMLP_AUTO && o.variant != BMLP_RMS_TC && o.variant != BMLP_RMS_PACKED &&
+        o.variant != BMLP_SMP_PACKED)
         return set_err(ctx, BMLP_ERR_INVALID_ARG, "variant %d is not a batch variant", o.variant);
+    for (int64_t i = 0; i < count; ++i)
+        if (probs[i].variant < 0 || probs[i].variant > BMLP_SMP_PACKED)
+            return set_err(ctx, BMLP_ERR_INVALID_ARG, "problem %lld: bad variant %d", static_cast<long long>(i),
+                           probs[i].variant);
     // Problems large enough to fill the GPU on their own (n >= batch_solo_n()) and not forced onto packed rows run
     // inside the same graph as device-driven single-problem pipelines (squarings on bit rows while R is sparse, then
     // on 4-bit operands on the tensor cores); the rest run together as one grouped batch. One graph launch, one

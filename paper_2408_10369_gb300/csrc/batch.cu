@@ -132,10 +132,12 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(const GroupProblem* pr
     for (int p = a; p < b; ++p) {
         const GroupProblem& g = probs[p];
         if (mode == 0) {
-            st->parity[p] = 0;
+            // frontier-engine problems (engine 2) take no part in the squaring loop; their closure rows are
+            // written into P[1] by the grouped frontier launch
+            st->parity[p] = g.engine == 2 ? 1 : 0;
             st->iters[p] = 0;
             st->notconv[p] = 0;
-            st->active[p] = g.n > 0 ? 1 : 0;
+            st->active[p] = (g.n > 0 && g.engine != 2) ? 1 : 0;
         } else if (mode == 1) {
             if (st->active[p]) {
                 st->iters[p] += 1;
@@ -450,6 +452,7 @@ struct BatchCache {
     cudaGraphExec_t exec = nullptr;
     size_t ws_bytes = 0;
     std::vector<int> h_iters, h_notconv;
+    FrontierJob* d_jobs = nullptr;   // closures by frontier expansion (engine 2), then a 64-bit row counter
     std::vector<int> solo;           // caller indices of the device-driven large problems, in run order
     int* d_solo = nullptr;           // SW_WORDS control words per large problem
     std::vector<int> h_solo;
@@ -464,6 +467,7 @@ void batch_cache_free(bmlp_ctx* ctx) {
     if (c->d_st) cudaFree(c->d_st);
     if (c->d_ints) cudaFree(c->d_ints);
     if (c->d_solo) cudaFree(c->d_solo);
+    if (c->d_jobs) cudaFree(c->d_jobs);
     delete c;
     ctx->batch = nullptr;
 }
@@ -495,22 +499,48 @@ bmlp_status add_kernel(bmlp_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* node, cons
     return BMLP_OK;
 }
 
+// 0: tensor-core squarings; 1: squarings on packed rows; 2: frontier expansion of every row (closures only).
 int engine_for(bmlp_ctx* ctx, const bmlp_problem& p, int variant) {
     if (p.kind == BMLP_PROBLEM_COMPOSE) return 0;
-    if (p.variant == BMLP_RMS_TC) return 0;
-    if (p.variant == BMLP_RMS_PACKED) return 1;
-    if (variant == BMLP_RMS_TC) return 0;
-    if (variant == BMLP_RMS_PACKED) return 1;
+    const int v = p.variant ? p.variant : variant;
+    if (v == BMLP_RMS_TC || v == BMLP_SMP_TC) return 0;
+    if (v == BMLP_RMS_PACKED) return 1;
+    if (v == BMLP_SMP_PACKED) return 2;
     const int b = bucket_of(p.n);
     if (b < 32 && ctx->tune[b] >= 0) return ctx->tune[b];
     return 0;
+}
+
+// Captures the grouped frontier launches into the batch graph after `after`; *tail receives the nodes the next
+// node must depend on.
+bmlp_status add_frontier_chain(bmlp_ctx* ctx, BatchCache* c, int njobs, int64_t max_n, int64_t max_ldw, int64_t total,
+                               cudaGraphNode_t after, std::vector<cudaGraphNode_t>* tail) {
+    cudaStream_t cs = nullptr;
+    BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    struct Stream {
+        cudaStream_t a;
+        ~Stream() { cudaStreamDestroy(a); }
+    } guard_stream{cs};
+    BCK(cudaStreamBeginCaptureToGraph(cs, c->graph, &after, nullptr, 1, cudaStreamCaptureModeRelaxed),
+        "begin capture of the frontier launches");
+    auto* counter = reinterpret_cast<unsigned long long*>(c->d_jobs + njobs);
+    cudaError_t e = launch_frontier_group(c->d_jobs, njobs, max_n, max_ldw, total, counter, ctx->sm_count, cs);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e == cudaSuccess) tail->assign(deps, deps + nd);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) return cuda_err(ctx, e != cudaSuccess ? e : e2, "frontier launches");
+    return BMLP_OK;
 }
 
 bool is_solo(const bmlp_problem& p, int variant, int64_t solo_n) {
     if (solo_n <= 0 || p.n < solo_n) return false;
     if (p.kind == BMLP_PROBLEM_COMPOSE) return true;
     const int v = p.variant ? p.variant : variant;
-    return v != BMLP_RMS_PACKED;
+    return v == BMLP_AUTO || v == BMLP_RMS_TC;
 }
 
 bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, long long wait_cycles,
@@ -541,6 +571,12 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
         return o;
     };
     std::vector<size_t> offM0(np), offM1(np), offT0(np), offT1(np), offX(np), offR1T(np), offP0(np), offP1(np);
+    std::vector<size_t> offPT(np), offPtr[2], offIdx[2], offVal[2];
+    for (int m = 0; m < 2; ++m) {
+        offPtr[m].resize(np);
+        offIdx[m].resize(np);
+        offVal[m].resize(np);
+    }
     for (int s = 0; s < np; ++s) {
         const bmlp_problem& p = probs[c->order[s]];
         GroupProblem& g = hp[s];
@@ -574,6 +610,14 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
             const size_t bytes = static_cast<size_t>(p.n * g.ldw * 8);
             offP0[s] = take(bytes);
             offP1[s] = take(bytes);
+            if (g.engine == 2) {  // R^T and the word indexes of R and R^T (entries sized for the dense worst case)
+                offPT[s] = take(bytes);
+                for (int m = 0; m < 2; ++m) {
+                    offPtr[m][s] = take(static_cast<size_t>((p.n + 2) * 8));
+                    offIdx[m][s] = take(static_cast<size_t>(p.n * g.ldw * 4));
+                    offVal[m][s] = take(bytes);
+                }
+            }
         }
     }
     void* base = nullptr;
@@ -602,6 +646,31 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
             g.P[1] = reinterpret_cast<uint64_t*>(b8 + offP1[s]);
         }
     }
+    // frontier jobs (engine 2): every row of the closure as one query, all jobs in one launch
+    std::vector<FrontierJob> jobs;
+    int64_t fr_total = 0, fr_max_n = 0, fr_max_ldw = 0;
+    for (int s = 0; s < np; ++s) {
+        const GroupProblem& g = hp[s];
+        if (g.n == 0 || g.engine != 2) continue;
+        FrontierJob j{};
+        j.P = g.P[0];
+        j.PT = reinterpret_cast<uint64_t*>(b8 + offPT[s]);
+        j.wptr = reinterpret_cast<int64_t*>(b8 + offPtr[0][s]);
+        j.widx = reinterpret_cast<int32_t*>(b8 + offIdx[0][s]);
+        j.wval = reinterpret_cast<uint64_t*>(b8 + offVal[0][s]);
+        j.wptrT = reinterpret_cast<int64_t*>(b8 + offPtr[1][s]);
+        j.widxT = reinterpret_cast<int32_t*>(b8 + offIdx[1][s]);
+        j.wvalT = reinterpret_cast<uint64_t*>(b8 + offVal[1][s]);
+        j.out = g.P[1];
+        j.n = g.n;
+        j.ldw = g.ldw;
+        j.first = fr_total;
+        j.levels = nullptr;  // set below, once the state array exists
+        jobs.push_back(j);
+        fr_total += g.n;
+        fr_max_n = std::max(fr_max_n, g.n);
+        fr_max_ldw = std::max(fr_max_ldw, g.ldw);
+    }
     // device copies
     BCK(cudaMalloc(&c->d_probs, sizeof(GroupProblem) * (np > 0 ? np : 1)), "cudaMalloc(batch problems)");
     BCK(cudaMemcpy(c->d_probs, hp.data(), sizeof(GroupProblem) * np, cudaMemcpyHostToDevice), "copy batch problems");
@@ -621,6 +690,15 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
     hs.pk_total = q; q += 1;
     BCK(cudaMalloc(&c->d_st, sizeof(GroupState)), "cudaMalloc(batch state)");
     BCK(cudaMemcpy(c->d_st, &hs, sizeof(GroupState), cudaMemcpyHostToDevice), "copy batch state");
+    if (!jobs.empty()) {
+        size_t k = 0;
+        for (int s = 0; s < np; ++s)
+            if (hp[s].n > 0 && hp[s].engine == 2) jobs[k++].levels = hs.iters + s;
+        BCK(cudaMalloc(&c->d_jobs, sizeof(FrontierJob) * jobs.size() + sizeof(unsigned long long)),
+            "cudaMalloc(frontier jobs)");
+        BCK(cudaMemcpy(c->d_jobs, jobs.data(), sizeof(FrontierJob) * jobs.size(), cudaMemcpyHostToDevice),
+            "copy frontier jobs");
+    }
     c->h_iters.assign(np, 0);
     c->h_notconv.assign(np, 0);
 
@@ -654,12 +732,16 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
         BST(add_kernel(ctx, c->graph, &n_init, &n_enc, 1, reinterpret_cast<void*>(&batch_plan_kernel), dim3(1),
                        dim3(1024), 0, a));
     }
+    // the closures by frontier expansion: one chain of grouped launches after the planner's start
+    std::vector<cudaGraphNode_t> before_while{n_init};
+    if (!jobs.empty()) BST(add_frontier_chain(ctx, c, static_cast<int>(jobs.size()), fr_max_n, fr_max_ldw, fr_total,
+                                              n_init, &before_while));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    BCK(cudaGraphAddNode(&n_while, c->graph, &n_init, nullptr, 1, &cp), "while node");
+    BCK(cudaGraphAddNode(&n_while, c->graph, before_while.data(), nullptr, before_while.size(), &cp), "while node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     {
         // the two engines touch disjoint problems, so their launches may overlap

@@ -429,6 +429,10 @@ struct Dispatch {
     float* d_small = nullptr;         // loss, scratch
     int* d_indeg = nullptr;
     int64_t indeg_cap = 0;
+    float* d_px = nullptr;            // prediction inputs / outputs / choices, grow-only (no allocation per call)
+    float* d_py = nullptr;
+    int* d_pc = nullptr;
+    int64_t pred_cap = 0;
 };
 
 void dispatch_free(bmlp_ctx* ctx) {
@@ -443,6 +447,9 @@ void dispatch_free(bmlp_ctx* ctx) {
     cudaFree(d->d_feat);
     cudaFree(d->d_small);
     cudaFree(d->d_indeg);
+    cudaFree(d->d_px);
+    cudaFree(d->d_py);
+    cudaFree(d->d_pc);
     delete d;
     ctx->dispatch = nullptr;
 }
@@ -501,12 +508,8 @@ bmlp_status to_device(bmlp_ctx* ctx, const T* h, size_t count, T** out) {
 
 }  // namespace
 
-// Features of a device matrix already in packed rows (n x ldw words).
-bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, float* feat_host,
-                                     cudaStream_t s) {
-    Dispatch* d = nullptr;
-    bmlp_status st = dispatch_state(ctx, &d);
-    if (st != BMLP_OK) return st;
+// The feature kernels of a device matrix in packed rows (n x ldw words): the 16 features land in d->d_feat.
+static bmlp_status launch_features(bmlp_ctx* ctx, Dispatch* d, const uint64_t* P, int64_t n, int64_t ldw, cudaStream_t s) {
     if (d->indeg_cap < n) {
         if (d->d_indeg) cudaFree(d->d_indeg);
         d->d_indeg = nullptr;
@@ -527,8 +530,56 @@ bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n
     feat_final_kernel<<<1, 1, 0, s>>>(d->d_acc, n, ns, d->d_feat);
     DCK(cudaGetLastError(), "feature kernels");
     ctx->stats.launches += 4;
+    return BMLP_OK;
+}
+
+static bmlp_status pred_buffers(bmlp_ctx* ctx, Dispatch* d, int64_t m) {
+    if (d->pred_cap >= m) return BMLP_OK;
+    cudaFree(d->d_px);
+    cudaFree(d->d_py);
+    cudaFree(d->d_pc);
+    d->d_px = d->d_py = nullptr;
+    d->d_pc = nullptr;
+    d->pred_cap = 0;
+    const int64_t cap = m < 256 ? 256 : m;
+    DCK(cudaMalloc(&d->d_px, cap * NF * sizeof(float)), "cudaMalloc(predict)");
+    DCK(cudaMalloc(&d->d_py, cap * NV * sizeof(float)), "cudaMalloc(predict)");
+    DCK(cudaMalloc(&d->d_pc, cap * sizeof(int)), "cudaMalloc(predict)");
+    d->pred_cap = cap;
+    return BMLP_OK;
+}
+
+// Features of a device matrix already in packed rows (n x ldw words).
+bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, float* feat_host,
+                                     cudaStream_t s) {
+    Dispatch* d = nullptr;
+    bmlp_status st = dispatch_state(ctx, &d);
+    if (st != BMLP_OK) return st;
+    st = launch_features(ctx, d, P, n, ldw, s);
+    if (st != BMLP_OK) return st;
     DCK(cudaMemcpyAsync(feat_host, d->d_feat, NF * sizeof(float), cudaMemcpyDeviceToHost, s), "read features");
     DCK(host_sync(ctx, s), "synchronise features");
+    return BMLP_OK;
+}
+
+// Features and prediction on the device in one go (the features never visit the host): *choice receives the
+// predicted fastest bmlp_variant; one host wait.
+bmlp_status dispatch_choose_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, int32_t* choice,
+                                   cudaStream_t s) {
+    Dispatch* d = nullptr;
+    bmlp_status st = dispatch_state(ctx, &d);
+    if (st != BMLP_OK) return st;
+    st = launch_features(ctx, d, P, n, ldw, s);
+    if (st != BMLP_OK) return st;
+    st = pred_buffers(ctx, d, 1);
+    if (st != BMLP_OK) return st;
+    mlp_predict_kernel<<<1, MLP_THREADS, 0, s>>>(d->d_w, d->d_norm, d->d_norm + NF, d->d_feat, 1, d->d_py, d->d_pc);
+    DCK(cudaGetLastError(), "predict kernel");
+    ctx->stats.launches++;
+    int c = 0;
+    DCK(cudaMemcpyAsync(&c, d->d_pc, sizeof(int), cudaMemcpyDeviceToHost, s), "read choice");
+    DCK(host_sync(ctx, s), "synchronise choice");
+    *choice = c + 1;  // bmlp_variant numbering
     return BMLP_OK;
 }
 
@@ -544,11 +595,11 @@ bmlp_status dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float
     bmlp_status st = dispatch_state(ctx, &d);
     if (st != BMLP_OK) return st;
     if (m <= 0) return BMLP_OK;
-    float *dX = nullptr, *dY = nullptr;
-    int* dC = nullptr;
-    DCK(cudaMalloc(&dX, m * NF * sizeof(float)), "cudaMalloc(predict)");
-    DCK(cudaMalloc(&dY, m * NV * sizeof(float)), "cudaMalloc(predict)");
-    DCK(cudaMalloc(&dC, m * sizeof(int)), "cudaMalloc(predict)");
+    st = pred_buffers(ctx, d, m);
+    if (st != BMLP_OK) return st;
+    float* dX = d->d_px;
+    float* dY = d->d_py;
+    int* dC = d->d_pc;
     DCK(cudaMemcpyAsync(dX, feats, m * NF * sizeof(float), cudaMemcpyHostToDevice, s), "copy features");
     const int blocks = static_cast<int>((m + MLP_THREADS - 1) / MLP_THREADS);
     mlp_predict_kernel<<<blocks, MLP_THREADS, 0, s>>>(d->d_w, d->d_norm, d->d_norm + NF, dX, static_cast<int>(m), dY, dC);
@@ -558,9 +609,6 @@ bmlp_status dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float
     DCK(cudaMemcpyAsync(y.data(), dY, m * NV * sizeof(float), cudaMemcpyDeviceToHost, s), "read predictions");
     DCK(cudaMemcpyAsync(c.data(), dC, m * sizeof(int), cudaMemcpyDeviceToHost, s), "read choices");
     DCK(host_sync(ctx, s), "synchronise predict");
-    cudaFree(dX);
-    cudaFree(dY);
-    cudaFree(dC);
     if (pred) memcpy(pred, y.data(), y.size() * sizeof(float));
     if (choice)
         for (int64_t i = 0; i < m; ++i) choice[i] = c[i] + 1;  // bmlp_variant numbering

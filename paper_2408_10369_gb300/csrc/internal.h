@@ -173,6 +173,9 @@ void batch_cache_free(bmlp_ctx* ctx);
 // ---- learned dispatcher (dispatch.cu)
 bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, float* feat_host,
                                      cudaStream_t s);
+// features and prediction on the device, one host wait: *choice = the predicted fastest bmlp_variant
+bmlp_status dispatch_choose_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, int32_t* choice,
+                                   cudaStream_t s);
 bool dispatch_trained(const bmlp_ctx* ctx);
 bmlp_status dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float* pred, int32_t* choice,
                              cudaStream_t s);
@@ -300,5 +303,24 @@ cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, i
 // out = in^T on n x n packed rows of ldw words (out cleared first)
 cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s);
 int smp_packed_max_words();
+// One closure by frontier expansion inside a grouped batch (device copy): every row of R1+ as one query row.
+struct FrontierJob {
+    const uint64_t* P;     // R as packed rows (n x ldw words, padding bits and words zero)
+    uint64_t* PT;          // R^T, written by the launch
+    int64_t* wptr;         // word index of R ((n + 2) offsets; entries sized for the dense worst case)
+    int32_t* widx;
+    uint64_t* wval;
+    int64_t* wptrT;        // word index of R^T
+    int32_t* widxT;
+    uint64_t* wvalT;
+    uint64_t* out;         // the closure rows (n x ldw words)
+    int64_t n, ldw;        // ldw even
+    int64_t first;         // first row of this job in the launch's row numbering (jobs in increasing order)
+    int* levels;           // receives the deepest level + 1 (atomicMax; cleared by the caller)
+};
+// Transposes, word indexes and the frontier expansion of every row of every job (device array `jobs`,
+// `total` rows in all; max_n / max_ldw over the jobs; *counter is cleared by the launch).
+cudaError_t launch_frontier_group(const FrontierJob* jobs, int njobs, int64_t max_n, int64_t max_ldw, int64_t total,
+                                  unsigned long long* counter, int sms, cudaStream_t s);
 
 }  // namespace bmlp

@@ -107,10 +107,10 @@ __global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __r
 }
 
 // ---- word-CSR of packed rows
-__global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, int64_t* __restrict__ wptr) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+// Rows warp_id, warp_id + nwarps, ... of P: their counts of nonzero words into wptr[i + 1].
+__device__ __forceinline__ void wcsr_count_rows(const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
+                                                int64_t* __restrict__ wptr, int64_t warp_id, int64_t nwarps,
+                                                int lane) {
     for (int64_t i = warp_id; i < n; i += nwarps) {
         int64_t c = 0;
         for (int64_t wb = 0; wb < ldw; wb += 32) {
@@ -122,9 +122,15 @@ __global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int
     }
 }
 
+__global__ void wcsr_count_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, int64_t* __restrict__ wptr) {
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    wcsr_count_rows(P, n, ldw, wptr, warp_id, nwarps, threadIdx.x & 31);
+}
+
 // In-place inclusive scan of wptr[1..n] by one block of 1024 threads, in tiles of 4,096 counts (4 consecutive
 // counts per thread, so a warp reads 1 KB contiguously); wptr[n + 1] = the largest count.
-__global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) {
+__device__ __forceinline__ void scan_block(int64_t* __restrict__ wptr, int64_t n) {
     __shared__ int64_t warp_tot[32];
     __shared__ int64_t carry;
     __shared__ unsigned long long top;
@@ -177,11 +183,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, 
     if (t == 0) wptr[n + 1] = static_cast<int64_t>(top);
 }
 
-__global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, const int64_t* __restrict__ wptr,
-                                 int32_t* __restrict__ widx, uint64_t* __restrict__ wval) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+__global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) { scan_block(wptr, n); }
+
+__device__ __forceinline__ void wcsr_fill_rows(const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
+                                               const int64_t* __restrict__ wptr, int32_t* __restrict__ widx,
+                                               uint64_t* __restrict__ wval, int64_t warp_id, int64_t nwarps, int lane) {
     for (int64_t i = warp_id; i < n; i += nwarps) {
         int64_t o = wptr[i];
         for (int64_t wb = 0; wb < ldw; wb += 32) {
@@ -197,12 +203,17 @@ __global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int6
     }
 }
 
+__global__ void wcsr_fill_kernel(const uint64_t* __restrict__ P, int64_t n, int64_t ldw, const int64_t* __restrict__ wptr,
+                                 int32_t* __restrict__ widx, uint64_t* __restrict__ wval) {
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    wcsr_fill_rows(P, n, ldw, wptr, widx, wval, warp_id, nwarps, threadIdx.x & 31);
+}
+
 // Bit-matrix transpose of n x n packed rows (ldw words each), one 64 x 64
 // tile per 64-thread block: out row c, word bi = bit c of the tile's rows.
-__global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
-                                     int64_t ldw) {
-    __shared__ uint64_t t[64];
-    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+__device__ __forceinline__ void bit_transpose_tile(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                   int64_t n, int64_t ldw, int64_t bi, int64_t bj, uint64_t* t) {
     const int tid = threadIdx.x;
     const int64_t r = bi * 64 + tid;
     t[tid] = r < n ? in[r * ldw + bj] : 0ull;
@@ -212,6 +223,13 @@ __global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* 
     for (int k = 0; k < 64; ++k) o |= ((t[k] >> tid) & 1ull) << k;
     const int64_t c = bj * 64 + tid;
     if (c < n) out[c * ldw + bi] = o;
+    __syncthreads();  // t is reused by the block's next tile
+}
+
+__global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
+                                     int64_t ldw) {
+    __shared__ uint64_t t[64];
+    bit_transpose_tile(in, out, n, ldw, blockIdx.y, blockIdx.x, t);
 }
 
 // Direction of a level, by the words each would touch: a push ORs the nonzero words of every frontier
@@ -379,6 +397,168 @@ __device__ __forceinline__ void push_balanced(uint64_t d, int64_t w, int lane, c
     }
 }
 
+// Algorithm 2 for one query row: the frontier expansion from the source row srcw(0 .. ) (words, bits >= n
+// ignored), visited set and result in V (ldw_out words), D / N / FL / GM the warp's shared-memory arrays
+// (sized for at least ldw words). Returns the levels run (the deepest BFS level + 1). Called by a whole warp.
+template <class SrcWord>
+__device__ __forceinline__ int smp_expand_row(SrcWord srcw, uint64_t* __restrict__ V, int64_t ldw_out, int reflexive,
+                                              const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
+                                              const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
+                                              int max_levels, const Deadline& dl, const int64_t* __restrict__ wptrT,
+                                              const int32_t* __restrict__ widxT, const uint64_t* __restrict__ wvalT,
+                                              uint64_t* D, uint64_t* N, uint16_t* FL, uint8_t* GM, int lane) {
+    const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+    const int64_t wpr = (n + 63) / 64;
+    // words of N form at most 64 groups of 2^gshift words; a push records the groups it wrote
+    int gshift = 0;
+    while ((int64_t(64) << gshift) < wpr) ++gshift;
+    const int ngroups = static_cast<int>((wpr + (int64_t(1) << gshift) - 1) >> gshift);
+    const uint64_t all_groups = ngroups >= 64 ? ~0ull : (1ull << ngroups) - 1ull;
+    const float w_out = wptrT != nullptr ? static_cast<float>(wptr[n]) / static_cast<float>(n) : 0.f;
+    const float w_in = wptrT != nullptr ? static_cast<float>(wptrT[n]) / static_cast<float>(n) : 0.f;
+    // D = sources; FL = their nonzero words (ballot compaction); V = 0
+    int fcount = 0;
+    for (int64_t w0 = 0; w0 < ldw; w0 += 32) {
+        const int64_t w = w0 + lane;
+        uint64_t s = 0;
+        if (w < wpr) {
+            s = srcw(w);
+            const int64_t valid = n - w * 64;
+            if (valid < 64) s &= (1ull << valid) - 1ull;
+        }
+        if (w < ldw) {
+            D[w] = s;
+            N[w] = 0;
+        }
+        if (w < ldw_out) V[w] = 0;
+        const unsigned m = __ballot_sync(FULL, s != 0ull);
+        if (s) FL[fcount + __popc(m & lt)] = static_cast<uint16_t>(w);
+        fcount += __popc(m);
+    }
+    __syncwarp();
+    int lv = 0;
+    bool pull = false;
+    int64_t nu = n;  // unvisited constants
+    while (true) {
+        if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
+        uint64_t gm = all_groups;  // groups of N that may be nonzero after this expansion
+        if (pull) {
+            // pull: unvisited j joins the next frontier iff some word of column j (row j of R^T) meets D;
+            // each lane owns whole words of N (no atomics)
+            for (int64_t w = lane; w < wpr; w += 32) {
+                uint64_t nw = 0;
+                {
+                    uint64_t u = ~V[w];
+                    const int64_t valid = n - w * 64;
+                    if (valid < 64) u &= (1ull << valid) - 1ull;
+                    while (u) {
+                        // two unvisited constants at a time: their column ranges, then the first two
+                        // entries of each, all loads in flight before the first test
+                        int bs[2];
+                        int64_t s0[2], s1[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            bs[q] = -1;
+                            if (u) {
+                                bs[q] = __ffsll(static_cast<long long>(u)) - 1;
+                                u &= u - 1;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int64_t j = w * 64 + (bs[q] < 0 ? 0 : bs[q]);
+                            s0[q] = bs[q] < 0 ? 0 : wptrT[j];
+                            s1[q] = bs[q] < 0 ? 0 : wptrT[j + 1];
+                        }
+                        int xi[2][2];
+                        uint64_t xv[2][2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+#pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                const bool in = s0[q] + r < s1[q];
+                                xi[q][r] = in ? widxT[s0[q] + r] : 0;
+                                xv[q][r] = in ? wvalT[s0[q] + r] : 0ull;
+                            }
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            if (bs[q] < 0) continue;
+                            bool hit = (xv[q][0] & D[xi[q][0]]) != 0ull || (xv[q][1] & D[xi[q][1]]) != 0ull;
+                            for (int64_t e = s0[q] + 2; !hit && e < s1[q]; ++e) hit = (wvalT[e] & D[widxT[e]]) != 0ull;
+                            if (hit) nw |= 1ull << bs[q];
+                        }
+                    }
+                    N[w] = nw;
+                }
+            }
+        } else {
+            // push: OR the nonzero words of every frontier row into N (no return values, so the
+            // atomics are reductions); each lane records the word groups it wrote
+            uint64_t tm = 0;
+            for (int i0 = 0; i0 < fcount; i0 += 32) {
+                const int i = i0 + lane;
+                const int64_t w = i < fcount ? FL[i] : 0;
+                uint64_t d = i < fcount ? D[w] : 0ull;  // FL[i] for i < fcount <= ldw only
+                // at most two constants per word: each lane takes its own; else the bits are dealt out
+                if (__reduce_max_sync(FULL, static_cast<unsigned>(__popcll(d))) <= 2u)
+                    push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
+                else
+                    push_balanced(d, w, lane, wptr, widx, wval, N, gshift, tm);
+            }
+            gm = static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm))) |
+                 (static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm >> 32))) << 32);
+        }
+        __syncwarp();
+        // D := 0 on the old frontier words, then D := N & ~V on the touched groups (V |= D, N := 0);
+        // the words that come out nonzero become the new frontier list FL
+        for (int i = lane; i < fcount; i += 32) D[FL[i]] = 0;
+        __syncwarp();
+        int nf = 0, fnew = 0;
+        // GM[r] = index of the r-th set group of gm; candidates are the words of those groups
+        for (int b = lane; b < 64; b += 32)
+            if ((gm >> b) & 1ull) GM[__popcll(gm & ((1ull << b) - 1ull))] = static_cast<uint8_t>(b);
+        __syncwarp();
+        const int cand = __popcll(gm) << gshift;
+        const int gmask = (1 << gshift) - 1;
+        for (int c0 = 0; c0 < cand; c0 += 32) {
+            const int c = c0 + lane;
+            int w = static_cast<int>(wpr);
+            if (c < cand) w = (static_cast<int>(GM[c >> gshift]) << gshift) + (c & gmask);
+            uint64_t nw = 0;
+            if (w < wpr) {
+                nw = N[w] & ~V[w];
+                N[w] = 0;
+                if (nw) {
+                    V[w] |= nw;
+                    D[w] = nw;
+                }
+            }
+            const unsigned m = __ballot_sync(FULL, nw != 0ull);
+            if (nw) FL[fnew + __popc(m & lt)] = static_cast<uint16_t>(w);
+            fnew += __popc(m);
+            nf += __popcll(nw);
+        }
+        nf = __reduce_add_sync(FULL, nf);
+        fcount = fnew;
+        __syncwarp();
+        nu -= nf;
+        ++lv;
+        if (nf == 0 || lv > max_levels) break;
+        // direction of the next level: the cheaper one by the words it touches (nf > 0 here)
+        pull = wptrT != nullptr &&
+               static_cast<float>(nf) * w_out >
+                   static_cast<float>(nu) * (PULL_OVERHEAD + fminf(w_in, static_cast<float>(n) / static_cast<float>(nf)));
+    }
+    if (reflexive)
+        for (int64_t w = lane; w < wpr; w += 32) {
+            uint64_t s = srcw(w);
+            const int64_t valid = n - w * 64;
+            if (valid < 64) s &= (1ull << valid) - 1ull;
+            V[w] |= s;
+        }
+    return lv;
+}
+
 __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __restrict__ wptr, const int32_t* __restrict__ widx,
                                                          const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
                                                          const uint64_t* __restrict__ src, int64_t ldw_src, int64_t q,
@@ -390,19 +570,10 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
     extern __shared__ uint64_t sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;  // lanes below this one
     uint64_t* D = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw));
     uint64_t* N = D + ldw;
     uint16_t* FL = reinterpret_cast<uint16_t*>(N + ldw);
     uint8_t* GM = reinterpret_cast<uint8_t*>(FL + ldw);
-    const int64_t wpr = (n + 63) / 64;
-    // words of N form at most 64 groups of 2^gshift words; a push records the groups it wrote
-    int gshift = 0;
-    while ((int64_t(64) << gshift) < wpr) ++gshift;
-    const int ngroups = static_cast<int>((wpr + (int64_t(1) << gshift) - 1) >> gshift);
-    const uint64_t all_groups = ngroups >= 64 ? ~0ull : (1ull << ngroups) - 1ull;
-    const float w_out = wptrT != nullptr ? static_cast<float>(wptr[n]) / static_cast<float>(n) : 0.f;
-    const float w_in = wptrT != nullptr ? static_cast<float>(wptrT[n]) / static_cast<float>(n) : 0.f;
     while (true) {
         unsigned long long qi = 0;
         if (lane == 0) qi = atomicAdd(qcounter, 1ull);
@@ -410,147 +581,80 @@ __global__ void __launch_bounds__(256, 4) smp_packed_kernel(const int64_t* __res
         if (qi >= static_cast<unsigned long long>(q)) break;
         const uint64_t* srow = src + static_cast<int64_t>(qi) * ldw_src;
         uint64_t* V = out + static_cast<int64_t>(qi) * ldw_out;
-        // D = sources; FL = their nonzero words (ballot compaction); V = 0
-        int fcount = 0;
-        for (int64_t w0 = 0; w0 < ldw; w0 += 32) {
-            const int64_t w = w0 + lane;
-            uint64_t s = 0;
-            if (w < wpr) {
-                s = srow[w];
-                const int64_t valid = n - w * 64;
-                if (valid < 64) s &= (1ull << valid) - 1ull;
-            }
-            if (w < ldw) {
-                D[w] = s;
-                N[w] = 0;
-            }
-            if (w < ldw_out) V[w] = 0;
-            const unsigned m = __ballot_sync(FULL, s != 0ull);
-            if (s) FL[fcount + __popc(m & lt)] = static_cast<uint16_t>(w);
-            fcount += __popc(m);
-        }
-        __syncwarp();
-        int lv = 0;
-        bool pull = false;
-        int64_t nu = n;  // unvisited constants
-        while (true) {
-            if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
-            uint64_t gm = all_groups;  // groups of N that may be nonzero after this expansion
-            if (pull) {
-                // pull: unvisited j joins the next frontier iff some word of column j (row j of R^T) meets D;
-                // each lane owns whole words of N (no atomics)
-                for (int64_t w = lane; w < wpr; w += 32) {
-                    uint64_t nw = 0;
-                    {
-                        uint64_t u = ~V[w];
-                        const int64_t valid = n - w * 64;
-                        if (valid < 64) u &= (1ull << valid) - 1ull;
-                        while (u) {
-                            // two unvisited constants at a time: their column ranges, then the first two
-                            // entries of each, all loads in flight before the first test
-                            int bs[2];
-                            int64_t s0[2], s1[2];
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                bs[q] = -1;
-                                if (u) {
-                                    bs[q] = __ffsll(static_cast<long long>(u)) - 1;
-                                    u &= u - 1;
-                                }
-                            }
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int64_t j = w * 64 + (bs[q] < 0 ? 0 : bs[q]);
-                                s0[q] = bs[q] < 0 ? 0 : wptrT[j];
-                                s1[q] = bs[q] < 0 ? 0 : wptrT[j + 1];
-                            }
-                            int xi[2][2];
-                            uint64_t xv[2][2];
-#pragma unroll
-                            for (int q = 0; q < 2; ++q)
-#pragma unroll
-                                for (int r = 0; r < 2; ++r) {
-                                    const bool in = s0[q] + r < s1[q];
-                                    xi[q][r] = in ? widxT[s0[q] + r] : 0;
-                                    xv[q][r] = in ? wvalT[s0[q] + r] : 0ull;
-                                }
-#pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                if (bs[q] < 0) continue;
-                                bool hit = (xv[q][0] & D[xi[q][0]]) != 0ull || (xv[q][1] & D[xi[q][1]]) != 0ull;
-                                for (int64_t e = s0[q] + 2; !hit && e < s1[q]; ++e) hit = (wvalT[e] & D[widxT[e]]) != 0ull;
-                                if (hit) nw |= 1ull << bs[q];
-                            }
-                        }
-                        N[w] = nw;
-                    }
-                }
-            } else {
-                // push: OR the nonzero words of every frontier row into N (no return values, so the
-                // atomics are reductions); each lane records the word groups it wrote
-                uint64_t tm = 0;
-                for (int i0 = 0; i0 < fcount; i0 += 32) {
-                    const int i = i0 + lane;
-                    const int64_t w = i < fcount ? FL[i] : 0;
-                    uint64_t d = i < fcount ? D[w] : 0ull;  // FL[i] for i < fcount <= ldw only
-                    // at most two constants per word: each lane takes its own; else the bits are dealt out
-                    if (__reduce_max_sync(FULL, static_cast<unsigned>(__popcll(d))) <= 2u)
-                        push_step<2>(d, w, lane, wptr, widx, wval, N, gshift, tm);
-                    else
-                        push_balanced(d, w, lane, wptr, widx, wval, N, gshift, tm);
-                }
-                gm = static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm))) |
-                     (static_cast<uint64_t>(__reduce_or_sync(FULL, static_cast<unsigned>(tm >> 32))) << 32);
-            }
-            __syncwarp();
-            // D := 0 on the old frontier words, then D := N & ~V on the touched groups (V |= D, N := 0);
-            // the words that come out nonzero become the new frontier list FL
-            for (int i = lane; i < fcount; i += 32) D[FL[i]] = 0;
-            __syncwarp();
-            int nf = 0, fnew = 0;
-            // GM[r] = index of the r-th set group of gm; candidates are the words of those groups
-            for (int b = lane; b < 64; b += 32)
-                if ((gm >> b) & 1ull) GM[__popcll(gm & ((1ull << b) - 1ull))] = static_cast<uint8_t>(b);
-            __syncwarp();
-            const int cand = __popcll(gm) << gshift;
-            const int gmask = (1 << gshift) - 1;
-            for (int c0 = 0; c0 < cand; c0 += 32) {
-                const int c = c0 + lane;
-                int w = static_cast<int>(wpr);
-                if (c < cand) w = (static_cast<int>(GM[c >> gshift]) << gshift) + (c & gmask);
-                uint64_t nw = 0;
-                if (w < wpr) {
-                    nw = N[w] & ~V[w];
-                    N[w] = 0;
-                    if (nw) {
-                        V[w] |= nw;
-                        D[w] = nw;
-                    }
-                }
-                const unsigned m = __ballot_sync(FULL, nw != 0ull);
-                if (nw) FL[fnew + __popc(m & lt)] = static_cast<uint16_t>(w);
-                fnew += __popc(m);
-                nf += __popcll(nw);
-            }
-            nf = __reduce_add_sync(FULL, nf);
-            fcount = fnew;
-            __syncwarp();
-            nu -= nf;
-            ++lv;
-            if (nf == 0 || lv > max_levels) break;
-            // direction of the next level: the cheaper one by the words it touches (nf > 0 here)
-            pull = wptrT != nullptr &&
-                   static_cast<float>(nf) * w_out >
-                       static_cast<float>(nu) * (PULL_OVERHEAD + fminf(w_in, static_cast<float>(n) / static_cast<float>(nf)));
-        }
-        if (reflexive)
-            for (int64_t w = lane; w < wpr; w += 32) {
-                uint64_t s = srow[w];
-                const int64_t valid = n - w * 64;
-                if (valid < 64) s &= (1ull << valid) - 1ull;
-                V[w] |= s;
-            }
+        const int lv = smp_expand_row([srow](int64_t w) { return srow[w]; }, V, ldw_out, reflexive, wptr, widx, wval,
+                                      n, ldw, max_levels, dl, wptrT, widxT, wvalT, D, N, FL, GM, lane);
         if (lane == 0) atomicMax(levels_max, lv);
+        __syncwarp();
+    }
+}
+
+// ---- closures by frontier expansion of many small relations in one launch (grouped batch)
+// Transpose and word index of R and of R^T for every job: blockIdx.y = job; blockIdx.z = 0 builds the
+// transpose, then (separate launches, stage 1-3) the word indexes of both matrices (blockIdx.z = matrix).
+__global__ void __launch_bounds__(64) frontier_transpose_kernel(const FrontierJob* __restrict__ jobs) {
+    __shared__ uint64_t t[64];
+    const FrontierJob& J = jobs[blockIdx.y];
+    const int64_t wpr = (J.n + 63) / 64;
+    for (int64_t tile = blockIdx.x; tile < wpr * wpr; tile += gridDim.x)
+        bit_transpose_tile(J.P, J.PT, J.n, J.ldw, tile / wpr, tile % wpr, t);
+    // padding words of the transpose's rows
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < J.n;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        for (int64_t w = wpr; w < J.ldw; ++w) J.PT[r * J.ldw + w] = 0ull;
+}
+
+__global__ void __launch_bounds__(256) frontier_wcsr_count_kernel(const FrontierJob* __restrict__ jobs) {
+    const FrontierJob& J = jobs[blockIdx.y];
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    if (blockIdx.z == 0) wcsr_count_rows(J.P, J.n, J.ldw, J.wptr, warp_id, nwarps, threadIdx.x & 31);
+    else wcsr_count_rows(J.PT, J.n, J.ldw, J.wptrT, warp_id, nwarps, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(1024) frontier_scan_kernel(const FrontierJob* __restrict__ jobs) {
+    const FrontierJob& J = jobs[blockIdx.y];
+    scan_block(blockIdx.z == 0 ? J.wptr : J.wptrT, J.n);
+}
+
+__global__ void __launch_bounds__(256) frontier_wcsr_fill_kernel(const FrontierJob* __restrict__ jobs) {
+    const FrontierJob& J = jobs[blockIdx.y];
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    if (blockIdx.z == 0) wcsr_fill_rows(J.P, J.n, J.ldw, J.wptr, J.widx, J.wval, warp_id, nwarps, threadIdx.x & 31);
+    else wcsr_fill_rows(J.PT, J.n, J.ldw, J.wptrT, J.widxT, J.wvalT, warp_id, nwarps, threadIdx.x & 31);
+}
+
+// Every row of every job as one query: the rows of all jobs are numbered job by job (job j owns rows
+// jobs[j].first .. jobs[j].first + n - 1), warps take them from *counter; the source of row i is constant i.
+__global__ void __launch_bounds__(256, 4) frontier_group_kernel(const FrontierJob* __restrict__ jobs, int njobs,
+                                                                int64_t total, int64_t ldw_max,
+                                                                unsigned long long* counter) {
+    extern __shared__ uint64_t sm[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint64_t* D = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sm) + wib * smp_warp_bytes(ldw_max));
+    uint64_t* N = D + ldw_max;
+    uint16_t* FL = reinterpret_cast<uint16_t*>(N + ldw_max);
+    uint8_t* GM = reinterpret_cast<uint8_t*>(FL + ldw_max);
+    const Deadline none{0, nullptr, nullptr};
+    while (true) {
+        unsigned long long qi = 0;
+        if (lane == 0) qi = atomicAdd(counter, 1ull);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= static_cast<unsigned long long>(total)) break;
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {  // the last job whose first row is <= qi
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].first <= static_cast<int64_t>(qi)) lo = mid; else hi = mid - 1;
+        }
+        const FrontierJob& J = jobs[lo];
+        const int64_t i = static_cast<int64_t>(qi) - J.first;
+        const int64_t wi = i >> 6;
+        const uint64_t bi = 1ull << (i & 63);
+        const int lv = smp_expand_row([wi, bi](int64_t w) { return w == wi ? bi : 0ull; }, J.out + i * J.ldw, J.ldw, 0,
+                                      J.wptr, J.widx, J.wval, J.n, J.ldw, static_cast<int>(J.n + 1), none, J.wptrT,
+                                      J.widxT, J.wvalT, D, N, FL, GM, lane);
+        if (lane == 0) atomicMax(J.levels, lv);
         __syncwarp();
     }
 }
@@ -871,6 +975,36 @@ cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, i
     if (e != cudaSuccess) return e;
     const int64_t wpr = (n + 63) / 64;
     bit_transpose_kernel<<<dim3(static_cast<unsigned>(wpr), static_cast<unsigned>(wpr)), 64, 0, s>>>(in, out, n, ldw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frontier_group(const FrontierJob* jobs, int njobs, int64_t max_n, int64_t max_ldw, int64_t total,
+                                  unsigned long long* counter, int sms, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    const int64_t per_warp = smp_warp_bytes(max_ldw);
+    if (per_warp > 200 * 1024 || njobs > 65535) return cudaErrorInvalidValue;
+    const unsigned nj = static_cast<unsigned>(njobs);
+    const int64_t wpr = (max_n + 63) / 64;
+    int64_t tb = wpr * wpr;
+    if (tb > 4096) tb = 4096;
+    frontier_transpose_kernel<<<dim3(static_cast<unsigned>(tb < 1 ? 1 : tb), nj), 64, 0, s>>>(jobs);
+    const int rows_grid = warps_grid(max_n, sms) / 8 + 1;  // the jobs of a launch share the GPU
+    frontier_wcsr_count_kernel<<<dim3(static_cast<unsigned>(rows_grid), nj, 2), 256, 0, s>>>(jobs);
+    frontier_scan_kernel<<<dim3(1, nj, 2), 1024, 0, s>>>(jobs);
+    frontier_wcsr_fill_kernel<<<dim3(static_cast<unsigned>(rows_grid), nj, 2), 256, 0, s>>>(jobs);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int warps = 8;
+    while (warps > 1 && warps * per_warp > 32 * 1024) warps >>= 1;
+    const size_t smem = static_cast<size_t>(warps) * per_warp;
+    e = cudaFuncSetAttribute(frontier_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = static_cast<int>((220 * 1024) / (smem + 1024));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (total + warps - 1) / warps;
+    if (blocks > static_cast<int64_t>(sms) * per_sm) blocks = static_cast<int64_t>(sms) * per_sm;
+    if (blocks < 1) blocks = 1;
+    frontier_group_kernel<<<static_cast<int>(blocks), warps * 32, smem, s>>>(jobs, njobs, total, max_ldw, counter);
     return cudaGetLastError();
 }
 

@@ -204,10 +204,11 @@ def live_pipeline(ctx, rows, n_max, return_outputs=False):
     """Time (a) plain single-instance squaring per graph with BMLP_RMS_TC
     (bit-row squarings while R is sparse for n >= 8192, then tensor cores),
     (a') the same with every squaring on the tensor cores (options.tc_only),
-    and (b) the dispatched path: features + prediction for every graph, then
-    the graphs predicted to be fastest with squaring run grouped in one
-    bmlp_batch_run (engine per problem from the prediction), the others one
-    by one with their frontier variant. Every output is compared with (a).
+    (a'') the same on E4M3 operands (options.e4m3_only: the kind::f8f6f4 form
+    of the plain tensor-core path), and (b) the dispatched path: features + prediction for every graph, then
+    the graphs with n <= 4,096 run grouped in one bmlp_batch_run (engine per
+    problem from the prediction: tensor-core or bit-row squaring, or frontier
+    expansion), the others one by one with their predicted variant. Every output is compared with (a).
     With return_outputs, also returns the graphs (corpus dict, device input)
     and the dispatched outputs (packed bit rows on the device)."""
     from . import bmlp
@@ -237,14 +238,28 @@ def live_pipeline(ctx, rows, n_max, return_outputs=False):
     bad_tc_only = sum(0 if torch.equal(a, b) else 1 for a, b in zip(outs_a, outs_b))
     for o in outs_b:
         o.zero_()
+    # (a'') the plain tensor-core path in its 8-bit form: every squaring on the tensor cores on E4M3 operands
+    # (kind::f8f6f4), no bit-row start, no 4-bit operands
+    for (g, P), o in list(zip(graphs, outs_b))[:4]:
+        ctx.rms(P, g["n"], o, fmt=F, variant="rms_tc", tc_only=True, e4m3_only=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (g, P), o in zip(graphs, outs_b):
+        ctx.rms(P, g["n"], o, fmt=F, variant="rms_tc", tc_only=True, e4m3_only=True)
+    torch.cuda.synchronize()
+    t_e4m3 = time.perf_counter() - t0
+    bad_e4m3 = sum(0 if torch.equal(a, b) else 1 for a, b in zip(outs_a, outs_b))
+    for o in outs_b:
+        o.zero_()
 
     def dispatched():
         feats = np.stack([ctx.dispatch_features(P, g["n"], fmt=F) for g, P in graphs])
         _, choice = ctx.dispatch_predict(feats)
         group = []
         for (g, P), o, c in zip(graphs, outs_b, choice):
-            if c in (bmlp.BMLP_RMS_TC, bmlp.BMLP_RMS_PACKED) and g["n"] <= GROUP_MAX_N:
-                # squaring on small graphs: grouped, the prediction picks each problem's engine
+            if c in (bmlp.BMLP_RMS_TC, bmlp.BMLP_RMS_PACKED, bmlp.BMLP_SMP_PACKED) and g["n"] <= GROUP_MAX_N:
+                # small graphs: grouped, the prediction picks each problem's engine (the frontier ones share one
+                # grouped frontier launch)
                 group.append(dict(n=g["n"], R1=P, out=o, fmt=F, variant=int(c)))
             else:
                 ctx.rms(P, g["n"], o, fmt=F, variant=int(c))
@@ -263,6 +278,8 @@ def live_pipeline(ctx, rows, n_max, return_outputs=False):
             "live_speedup": t_plain / t_disp, "live_bit_mismatches": bad,
             "live_tc_only_s": t_tc_only, "live_speedup_vs_tc_only": t_tc_only / t_disp,
             "live_tc_only_bit_mismatches": bad_tc_only,
+            "live_tc_only_e4m3_s": t_e4m3, "live_speedup_vs_tc_only_e4m3": t_e4m3 / t_disp,
+            "live_tc_only_e4m3_bit_mismatches": bad_e4m3,
             "live_choice_hist": {VARIANT_NAMES[v - 1]: int((choice == v).sum()) for v in (1, 2, 3, 4)}}
     if return_outputs:
         del outs_a

@@ -224,3 +224,51 @@ def test_single_problem_device_loop_large(ctx):
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), oracle.closure(n, ip, ix))
     assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
     assert ctx.stats()["host_syncs"] == 1
+
+
+@pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
+def test_batch_frontier_engine(ctx, fmt):
+    """Closures with variant smp_packed in a batch: every row of each is one
+    query of one grouped frontier launch, next to squaring problems and a
+    composition; every output bit and the level counts (deepest BFS level + 1)
+    against the oracle."""
+    items, expect, keep = [], [], []
+    cases = [(1, 0.0, 1, "smp_packed"), (64, 1.5, 2, "smp_packed"), (700, 1.2, 3, "smp_packed"),
+             (1500, 2.5, 4, "rms_tc"), (2100, 0.9, 5, "smp_packed"), (333, 3.0, 6, "rms_packed"),
+             (4000, 1.1, 7, "smp_packed")]
+    for n, d, seed, v in cases:
+        ip, ix = wl.er_graph(n, d, seed)
+        m = wl.dense_u8(n, ip, ix)
+        R = dev(m if fmt == bmlp.BMLP_FMT_U8 else wl.pack_rows(m).view(np.int64))
+        out = torch.zeros_like(R)
+        keep += [R, out]
+        items.append(dict(kind=bmlp.BMLP_PROBLEM_CLOSURE, n=n, R1=R, out=out, fmt=fmt, variant=v))
+        expect.append(("closure", n, ip, ix))
+    n = 900
+    c1, c2 = wl.er_graph(n, 1.0, 8), wl.er_graph(n, 1.3, 9)
+    m1, m2 = wl.dense_u8(n, *c1), wl.dense_u8(n, *c2)
+    if fmt != bmlp.BMLP_FMT_U8:
+        m1, m2 = wl.pack_rows(m1).view(np.int64), wl.pack_rows(m2).view(np.int64)
+    R1, R2 = dev(m1), dev(m2)
+    out = torch.zeros_like(R1)
+    keep += [R1, R2, out]
+    items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=out, fmt=fmt))
+    expect.append(("compose", n, c1, c2))
+    iters = ctx.batch_run(items)
+    torch.cuda.synchronize()
+    check(items, expect)
+    for (n, d, seed, v), ex, k in zip(cases, expect, iters):
+        ip, ix = ex[2], ex[3]
+        if v == "smp_packed":
+            _, depth, _ = oracle.reach_rows(n, ip, ix, np.arange(n, dtype=np.int32), want_rows=False)
+            assert k == int(depth.max()) + 1, (n, k)
+        else:
+            assert k == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+    # the whole batch with the frontier engine, and again from the cached graph
+    for it in items:
+        it["out"].zero_()
+        it.pop("variant", None)
+    ctx.batch_run(items, variant="smp_packed")
+    ctx.batch_run(items, variant="smp_packed")
+    torch.cuda.synchronize()
+    check(items, expect)
