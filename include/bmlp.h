@@ -18,6 +18,15 @@
  *                      row i is bit (j % 64), least significant first, of word
  *                      j / 64 (the bit code b_i of Sec. 3.2). Input bits at
  *                      columns >= n are ignored; output padding bits are 0.
+ *   BMLP_FMT_I8        n x n int8, row-major: read and written as BMLP_FMT_U8
+ *                      (nonzero means 1; outputs 0 or 1).
+ *   BMLP_FMT_E4M3      n x n FP8 E4M3 bytes, row-major, the operand form of the
+ *                      8-bit tensor-core path: 0x00 and 0x80 (the two zeros)
+ *                      mean 0, any other byte means 1; outputs are 0x00 or
+ *                      0x38 (1.0). Inputs are converted in a context buffer
+ *                      and outputs written back from one (two extra passes
+ *                      over n^2 bytes). Not accepted by bmlp_batch_run or
+ *                      bmlp_rms_tc_noalloc (BMLP_ERR_INVALID_ARG).
  *
  * Pointers: every matrix pointer may be device memory or host memory
  * (pageable or pinned); the library detects which with
@@ -58,7 +67,9 @@ typedef enum bmlp_status {
 
 typedef enum bmlp_format {
     BMLP_FMT_U8 = 0,
-    BMLP_FMT_PACKED64 = 1
+    BMLP_FMT_PACKED64 = 1,
+    BMLP_FMT_I8 = 2,
+    BMLP_FMT_E4M3 = 3
 } bmlp_format;
 
 /* Which kernel family evaluates the fixpoint. Every variant returns the same

@@ -30,6 +30,8 @@ BMLP_ERR_BUDGET = 7
 
 BMLP_FMT_U8 = 0
 BMLP_FMT_PACKED64 = 1
+BMLP_FMT_I8 = 2
+BMLP_FMT_E4M3 = 3
 
 BMLP_AUTO = 0
 BMLP_RMS_TC = 1

@@ -97,6 +97,8 @@ constexpr int WS_WVALT = 20;
 constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
 // R + R R and its word index, before a frontier closure of a path-like R.
 constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
+// E4M3 inputs turned into 0 / 1 bytes, and the 0 / 1 result before it becomes E4M3 bytes.
+constexpr int WS_E8_IN0 = 31, WS_E8_IN1 = 32, WS_E8_OUT = 33;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // A squaring is kept while it grows the rows' nonzero words by at most this factor (path-like relations).
@@ -985,7 +987,7 @@ bmlp_status bmlp_get_stats(const bmlp_ctx* ctx, bmlp_stats* out) {
     return BMLP_OK;
 }
 
-bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
                      int32_t* iters_out, cudaStream_t s) {
     NvtxRange nvtx_("bmlp_rms");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
@@ -1154,7 +1156,7 @@ bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void*
     return finish_out(ctx, ov, s);
 }
 
-bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
+static bmlp_status core_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
                         cudaStream_t s) {
     NvtxRange nvtx_("bmlp_insert");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
@@ -1203,7 +1205,7 @@ bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, co
     return BMLP_OK;
 }
 
-bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
+static bmlp_status core_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
                      uint64_t* out_rows, const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
     NvtxRange nvtx_("bmlp_smp");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
@@ -1240,7 +1242,7 @@ bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const
     return finish_out(ctx, ov, s);
 }
 
-bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt, void* out,
+static bmlp_status core_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt, void* out,
                          const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
     NvtxRange nvtx_("bmlp_compose");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
@@ -1339,7 +1341,7 @@ bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t 
 // Algorithm 1 as printed: R* = (I + R1)^(2^k) by squaring until a squaring changes nothing, then one product
 // R* R1 = R1+. With I inside R the squaring step R <- R + R R is R <- R R, so the squaring loop of bmlp_rms run on
 // I + R1 is Algorithm 1's loop (same engines and switches); the last product runs on the tensor cores.
-bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+static bmlp_status core_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
                           int32_t* iters_out, cudaStream_t s) {
     NvtxRange nvtx_("bmlp_rms_alg1");
     if (!ctx) return BMLP_ERR_INVALID_ARG;
@@ -1377,7 +1379,7 @@ bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, 
     o2.reflexive = 0;
     o2.loop = BMLP_LOOP_HOST;
     int32_t squarings = 0;
-    ST(bmlp_rms(ctx, p0, n, BMLP_FMT_PACKED64, q, &o2, &squarings, s));
+    ST(core_rms(ctx, p0, n, BMLP_FMT_PACKED64, q, &o2, &squarings, s));
     ctx->stats.launches += fmt == BMLP_FMT_U8 ? 2 : 1;
     // R1+ = (I + R1+) R1 on the tensor cores
     const int64_t n_pad = round_up(n, TC_PAD);
@@ -1420,7 +1422,7 @@ static bmlp_status packed_operand(bmlp_ctx* ctx, const void* R, int64_t n, int32
     return to_packed(ctx, in, fmt, n, *P, words_of(n), s);
 }
 
-bmlp_status bmlp_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
+static bmlp_status core_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     ST(op_args(ctx, n, fmt));
     if (n == 0) return BMLP_OK;
@@ -1441,7 +1443,7 @@ bmlp_status bmlp_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
     return finish_out(ctx, ov, s);
 }
 
-bmlp_status bmlp_union(bmlp_ctx* ctx, const void* A, const void* B, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
+static bmlp_status core_union(bmlp_ctx* ctx, const void* A, const void* B, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     ST(op_args(ctx, n, fmt));
     if (n == 0) return BMLP_OK;
@@ -1472,7 +1474,7 @@ static bmlp_status type_vector(bmlp_ctx* ctx, const uint64_t* v, int64_t n, int 
     return BMLP_OK;
 }
 
-bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* rows,
+static bmlp_status core_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* rows,
                         const uint64_t* cols, void* out, cudaStream_t s) {
     if (!ctx) return BMLP_ERR_INVALID_ARG;
     ST(op_args(ctx, n, fmt));
@@ -1495,7 +1497,7 @@ bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, co
     return finish_out(ctx, ov, s);
 }
 
-bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
+static bmlp_status core_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
                             int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
                             cudaStream_t s) {
     NvtxRange nvtx_("bmlp_is_foreign");
@@ -1518,7 +1520,7 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
     bmlp_options oc = o;
     oc.reflexive = 0;
     int32_t it0 = 0, it1 = 0;
-    ST(bmlp_rms(ctx, PC, n, BMLP_FMT_PACKED64, PH, &oc, &it0, s));
+    ST(core_rms(ctx, PC, n, BMLP_FMT_PACKED64, PH, &oc, &it0, s));
     bmlp_stats acc = ctx->stats;
     // P4: indirectlyPartOf = adjoins u adjoins^T u hasPlace^T . indirectlyPartOf = (I + (hasPlace^T)+) B
     CK(launch_bit_transpose(PH, PC, n, ldw, s), "transpose launch");  // PC := hasPlace^T
@@ -1526,7 +1528,7 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
     launch_packed_or(PH, ldw, PA, ldw, n, n, s);                     // PH := B = adjoins u adjoins^T
     CK(cudaGetLastError(), "union launch");
     oc.variant = (o.variant == BMLP_RMS_TC || o.variant == BMLP_SMP_TC) ? BMLP_RMS_TC : BMLP_RMS_PACKED;
-    ST(bmlp_compose(ctx, PH, PC, n, BMLP_FMT_PACKED64, PA, &oc, &it1, s));  // PA := indirectlyPartOf
+    ST(core_compose(ctx, PH, PC, n, BMLP_FMT_PACKED64, PA, &oc, &it1, s));  // PA := indirectlyPartOf
     // P5: isForeign = location x location AND NOT indirectlyPartOf
     const uint64_t* loc = nullptr;
     ST(type_vector(ctx, location, n, WS_VEC0, s, &loc));
@@ -1567,6 +1569,16 @@ bmlp_status bmlp_batch_run(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t cou
     // inside the same graph as device-driven single-problem pipelines (squarings on bit rows while R is sparse, then
     // on 4-bit operands on the tensor cores); the rest run together as one grouped batch. One graph launch, one
     // read of the results.
+    // I8 problems are read and written as U8
+    std::vector<bmlp_problem> canon;
+    for (int64_t i = 0; i < count; ++i)
+        if (probs[i].fmt == BMLP_FMT_I8) {
+            canon.assign(probs, probs + count);
+            for (bmlp_problem& q : canon)
+                if (q.fmt == BMLP_FMT_I8) q.fmt = BMLP_FMT_U8;
+            probs = canon.data();
+            break;
+        }
     reset_stats(ctx, o.variant, 0);
     ProductTimer tm{ctx, o.profile != 0, s};
     ST(tm.begin());
@@ -1645,7 +1657,7 @@ bmlp_status bmlp_batch_autotune(bmlp_ctx* ctx, const bmlp_problem* probs, int64_
     return BMLP_OK;
 }
 
-bmlp_status bmlp_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats, cudaStream_t s) {
+static bmlp_status core_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats, cudaStream_t s) {
     if (!ctx || !feats) return BMLP_ERR_INVALID_ARG;
     if (n <= 0 || !R) return set_err(ctx, BMLP_ERR_INVALID_ARG, "features need n > 0 and a matrix");
     if (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
@@ -1709,6 +1721,168 @@ bmlp_status bmlp_dispatch_load(bmlp_ctx* ctx, const char* path) {
     return dispatch_load(ctx, path);
 }
 
+
+// ---- byte formats: I8 is read and written as U8 (nonzero = 1, outputs 0 / 1); E4M3 inputs are turned into 0 / 1
+// bytes (0x00 and 0x80 are zero, any other byte is one) in a context buffer, the U8 path runs, and the 0 / 1
+// result becomes E4M3 bytes (0x00 / 0x38) in the caller's buffer.
+#define FMT_WRAP_CHECK(fmt)                                                                       \
+    do {                                                                                          \
+        if ((fmt) == BMLP_FMT_I8) (fmt) = BMLP_FMT_U8;                                            \
+    } while (0)
+
+static bmlp_status e4m3_in(bmlp_ctx* ctx, const void* p, int64_t n, int slot, cudaStream_t s, const void** out) {
+    if (!p) {
+        *out = nullptr;
+        return BMLP_OK;
+    }
+    const size_t bytes = static_cast<size_t>(n) * static_cast<size_t>(n);
+    void* d = nullptr;
+    ST(ws_get(ctx, slot, bytes, &d));
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyDefault, s), "copy E4M3 input");
+    launch_e4m3_bytes_to_01(static_cast<uint8_t*>(d), static_cast<int64_t>(bytes), s);
+    CK(cudaGetLastError(), "E4M3 input");
+    *out = d;
+    return BMLP_OK;
+}
+
+static bmlp_status e4m3_out_buf(bmlp_ctx* ctx, int64_t n, void** out) {
+    return ws_get(ctx, WS_E8_OUT, static_cast<size_t>(n) * static_cast<size_t>(n), out);
+}
+
+static bmlp_status e4m3_out_done(bmlp_ctx* ctx, const void* tmp, void* out, int64_t n, cudaStream_t s) {
+    const size_t bytes = static_cast<size_t>(n) * static_cast<size_t>(n);
+    launch_01_to_e4m3_bytes(static_cast<uint8_t*>(const_cast<void*>(tmp)), static_cast<int64_t>(bytes), s);
+    CK(cudaGetLastError(), "E4M3 output");
+    CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDefault, s), "copy E4M3 output");
+    if (!is_device_ptr(out)) CK(host_sync(ctx, s), "synchronise E4M3 output");
+    return BMLP_OK;
+}
+
+bmlp_status bmlp_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+                     int32_t* iters_out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R || !out) return core_rms(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, opts, iters_out, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_rms(ctx, r, n, BMLP_FMT_U8, t, opts, iters_out, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, const bmlp_options* opts,
+                          int32_t* iters_out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R || !out) return core_rms_alg1(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, opts, iters_out, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_rms_alg1(ctx, r, n, BMLP_FMT_U8, t, opts, iters_out, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* src_rows, int64_t q,
+                     uint64_t* out_rows, const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R) return core_smp(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, src_rows, q, out_rows, opts, iters_out, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    return core_smp(ctx, r, n, BMLP_FMT_U8, src_rows, q, out_rows, opts, iters_out, s);
+}
+
+bmlp_status bmlp_compose(bmlp_ctx* ctx, const void* R1, const void* R2, int64_t n, int32_t fmt, void* out,
+                         const bmlp_options* opts, int32_t* iters_out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R1 || !R2 || !out) return core_compose(ctx, R1, R2, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, opts, iters_out, s);
+    DeviceGuard g(ctx->device);
+    const void *a = nullptr, *b = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, R1, n, WS_E8_IN0, s, &a));
+    ST(e4m3_in(ctx, R2, n, WS_E8_IN1, s, &b));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_compose(ctx, a, b, n, BMLP_FMT_U8, t, opts, iters_out, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_insert(bmlp_ctx* ctx, void* closure, int64_t n, int32_t fmt, const int32_t* pairs, int64_t m,
+                        cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !closure) return core_insert(ctx, closure, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, pairs, m, s);
+    DeviceGuard g(ctx->device);
+    const void* c = nullptr;
+    ST(e4m3_in(ctx, closure, n, WS_E8_IN0, s, &c));
+    ST(core_insert(ctx, const_cast<void*>(c), n, BMLP_FMT_U8, pairs, m, s));
+    return e4m3_out_done(ctx, c, closure, n, s);
+}
+
+bmlp_status bmlp_transpose(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, void* out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R || !out) return core_transpose(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_transpose(ctx, r, n, BMLP_FMT_U8, t, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_union(bmlp_ctx* ctx, const void* A, const void* B, int64_t n, int32_t fmt, void* out,
+                       cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !A || !B || !out) return core_union(ctx, A, B, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, s);
+    DeviceGuard g(ctx->device);
+    const void *a = nullptr, *b = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, A, n, WS_E8_IN0, s, &a));
+    ST(e4m3_in(ctx, B, n, WS_E8_IN1, s, &b));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_union(ctx, a, b, n, BMLP_FMT_U8, t, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_negate(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, const uint64_t* rows,
+                        const uint64_t* cols, void* out, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R || !out) return core_negate(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, rows, cols, out, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_negate(ctx, r, n, BMLP_FMT_U8, rows, cols, t, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adjoins, const uint64_t* location,
+                            int64_t n, int32_t fmt, void* out, const bmlp_options* opts, int32_t* iters_out,
+                            cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !contains || !adjoins || !out)
+        return core_is_foreign(ctx, contains, adjoins, location, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, out, opts, iters_out, s);
+    DeviceGuard g(ctx->device);
+    const void *c = nullptr, *a = nullptr;
+    void* t = nullptr;
+    ST(e4m3_in(ctx, contains, n, WS_E8_IN0, s, &c));
+    ST(e4m3_in(ctx, adjoins, n, WS_E8_IN1, s, &a));
+    ST(e4m3_out_buf(ctx, n, &t));
+    ST(core_is_foreign(ctx, c, a, location, n, BMLP_FMT_U8, t, opts, iters_out, s));
+    return e4m3_out_done(ctx, t, out, n, s);
+}
+
+bmlp_status bmlp_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats, cudaStream_t s) {
+    FMT_WRAP_CHECK(fmt);
+    if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R) return core_dispatch_features(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, feats, s);
+    DeviceGuard g(ctx->device);
+    const void* r = nullptr;
+    ST(e4m3_in(ctx, R, n, WS_E8_IN0, s, &r));
+    return core_dispatch_features(ctx, r, n, BMLP_FMT_U8, feats, s);
+}
+#undef FMT_WRAP_CHECK
 }  // extern "C"
 
 namespace bmlp {

@@ -470,4 +470,30 @@ void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t 
     block_flags_kernel<<<grid, 256, 0, s>>>(A, ld, flags_ld > 0 ? flags_ld : n_pad / 128, flags);
 }
 
+namespace {
+__global__ void e4m3_to_01_kernel(uint8_t* __restrict__ p, int64_t bytes) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < bytes;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        p[i] = (p[i] & 0x7Fu) != 0 ? 1 : 0;
+}
+__global__ void to_e4m3_bytes_kernel(uint8_t* __restrict__ p, int64_t bytes) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < bytes;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        p[i] = p[i] != 0 ? static_cast<uint8_t>(BMLP_E4M3_ONE) : 0;
+}
+int byte_grid(int64_t bytes) {
+    int64_t g = (bytes + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    return static_cast<int>(g < 1 ? 1 : g);
+}
+}  // namespace
+
+void launch_e4m3_bytes_to_01(uint8_t* p, int64_t bytes, cudaStream_t s) {
+    e4m3_to_01_kernel<<<byte_grid(bytes), 256, 0, s>>>(p, bytes);
+}
+
+void launch_01_to_e4m3_bytes(uint8_t* p, int64_t bytes, cudaStream_t s) {
+    to_e4m3_bytes_kernel<<<byte_grid(bytes), 256, 0, s>>>(p, bytes);
+}
+
 }  // namespace bmlp

@@ -130,7 +130,7 @@ struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
     char err[512] = {0};
-    bmlp::DevBuf ws[32];
+    bmlp::DevBuf ws[40];
     void* batch = nullptr;       // cached grouped-batch graph (batch.cu)
     int tune[32];                // autotuned engine per size bucket (-1 = unknown)
     int* d_ctl = nullptr;        // device control words (see CTL_* below)
@@ -232,6 +232,9 @@ void launch_input_block_flags(const void* in, int32_t fmt, int64_t ldw_in, int64
 // out = rows x cols AND NOT in over n x n packed rows (null vector = all constants)
 void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const uint64_t* rows, const uint64_t* cols,
                           uint64_t* out, int64_t ldw_out, cudaStream_t s);
+// E4M3 bytes -> 0 / 1 in place (0x00 and 0x80 are zero, any other byte one), and 0 / 1 -> E4M3 0x00 / 0x38
+void launch_e4m3_bytes_to_01(uint8_t* p, int64_t bytes, cudaStream_t s);
+void launch_01_to_e4m3_bytes(uint8_t* p, int64_t bytes, cudaStream_t s);
 // set the diagonal of an n x n byte matrix (ld) to E4M3 one
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s);
 // per (M block, K block) nonzero flags of a byte matrix rows_pad x n_pad

@@ -88,6 +88,7 @@ using namespace bmlp;
 extern "C" bmlp_status bmlp_rms_tc_noalloc(const void* R, int64_t n, int32_t fmt, void* out, int32_t reflexive,
                                            int32_t max_iters, int32_t* iters_out, cudaStream_t s) {
     if (iters_out) *iters_out = 0;
+    if (fmt == BMLP_FMT_I8) fmt = BMLP_FMT_U8;  // same bytes, same meaning
     if (n < 0 || (fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64)) return BMLP_ERR_INVALID_ARG;
     if (n == 0) return BMLP_OK;
     if (R == nullptr || out == nullptr) return BMLP_ERR_INVALID_ARG;
