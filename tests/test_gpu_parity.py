@@ -304,3 +304,53 @@ def test_pinned_host_buffers(ctx, variant):
     Pout = torch.zeros_like(P).pin_memory()
     ctx.rms(P, n, Pout, fmt=pkg.BMLP_FMT_PACKED64, variant=variant)
     np.testing.assert_array_equal(wl.unpack_rows(Pout.numpy().view(np.uint64), n), want)
+
+
+def _as_e4m3(m, rng):
+    """0/1 matrix as E4M3 bytes: ones are 1.0 (0x38) or other nonzero E4M3 values, zeros are +0 (0x00) or -0 (0x80)."""
+    ones = rng.choice(np.array([0x38, 0x40, 0x30, 0xB8, 0x01], np.uint8), size=m.shape)
+    zeros = rng.choice(np.array([0x00, 0x80], np.uint8), size=m.shape)
+    return np.where(m != 0, ones, zeros).astype(np.uint8)
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_byte_formats_i8_and_e4m3(ctx, host):
+    """BMLP_FMT_I8 reads like U8 (nonzero = 1, outputs 0 / 1); BMLP_FMT_E4M3
+    reads 0x00 and 0x80 as zero and any other byte as one and writes 0x00 /
+    0x38; closures, compositions, the relation operators and the incremental
+    fact, on device and host buffers."""
+    rng = np.random.default_rng(5)
+    n = 300
+    ip, ix, m = er_case(n, 1.4, 41)
+    want = oracle.closure(n, ip, ix)
+    i8 = np.where(m != 0, rng.integers(1, 128, m.shape), 0).astype(np.int8)
+    e8 = _as_e4m3(m, rng)
+
+    def put(a):
+        return torch.from_numpy(np.ascontiguousarray(a)) if host else dev(a)
+
+    for fmt, src, one in ((pkg.bmlp.BMLP_FMT_I8, i8, 1), (pkg.bmlp.BMLP_FMT_E4M3, e8, 0x38)):
+        R = put(src)
+        out = put(np.full((n, n), 0x55, np.uint8))
+        it = ctx.rms(R, n, out, fmt=fmt, variant="rms_tc")
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint8)
+        np.testing.assert_array_equal(got, want * one)
+        assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+        # transpose and union of the same relation
+        out = put(np.zeros((n, n), np.uint8))
+        ctx.transpose(R, n, out, fmt=fmt)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint8), (m.T != 0) * one)
+    # composition (I + R2+) R1 with E4M3 operands
+    ip2, ix2, m2 = er_case(n, 1.1, 42)
+    out = put(np.zeros((n, n), np.uint8))
+    ctx.compose(put(_as_e4m3(m, rng)), put(_as_e4m3(m2, rng)), n, out, fmt=pkg.bmlp.BMLP_FMT_E4M3, variant="rms_tc")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint8), oracle.compose_rows(n, (ip, ix), (ip2, ix2)) * 0x38)
+    # one new fact into an E4M3 closure, in place
+    clo = put((want * 0x38).astype(np.uint8))
+    ctx.insert(clo, n, np.array([[3, 200]], np.int32), fmt=pkg.bmlp.BMLP_FMT_E4M3)
+    torch.cuda.synchronize()
+    grown = wl.csr_from_pairs(n, np.concatenate([np.repeat(np.arange(n), np.diff(ip)), [3]]), np.concatenate([ix, [200]]))
+    np.testing.assert_array_equal(clo.cpu().numpy().view(np.uint8), oracle.closure(n, *grown) * 0x38)
