@@ -72,6 +72,8 @@ def parse():
                          "1,000 new contains facts added incrementally to hasPlace of that hierarchy; dg_partial: one "
                          "partially grounded query path(c, Y) on an ER graph of n = 5,000 with --degree (default 50)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="oracle sample rows (0 = sized automatically)")
+    ap.add_argument("--heldout", type=int, default=1000,
+                    help="held-out corpus graphs (seeds 9,000 on) for the dispatcher measurement")
     ap.add_argument("--sharded", action="store_true",
                     help="powerlaw_smp / kg_batch: the multi-rank path (cost partition + all-gather) even on one "
                          "rank; under torchrun with N > 1 it is the default")
@@ -320,9 +322,10 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
     to seconds: the E4M3-only closure, the issue-rate probes, the bit-row
     product and the frontier kernels against their rooflines, the selective
     query batch (4,096 rows on the n = 65,536 power-law graph), the grouped
-    knowledge-graph batch (1,545 programs) and the learned dispatcher on 200
-    held-out corpus graphs. With `check`, the CPU (oracle) leg afterwards
-    compares the query rows and every dispatched closure with the oracle."""
+    knowledge-graph batch (1,545 programs) and the learned dispatcher on the
+    held-out corpus graphs (all 1,000 by default). With `check`, the CPU
+    (oracle) leg afterwards compares the query rows and every dispatched
+    closure with the oracle."""
     import numpy as np
     import torch
     import workloads as wl
@@ -427,14 +430,14 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
                       "form": "one graph launch: grouped problems plus device-driven pipelines for n >= 4,096"}
     del items, keep, arr
 
-    # -- learned dispatcher on 200 held-out corpus graphs (seeds 9,000-9,199)
+    # -- learned dispatcher on the 1,000 held-out corpus graphs (seeds 9,000-9,999)
     model = os.path.join(ROOT, "paper_2408_10369_gb300", "dispatch_model.bin")
     disp = None
     if os.path.exists(model):
         ctx.dispatch_load(model)
-        rows = [{"index": i} for i in range(9000, 9200)]
+        rows = [{"index": i} for i in range(9000, 9000 + args.heldout)]
         rep, graphs, outs = dc.live_pipeline(ctx, rows, 32768, return_outputs=True)
-        ex["dispatch_heldout200"] = {k: v for k, v in rep.items()}
+        ex["dispatch_heldout"] = {k: v for k, v in rep.items()}
         disp = (graphs, outs)
     if check:
         ex.update(extras_oracle_check(pl, disp))
@@ -463,7 +466,7 @@ def extras_oracle_check(pl, disp):
             for r0, blk in oracle.closure_bits_chunks(n, g["indptr"], g["indices"], 4096):
                 bad += int((h[r0:r0 + blk.shape[0], :blk.shape[1]] != blk).any(axis=1).sum())
             bits += n * n
-        res["dispatch_heldout200_parity"] = {"result": "bit-exact vs oracle" if bad == 0 else "MISMATCH",
+        res["dispatch_heldout_parity"] = {"result": "bit-exact vs oracle" if bad == 0 else "MISMATCH",
                                              "graphs": len(graphs), "bits_compared": bits, "mismatched_rows": bad,
                                              "check_s": time.perf_counter() - t0}
     return res

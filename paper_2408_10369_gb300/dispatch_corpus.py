@@ -13,6 +13,8 @@ sweep  times the four closure variants on the mixed corpus (graph i has seed
        per graph and resumes by index.
 train  fits the MLP on the GPU (bmlp_dispatch_train) on graphs with index <
        the split (9,000 by default) and saves the model.
+retime times some variants again on every graph of a corpus file (after a
+       kernel changed), keeping the other variants' times, and writes a new file.
 eval   on the held-out graphs: regret of the chosen variant against the best
        one, and the time of the dispatched pipeline (features + prediction +
        chosen variant, closures grouped in one bmlp_batch_run) against plain
@@ -48,7 +50,8 @@ def _torch():
 def load_jsonl(path):
     rows = {}
     if os.path.exists(path):
-        with open(path) as f:
+        import gzip
+        with (gzip.open(path, "rt") if path.endswith(".gz") else open(path)) as f:
             for ln in f:
                 ln = ln.strip()
                 if ln:
@@ -143,6 +146,47 @@ def sweep(args):
                 print("VARIANTS DISAGREE on graph", index, flush=True)
             del P, ref_out
     ctx.close()
+
+
+def retime(args):
+    """Re-time some variants on every graph of an existing corpus file (after a kernel changed): the other
+    variants' times are kept; a re-timed variant runs with a budget of 4x the fastest kept time (2 s at most)
+    and its output is compared bit for bit with that fastest variant's. Writes a new corpus file."""
+    from . import bmlp
+    import paper_2408_10369_gb300 as pkg
+    torch = _torch()
+    import gzip
+    opener = gzip.open if args.data.endswith(".gz") else open
+    with opener(args.data, "rt") as f:
+        rows = [json.loads(ln) for ln in f if ln.strip()]
+    which = [VARIANT_NAMES.index(v) for v in args.variants.split(",")]
+    ctx = pkg.Context(0)
+    warm(ctx, args.n_max)
+    t_start = time.time()
+    bad = 0
+    with open(args.out, "w") as fo:
+        for r in rows:
+            keep = [k for k in range(4) if k not in which and not r["censored"][k]]
+            best_k = min(keep, key=lambda k: r["ms"][k]) if keep else None
+            g, P = graph_on_device(r["index"], args.n_max)
+            n = g["n"]
+            ref = None
+            if best_k is not None:
+                ref = torch.zeros_like(P)
+                ctx.rms(P, n, ref, fmt=bmlp.BMLP_FMT_PACKED64, variant=VARIANT_NAMES[best_k])
+            budget = min(CAP_S, 4.0 * r["ms"][best_k] / 1e3) if best_k is not None else CAP_S
+            for k in which:
+                out = torch.zeros_like(P)
+                t, c, it = time_variant(ctx, P, n, out, VARIANT_NAMES[k], budget)
+                r["ms"][k], r["censored"][k], r["iters"][k] = t, c, it
+                if not c and ref is not None and not torch.equal(out, ref):
+                    r["agree"] = False
+                    bad += 1
+            fo.write(json.dumps(r) + "\n")
+            del P, ref
+    ctx.close()
+    print(json.dumps({"retimed": len(rows), "variants": args.variants, "disagreements": bad,
+                      "seconds": time.time() - t_start}))
 
 
 def arrays(rows):
@@ -289,7 +333,7 @@ def live_pipeline(ctx, rows, n_max, return_outputs=False):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["sweep", "train", "eval"])
+    ap.add_argument("cmd", choices=["sweep", "train", "eval", "retime"])
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--count", type=int, default=10000)
     ap.add_argument("--out", default="corpus.jsonl")
@@ -302,8 +346,9 @@ def main():
     ap.add_argument("--n-max", type=int, default=32768)
     ap.add_argument("--time-limit", type=float, default=0.0)
     ap.add_argument("--live", action="store_true")
+    ap.add_argument("--variants", default="rms_tc", help="retime: comma-separated variants to time again")
     args = ap.parse_args()
-    {"sweep": sweep, "train": train, "eval": evaluate}[args.cmd](args)
+    {"sweep": sweep, "train": train, "eval": evaluate, "retime": retime}[args.cmd](args)
 
 
 if __name__ == "__main__":
