@@ -140,9 +140,12 @@ typedef struct bmlp_stats {
                                   bit rows before the tensor cores took over
                                   (counted in iterations, not in
                                   product_launches)                             */
-    int32_t sliced_closures;   /* BMLP_SMP_PACKED closures whose first squaring
-                                  widened the rows: every row expanded 64
-                                  sources at a time (bit-sliced frontiers)      */
+    int32_t sliced_closures;   /* BMLP_SMP_PACKED closures, and query batches
+                                  of >= 64 rows (n >= 4096), whose relation
+                                  widens the rows fast (R + R R has > 2.8 x
+                                  the words of R): expanded 64 rows at a time
+                                  (bit-sliced frontiers, one thread-block
+                                  cluster per 64 rows for n <= 65,536)          */
     double sparse_ms;          /* their summed device time (options.profile)    */
     double sparse_words;       /* the word ORs they issued                      */
     int32_t host_syncs;        /* times the host waited for the device during
@@ -218,7 +221,9 @@ bmlp_status bmlp_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, 
  * above; several set bits = a union of constants). out_rows has the same
  * layout. A source is in its own output row only if it lies on a cycle.
  * R is n x n in format fmt. *iters_out receives the deepest frontier level.
- * Variants: BMLP_SMP_PACKED, BMLP_SMP_TC, BMLP_AUTO.
+ * Variants: BMLP_SMP_PACKED, BMLP_SMP_TC, BMLP_AUTO. BMLP_SMP_PACKED expands
+ * one query row per warp, or, for batches of >= 64 rows over a relation whose
+ * rows widen fast (n >= 4096), 64 rows at a time with bit-sliced frontiers.
  */
 bmlp_status bmlp_smp(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt,
                      const uint64_t* src_rows, int64_t nq, uint64_t* out_rows,

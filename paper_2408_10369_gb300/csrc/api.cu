@@ -110,6 +110,10 @@ constexpr double kSlicedMinGrowth = 2.8;
 // ... and no column of R has more than this many times the mean nonzero words of a column (a pull rescans a hub's
 // in-list at every level until every active source reaches it).
 constexpr double kSlicedMaxSkew = 16.0;
+// Query batches of at least this many rows take the same test (a batch of 64 rows is one cluster's work) ...
+constexpr int64_t kSlicedMinQueries = 64;
+// ... which first bounds the growth by the word ORs of R R (cheap) and squares R only between the two thresholds.
+constexpr double kSlicedSureGrowth = 16.0;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 
@@ -792,6 +796,45 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
             ctx->stats.frontier_squarings++;
         }
     }
+    if (!square_first && q >= kSlicedMinQueries && n >= kSquareMinN && ldw <= 2048 && smp_sliced_enabled()) {
+        // query rows 64 at a time (bit-sliced) when the rows of R widen fast: the growth of R + R R over R, bounded
+        // first by R's words plus the word ORs of R R; R itself is left as it is (the levels stay those of R)
+        auto* cost = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
+        CK(cudaMemsetAsync(cost, 0, 2 * sizeof(unsigned long long), s), "reset cost");
+        CK(launch_square_cost(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
+                              n, cost, ctx->sm_count, s),
+           "squaring cost launch");
+        int64_t W = 0;
+        CK(cudaMemcpyAsync(&W, static_cast<const int64_t*>(wptr) + n, sizeof(W), cudaMemcpyDeviceToHost, s),
+           "read word count");
+        ST(read_ctl(ctx, s, nullptr));
+        ctx->stats.launches++;
+        unsigned long long ors = 0;
+        memcpy(&ors, ctx->h_ctl + CTL_COST, sizeof(ors));
+        const double bound = static_cast<double>(W + static_cast<int64_t>(ors)) / static_cast<double>(W > 0 ? W : 1);
+        if (W > 0 && bound > kSlicedSureGrowth) {
+            dense_reach = true;
+        } else if (W > 0 && bound > kSlicedMinGrowth) {
+            void *P2 = nullptr, *wptr2 = nullptr, *widx2 = nullptr, *wval2 = nullptr;
+            ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &P2));
+            ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 2) * 8), &wptr2));
+            ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx2));
+            ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval2));
+            CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                                  static_cast<uint64_t*>(wval), static_cast<uint64_t*>(P), n, ldw,
+                                  static_cast<uint64_t*>(P2), ctx->sm_count, s),
+               "squaring launch");
+            CK(launch_wcsr_build(static_cast<uint64_t*>(P2), n, ldw, static_cast<int64_t*>(wptr2),
+                                 static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s),
+               "word index build");
+            ctx->stats.launches += 4;
+            int64_t W2 = 0;
+            CK(cudaMemcpyAsync(&W2, static_cast<const int64_t*>(wptr2) + n, sizeof(W2), cudaMemcpyDeviceToHost, s),
+               "read word count");
+            CK(host_sync(ctx, s), "read word count");
+            dense_reach = static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
+        }
+    }
     // transposed word index for the pull direction (levels whose frontier is large)
     void *PT = nullptr, *wptrT = nullptr, *widxT = nullptr, *wvalT = nullptr;
     ST(ws_get(ctx, WS_PT, static_cast<size_t>(n * ldw * 8), &PT));
@@ -814,7 +857,27 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         CK(host_sync(ctx, s), "read column word counts");
         dense_reach = static_cast<double>(wt[1]) * static_cast<double>(n) <= kSlicedMaxSkew * static_cast<double>(wt[0]);
     }
-    if (dense_reach && smp_sliced_enabled()) {
+    if (dense_reach && smp_sliced_enabled() && !square_first && smp_cluster_fits(n, q, ctx->sm_count)) {
+        // query rows, 64 per thread-block cluster with the frontier in the cluster's shared memory
+        ST(tm.begin());
+        CK(launch_smp_cluster(static_cast<int64_t*>(wptrT), static_cast<int32_t*>(widxT),
+                              static_cast<uint64_t*>(wvalT), n, src, ldw_src, q, out, ldw_out, o.reflexive,
+                              ctx->d_ctl + CTL_LEVELS,
+                              static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF), ctx->sm_count, s,
+                              deadline_of(ctx)),
+           "cluster frontier kernel launch");
+        ST(tm.end());
+        ctx->stats.product_launches++;
+        ctx->stats.launches++;
+        ctx->stats.sliced_closures++;
+        ST(read_ctl(ctx, s, nullptr));
+        ST(tm.collect());
+        *levels = ctx->h_ctl[CTL_LEVELS];
+        const int cap = o.max_iters > 0 ? o.max_iters : static_cast<int>(n + 1);
+        if (*levels > cap) return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "frontier did not empty within %d levels", cap);
+        return BMLP_OK;
+    }
+    if (dense_reach && smp_sliced_enabled() && square_first) {
         // every row of the closure (src = the identity), 64 sources per CTA over the word index of R^T
         void* scratch = nullptr;
         ST(ws_get(ctx, WS_V, static_cast<size_t>(smp_sliced_grid(n, ctx->sm_count) * 3 * n * 8), &scratch));

@@ -297,6 +297,16 @@ int64_t smp_sliced_grid(int64_t n, int sms);
 cudaError_t launch_smp_sliced(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
                               uint64_t* scratch, uint64_t* out, int64_t ldw_out, unsigned long long* bcounter,
                               int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl);
+// The same expansion for query rows, with the frontier of each 64-row batch in the distributed shared memory of a
+// thread-block cluster (one cluster per batch, n <= 65,536): rows 0 .. rows - 1 of out (ldw_out words each) are
+// v_q R+ for the query rows in src (ldw_src words each), OR-ed with v_q when reflexive. *levels = 0 beforehand
+// receives the largest level count. smp_cluster_fits: the shape exists for n and the device can hold one such
+// cluster.
+bool smp_cluster_shape(int64_t n, int64_t batches, int sms, int* ctas, int* log2_chunk);
+bool smp_cluster_fits(int64_t n, int64_t rows, int sms);
+cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
+                               const uint64_t* src, int64_t ldw_src, int64_t rows, uint64_t* out, int64_t ldw_out,
+                               int reflexive, int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl);
 // word ORs of the next squaring step (sum over the set bits k of a row of the nonzero words of row k):
 // cost[0] += their total over all rows, cost[1] = max(cost[1], the largest row's)
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,

@@ -20,8 +20,12 @@
 //                 query has converged).
 //  * square_rows  R + R R through the word index, before the frontier closure
 //                 of a path-like relation (same closure, fewer levels).
+//  * smp_cluster  Algorithm 2 for 64 sources or 64 query rows at once,
+//                 bit-sliced, with the frontier spread over the shared
+//                 memory of a thread-block cluster (read through DSMEM).
 //  * insert_fact  one new fact into a transitive closure (rank-1 update).
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace bmlp {
 namespace {
@@ -868,6 +872,235 @@ __global__ void __launch_bounds__(kSlicedThreads) smp_sliced_kernel(const int64_
     }
 }
 
+// ---- Algorithm 2 for 64 query rows at once (bit-sliced), the frontier in distributed shared memory
+// A cluster of C CTAs (1..8) expands one batch of 64 rows, the query rows s0 .. s0 + 63 of src (a batch of query
+// rows does not fill the GPU with one CTA per 64 rows, as the closures' 64-source batches do; measured, the global
+// -memory kernel above stays faster for closures). CTA r of the cluster owns the constants w in
+// [r chunk, (r + 1) chunk) (chunk a power of two) and keeps in its shared memory their words of D (bit j: w is in
+// the frontier of row j), Dn (the next frontier) and V (bit j: w reached from row j). A level pulls as the kernel
+// above does, Dn[w] = (OR of D[v] over the in-neighbours v of w) AND NOT V[w] for every w that some active row has
+// not reached, but D[v] comes from the shared memory of v's owner instead of L2, and a warp takes 32 consecutive
+// constants at a time (from a per-level counter) and walks their in-lists together, 64 entries per step (coalesced
+// index loads, no lane waiting for the longest list). One cluster barrier per level publishes Dn and each CTA's OR
+// of its new words; every CTA then reads all of them, so the active rows, the level count and the stop flag (CTA
+// 0's deadline check) are the same in every CTA, and all CTAs of a cluster run the same number of barriers.
+constexpr int kClusterThreads = 1024;
+constexpr int kClusterWarps = kClusterThreads / 32;
+constexpr int kClusterMaxLog2Chunk = 13;  // 8,192 constants per CTA: D, Dn and V take 192 KiB
+constexpr int kClusterMinLog2Chunk = 10;  // clusters are widened down to 1,024 constants per CTA
+constexpr int kClusterMaxCtas = 8;        // portable cluster size
+
+struct ClusterArgs {
+    const int64_t* wptrT;  // word index of R^T: the in-neighbours of a constant
+    const int32_t* widxT;
+    const uint64_t* wvalT;
+    const uint64_t* src;  // query rows (ldw_src words each)
+    int64_t ldw_src;
+    int64_t n;
+    int64_t rows;  // query rows
+    uint64_t* out;
+    int64_t ldw_out;
+    int* levels_max;
+    int max_levels;
+    int reflexive;
+    int log2_chunk;
+    Deadline dl;
+};
+
+// 64 x 64 bit transpose across a warp: lane l holds rows l (a0) and l + 32 (a1) and receives columns l (c0) and
+// l + 32 (c1), where bit r of column c is bit c of row r.
+__device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int lane, uint64_t& c0, uint64_t& c1) {
+    c0 = 0ull;
+    c1 = 0ull;
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) {
+        const unsigned lo = __ballot_sync(FULL, ((a0 >> j) & 1ull) != 0ull);
+        const unsigned hi = __ballot_sync(FULL, ((a1 >> j) & 1ull) != 0ull);
+        const uint64_t col = static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+        if (j == lane) c0 = col;
+        if (j == lane + 32) c1 = col;
+    }
+}
+
+__device__ __forceinline__ uint64_t or_reduce_warp(uint64_t x) {
+    const unsigned lo = __reduce_or_sync(FULL, static_cast<unsigned>(x));
+    const unsigned hi = __reduce_or_sync(FULL, static_cast<unsigned>(x >> 32));
+    return static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+}
+
+// The entries of a tile's lists, 64 per step: lane l owns cnt entries from index es on (cnt = 0: none). fn(x, e)
+// gets, for this lane's two entries of the step, the owning lane (-1: past the end) and the entry index; it runs in
+// every lane (shuffles inside it see the whole warp).
+template <typename Fn>
+__device__ __forceinline__ void walk_lists(int es, int cnt, int lane, Fn&& fn) {
+    int incl = cnt;  // entries of lanes 0 .. lane
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int ebase = es - (incl - cnt);  // entry k of the warp is entry ebase(owner) + k of the index
+    for (int k0 = 0; k0 < total; k0 += 64) {
+        int x[2], e[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = k0 + 32 * h + lane;
+            int o = 0;  // owner of entry k: the first lane whose inclusive count exceeds k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(FULL, incl, o + step - 1) <= k) o += step;
+            e[h] = __shfl_sync(FULL, ebase, o < 32 ? o : 31) + k;
+            x[h] = k < total ? o : -1;
+        }
+        fn(x, e);
+    }
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) smp_cluster_kernel(const ClusterArgs a) {
+    extern __shared__ uint64_t cl_sm[];
+    __shared__ uint64_t s_grown[2];                // by level parity: the OR of this CTA's new frontier words
+    __shared__ int s_stop[2];                      // by level parity, CTA 0 only: the time budget is used up
+    __shared__ uint64_t s_warp[kClusterWarps];
+    __shared__ uint64_t s_acc[kClusterWarps][32];  // per warp: the OR of D over each tile constant's entries
+    __shared__ int s_tile[2];                      // by level parity: the next tile of 32 constants
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t ctas = cluster_nctarank();
+    const int lg = a.log2_chunk;
+    const int chunk = 1 << lg;
+    const int n = static_cast<int>(a.n);
+    const int64_t s0 = static_cast<int64_t>(cluster_id_x()) * 64;
+    const int cnt = static_cast<int>(a.rows - s0 < 64 ? a.rows - s0 : 64);
+    const int base = static_cast<int>(rank) * chunk;
+    const int own = n - base <= 0 ? 0 : (n - base < chunk ? n - base : chunk);
+    const int own_words = (own + 63) >> 6;
+    const int64_t wpr = (a.n + 63) >> 6;
+    uint64_t* D = cl_sm;
+    uint64_t* Dn = cl_sm + chunk;
+    uint64_t* V = cl_sm + 2 * chunk;
+    if (tid < 2) s_tile[tid] = 0;
+
+    // level 0 frontier of this CTA's constants: word wd of the batch's 64 query rows, transposed, D[64 wd + k]
+    // bit j = bit k of word wd of row s0 + j
+    for (int wl = warp; wl < own_words; wl += kClusterWarps) {
+        const int64_t wd = (base >> 6) + wl;
+        const int64_t valid = a.n - wd * 64;
+        const uint64_t m = valid < 64 ? (1ull << valid) - 1ull : ~0ull;
+        const uint64_t a0 = lane < cnt ? a.src[(s0 + lane) * a.ldw_src + wd] & m : 0ull;
+        const uint64_t a1 = lane + 32 < cnt ? a.src[(s0 + lane + 32) * a.ldw_src + wd] & m : 0ull;
+        uint64_t c0, c1;
+        warp_transpose64(a0, a1, lane, c0, c1);
+        const int i0 = wl * 64 + lane;
+        if (i0 < own) {
+            D[i0] = c0;
+            V[i0] = 0ull;
+        }
+        if (i0 + 32 < own) {
+            D[i0 + 32] = c1;
+            V[i0 + 32] = 0ull;
+        }
+    }
+    uint64_t act = cnt == 64 ? ~0ull : (1ull << cnt) - 1ull;  // rows whose frontier may be nonempty
+    cluster_sync();  // every CTA's level 0 frontier is in place
+
+    int lv = 0;
+    while (true) {
+        const int p = lv & 1;
+        if (tid == 0) s_tile[p ^ 1] = 0;  // the next level's tile counter (its last use ended before the last barrier)
+        if (rank == 0 && tid == 0) s_stop[p] = (a.dl.budget_ns && a.dl.past()) ? 1 : 0;
+        const uint32_t d_s = smem_u32(D);
+        uint64_t grown = 0ull;
+        uint64_t* acc_s = s_acc[warp];
+        while (true) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_tile[p], 1);
+            t = __shfl_sync(FULL, t, 0);
+            if (t * 32 >= own) break;
+            const int i = t * 32 + lane;
+            const bool in = i < own;
+            const uint64_t vw = in ? V[i] : ~0ull;
+            const uint64_t need = act & ~vw;  // active rows that have not reached w = base + i
+            int es = 0, c = 0;
+            if (need) {
+                es = static_cast<int>(a.wptrT[base + i]);
+                c = static_cast<int>(a.wptrT[base + i + 1]) - es;
+            }
+            acc_s[lane] = 0ull;
+            __syncwarp();
+            walk_lists(es, c, lane, [&](const int (&x)[2], const int (&e)[2]) {
+                uint64_t bits[2];
+                int vb[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    bits[h] = x[h] >= 0 ? a.wvalT[e[h]] : 0ull;
+                    vb[h] = x[h] >= 0 ? a.widxT[e[h]] << 6 : 0;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint64_t r = 0ull;
+                    uint64_t b = bits[h];
+                    while (b) {
+                        const int v = vb[h] + (__ffsll(static_cast<long long>(b)) - 1);
+                        b &= b - 1ull;
+                        const uint32_t owner = static_cast<uint32_t>(v >> lg);
+                        const uint32_t off = static_cast<uint32_t>(v & (chunk - 1));
+                        r |= owner == rank ? D[off] : ld_dsmem_u64(mapa_shared(d_s + off * 8u, owner));
+                    }
+                    if (r) atomicOr(reinterpret_cast<unsigned long long*>(&acc_s[x[h]]), r);
+                }
+            });
+            __syncwarp();
+            const uint64_t nn = acc_s[lane] & need;
+            if (in) {
+                Dn[i] = nn;
+                if (nn) V[i] = vw | nn;
+            }
+            grown |= nn;
+            __syncwarp();  // acc_s is cleared for the next tile
+        }
+        grown = or_reduce_warp(grown);
+        if (lane == 0) s_warp[warp] = grown;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t g = or_reduce_warp(s_warp[lane]);
+            if (lane == 0) s_grown[p] = g;
+        }
+        cluster_sync();  // Dn and s_grown[p] of every CTA are visible cluster-wide
+        act = 0ull;
+        for (uint32_t c = 0; c < ctas; ++c) act |= ld_dsmem_u64(mapa_shared(smem_u32(&s_grown[p]), c));
+        const int stop = ld_dsmem_s32(mapa_shared(smem_u32(&s_stop[p]), 0));
+        ++lv;
+        uint64_t* t = D;
+        D = Dn;
+        Dn = t;
+        if (act == 0ull || lv > a.max_levels || stop) break;
+    }
+    if (rank == 0 && tid == 0) atomicMax(a.levels_max, lv);
+
+    // output words of this CTA's constants: word wd of row s0 + j = bit j of V[64 wd .. 64 wd + 63]
+    for (int wl = warp; wl < own_words; wl += kClusterWarps) {
+        const int64_t wd = (base >> 6) + wl;
+        const int i0 = wl * 64 + lane;
+        const uint64_t v0 = i0 < own ? V[i0] : 0ull;
+        const uint64_t v1 = i0 + 32 < own ? V[i0 + 32] : 0ull;
+        uint64_t m0, m1;
+        warp_transpose64(v0, v1, lane, m0, m1);
+        if (a.reflexive) {
+            const int64_t valid = a.n - wd * 64;
+            const uint64_t m = valid < 64 ? (1ull << valid) - 1ull : ~0ull;
+            if (lane < cnt) m0 |= a.src[(s0 + lane) * a.ldw_src + wd] & m;
+            if (lane + 32 < cnt) m1 |= a.src[(s0 + lane + 32) * a.ldw_src + wd] & m;
+        }
+        if (lane < cnt) a.out[(s0 + lane) * a.ldw_out + wd] = m0;
+        if (lane + 32 < cnt) a.out[(s0 + lane + 32) * a.ldw_out + wd] = m1;
+    }
+    const int64_t pad = a.ldw_out - wpr;  // words of an output row beyond n
+    if (rank == ctas - 1 && pad > 0)
+        for (int64_t x = tid; x < cnt * pad; x += kClusterThreads) a.out[(s0 + x / pad) * a.ldw_out + wpr + x % pad] = 0ull;
+    cluster_sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
 inline int warps_grid(int64_t rows, int sms) {
     int64_t blocks = (rows + 7) / 8;  // 8 warps of 256 threads
     const int64_t cap = static_cast<int64_t>(sms) * 8;
@@ -937,6 +1170,76 @@ cudaError_t launch_smp_sliced(const int64_t* wptrT, const int32_t* widxT, const 
     smp_sliced_kernel<<<static_cast<int>(grid), kSlicedThreads, 0, s>>>(wptrT, widxT, wvalT, n, (n + 63) / 64, scratch, out,
                                                              ldw_out, bcounter, levels, max_levels, dl);
     return cudaGetLastError();
+}
+
+// Cluster shape of smp_cluster_kernel: the fewest CTAs whose shared memory holds the state of n constants (at most
+// 8,192 per CTA), widened (down to 1,024 constants per CTA) while the batches alone leave SMs idle. False when n
+// needs more than 8 CTAs.
+bool smp_cluster_shape(int64_t n, int64_t batches, int sms, int* ctas, int* log2_chunk) {
+    int lg = 6;
+    while ((int64_t(1) << lg) < n && lg < kClusterMaxLog2Chunk) ++lg;
+    int64_t c = (n + (int64_t(1) << lg) - 1) >> lg;
+    if (n < 1 || c > kClusterMaxCtas) return false;
+    while (lg > kClusterMinLog2Chunk && batches * c < sms) {
+        const int64_t c2 = (n + (int64_t(1) << (lg - 1)) - 1) >> (lg - 1);
+        if (c2 > kClusterMaxCtas) break;
+        --lg;
+        c = c2;
+    }
+    *ctas = static_cast<int>(c);
+    *log2_chunk = lg;
+    return true;
+}
+
+namespace {
+cudaLaunchConfig_t cluster_config(int64_t clusters, int ctas, int lg, cudaStream_t s, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(clusters * ctas), 1, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = 3 * (size_t(8) << lg);
+    cfg.stream = s;
+    at->id = cudaLaunchAttributeClusterDimension;
+    at->val.clusterDim.x = static_cast<unsigned>(ctas);
+    at->val.clusterDim.y = 1;
+    at->val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+}  // namespace
+
+bool smp_cluster_fits(int64_t n, int64_t rows, int sms) {
+    int ctas = 0, lg = 0;
+    if (rows < 1 || !smp_cluster_shape(n, (rows + 63) / 64, sms, &ctas, &lg)) return false;
+    cudaLaunchAttribute at;
+    const cudaLaunchConfig_t cfg = cluster_config(1, ctas, lg, nullptr, &at);
+    if (cudaFuncSetAttribute(smp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cfg.dynamicSmemBytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, smp_cluster_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters > 0;
+}
+
+cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
+                               const uint64_t* src, int64_t ldw_src, int64_t rows, uint64_t* out, int64_t ldw_out,
+                               int reflexive, int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl) {
+    const int64_t batches = (rows + 63) / 64;
+    int ctas = 0, lg = 0;
+    if (rows < 1 || !smp_cluster_shape(n, batches, sms, &ctas, &lg)) return cudaErrorInvalidValue;
+    cudaLaunchAttribute at;
+    const cudaLaunchConfig_t cfg = cluster_config(batches, ctas, lg, s, &at);
+    cudaError_t e = cudaFuncSetAttribute(smp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(cfg.dynamicSmemBytes));
+    if (e != cudaSuccess) return e;
+    const ClusterArgs a{wptrT, widxT, wvalT, src, ldw_src, n, rows, out, ldw_out, levels, max_levels, reflexive, lg,
+                        dl};
+    return cudaLaunchKernelEx(&cfg, smp_cluster_kernel, a);
 }
 
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,

@@ -1,12 +1,15 @@
-"""Full frontier closures expanded 64 sources at a time (bit-sliced frontiers).
+"""Frontier expansion 64 rows at a time (bit-sliced frontiers).
 
 BMLP_SMP_PACKED closures with n >= 4096 whose first squaring widens the rows
-fast (not path-like, no hub columns) run Algorithm 2 for 64 source rows per CTA, with bit j of the
-state word of constant w standing for source s0 + j, pulling over the word
-index of R^T. Bits against the oracle, the reported level count (deepest BFS
-level + 1, as for the one-query-per-warp kernel), ragged batches (n not a
-multiple of 64), both formats, the reflexive option, host buffers and the
-time budget.
+fast (not path-like, no hub columns), and query batches of >= 64 rows over
+such relations, run Algorithm 2 for 64 rows at once, with bit j of the state
+word of constant w standing for row s0 + j, pulling over the word index of
+R^T: closures one CTA per 64 sources with the state in global memory, query
+batches (n <= 65,536) one thread-block cluster per 64 rows with the frontier
+in the cluster's shared memory. Bits against the oracle, the reported level
+count (deepest BFS level + 1, as for the one-query-per-warp kernel), the
+cluster shapes, ragged batches (n or q not a multiple of 64), empty query
+rows, both formats, the reflexive option, host buffers and the time budget.
 """
 import numpy as np
 import pytest
@@ -108,3 +111,97 @@ def test_sliced_budget_is_reported(ctx):
     rows = np.arange(0, n, 97, dtype=np.int32)
     want, _, _ = oracle.reach_rows(n, ip, ix, rows)
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64)[rows], n), want)
+
+
+# ------------------------------------------------------------------ larger closures, query batches --
+def sample_rows(n, k=257):
+    return np.unique(np.linspace(0, n - 1, k).astype(np.int32))
+
+
+@pytest.mark.parametrize("n,seed", [(16384, 11), (40000, 12), (65536, 13), (66000, 14)])
+def test_sliced_closure_large(ctx, n, seed):
+    """Closures of 256 to 1,032 batches of 64 sources (several rounds over the CTAs), sampled rows against the
+    oracle."""
+    ip, ix = wl.er_graph(n, 5.0, seed)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros_like(P)
+    ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
+    torch.cuda.synchronize()
+    assert ctx.stats()["sliced_closures"] == 1
+    rows = sample_rows(n)
+    want, _, _ = oracle.reach_rows(n, ip, ix, rows)
+    got = wl.unpack_rows(out.cpu().numpy().view(np.uint64)[rows], n)
+    np.testing.assert_array_equal(got, want)
+    del P, out
+
+
+def query_case(n, q, seed, empty=()):
+    src = wl.query_rows(n, q, 1, 64, seed)
+    src[list(empty)] = 0
+    return src
+
+
+# Cluster shapes (CTA r of a cluster owns a power-of-two chunk of constants; a cluster is widened while the batches
+# leave SMs idle): 4 CTAs of 1,024 constants (n = 4,096, one batch), 5 of 1,024 with a ragged last chunk (n = 5,000),
+# 5 of 2,048 (n = 9,001), 8 of 1,024 (n = 8,000, 10 batches), 1 CTA of 4,096 (n = 4,096, 154 batches), 2 of 8,192
+# (n = 16,384, 80 batches) and 8 of 8,192 (n = 65,536, below).
+@pytest.mark.parametrize("kind,n,p,q,seed,reflexive", [("er", 4096, 6.0, 64, 1, False), ("er", 5000, 5.0, 130, 2, True),
+                                                       ("er", 9001, 4.0, 200, 3, False),
+                                                       ("powerlaw", 5000, 2.1, 100, 4, False),
+                                                       ("powerlaw", 8000, 2.1, 640, 5, True),
+                                                       ("er", 4096, 6.0, 9800, 6, False),
+                                                       ("er", 16384, 4.0, 5120, 7, True)])
+def test_sliced_query_batches(ctx, kind, n, p, q, seed, reflexive):
+    """Query rows of 1-64 sources (some rows empty), 64 rows per cluster: bits, level count and reflexive rows
+    against the oracle; batches of >= 64 rows over a relation that widens its rows fast take the sliced kernel."""
+    ip, ix = graph(kind, n, p, seed)
+    src = query_case(n, q, seed, empty=(0, q // 2, q - 1))
+    want, levels = oracle.smp(n, ip, ix, src)
+    if reflexive:
+        want = want | wl.unpack_rows(src, n)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.full((q, src.shape[1]), -1, dtype=torch.int64, device="cuda")
+    it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed",
+                 reflexive=reflexive)
+    torch.cuda.synchronize()
+    if kind == "er":
+        assert ctx.stats()["sliced_closures"] == 1
+    got = out.cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(wl.unpack_rows(got, n), want)
+    # the padding bits of every row's last word stay zero
+    np.testing.assert_array_equal(got, wl.pack_rows(want))
+    assert it == int(levels.max()) + 1
+
+
+def test_query_batch_powerlaw_full_size(ctx):
+    """The selective-query workload: 4,096 rows of 1-64 sources on the n = 65,536 power-law graph (Zipf 2.1
+    out-degrees capped at 1,000), every bit and the level count against the oracle, 64 rows per 8-CTA cluster."""
+    n, q = 65536, 4096
+    ip, ix = wl.powerlaw_csr(n, 2.1, 1000, 0)
+    src = wl.query_rows(n, q, 1, 64, 0)
+    want, levels = oracle.smp(n, ip, ix, src)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
+    it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
+    torch.cuda.synchronize()
+    assert ctx.stats()["sliced_closures"] == 1
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint64), wl.pack_rows(want))
+    assert it == int(levels.max()) + 1
+    del P, out
+
+
+def test_query_batch_path_like_keeps_the_query_kernel(ctx):
+    """Query rows over a chain with 1 % shortcuts (rows that do not widen): one query per warp, same bits."""
+    n, q = 6000, 96
+    src0 = np.arange(n - 1)
+    a, b = wl.random_pairs(n, 60, 9)
+    ip, ix = wl.csr_from_pairs(n, np.concatenate([src0, a]), np.concatenate([src0 + 1, b]))
+    src = query_case(n, q, 10)
+    want, levels = oracle.smp(n, ip, ix, src)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
+    it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
+    torch.cuda.synchronize()
+    assert ctx.stats()["sliced_closures"] == 0
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
+    assert it == int(levels.max()) + 1
