@@ -415,7 +415,7 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
     del expanded
     st = ctx.stats()
     ex["powerlaw_smp"] = {"queries_per_s": q / ms * 1e3, "ms_per_batch": ms,
-                          "kernel": "smp_cluster_kernel" if st["sliced_closures"] else "smp_packed_kernel",
+                          "kernel": "smp_cluster_kernel" if st["cluster_frontiers"] else "smp_packed_kernel",
                           "kernel_ms": kms, "levels": st["iterations"], "algorithmic_bytes": alg_bytes,
                           "effective_gbs": alg_bytes / kms / 1e6,
                           "note": "bytes a query-at-a-time expansion reads, over the kernel time; the bit-sliced "

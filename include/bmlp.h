@@ -152,7 +152,10 @@ typedef struct bmlp_stats {
                                   the call to read back a flag, a decision or
                                   the results (1 for a batch that ran as one
                                   device-driven graph: the final read)          */
-    int32_t reserved;
+    int32_t cluster_frontiers; /* of sliced_closures, those run one thread-block
+                                  cluster per 64 rows with the frontier in
+                                  the cluster's shared memory (query batches,
+                                  and closures whose columns are skewed)        */
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

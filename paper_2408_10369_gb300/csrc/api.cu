@@ -110,6 +110,11 @@ constexpr double kSlicedMinGrowth = 2.8;
 // ... and no column of R has more than this many times the mean nonzero words of a column (a pull rescans a hub's
 // in-list at every level until every active source reaches it).
 constexpr double kSlicedMaxSkew = 16.0;
+// Closures whose largest column holds more than this many times the mean nonzero words of a column run on the
+// cluster kernel, whose warps walk many constants' in-lists together (measured on the corpus at n = 22,535-32,629:
+// power-law targets, column skew 7.8-15.6, 0.71-0.93 of the global-memory kernel's time; ER and SBM, skew 2.9-5.3,
+// 0.99-1.33 of it).
+constexpr double kClusterClosureSkew = 6.5;
 // Query batches of at least this many rows take the same test (a batch of 64 rows is one cluster's work) ...
 constexpr int64_t kSlicedMinQueries = 64;
 // ... which first bounds the growth by the word ORs of R R (cheap) and squares R only between the two thresholds.
@@ -848,6 +853,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     ctx->stats.launches += 4;
     CK(cudaMemsetAsync(ctx->d_ctl + CTL_LEVELS, 0, 3 * sizeof(int), s), "reset level and query counters");
     ProductTimer tm{ctx, o.profile != 0, s};
+    double skew = 0.0;  // largest column's nonzero words over the mean
     if (dense_reach && smp_sliced_enabled()) {
         // no hubs among the columns: a pull scans a hub's whole in-list at every level until all active sources
         // reach it (power-law targets), which the one-query-per-warp kernel avoids
@@ -855,13 +861,17 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         CK(cudaMemcpyAsync(wt, static_cast<const int64_t*>(wptrT) + n, sizeof(wt), cudaMemcpyDeviceToHost, s),
            "read column word counts");
         CK(host_sync(ctx, s), "read column word counts");
-        dense_reach = static_cast<double>(wt[1]) * static_cast<double>(n) <= kSlicedMaxSkew * static_cast<double>(wt[0]);
+        skew = static_cast<double>(wt[1]) * static_cast<double>(n) / static_cast<double>(wt[0] > 0 ? wt[0] : 1);
+        dense_reach = skew <= kSlicedMaxSkew;
     }
-    if (dense_reach && smp_sliced_enabled() && !square_first && smp_cluster_fits(n, q, ctx->sm_count)) {
-        // query rows, 64 per thread-block cluster with the frontier in the cluster's shared memory
+    if (dense_reach && smp_sliced_enabled() && (!square_first || skew > kClusterClosureSkew) &&
+        smp_cluster_fits(n, q, ctx->sm_count)) {
+        // 64 rows per thread-block cluster with the frontier in the cluster's shared memory: query rows, or the
+        // closure's identity rows
         ST(tm.begin());
         CK(launch_smp_cluster(static_cast<int64_t*>(wptrT), static_cast<int32_t*>(widxT),
-                              static_cast<uint64_t*>(wvalT), n, src, ldw_src, q, out, ldw_out, o.reflexive,
+                              static_cast<uint64_t*>(wvalT), n, src, ldw_src, q, out, ldw_out,
+                              square_first ? 0 : o.reflexive,
                               ctx->d_ctl + CTL_LEVELS,
                               static_cast<int>(n + 1 < 0x7FFFFFFF ? n + 1 : 0x7FFFFFFF), ctx->sm_count, s,
                               deadline_of(ctx)),
@@ -870,6 +880,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         ctx->stats.product_launches++;
         ctx->stats.launches++;
         ctx->stats.sliced_closures++;
+        ctx->stats.cluster_frontiers++;
         ST(read_ctl(ctx, s, nullptr));
         ST(tm.collect());
         *levels = ctx->h_ctl[CTL_LEVELS];

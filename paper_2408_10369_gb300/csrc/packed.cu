@@ -873,9 +873,10 @@ __global__ void __launch_bounds__(kSlicedThreads) smp_sliced_kernel(const int64_
 }
 
 // ---- Algorithm 2 for 64 query rows at once (bit-sliced), the frontier in distributed shared memory
-// A cluster of C CTAs (1..8) expands one batch of 64 rows, the query rows s0 .. s0 + 63 of src (a batch of query
-// rows does not fill the GPU with one CTA per 64 rows, as the closures' 64-source batches do; measured, the global
-// -memory kernel above stays faster for closures). CTA r of the cluster owns the constants w in
+// A cluster of C CTAs (1..8) expands one batch of 64 rows, the query rows s0 .. s0 + 63 of src (query batches,
+// which do not fill the GPU with one CTA per 64 rows as a closure's 64-source batches do, and closures with skewed
+// columns, as the identity rows; the global-memory kernel above measured faster on the rest). CTA r owns the
+// constants w in
 // [r chunk, (r + 1) chunk) (chunk a power of two) and keeps in its shared memory their words of D (bit j: w is in
 // the frontier of row j), Dn (the next frontier) and V (bit j: w reached from row j). A level pulls as the kernel
 // above does, Dn[w] = (OR of D[v] over the in-neighbours v of w) AND NOT V[w] for every w that some active row has

@@ -57,10 +57,34 @@ def test_sliced_closure_matches_oracle(ctx, kind, n, p, seed, sliced):
     st = ctx.stats()
     if sliced is not None:
         assert st["sliced_closures"] == int(sliced)
+    if kind != "powerlaw":
+        assert st["cluster_frontiers"] == 0  # columns without hubs: the global-memory kernel
     got = wl.unpack_rows(out.cpu().numpy().view(np.uint64), n)
     want, depth, _ = oracle.reach_rows(n, ip, ix, np.arange(n, dtype=np.int32))
     np.testing.assert_array_equal(got, want)
     assert lv == int(depth.max()) + 1
+
+
+@pytest.mark.parametrize("n,alpha,seed", [(8192, 2.0, 1), (6000, 2.0, 6), (9000, 2.2, 5)])
+def test_sliced_closure_skewed_columns(ctx, n, alpha, seed):
+    """Power-law closures (preferential-attachment targets: largest column 7-12 times the mean) whose rows widen
+    fast run on the cluster kernel with the identity rows as queries: every bit and the level count."""
+    ip, ix = wl.powerlaw_csr(n, alpha, 1000, seed)
+    P = dev(wl.csr_to_packed(n, ip, ix).view(np.int64))
+    out = torch.zeros_like(P)
+    lv = ctx.rms(P, n, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert st["sliced_closures"] == 1 and st["cluster_frontiers"] == 1
+    want, depth, _ = oracle.reach_rows(n, ip, ix, np.arange(n, dtype=np.int32))
+    np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
+    assert lv == int(depth.max()) + 1
+    R = dev(wl.dense_u8(n, ip, ix))
+    o8 = torch.zeros_like(R)
+    ctx.rms(R, n, o8, fmt=bmlp.BMLP_FMT_U8, variant="smp_packed", reflexive=True)
+    torch.cuda.synchronize()
+    assert ctx.stats()["cluster_frontiers"] == 1
+    np.testing.assert_array_equal(o8.cpu().numpy(), want | np.eye(n, dtype=np.uint8))
 
 
 def test_sliced_u8_reflexive_and_host_buffers(ctx):
@@ -165,7 +189,7 @@ def test_sliced_query_batches(ctx, kind, n, p, q, seed, reflexive):
                  reflexive=reflexive)
     torch.cuda.synchronize()
     if kind == "er":
-        assert ctx.stats()["sliced_closures"] == 1
+        assert ctx.stats()["sliced_closures"] == ctx.stats()["cluster_frontiers"] == 1
     got = out.cpu().numpy().view(np.uint64)
     np.testing.assert_array_equal(wl.unpack_rows(got, n), want)
     # the padding bits of every row's last word stay zero
@@ -184,7 +208,7 @@ def test_query_batch_powerlaw_full_size(ctx):
     out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
     it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
     torch.cuda.synchronize()
-    assert ctx.stats()["sliced_closures"] == 1
+    assert ctx.stats()["cluster_frontiers"] == 1
     np.testing.assert_array_equal(out.cpu().numpy().view(np.uint64), wl.pack_rows(want))
     assert it == int(levels.max()) + 1
     del P, out
@@ -202,6 +226,6 @@ def test_query_batch_path_like_keeps_the_query_kernel(ctx):
     out = torch.zeros((q, src.shape[1]), dtype=torch.int64, device="cuda")
     it = ctx.smp(P, n, dev(src.view(np.int64)), q, out, fmt=bmlp.BMLP_FMT_PACKED64, variant="smp_packed")
     torch.cuda.synchronize()
-    assert ctx.stats()["sliced_closures"] == 0
+    assert ctx.stats()["sliced_closures"] == ctx.stats()["cluster_frontiers"] == 0
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), want)
     assert it == int(levels.max()) + 1
