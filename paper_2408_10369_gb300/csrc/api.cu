@@ -115,10 +115,8 @@ constexpr double kSlicedMaxSkew = 16.0;
 // power-law targets, column skew 7.8-15.6, 0.71-0.93 of the global-memory kernel's time; ER and SBM, skew 2.9-5.3,
 // 0.99-1.33 of it).
 constexpr double kClusterClosureSkew = 6.5;
-// Query batches of at least this many rows take the same test (a batch of 64 rows is one cluster's work) ...
+// Query batches of at least this many rows take the same test (a batch of 64 rows is one cluster's work).
 constexpr int64_t kSlicedMinQueries = 64;
-// ... which first bounds the growth by the word ORs of R R (cheap) and squares R only between the two thresholds.
-constexpr double kSlicedSureGrowth = 16.0;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
 
@@ -750,76 +748,52 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     if (ldw > smp_packed_max_words())
         return set_err(ctx, BMLP_ERR_UNSUPPORTED, "packed frontier path supports n <= %d", smp_packed_max_words() * 64);
     void *P = nullptr, *wptr = nullptr, *widx = nullptr, *wval = nullptr;
-    ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &P));
     ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 2) * 8), &wptr));
     ST(ws_get(ctx, WS_WIDX, static_cast<size_t>(n * ldw * 4), &widx));
     ST(ws_get(ctx, WS_WVAL, static_cast<size_t>(n * ldw * 8), &wval));
-    ST(to_packed(ctx, R, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+    if (!square_first && fmt == BMLP_FMT_PACKED64 && words_of(n) == ldw) {
+        // query rows: R is only read, so packed rows of the working width are used where they are
+        P = const_cast<void*>(R.dev);
+    } else {
+        ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &P));
+        ST(to_packed(ctx, R, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+    }
     CK(launch_wcsr_build(static_cast<uint64_t*>(P), n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
                          static_cast<uint64_t*>(wval), s),
        "word index build");
     ctx->stats.launches += 3;
+    // nonzero words of R (W) and of R + R R (W2, counted from the word index of R without forming R + R R)
+    auto growth = [&](int64_t* W, int64_t* W2) -> bmlp_status {
+        auto* cnt = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset counts");
+        CK(launch_square_growth(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                                static_cast<uint64_t*>(wval), n, ldw, cnt, ctx->sm_count, s),
+           "squaring growth launch");
+        CK(cudaMemcpyAsync(ctx->h_ctl + CTL_HOST_I64, static_cast<const int64_t*>(wptr) + n, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s),
+           "read word count");
+        ST(read_ctl(ctx, s, nullptr));
+        ctx->stats.launches++;
+        unsigned long long w2 = 0;
+        memcpy(&w2, ctx->h_ctl + CTL_COST, sizeof(w2));
+        memcpy(W, ctx->h_ctl + CTL_HOST_I64, sizeof(int64_t));
+        *W2 = static_cast<int64_t>(w2);
+        return BMLP_OK;
+    };
     bool dense_reach = false;
     if (square_first && n >= kSquareMinN && ldw <= 2048) {
         // Long shortest paths make the frontier latency-bound (one level per path step). closure(R + R R) =
         // closure(R) with half the levels, so R is squared while that keeps its rows within ~1.5x the nonzero
         // words (path-like structure); once the words grow faster, the frontier would pay more per level than
-        // it saves in levels, and the last squaring is dropped.
-        void *P2 = nullptr, *wptr2 = nullptr, *widx2 = nullptr, *wval2 = nullptr;
-        ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &P2));
-        ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 2) * 8), &wptr2));
-        ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx2));
-        ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval2));
-        auto words = [&](const void* wp, int64_t* total) -> bmlp_status {
-            CK(cudaMemcpyAsync(total, static_cast<const int64_t*>(wp) + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
-               "read word count");
-            CK(host_sync(ctx, s), "read word count");
-            return BMLP_OK;
-        };
-        int64_t W = 0, W2 = 0;
-        ST(words(wptr, &W));
+        // it saves in levels, and that squaring is not formed.
         for (int k = 0; k < kSquareMaxSteps; ++k) {
-            CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
-                                  static_cast<uint64_t*>(wval), static_cast<uint64_t*>(P), n, ldw,
-                                  static_cast<uint64_t*>(P2), ctx->sm_count, s),
-               "squaring launch");
-            CK(launch_wcsr_build(static_cast<uint64_t*>(P2), n, ldw, static_cast<int64_t*>(wptr2),
-                                 static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s),
-               "word index build");
-            ctx->stats.launches += 4;
-            ST(words(wptr2, &W2));
+            int64_t W = 0, W2 = 0;
+            ST(growth(&W, &W2));
             if (static_cast<double>(W2) > kSquareMaxGrowth * static_cast<double>(W)) {
                 // the first squaring widens the rows fast: closure rows fill up within a few levels
                 dense_reach = k == 0 && static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
                 break;
             }
-            std::swap(P, P2);
-            std::swap(wptr, wptr2);
-            std::swap(widx, widx2);
-            std::swap(wval, wval2);
-            W = W2;
-            ctx->stats.frontier_squarings++;
-        }
-    }
-    if (!square_first && q >= kSlicedMinQueries && n >= kSquareMinN && ldw <= 2048 && smp_sliced_enabled()) {
-        // query rows 64 at a time (bit-sliced) when the rows of R widen fast: the growth of R + R R over R, bounded
-        // first by R's words plus the word ORs of R R; R itself is left as it is (the levels stay those of R)
-        auto* cost = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
-        CK(cudaMemsetAsync(cost, 0, 2 * sizeof(unsigned long long), s), "reset cost");
-        CK(launch_square_cost(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
-                              n, cost, ctx->sm_count, s),
-           "squaring cost launch");
-        int64_t W = 0;
-        CK(cudaMemcpyAsync(&W, static_cast<const int64_t*>(wptr) + n, sizeof(W), cudaMemcpyDeviceToHost, s),
-           "read word count");
-        ST(read_ctl(ctx, s, nullptr));
-        ctx->stats.launches++;
-        unsigned long long ors = 0;
-        memcpy(&ors, ctx->h_ctl + CTL_COST, sizeof(ors));
-        const double bound = static_cast<double>(W + static_cast<int64_t>(ors)) / static_cast<double>(W > 0 ? W : 1);
-        if (W > 0 && bound > kSlicedSureGrowth) {
-            dense_reach = true;
-        } else if (W > 0 && bound > kSlicedMinGrowth) {
             void *P2 = nullptr, *wptr2 = nullptr, *widx2 = nullptr, *wval2 = nullptr;
             ST(ws_get(ctx, WS_SQP, static_cast<size_t>(n * ldw * 8), &P2));
             ST(ws_get(ctx, WS_SQPTR, static_cast<size_t>((n + 2) * 8), &wptr2));
@@ -833,12 +807,19 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                                  static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s),
                "word index build");
             ctx->stats.launches += 4;
-            int64_t W2 = 0;
-            CK(cudaMemcpyAsync(&W2, static_cast<const int64_t*>(wptr2) + n, sizeof(W2), cudaMemcpyDeviceToHost, s),
-               "read word count");
-            CK(host_sync(ctx, s), "read word count");
-            dense_reach = static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
+            std::swap(P, P2);
+            std::swap(wptr, wptr2);
+            std::swap(widx, widx2);
+            std::swap(wval, wval2);
+            ctx->stats.frontier_squarings++;
         }
+    }
+    if (!square_first && q >= kSlicedMinQueries && n >= kSquareMinN && ldw <= 2048 && smp_sliced_enabled()) {
+        // query rows 64 at a time (bit-sliced) when the rows of R widen fast, the closures' test; R itself is used
+        // as it is (the levels stay those of R)
+        int64_t W = 0, W2 = 0;
+        ST(growth(&W, &W2));
+        dense_reach = W > 0 && static_cast<double>(W2) > kSlicedMinGrowth * static_cast<double>(W);
     }
     // transposed word index for the pull direction (levels whose frontier is large)
     void *PT = nullptr, *wptrT = nullptr, *widxT = nullptr, *wvalT = nullptr;
@@ -1026,7 +1007,7 @@ bmlp_status bmlp_ctx_create(bmlp_ctx** out, int32_t device) {
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ctl, CTL_HOST_WORDS * sizeof(int)) != cudaSuccess ||
         cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess) {
         cudaGetLastError();
         bmlp_ctx_destroy(ctx);

@@ -150,6 +150,9 @@ enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
     CTL_ISSUED = 10, CTL_COST = 12, CTL_WORDS = 16
 };
+// The pinned host mirror has two more ints: CTL_HOST_I64 is a 64-bit slot for values read from elsewhere.
+constexpr int CTL_HOST_I64 = CTL_WORDS;
+constexpr int CTL_HOST_WORDS = CTL_WORDS + 2;
 
 // Workspace slots of the grouped batch and of its device-driven large problems (the others are private to api.cu).
 constexpr int WS_BATCH = 15;
@@ -307,13 +310,17 @@ bool smp_cluster_fits(int64_t n, int64_t rows, int sms);
 cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const uint64_t* wvalT, int64_t n,
                                const uint64_t* src, int64_t ldw_src, int64_t rows, uint64_t* out, int64_t ldw_out,
                                int reflexive, int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl);
+// nonzero words of R + R R (out[0] += their total) and the word ORs of that squaring (out[1] += their total), from
+// the word index of R (ldw words per row, at most 49,152), without forming R + R R
+cudaError_t launch_square_growth(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s);
 // word ORs of the next squaring step (sum over the set bits k of a row of the nonzero words of row k):
 // cost[0] += their total over all rows, cost[1] = max(cost[1], the largest row's)
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
                                unsigned long long* cost, int sms, cudaStream_t s);
 // (R+ + {(u, v)})+ in place on a transitive R+ (n packed rows of ldw words)
 cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, int64_t v, int sms, cudaStream_t s);
-// out = in^T on n x n packed rows of ldw words (out cleared first)
+// out = in^T on n x n packed rows of ldw words (every word of out written, padding words with zeros)
 cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s);
 int smp_packed_max_words();
 // One closure by frontier expansion inside a grouped batch (device copy): every row of R1+ as one query row.

@@ -39,6 +39,21 @@ __device__ __forceinline__ void or4(uint4& a, const uint4& b) {
     a.w |= b.w;
 }
 
+// 64 x 64 bit transpose across a warp: lane l holds rows l (a0) and l + 32 (a1) and receives columns l (c0) and
+// l + 32 (c1), where bit r of column c is bit c of row r.
+__device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int lane, uint64_t& c0, uint64_t& c1) {
+    c0 = 0ull;
+    c1 = 0ull;
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) {
+        const unsigned lo = __ballot_sync(FULL, ((a0 >> j) & 1ull) != 0ull);
+        const unsigned hi = __ballot_sync(FULL, ((a1 >> j) & 1ull) != 0ull);
+        const uint64_t col = static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+        if (j == lane) c0 = col;
+        if (j == lane + 32) c1 = col;
+    }
+}
+
 template <int VEC>
 __global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
                                                              uint64_t* __restrict__ dst, int64_t n, int64_t ldw, int or_a,
@@ -230,10 +245,38 @@ __device__ __forceinline__ void bit_transpose_tile(const uint64_t* __restrict__ 
     __syncthreads();  // t is reused by the block's next tile
 }
 
-__global__ void bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
-                                     int64_t ldw) {
-    __shared__ uint64_t t[64];
-    bit_transpose_tile(in, out, n, ldw, blockIdx.y, blockIdx.x, t);
+// The whole-matrix transpose, a tile of 256 rows (4 groups of 64) x 8 words (512 columns) per block: the tile is
+// read with sector-wide loads into shared memory, transposed 64 x 64 at a time by warp ballots (all-zero blocks
+// skipped), and written as 512 output rows x 4 words (one 32-byte sector each). Every word of out, padding words
+// included, is written.
+constexpr int kTrRows = 256, kTrWords = 8;
+__global__ void __launch_bounds__(256) bit_transpose_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                            int64_t n, int64_t ldw) {
+    __shared__ uint64_t ti[kTrRows][kTrWords + 1];
+    __shared__ uint64_t to[kTrWords * 64][5];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTrRows;   // first input row
+    const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kTrWords;  // first input word
+    for (int k = tid; k < kTrRows * kTrWords; k += 256) {
+        const int r = k >> 3, w = k & 7;
+        const int64_t gr = r0 + r, gw = w0 + w;
+        ti[r][w] = (gr < n && gw < ldw) ? in[gr * ldw + gw] : 0ull;
+    }
+    __syncthreads();
+    for (int b = warp; b < 4 * kTrWords; b += 8) {
+        const int g = b / kTrWords, w = b % kTrWords;
+        const uint64_t a0 = ti[64 * g + lane][w], a1 = ti[64 * g + lane + 32][w];
+        uint64_t c0 = 0ull, c1 = 0ull;
+        if (__any_sync(FULL, (a0 | a1) != 0ull)) warp_transpose64(a0, a1, lane, c0, c1);
+        to[64 * w + lane][g] = c0;  // output row 64 (w0 + w) + lane, word 4 blockIdx.y + g
+        to[64 * w + lane + 32][g] = c1;
+    }
+    __syncthreads();
+    for (int k = tid; k < kTrWords * 64 * 4; k += 256) {
+        const int orow = k >> 2, ow = k & 3;
+        const int64_t gr = w0 * 64 + orow, gw = static_cast<int64_t>(blockIdx.y) * 4 + ow;
+        if (gr < n && gw < ldw) out[gr * ldw + gw] = to[orow][ow];
+    }
 }
 
 // Direction of a level, by the words each would touch: a push ORs the nonzero words of every frontier
@@ -763,6 +806,53 @@ __global__ void __launch_bounds__(256) square_cost_kernel(const int64_t* __restr
     }
 }
 
+// ---- the next squaring step's nonzero words without forming it: per row (one warp), the union of the row's own
+// word indices and those of every row k it names (R + R R), in a shared-memory bitmap of ldw bits.
+// out[0] += the total nonzero words of R + R R, out[1] += the word ORs the squaring would issue.
+__global__ void __launch_bounds__(256) square_growth_kernel(const int64_t* __restrict__ wptr,
+                                                            const int32_t* __restrict__ widx,
+                                                            const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
+                                                            unsigned long long* __restrict__ out) {
+    extern __shared__ uint32_t growth_bm[];
+    const int lane = threadIdx.x & 31;
+    const int bw = static_cast<int>((ldw + 31) / 32);  // bitmap words per warp
+    uint32_t* bm = growth_bm + (threadIdx.x >> 5) * bw;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    unsigned long long words = 0, ors = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        for (int j = lane; j < bw; j += 32) bm[j] = 0u;
+        __syncwarp();
+        const int64_t e1 = wptr[i + 1];
+        for (int64_t e = wptr[i] + lane; e < e1; e += 32) {
+            const int x = widx[e];
+            atomicOr(&bm[x >> 5], 1u << (x & 31));
+            uint64_t d = wval[e];
+            const int64_t base = static_cast<int64_t>(x) << 6;
+            while (d) {
+                const int64_t k = base + (__ffsll(static_cast<long long>(d)) - 1);
+                d &= d - 1ull;
+                const int64_t f1 = wptr[k + 1];
+                for (int64_t f = wptr[k]; f < f1; ++f) {
+                    const int y = widx[f];
+                    atomicOr(&bm[y >> 5], 1u << (y & 31));
+                    ++ors;
+                }
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < bw; j += 32) words += static_cast<unsigned long long>(__popc(bm[j]));
+        __syncwarp();  // the bitmap is cleared for the next row
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        words += __shfl_xor_sync(FULL, words, off);
+        ors += __shfl_xor_sync(FULL, ors, off);
+    }
+    if (lane == 0 && (words | ors) != 0ull) {
+        atomicAdd(out, words);
+        atomicAdd(out + 1, ors);
+    }
+}
+
 // ---- frontier expansion of 64 sources at once (closures whose rows reach most constants)
 // Algorithm 2 for the 64 query rows e_s0 .. e_s0+63 together, bit-sliced: word w of V, D and Dn holds, in bit j,
 // whether constant w is visited by / in the frontier of / in the next frontier of source s0 + j. A level pulls:
@@ -907,21 +997,6 @@ struct ClusterArgs {
     int log2_chunk;
     Deadline dl;
 };
-
-// 64 x 64 bit transpose across a warp: lane l holds rows l (a0) and l + 32 (a1) and receives columns l (c0) and
-// l + 32 (c1), where bit r of column c is bit c of row r.
-__device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int lane, uint64_t& c0, uint64_t& c1) {
-    c0 = 0ull;
-    c1 = 0ull;
-#pragma unroll 8
-    for (int j = 0; j < 64; ++j) {
-        const unsigned lo = __ballot_sync(FULL, ((a0 >> j) & 1ull) != 0ull);
-        const unsigned hi = __ballot_sync(FULL, ((a1 >> j) & 1ull) != 0ull);
-        const uint64_t col = static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
-        if (j == lane) c0 = col;
-        if (j == lane + 32) c1 = col;
-    }
-}
 
 __device__ __forceinline__ uint64_t or_reduce_warp(uint64_t x) {
     const unsigned lo = __reduce_or_sync(FULL, static_cast<unsigned>(x));
@@ -1243,6 +1318,14 @@ cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const
     return cudaLaunchKernelEx(&cfg, smp_cluster_kernel, a);
 }
 
+cudaError_t launch_square_growth(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s) {
+    const size_t smem = static_cast<size_t>(8) * ((ldw + 31) / 32) * 4;
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    square_growth_kernel<<<warps_grid(n, sms), 256, smem, s>>>(wptr, widx, wval, n, ldw, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
                                unsigned long long* cost, int sms, cudaStream_t s) {
     square_cost_kernel<<<warps_grid(n, sms), 256, 0, s>>>(wptr, widx, wval, n, cost);
@@ -1275,10 +1358,9 @@ cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const ui
 }
 
 cudaError_t launch_bit_transpose(const uint64_t* in, uint64_t* out, int64_t n, int64_t ldw, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(n * ldw * 8), s);
-    if (e != cudaSuccess) return e;
-    const int64_t wpr = (n + 63) / 64;
-    bit_transpose_kernel<<<dim3(static_cast<unsigned>(wpr), static_cast<unsigned>(wpr)), 64, 0, s>>>(in, out, n, ldw);
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(static_cast<unsigned>((ldw + kTrWords - 1) / kTrWords), static_cast<unsigned>((ldw + 3) / 4));
+    bit_transpose_kernel<<<grid, 256, 0, s>>>(in, out, n, ldw);
     return cudaGetLastError();
 }
 

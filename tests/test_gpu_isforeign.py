@@ -74,6 +74,20 @@ def test_operators(ctx, n):
     np.testing.assert_array_equal(host_out, a.T)
 
 
+@pytest.mark.parametrize("n,dens", [(257, 0.05), (5000, 0.002), (12001, 0.0002), (3000, 0.6)])
+def test_transpose_packed_tiles(ctx, n, dens):
+    """TRANSP on packed rows across many transpose tiles (256 rows x 512 columns each; ragged n, sparse and dense):
+    every word of the output, padding bits of the last word included, against numpy."""
+    rng = np.random.default_rng(n)
+    m = int(dens * n * n)
+    a = np.zeros((n, n), np.uint8)
+    a[rng.integers(0, n, m), rng.integers(0, n, m)] = 1
+    P = packed_dev(a)
+    out = torch.full_like(P, -1)
+    ctx.transpose(P, n, out, fmt=PACKED)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint64), wl.pack_rows(np.ascontiguousarray(a.T)))
+
+
 @pytest.mark.parametrize("variant", ["auto", "rms_tc", "rms_packed", "smp_packed", "smp_tc"])
 def test_is_foreign_example(ctx, variant):
     consts, facts = read_facts("p3p5_isforeign.txt")
