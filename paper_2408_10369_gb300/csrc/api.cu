@@ -99,6 +99,8 @@ constexpr int WS_PIPE0 = 21, WS_PIPE1 = 22, WS_PIPE2 = 23, WS_VEC0 = 24;
 constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
 // E4M3 inputs turned into 0 / 1 bytes, and the 0 / 1 result before it becomes E4M3 bytes.
 constexpr int WS_E8_IN0 = 31, WS_E8_IN1 = 32, WS_E8_OUT = 33;
+// Block totals of the prefix over many blocks in a word-index build.
+constexpr int WS_SCAN = 34;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // A squaring is kept while it grows the rows' nonzero words by at most this factor (path-like relations).
@@ -632,6 +634,14 @@ struct SparseStart {
     bool done = false;      // the last of them changed nothing: P is the closure
 };
 
+// Device scratch for the prefix of a word-index build (kScanMaxChunks x 2 words).
+int64_t* scan_scratch(bmlp_ctx* ctx) {
+    void* p = nullptr;
+    return ws_get(ctx, WS_SCAN, static_cast<size_t>(kScanMaxChunks) * 2 * sizeof(int64_t), &p) == BMLP_OK
+               ? static_cast<int64_t*>(p)
+               : nullptr;
+}
+
 // Squarings R <- R + R R on word-indexed bit rows (square_rows_kernel) for as long as the next one costs less than a
 // tensor-core product. Each step is the squaring the tensor cores would run, so the fixpoint and the count of
 // products are the same (R_k covers the paths of length 1 .. 2^k whichever engine squared it); the cost of a step is
@@ -656,7 +666,7 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
     int cur = 0;
     for (;;) {
         CK(launch_wcsr_build(P[cur], n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
-                             static_cast<uint64_t*>(wval), s),
+                             static_cast<uint64_t*>(wval), s, scan_scratch(ctx)),
            "word index build");
         CK(cudaMemsetAsync(cost, 0, 2 * sizeof(unsigned long long), s), "reset cost");
         CK(launch_square_cost(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
@@ -759,7 +769,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
         ST(to_packed(ctx, R, fmt, n, static_cast<uint64_t*>(P), ldw, s));
     }
     CK(launch_wcsr_build(static_cast<uint64_t*>(P), n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
-                         static_cast<uint64_t*>(wval), s),
+                         static_cast<uint64_t*>(wval), s, scan_scratch(ctx)),
        "word index build");
     ctx->stats.launches += 3;
     // nonzero words of R (W) and of R + R R (W2, counted from the word index of R without forming R + R R)
@@ -804,7 +814,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
                                   static_cast<uint64_t*>(P2), ctx->sm_count, s),
                "squaring launch");
             CK(launch_wcsr_build(static_cast<uint64_t*>(P2), n, ldw, static_cast<int64_t*>(wptr2),
-                                 static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s),
+                                 static_cast<int32_t*>(widx2), static_cast<uint64_t*>(wval2), s, scan_scratch(ctx)),
                "word index build");
             ctx->stats.launches += 4;
             std::swap(P, P2);
@@ -829,7 +839,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     ST(ws_get(ctx, WS_WVALT, static_cast<size_t>(n * ldw * 8), &wvalT));
     CK(launch_bit_transpose(static_cast<uint64_t*>(P), static_cast<uint64_t*>(PT), n, ldw, s), "bit transpose");
     CK(launch_wcsr_build(static_cast<uint64_t*>(PT), n, ldw, static_cast<int64_t*>(wptrT),
-                         static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT), s),
+                         static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT), s, scan_scratch(ctx)),
        "transposed word index build");
     ctx->stats.launches += 4;
     CK(cudaMemsetAsync(ctx->d_ctl + CTL_LEVELS, 0, 3 * sizeof(int), s), "reset level and query counters");

@@ -284,8 +284,11 @@ cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t
 // word-CSR of packed rows: counts -> (exclusive scan by caller kernel) -> fill
 // (widx / wval must hold n * ldw entries: the dense worst case; wptr holds n + 2 entries, wptr[n + 1] receives
 // the largest row's count)
+// scan_scratch: kScanMaxChunks x 2 int64 of device memory for a prefix over many blocks (n > 4096), or nullptr
+// for one block; the two may not be shared by calls that overlap in time.
+constexpr int kScanMaxChunks = 512;
 cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx,
-                              uint64_t* wval, cudaStream_t s);
+                              uint64_t* wval, cudaStream_t s, int64_t* scan_scratch = nullptr);
 cudaError_t launch_smp_packed(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
                               int64_t ldw, const uint64_t* src, int64_t ldw_src, int64_t q, uint64_t* out,
                               int64_t ldw_out, int* levels, int* qcounter, int reflexive, int sms, cudaStream_t s,

@@ -131,9 +131,18 @@ __device__ __forceinline__ void wcsr_count_rows(const uint64_t* __restrict__ P, 
                                                 int64_t* __restrict__ wptr, int64_t warp_id, int64_t nwarps,
                                                 int lane) {
     for (int64_t i = warp_id; i < n; i += nwarps) {
+        const uint64_t* row = P + i * ldw;
         int64_t c = 0;
-        for (int64_t wb = 0; wb < ldw; wb += 32) {
-            const uint64_t w = (wb + lane < ldw) ? P[i * ldw + wb + lane] : 0ull;
+        int64_t wb = 0;
+        for (; wb + 128 <= ldw; wb += 128) {  // four loads in flight per lane
+            uint64_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = row[wb + 32 * k + lane];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c += __popc(__ballot_sync(FULL, w[k] != 0ull));
+        }
+        for (; wb < ldw; wb += 32) {
+            const uint64_t w = (wb + lane < ldw) ? row[wb + lane] : 0ull;
             c += __popc(__ballot_sync(FULL, w != 0ull));
         }
         if (lane == 0) wptr[i + 1] = c;
@@ -204,16 +213,120 @@ __device__ __forceinline__ void scan_block(int64_t* __restrict__ wptr, int64_t n
 
 __global__ void __launch_bounds__(1024) scan_kernel(int64_t* __restrict__ wptr, int64_t n) { scan_block(wptr, n); }
 
+// The same prefix over many blocks. Pass 1: chunk b, the counts wptr[1 + 4096 b .. 4096 (b + 1)], is scanned in
+// place (inclusive within the chunk); sums[b] = its total and sums[chunks + b] = its largest count.
+constexpr int kScanChunk = 4096;
+__global__ void __launch_bounds__(1024) scan_chunks_kernel(int64_t* __restrict__ wptr, int64_t n,
+                                                           int64_t* __restrict__ sums, int chunks) {
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t warp_max[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int64_t base = 1 + static_cast<int64_t>(blockIdx.x) * kScanChunk + 4 * t;
+    int64_t v[4];
+    int64_t s = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t c = base + k <= n ? wptr[base + k] : 0;
+        mx = c > mx ? c : mx;
+        s += c;
+        v[k] = s;
+    }
+    int64_t ws = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, ws, off);
+        if (lane >= off) ws += y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const int64_t y = __shfl_xor_sync(FULL, mx, off);
+        mx = y > mx ? y : mx;
+    }
+    if (lane == 31) warp_tot[wid] = ws;
+    if (lane == 0) warp_max[wid] = mx;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t x = warp_tot[lane], m = warp_max[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const int64_t y = __shfl_xor_sync(FULL, m, off);
+            m = y > m ? y : m;
+        }
+        warp_tot[lane] = x;
+        if (lane == 31) {
+            sums[blockIdx.x] = x;
+            sums[chunks + blockIdx.x] = m;
+        }
+    }
+    __syncthreads();
+    const int64_t before = (wid > 0 ? warp_tot[wid - 1] : 0) + (ws - s);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k <= n) wptr[base + k] = before + v[k];
+}
+
+// Pass 2: chunk b gains the totals of the chunks before it; block 0 writes wptr[0] = 0 and wptr[n + 1] = the
+// largest count.
+__global__ void __launch_bounds__(1024) scan_add_kernel(int64_t* __restrict__ wptr, int64_t n,
+                                                        const int64_t* __restrict__ sums, int chunks) {
+    __shared__ int64_t offset;
+    const int t = threadIdx.x, lane = t & 31;
+    if (t < 32) {
+        int64_t o = 0, m = 0;
+        for (int b = lane; b < chunks; b += 32) {
+            if (b < static_cast<int>(blockIdx.x)) o += sums[b];
+            m = sums[chunks + b] > m ? sums[chunks + b] : m;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            o += __shfl_xor_sync(FULL, o, off);
+            const int64_t y = __shfl_xor_sync(FULL, m, off);
+            m = y > m ? y : m;
+        }
+        if (t == 0) {
+            offset = o;
+            if (blockIdx.x == 0) {
+                wptr[0] = 0;
+                wptr[n + 1] = m;
+            }
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) return;  // the first chunk's prefix is already final
+    const int64_t base = 1 + static_cast<int64_t>(blockIdx.x) * kScanChunk + 4 * t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k <= n) wptr[base + k] += offset;
+}
+
 __device__ __forceinline__ void wcsr_fill_rows(const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
                                                const int64_t* __restrict__ wptr, int32_t* __restrict__ widx,
                                                uint64_t* __restrict__ wval, int64_t warp_id, int64_t nwarps, int lane) {
+    const unsigned below = (1u << lane) - 1u;
     for (int64_t i = warp_id; i < n; i += nwarps) {
+        const uint64_t* row = P + i * ldw;
         int64_t o = wptr[i];
-        for (int64_t wb = 0; wb < ldw; wb += 32) {
-            const uint64_t w = (wb + lane < ldw) ? P[i * ldw + wb + lane] : 0ull;
+        int64_t wb = 0;
+        for (; wb + 128 <= ldw; wb += 128) {  // four loads in flight per lane
+            uint64_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = row[wb + 32 * k + lane];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned m = __ballot_sync(FULL, w[k] != 0ull);
+                if (w[k]) {
+                    const int64_t at = o + __popc(m & below);
+                    widx[at] = static_cast<int32_t>(wb + 32 * k + lane);
+                    wval[at] = w[k];
+                }
+                o += __popc(m);
+            }
+        }
+        for (; wb < ldw; wb += 32) {
+            const uint64_t w = (wb + lane < ldw) ? row[wb + lane] : 0ull;
             const unsigned m = __ballot_sync(FULL, w != 0ull);
             if (w) {
-                const int64_t at = o + __popc(m & ((1u << lane) - 1u));
+                const int64_t at = o + __popc(m & below);
                 widx[at] = static_cast<int32_t>(wb + lane);
                 wval[at] = w;
             }
@@ -257,10 +370,17 @@ __global__ void __launch_bounds__(256) bit_transpose_kernel(const uint64_t* __re
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTrRows;   // first input row
     const int64_t w0 = static_cast<int64_t>(blockIdx.x) * kTrWords;  // first input word
-    for (int k = tid; k < kTrRows * kTrWords; k += 256) {
-        const int r = k >> 3, w = k & 7;
+    uint64_t v[kTrRows * kTrWords / 256];  // all of a thread's loads in flight at once
+#pragma unroll
+    for (int j = 0; j < kTrRows * kTrWords / 256; ++j) {
+        const int k = tid + 256 * j, r = k >> 3, w = k & 7;
         const int64_t gr = r0 + r, gw = w0 + w;
-        ti[r][w] = (gr < n && gw < ldw) ? in[gr * ldw + gw] : 0ull;
+        v[j] = (gr < n && gw < ldw) ? in[gr * ldw + gw] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kTrRows * kTrWords / 256; ++j) {
+        const int k = tid + 256 * j;
+        ti[k >> 3][k & 7] = v[j];
     }
     __syncthreads();
     for (int b = warp; b < 4 * kTrWords; b += 8) {
@@ -1205,10 +1325,16 @@ cudaError_t launch_insert_fact(uint64_t* P, int64_t n, int64_t ldw, int64_t u, i
 }
 
 cudaError_t launch_wcsr_build(const uint64_t* P, int64_t n, int64_t ldw, int64_t* wptr, int32_t* widx, uint64_t* wval,
-                              cudaStream_t s) {
+                              cudaStream_t s, int64_t* scan_scratch) {
     const int grid = warps_grid(n, 152);
     wcsr_count_kernel<<<grid, 256, 0, s>>>(P, n, ldw, wptr);
-    scan_kernel<<<1, 1024, 0, s>>>(wptr, n);
+    const int64_t chunks = (n + kScanChunk - 1) / kScanChunk;
+    if (scan_scratch != nullptr && chunks > 1 && chunks <= kScanMaxChunks) {
+        scan_chunks_kernel<<<static_cast<unsigned>(chunks), 1024, 0, s>>>(wptr, n, scan_scratch, static_cast<int>(chunks));
+        scan_add_kernel<<<static_cast<unsigned>(chunks), 1024, 0, s>>>(wptr, n, scan_scratch, static_cast<int>(chunks));
+    } else {
+        scan_kernel<<<1, 1024, 0, s>>>(wptr, n);
+    }
     wcsr_fill_kernel<<<grid, 256, 0, s>>>(P, n, ldw, wptr, widx, wval);
     return cudaGetLastError();
 }
