@@ -360,14 +360,12 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
                        "bit_exact_vs_headline": bool(torch.equal(o2, out_main))}
     del o2
 
-    # -- one bit-row product R <- R + R R (product_packed_kernel) on the sparse input: ER mean out-degree 4
+    # -- one bit-row squaring R <- R + R R (rms_packed) on the sparse input (ER mean out-degree 4; through the word
+    # index, square_rows_kernel) and on a dense one (the closure of the n = 8,192 graph; whole rows,
+    # product_packed_kernel)
     pk = {}
-    for nn in (8192, n):
-        if nn == n and FMT == PK:
-            Pn, nnz = R, len(ix)
-        else:
-            pip, pix = wl.er_graph(nn, args.degree, 0)
-            Pn, nnz = torch.from_numpy(wl.csr_to_packed(nn, pip, pix).view(np.int64)).cuda(), len(pix)
+
+    def packed_step(Pn, nn):
         on = torch.zeros_like(Pn)
         tms = []
         for _ in range(4):
@@ -377,17 +375,31 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
                 if e.status != bmlp.BMLP_ERR_NOT_CONVERGED:
                     raise
             tms.append(ctx.stats()["product_ms"])
-        t = statistics.median(tms[1:]) / 1e3
+        kern = "square_rows_kernel" if ctx.stats()["sparse_squarings"] else "product_packed_kernel"
+        return statistics.median(tms[1:]) / 1e3, kern
+
+    dense8k = None
+    for nn in (8192, n):
+        if nn == n and FMT == PK:
+            Pn, nnz = R, len(ix)
+        else:
+            pip, pix = wl.er_graph(nn, args.degree, 0)
+            Pn, nnz = torch.from_numpy(wl.csr_to_packed(nn, pip, pix).view(np.int64)).cuda(), len(pix)
+        t, kern = packed_step(Pn, nn)
         words = (nn + 63) // 64
         hbm_bytes = 2.0 * nn * words * 8          # read R (A operand and old R), write R' (compulsory)
-        gathered = float(nnz) * words * 8         # the B rows named by A's bits
-        ors = float(nnz) * words
-        pk["n%d" % nn] = {"ms": t * 1e3, "nnz": nnz, "compulsory_hbm_bytes": hbm_bytes,
-                          "hbm_gbs": hbm_bytes / t / 1e9, "hbm_frac": hbm_bytes / t / 1e9 / hbm,
-                          "gathered_bytes": gathered, "gathered_gbs": gathered / t / 1e9,
-                          "word_or_tera_per_s": ors / t / 1e12,
-                          "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"]}
-        del on
+        pk["n%d" % nn] = {"ms": t * 1e3, "nnz": nnz, "kernel": kern, "compulsory_hbm_bytes": hbm_bytes,
+                          "hbm_gbs": hbm_bytes / t / 1e9, "hbm_frac": hbm_bytes / t / 1e9 / hbm}
+        if nn == 8192:
+            dense8k = torch.zeros_like(Pn)
+            ctx.rms(Pn, nn, dense8k, fmt=PK, variant="rms_tc", stream=stream)
+    # dense rows: the word ORs (nnz(R) x n / 64) against the integer-ALU rate
+    t, kern = packed_step(dense8k, 8192)
+    bits = int(np.unpackbits(dense8k.cpu().numpy().view(np.uint8)).sum())
+    ors = float(bits) * (8192 // 64)
+    pk["n8192_dense"] = {"ms": t * 1e3, "ones": bits, "kernel": kern, "word_or_tera_per_s": ors / t / 1e12,
+                         "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"]}
+    del dense8k
     ex["packed_product"] = pk
 
     # -- selective queries: 4,096 rows of 1-64 sources on the n = 65,536 power-law graph (Zipf 2.1 out-degrees)

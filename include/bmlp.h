@@ -136,10 +136,12 @@ typedef struct bmlp_stats {
                                   R <- R + R R taken before the frontier
                                   expansion (path-like relations; same closure,
                                   fewer levels)                                 */
-    int32_t sparse_squarings;  /* BMLP_RMS_TC: squarings run on word-indexed
-                                  bit rows before the tensor cores took over
+    int32_t sparse_squarings;  /* squarings run on word-indexed bit rows:
+                                  BMLP_RMS_TC before the tensor cores took over
                                   (counted in iterations, not in
-                                  product_launches)                             */
+                                  product_launches); BMLP_RMS_PACKED while
+                                  fewer than half of R's words were nonzero
+                                  (counted in both)                             */
     int32_t sliced_closures;   /* BMLP_SMP_PACKED closures, and query batches
                                   of >= 64 rows (n >= 4096), whose relation
                                   widens the rows fast (R + R R has > 2.8 x

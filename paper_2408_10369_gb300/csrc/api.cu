@@ -519,22 +519,68 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
 }
 
-// Packed squaring fixpoint on P[0] (n rows x ldw words). *res = R1+.
+// Device scratch for the prefix of a word-index build (kScanMaxChunks x 2 words).
+int64_t* scan_scratch(bmlp_ctx* ctx) {
+    void* p = nullptr;
+    return ws_get(ctx, WS_SCAN, static_cast<size_t>(kScanMaxChunks) * 2 * sizeof(int64_t), &p) == BMLP_OK
+               ? static_cast<int64_t*>(p)
+               : nullptr;
+}
+
+// Packed squaring fixpoint on P[0] (n rows x ldw words). *res = R1+. While fewer than half of R's words are
+// nonzero a squaring runs through R's word index (square_rows_kernel: only the nonzero words of the named rows are
+// ORed in, and the step streams R in and R' out), after that as the whole-row product (product_packed_kernel); a
+// squaring that widens the rows past half their words hands the next ones to the whole-row product.
 bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2], int max_iters,
                             const bmlp_options& o, cudaStream_t s, int* iters, uint64_t** res) {
     ProductTimer tm{ctx, o.profile != 0, s};
+    void *wptr = nullptr, *widx = nullptr, *wval = nullptr;
+    ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 2) * 8), &wptr));
+    ST(ws_get(ctx, WS_WIDX, static_cast<size_t>(n * ldw * 4), &widx));
+    ST(ws_get(ctx, WS_WVAL, static_cast<size_t>(n * ldw * 8), &wval));
+    const bool index_fits = ldw * 8 <= 200 * 1024;  // square_rows_kernel assembles a row in shared memory
+    bool sparse = index_fits;
+    auto index_of = [&](const uint64_t* Pm) -> bmlp_status {
+        CK(launch_wcsr_build(Pm, n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                             static_cast<uint64_t*>(wval), s, scan_scratch(ctx)),
+           "word index build");
+        CK(cudaMemcpyAsync(ctx->h_ctl + CTL_HOST_I64, static_cast<const int64_t*>(wptr) + n, sizeof(int64_t),
+                           cudaMemcpyDeviceToHost, s),
+           "read word count");
+        ctx->stats.launches += 3;
+        return BMLP_OK;
+    };
+    auto half_full = [&]() {
+        int64_t W = 0;
+        memcpy(&W, ctx->h_ctl + CTL_HOST_I64, sizeof(W));
+        return 2 * W >= n * ldw;
+    };
     int cur = 0;
     *iters = 0;
+    if (sparse) {
+        ST(index_of(P[0]));
+        CK(host_sync(ctx, s), "read word count");
+        sparse = !half_full();
+    }
     for (int it = 0; it < max_iters; ++it) {
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
         ST(tm.begin());
-        CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s,
-                                 deadline_of(ctx)),
-           "packed product launch");
+        if (sparse) {
+            CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                                  static_cast<uint64_t*>(wval), P[cur], n, ldw, P[nxt], ctx->sm_count, s,
+                                  ctx->d_ctl + CTL_CHANGED),
+               "word-indexed squaring launch");
+            ctx->stats.sparse_squarings++;
+        } else {
+            CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s,
+                                     deadline_of(ctx)),
+               "packed product launch");
+        }
         ST(tm.end());
         ctx->stats.product_launches++;
         ctx->stats.launches += 2;
+        if (sparse) ST(index_of(P[nxt]));  // the next step's index, read back with the flag
         int changed = 0;
         ST(read_ctl(ctx, s, &changed));
         ST(tm.collect());
@@ -544,6 +590,7 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
             *res = P[cur];
             return BMLP_OK;
         }
+        if (sparse) sparse = !half_full();
     }
     *res = P[cur];
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
@@ -633,14 +680,6 @@ struct SparseStart {
     int iters = 0;          // squarings run on bit rows
     bool done = false;      // the last of them changed nothing: P is the closure
 };
-
-// Device scratch for the prefix of a word-index build (kScanMaxChunks x 2 words).
-int64_t* scan_scratch(bmlp_ctx* ctx) {
-    void* p = nullptr;
-    return ws_get(ctx, WS_SCAN, static_cast<size_t>(kScanMaxChunks) * 2 * sizeof(int64_t), &p) == BMLP_OK
-               ? static_cast<int64_t*>(p)
-               : nullptr;
-}
 
 // Squarings R <- R + R R on word-indexed bit rows (square_rows_kernel) for as long as the next one costs less than a
 // tensor-core product. Each step is the squaring the tensor cores would run, so the fixpoint and the count of
