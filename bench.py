@@ -828,13 +828,14 @@ def main():
             torch.distributed.destroy_process_group()
         return
     extras = None
-    if not args.no_extras:
+    if not args.no_extras and world == 1:  # single-GPU measurements: the N = 1 run reports them
         extras = run_extras(args, ctx, stream, n, ip, ix, R, FMT, out, bf16, hbm, check=not args.no_cpu)
     cpu = None
     parity = None
     if not args.no_cpu:
         # the oracle's full closure of the benchmark graph against the last timed output, every bit
         parity = oracle_parity(n, ip, ix, out, args.fmt)
+    if not args.no_cpu and world == 1:
         # the oracle on all host cores (median of 3 samples of rows) and on one core (median of 3 smaller samples)
         rows = args.cpu_rows or max(64, n // 4)
         tc = statistics.median(cpu_oracle_closure(n, ip, ix, rows) for _ in range(3))
