@@ -723,7 +723,7 @@ def main():
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    prod_ms, prod_n, launches, issued, e2m1_n, sparse_n = 0.0, 0, 0, 0.0, 0, 0
+    prod_ms, prod_n, launches, issued, e2m1_n, sparse_n, thin_n = 0.0, 0, 0, 0.0, 0, 0, 0
     for _ in range(args.steps):
         iters = step(True)
         st = ctx.stats()
@@ -733,6 +733,7 @@ def main():
         issued += st["issued_ops"]
         e2m1_n += st["e2m1_products"]
         sparse_n += st["sparse_squarings"]
+        thin_n += st["thin_squarings"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -856,7 +857,8 @@ def main():
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
                        "seed": "rank", "variant": args.variant, "iterations": iters,
                        "bit_row_squarings": sparse_n // max(args.steps, 1),
-                       "tensor_core_squarings": prod_n // max(args.steps, 1), "nnz": int(len(ix)),
+                       "tensor_core_squarings": prod_n // max(args.steps, 1),
+                       "zero_row_column_squarings": thin_n // max(args.steps, 1), "nnz": int(len(ix)),
                        "graphs_per_s": args.steps * world / t,
                        "fmt": args.fmt,
                        "l2": ("operands larger than L2 (%.2f GiB per E2M1 matrix, %.0f MiB input)"

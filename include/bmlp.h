@@ -158,6 +158,12 @@ typedef struct bmlp_stats {
                                   cluster per 64 rows with the frontier in
                                   the cluster's shared memory (query batches,
                                   and closures whose columns are skewed)        */
+    int32_t thin_squarings;    /* BMLP_RMS_TC: squarings computed only on the
+                                  rows and columns of R that still held zeros
+                                  (few, and holding few ones: R close to its
+                                  closure); counted in iterations, not in
+                                  product_launches                              */
+    int32_t reserved2;         /* 0                                             */
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

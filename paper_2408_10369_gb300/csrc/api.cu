@@ -101,6 +101,9 @@ constexpr int WS_SQP = 27, WS_SQPTR = 28, WS_SQIDX = 29, WS_SQVAL = 30;
 constexpr int WS_E8_IN0 = 31, WS_E8_IN1 = 32, WS_E8_OUT = 33;
 // Block totals of the prefix over many blocks in a word-index build.
 constexpr int WS_SCAN = 34;
+// Bit rows of R and R^T, their ones, the column mask and the row and column lists, and the computed rows of a
+// squaring restricted to the rows and columns that still hold zeros.
+constexpr int WS_THIN_P = 35, WS_THIN_AUX = 36, WS_THIN_T = 37;
 constexpr int64_t kSquareMinN = 4096;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // A squaring is kept while it grows the rows' nonzero words by at most this factor (path-like relations).
@@ -121,6 +124,13 @@ constexpr double kClusterClosureSkew = 6.5;
 constexpr int64_t kSlicedMinQueries = 64;
 // Fraction of nonzero 128 x 128 blocks of R below which a squaring skips empty K blocks.
 constexpr double kSkipMaxDensity = 0.5;
+// Fixed device and host time of a squaring restricted to the rows and columns of R that hold zeros: the bit rows of
+// R and R^T (reading both E2M1 matrices, writing both bit-row copies and reading R's again: about 1.4 bytes per
+// entry at about 6 TB/s), the row and column lists and two flag read-backs; the row ORs are costed per word as the
+// bit-row squarings' are.
+double thin_fixed_s(int64_t n_pad) {
+    return 30e-6 + static_cast<double>(n_pad) * static_cast<double>(n_pad) * 1.4 / 6.0e12;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -278,6 +288,15 @@ struct ProductTimer {
     }
 };
 
+// 4-bit tensor-core closures try squarings restricted to the rows and columns that hold zeros unless BMLP_THIN=0.
+bool thin_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("BMLP_THIN");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // Full frontier closures whose first squaring widens the rows run 64 sources per CTA (bit-sliced) unless
 // BMLP_SMP_SLICED=0.
 bool smp_sliced_enabled() {
@@ -312,7 +331,7 @@ bool tc_skip_enabled() {
 // its transpose). With res_f4 set, the caller has instead encoded R / R^T as
 // packed E2M1 into the halves of M[1] / T[1]; every squaring then runs on
 // 4-bit operands and *res_f4 receives the E2M1 result (row stride n_pad / 2).
-bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
+bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
                         const uint8_t** res_f4 = nullptr) {
     NvtxRange nvtx_("tensor-core squarings");
@@ -391,6 +410,46 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
         *rt = T[sw];
         return BMLP_OK;
     };
+    // Once a 4-bit squaring has run, the next one is first sized on the rows and columns of R that still hold
+    // zeros (thin.cu); when those hold few ones, it runs there, on bit rows, at a fraction of a dense product.
+    const int64_t ldw_t = n_pad / 64;
+    int f4_products = 0;
+    auto thin_step = [&](bool* ran, int* changed) -> bmlp_status {
+        *ran = false;
+        void *pp = nullptr, *aux = nullptr;
+        ST(ws_get(ctx, WS_THIN_P, static_cast<size_t>(2 * n * ldw_t * 8), &pp));
+        const size_t aux_bytes = static_cast<size_t>(2 * n * 8 + (ldw_t + 1) * 8 + 2 * n * 4);
+        ST(ws_get(ctx, WS_THIN_AUX, aux_bytes, &aux));
+        uint64_t* P = static_cast<uint64_t*>(pp);
+        uint64_t* PT = P + n * ldw_t;
+        int64_t* rowcnt = static_cast<int64_t*>(aux);
+        int64_t* colcnt = rowcnt + n;
+        uint64_t* Bmask = reinterpret_cast<uint64_t*>(colcnt + n);
+        int32_t* blist = reinterpret_cast<int32_t*>(Bmask + ldw_t + 1);
+        int32_t* rlist = blist + n;
+        auto* stat = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_THIN);
+        CK(launch_thin_stats(Q[qcur], QT[qcur], ld4, n, P, PT, ldw_t, rowcnt, colcnt, Bmask, blist, rlist, stat,
+                             ctx->sm_count, s),
+           "thin squaring statistics");
+        ctx->stats.launches += 4;
+        ST(read_ctl(ctx, s, nullptr));
+        unsigned long long st[4];
+        memcpy(st, ctx->h_ctl + CTL_THIN, sizeof(st));
+        const double words = static_cast<double>(st[2] + st[3]) * static_cast<double>(ldw_t);
+        if (thin_fixed_s(n_pad) + words * bitrow_s_per_word() >= tc4_product_s(n_pad)) return BMLP_OK;
+        const int64_t nb = static_cast<int64_t>(st[0]), nr = static_cast<int64_t>(st[1]);
+        void* tt = nullptr;
+        ST(ws_get(ctx, WS_THIN_T, static_cast<size_t>((nb + nr + 1) * ldw_t * 8), &tt));
+        uint64_t* T1 = static_cast<uint64_t*>(tt);
+        CK(launch_thin_squaring(P, PT, ldw_t, blist, nb, rlist, nr, T1, T1 + nb * ldw_t, Q[qcur], QT[qcur], ld4,
+                                ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s),
+           "thin squaring");
+        ctx->stats.launches += 4;
+        ctx->stats.thin_squarings++;
+        ST(read_ctl(ctx, s, changed));
+        *ran = true;
+        return BMLP_OK;
+    };
     int cur = 0;
     *iters = 0;
     if (res_f4 != nullptr) {
@@ -431,6 +490,23 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             on_f4 = true;
             qcur = 0;
         }
+        if (on_f4 && f4_products > 0 && !o.tc_only && thin_enabled() && thin_fixed_s(n_pad) < tc4_product_s(n_pad)) {
+            bool ran = false;
+            int changed = 0;
+            ST(thin_step(&ran, &changed));
+            if (ran) {
+                *iters = it + 1;
+                if (!changed) {  // R is its closure; Q[qcur], QT[qcur] hold it
+                    if (res_f4 != nullptr) {
+                        *res_f4 = Q[qcur];
+                        *res = *res_t = nullptr;
+                        return BMLP_OK;
+                    }
+                    return finish_f4(res, res_t);
+                }
+                continue;
+            }
+        }
         if (on_f4) {
             TcParams p4 = p;
             p4.ld = ld4;
@@ -447,6 +523,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n_pad, uint8_t* M[2], uint8_t* T[
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;
             ctx->stats.launches += 2;
+            ++f4_products;
             int changed = 0;
             ST(read_ctl(ctx, s, &changed));
             ST(tm.collect());
@@ -1194,7 +1271,7 @@ static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt
             CK(cudaGetLastError(), "E2M1 encode");
             ctx->stats.launches++;
             const uint8_t* q = nullptr;
-            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q);
+            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q);
             if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) {
                 if (fmt == BMLP_FMT_U8)
                     launch_e2m1_to_u8(q, ld4, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
@@ -1205,7 +1282,7 @@ static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt
             }
         } else {
             ST(to_e4m3(ctx, src, sfmt, n, M[0], T[0], n_pad, s, sldw));
-            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
+            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
             if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED)
                 ST(bytes_out(ctx, res, n_pad, n, fmt, ov.dev, o.reflexive, s));
         }
@@ -1400,7 +1477,7 @@ static bmlp_status core_compose(bmlp_ctx* ctx, const void* R1, const void* R2, i
             res_t = T[0];
             st = BMLP_OK;
         } else {
-            st = rms_tc_loop(ctx, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
+            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
         }
         iters += sp.iters;
         if (st != BMLP_OK) return st;

@@ -74,12 +74,12 @@ def test_switch_matches_oracle_and_iteration_count(ctx, kind, n, p, seed):
     got, it, st = closure_packed(ctx, n, ip, ix)
     np.testing.assert_array_equal(got, want)
     assert st["sparse_squarings"] >= 1
-    assert st["sparse_squarings"] + st["product_launches"] == it
+    assert st["sparse_squarings"] + st["product_launches"] + st["thin_squarings"] == it
     assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
     # every squaring on the tensor cores: the same bits and the same count
     got2, it2, st2 = closure_packed(ctx, n, ip, ix, tc_only=True)
     np.testing.assert_array_equal(got2, want)
-    assert st2["sparse_squarings"] == 0 and st2["product_launches"] == it2 == it
+    assert st2["sparse_squarings"] == st2["thin_squarings"] == 0 and st2["product_launches"] == it2 == it
 
 
 def test_fixpoint_reached_on_bit_rows(ctx):
@@ -228,3 +228,44 @@ def test_alg1_large_dag_with_bit_row_start(ctx):
     assert ctx.stats()["sparse_squarings"] >= 1
     np.testing.assert_array_equal(wl.unpack_rows(out.cpu().numpy().view(np.uint64), n), oracle.closure(n, ip, ix))
     assert it == oracle.alg1_products(oracle.longest_shortest_path(n, ip, ix))
+
+
+# Once a 4-bit squaring has made R nearly its closure, a squaring runs only on the rows and columns that still hold
+# zeros (columns with fewer than n / 2 ones, and the rows with a zero elsewhere), on bit rows: same bits, same count.
+@pytest.mark.parametrize("n,d,seed", [(12000, 4.0, 31), (20001, 2.5, 32)])
+def test_squaring_on_zero_rows_and_columns(ctx, n, d, seed):
+    ip, ix = wl.er_graph(n, d, seed)
+    want = oracle.closure(n, ip, ix)
+    got, it, st = closure_packed(ctx, n, ip, ix)
+    np.testing.assert_array_equal(got, want)
+    assert st["thin_squarings"] >= 1
+    assert st["sparse_squarings"] + st["product_launches"] + st["thin_squarings"] == it
+    assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+
+
+def test_zero_rows_and_columns_that_fill_in():
+    """A dense random part with a 60-node chain hanging off it: the chain's columns are reached by most rows only
+    after several squarings, so squarings restricted to the rows and columns holding zeros find new ones (here in
+    u8 and with I + R1+ as well)."""
+    c = pkg.Context(0)
+    try:
+        n0, tail = 9000, 60
+        n = n0 + tail
+        ip0, ix0 = wl.er_graph(n0, 5.0, 33)
+        src = np.concatenate([np.repeat(np.arange(n0), np.diff(ip0)), [0], n0 + np.arange(tail - 1)])
+        dst = np.concatenate([ix0, [n0], n0 + 1 + np.arange(tail - 1)])
+        ip, ix = wl.csr_from_pairs(n, src, dst)
+        want = oracle.closure(n, ip, ix)
+        got, it, st = closure_packed(c, n, ip, ix)
+        np.testing.assert_array_equal(got, want)
+        assert st["thin_squarings"] >= 1
+        assert st["sparse_squarings"] + st["product_launches"] + st["thin_squarings"] == it
+        assert it == oracle.rms_iterations(oracle.longest_shortest_path(n, ip, ix))
+        R = dev(wl.dense_u8(n, ip, ix))
+        out = torch.zeros_like(R)
+        c.rms(R, n, out, fmt=bmlp.BMLP_FMT_U8, variant="rms_tc", reflexive=True)
+        torch.cuda.synchronize()
+        np.fill_diagonal(want, 1)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+    finally:
+        c.close()

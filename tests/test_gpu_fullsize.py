@@ -103,7 +103,7 @@ def test_largest_tensor_core_closure(ctx):
     torch.cuda.synchronize()
     st = ctx.stats()
     assert st["e2m1_products"] == st["product_launches"] >= 1
-    assert st["sparse_squarings"] + st["product_launches"] == it
+    assert st["sparse_squarings"] + st["product_launches"] + st["thin_squarings"] == it
     got = out.cpu().numpy().view(np.uint64)
     del P, out
     _, depth, _ = oracle.reach_rows(n, ip, ix, np.arange(n, dtype=np.int32), want_rows=False)
