@@ -131,6 +131,11 @@ constexpr double kSkipMaxDensity = 0.5;
 double thin_fixed_s(int64_t n_pad) {
     return 30e-6 + static_cast<double>(n_pad) * static_cast<double>(n_pad) * 1.4 / 6.0e12;
 }
+// The rows and columns holding zeros are sized only after a squaring whose R, in kThinSampleRows rows spread over it,
+// has its rows with at least n / 2 ones within this fraction of n of one another in count (the rows that reach most
+// constants are saturated, their zeros in common columns).
+constexpr double kThinRowSpread = 1.0 / 32.0;
+constexpr int kThinSampleRows = 256;
 
 struct DeviceGuard {
     int prev = -1;
@@ -413,7 +418,8 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
     // Once a 4-bit squaring has run, the next one is first sized on the rows and columns of R that still hold
     // zeros (thin.cu); when those hold few ones, it runs there, on bit rows, at a fraction of a dense product.
     const int64_t ldw_t = n_pad / 64;
-    int f4_products = 0;
+    const bool thin_on = !o.tc_only && thin_enabled() && thin_fixed_s(n_pad) < tc4_product_s(n_pad);
+    bool thin_try = false;  // the last 4-bit squaring left R dense enough (sampled) to size the next one
     auto thin_step = [&](bool* ran, int* changed) -> bmlp_status {
         *ran = false;
         void *pp = nullptr, *aux = nullptr;
@@ -433,10 +439,13 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
            "thin squaring statistics");
         ctx->stats.launches += 4;
         ST(read_ctl(ctx, s, nullptr));
-        unsigned long long st[4];
+        unsigned long long st[6];
         memcpy(st, ctx->h_ctl + CTL_THIN, sizeof(st));
+        // the word ORs over the GPU, or one warp's list entry with the most ones, whichever takes longer
         const double words = static_cast<double>(st[2] + st[3]) * static_cast<double>(ldw_t);
-        if (thin_fixed_s(n_pad) + words * bitrow_s_per_word() >= tc4_product_s(n_pad)) return BMLP_OK;
+        const double row_words = static_cast<double>(st[4] > st[5] ? st[4] : st[5]) * static_cast<double>(ldw_t);
+        const double t = thin_fixed_s(n_pad) + std::max(words * bitrow_s_per_word(), row_words * bitrow_row_s_per_word());
+        if (t >= tc4_product_s(n_pad)) return BMLP_OK;
         const int64_t nb = static_cast<int64_t>(st[0]), nr = static_cast<int64_t>(st[1]);
         void* tt = nullptr;
         ST(ws_get(ctx, WS_THIN_T, static_cast<size_t>((nb + nr + 1) * ldw_t * 8), &tt));
@@ -490,7 +499,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
             on_f4 = true;
             qcur = 0;
         }
-        if (on_f4 && f4_products > 0 && !o.tc_only && thin_enabled() && thin_fixed_s(n_pad) < tc4_product_s(n_pad)) {
+        if (on_f4 && thin_try) {
             bool ran = false;
             int changed = 0;
             ST(thin_step(&ran, &changed));
@@ -523,7 +532,14 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;
             ctx->stats.launches += 2;
-            ++f4_products;
+            auto* sample = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_THIN) + 6;
+            if (thin_on) {
+                // whether the rows of the new R that reach most constants are saturated (a sample of 256 rows),
+                // read back with the changed flag
+                CK(cudaMemsetAsync(sample, 0, 2 * sizeof(unsigned long long), s), "reset row sample");
+                CK(launch_thin_sample(Q[qcur ^ 1], ld4, n, kThinSampleRows, sample, s), "row sample");
+                ctx->stats.launches++;
+            }
             int changed = 0;
             ST(read_ctl(ctx, s, &changed));
             ST(tm.collect());
@@ -539,6 +555,14 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
                     return BMLP_OK;
                 }
                 return finish_f4(res, res_t);
+            }
+            if (thin_on) {
+                // every zero of a row that reaches most constants must lie in the few columns of B: such rows have
+                // (nearly) the same count
+                unsigned long long smp[2];
+                memcpy(smp, ctx->h_ctl + CTL_THIN + 12, sizeof(smp));
+                const double spread = static_cast<double>(smp[0]) - (static_cast<double>(n) - static_cast<double>(smp[1]));
+                thin_try = smp[0] > 0 && spread <= kThinRowSpread * static_cast<double>(n);
             }
             continue;
         }

@@ -145,11 +145,11 @@ struct bmlp_ctx {
 
 namespace bmlp {
 
-// CTL_QCOUNT, CTL_T0 and CTL_ISSUED are 64-bit words, CTL_COST two of them and CTL_THIN four (two ints each,
+// CTL_QCOUNT, CTL_T0 and CTL_ISSUED are 64-bit words, CTL_COST two of them and CTL_THIN eight (two ints each,
 // 8-byte aligned).
 enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
-    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_WORDS = 24
+    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_WORDS = 32
 };
 // The pinned host mirror has two more ints: CTL_HOST_I64 is a 64-bit slot for values read from elsewhere.
 constexpr int CTL_HOST_I64 = CTL_WORDS;
@@ -317,12 +317,17 @@ cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const
 // ---- a squaring restricted to the rows and columns of R that still hold zeros (thin.cu)
 // launch_thin_stats: bit rows P, PT (n rows of ldw = n_pad / 64 words) of the E2M1 R, R^T (ld4 = n_pad / 2 bytes per
 // row) with their ones (rowcnt, colcnt); B = the columns with fewer than n / 2 ones (Bmask, blist) and Rb = the rows
-// with a zero outside B (rlist); stat[0..3] = |B|, |Rb|, ones in B's columns, ones in Rb's rows.
+// with a zero outside B (rlist); stat[0..5] = |B|, |Rb|, ones in B's columns, ones in Rb's rows, the most ones of a
+// column of B and of a row of Rb.
+// launch_thin_sample: of `rows` rows of Q spread over its n rows, those with at least n / 2 ones: stat[0] = the most
+// ones of one, stat[1] = the most zeros of one (stat[0..1] zero beforehand).
 // launch_thin_squaring: R' = R + R R on those columns and rows, the new ones ORed into Q (R) and QT (R^T) in place,
 // *changed raised when there are any; T1, T2: nb x ldw and nr x ldw words of scratch.
 cudaError_t launch_thin_stats(const uint8_t* Q, const uint8_t* QT, int64_t ld4, int64_t n, uint64_t* P, uint64_t* PT,
                               int64_t ldw, int64_t* rowcnt, int64_t* colcnt, uint64_t* Bmask, int32_t* blist,
                               int32_t* rlist, unsigned long long* stat, int sms, cudaStream_t s);
+cudaError_t launch_thin_sample(const uint8_t* Q, int64_t ld4, int64_t n, int rows, unsigned long long* stat,
+                               cudaStream_t s);
 cudaError_t launch_thin_squaring(const uint64_t* P, const uint64_t* PT, int64_t ldw, const int32_t* blist,
                                  int64_t nb, const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2,
                                  uint8_t* Q, uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) e2m1_to_bits_kernel(const uint8_t* __rest
 }
 
 // Columns of B: colcnt[j] < n / 2 (j < n). Bmask gets their bits, blist the columns (in no particular order);
-// stat[0] += |B|, stat[2] += the ones in those columns.
+// stat[0] += |B|, stat[2] += the ones in those columns, stat[4] = the most ones of one of them.
 __global__ void thin_columns_kernel(const int64_t* __restrict__ colcnt, int64_t n, uint64_t* __restrict__ Bmask,
                                     int32_t* __restrict__ blist, unsigned long long* __restrict__ stat) {
     const int64_t wpr = (n + 63) >> 6;
@@ -82,16 +82,21 @@ __global__ void thin_columns_kernel(const int64_t* __restrict__ colcnt, int64_t 
         if (m) {
             const unsigned long long at = atomicAdd(&stat[0], static_cast<unsigned long long>(__popcll(m)));
             uint64_t mm = m;
+            unsigned long long top = 0;
             for (unsigned long long k = at; mm; ++k) {
-                blist[k] = static_cast<int32_t>(w * 64 + (__ffsll(static_cast<long long>(mm)) - 1));
+                const int64_t j = w * 64 + (__ffsll(static_cast<long long>(mm)) - 1);
+                blist[k] = static_cast<int32_t>(j);
+                top = static_cast<unsigned long long>(colcnt[j]) > top ? static_cast<unsigned long long>(colcnt[j]) : top;
                 mm &= mm - 1ull;
             }
             atomicAdd(&stat[2], ones);
+            atomicMax(&stat[4], top);
         }
     }
 }
 
-// Rows of Rb: a zero at some column j < n outside B. rlist gets them; stat[1] += |Rb|, stat[3] += their ones.
+// Rows of Rb: a zero at some column j < n outside B. rlist gets them; stat[1] += |Rb|, stat[3] += their ones,
+// stat[5] = the most ones of one of them.
 __global__ void __launch_bounds__(256) thin_rows_kernel(const uint64_t* __restrict__ P, int64_t ldw, int64_t n,
                                                         const int64_t* __restrict__ rowcnt,
                                                         const uint64_t* __restrict__ Bmask, int32_t* __restrict__ rlist,
@@ -109,12 +114,34 @@ __global__ void __launch_bounds__(256) thin_rows_kernel(const uint64_t* __restri
         if (__any_sync(FULL, gap) && lane == 0) {
             rlist[atomicAdd(&stat[1], 1ull)] = static_cast<int32_t>(i);
             atomicAdd(&stat[3], static_cast<unsigned long long>(rowcnt[i]));
+            atomicMax(&stat[5], static_cast<unsigned long long>(rowcnt[i]));
         }
     }
 }
 
-// T[l] = OR of Src[k] over the set bits k of Src[list[l]] (bit rows of ldw words; warp per list entry, a lane holds
-// up to 64 words of the accumulator in registers, ldw <= 2048).
+// Of `rows` rows of the E2M1 matrix Q spread evenly over its n rows, those with at least n / 2 ones: stat[0] = the
+// most ones of one, stat[1] = the most zeros (among columns < n) of one (warp per row).
+__global__ void __launch_bounds__(256) e2m1_sample_kernel(const uint8_t* __restrict__ Q, int64_t ld4, int64_t n,
+                                                          int rows, unsigned long long* __restrict__ stat) {
+    const int lane = threadIdx.x & 31;
+    const int r = static_cast<int>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const int64_t i = static_cast<int64_t>(r) * n / rows;
+    const uint4* row = reinterpret_cast<const uint4*>(Q + i * ld4);
+    unsigned long long c = 0;
+    for (int64_t u = lane; u * 16 < ld4; u += 32) {  // 16 bytes = 32 nibbles
+        const uint4 v = row[u];
+        c += __popc(nib_bits8(v.x)) + __popc(nib_bits8(v.y)) + __popc(nib_bits8(v.z)) + __popc(nib_bits8(v.w));
+    }
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+    if (lane == 0 && 2 * c >= static_cast<unsigned long long>(n)) {
+        atomicMax(&stat[0], c);
+        atomicMax(&stat[1], static_cast<unsigned long long>(n) - c);
+    }
+}
+
+// T[l] = OR of Src[k] over the set bits k of Src[list[l]] (bit rows of ldw words; warp per list entry, each lane
+// ORing its own words of T[l], so one entry's work runs on one warp).
 __global__ void __launch_bounds__(256) thin_row_or_kernel(const uint64_t* __restrict__ Src, int64_t ldw,
                                                           const int32_t* __restrict__ list, int64_t count,
                                                           uint64_t* __restrict__ T) {
@@ -189,10 +216,17 @@ int rows_grid(int64_t rows, int sms) {
 
 }  // namespace
 
+cudaError_t launch_thin_sample(const uint8_t* Q, int64_t ld4, int64_t n, int rows, unsigned long long* stat,
+                               cudaStream_t s) {
+    if (rows < 1) return cudaSuccess;
+    e2m1_sample_kernel<<<(rows + 7) / 8, 256, 0, s>>>(Q, ld4, n, rows, stat);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_thin_stats(const uint8_t* Q, const uint8_t* QT, int64_t ld4, int64_t n, uint64_t* P, uint64_t* PT,
                               int64_t ldw, int64_t* rowcnt, int64_t* colcnt, uint64_t* Bmask, int32_t* blist,
                               int32_t* rlist, unsigned long long* stat, int sms, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(stat, 0, 4 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(stat, 0, 6 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(Q, ld4, n, P, ldw, rowcnt);
     e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(QT, ld4, n, PT, ldw, colcnt);
