@@ -334,7 +334,8 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
     PK = bmlp.BMLP_FMT_PACKED64
     ex = {}
     probes = {"e4m3_m128n256k32": ctx.mma_issue_rate(0), "e2m1_m128n256k64": ctx.mma_issue_rate(1),
-              "e2m1_2sm_m256n256k64": ctx.mma_issue_rate(2), "word_or_tera_per_s": ctx.mma_issue_rate(3)}
+              "e2m1_2sm_m256n256k64": ctx.mma_issue_rate(2), "e2m1_2sm_m256n480k64": ctx.mma_issue_rate(4),
+              "word_or_tera_per_s": ctx.mma_issue_rate(3)}
     ex["issue_rate_probes_tflops"] = probes
 
     # -- every tensor-core squaring on E4M3 operands (options.e4m3_only), same graph

@@ -328,7 +328,11 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
  * kind 3: the integer ALU instead: 64-bit word ORs from registers by 8
  * warps per SM scheduler (the operation of the bit-row kernels); iters: 128
  * ORs per thread each (e.g. 20000); *tflops receives tera word-ORs per
- * second. Runs on the legacy default stream and synchronises the device.
+ * second.
+ * kind 4: the dense squaring kernel's exact MMA mix: per 64-deep K step one
+ * M256 N256 K64 and one M256 N224 K64 .cta_group::2 kind::mxf4 MMA per CTA
+ * pair (its 256 x 480 pair tile).
+ * Runs on the legacy default stream and synchronises the device.
  */
 bmlp_status bmlp_mma_issue_rate(bmlp_ctx* ctx, int32_t kind, int32_t iters, double* tflops);
 

@@ -402,7 +402,8 @@ class Context:
 
     def mma_issue_rate(self, kind, iters=20000):
         """bmlp_mma_issue_rate: TFLOP/s of back-to-back tcgen05.mma (kind 0: E4M3 M128 N256 K32, 1: E2M1
-        M128 N256 K64, 2: E2M1 M256 N256 K64 over a CTA pair), or (kind 3) tera 64-bit word ORs per second."""
+        M128 N256 K64, 2: E2M1 M256 N256 K64 over a CTA pair, 4: E2M1 M256 N256 K64 + M256 N224 K64 over a CTA
+        pair), or (kind 3) tera 64-bit word ORs per second."""
         v = ctypes.c_double(0.0)
         self._check(self._L.bmlp_mma_issue_rate(self.handle, int(kind), int(iters), ctypes.byref(v)))
         return v.value

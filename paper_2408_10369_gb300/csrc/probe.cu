@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(128, 1) mma_rate_kernel(int iters, int* err) {
 }
 
 // The 2-SM form: CTA pairs (2-CTA clusters); the even CTA issues M256 N256 K64
-// kind::mxf4 MMAs over both CTAs' tiles and TMEM.
+// kind::mxf4 MMAs over both CTAs' tiles and TMEM. With N1 = 224, each K step
+// also issues an M256 N224 K64 MMA into columns 256..479 (the squaring
+// kernel's 480-column pair tile; scale factors in columns 480..511).
+template <int N1>
 __global__ void __launch_bounds__(128, 1) __cluster_dims__(2, 1, 1) mma_rate_2sm_kernel(int iters, int* err) {
     extern __shared__ uint8_t raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
@@ -103,8 +106,13 @@ __global__ void __launch_bounds__(128, 1) __cluster_dims__(2, 1, 1) mma_rate_2sm
         const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
         const uint32_t ones[8] = {0x7F7F7F7Fu, 0x7F7F7F7Fu, 0x7F7F7F7Fu, 0x7F7F7F7Fu,
                                   0x7F7F7F7Fu, 0x7F7F7F7Fu, 0x7F7F7F7Fu, 0x7F7F7F7Fu};
-        tmem_st_32x32b_x8(base + lanes + 256, ones);
-        tmem_st_32x32b_x8(base + lanes + 384, ones);
+        if (N1) {
+#pragma unroll
+            for (int c = 480; c < 512; c += 8) tmem_st_32x32b_x8(base + lanes + c, ones);
+        } else {
+            tmem_st_32x32b_x8(base + lanes + 256, ones);
+            tmem_st_32x32b_x8(base + lanes + 384, ones);
+        }
         tmem_st_wait();
     }
     tc_fence_before();
@@ -112,12 +120,18 @@ __global__ void __launch_bounds__(128, 1) __cluster_dims__(2, 1, 1) mma_rate_2sm
     cluster_sync();  // both CTAs' tiles, scale factors and barriers are in place
     tc_fence_after();
     if (leader && threadIdx.x == 0) {
-        const uint32_t a0 = smem_u32(sm), b0 = smem_u32(sm + 16384);
+        const uint32_t a0 = smem_u32(sm), b0 = smem_u32(sm + 16384), b1 = smem_u32(sm + 32768);
+        const uint32_t sfa = base + (N1 ? 480 : 256), sfb = base + (N1 ? 480 : 384);
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tc_mma_mxf4_2sm(base, smem_desc_kmajor_sw128(a0 + k * 32), smem_desc_kmajor_sw128(b0 + k * 32),
-                                idesc_mxf4_ue8m0(256, 256), base + 256, base + 384, 1);
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t da = smem_desc_kmajor_sw128(a0 + k * 32);
+                tc_mma_mxf4_2sm(base, da, smem_desc_kmajor_sw128(b0 + k * 32), idesc_mxf4_ue8m0(256, 256), sfa, sfb,
+                                1);
+                if (N1)
+                    tc_mma_mxf4_2sm(base + 256, da, smem_desc_kmajor_sw128(b1 + k * 32), idesc_mxf4_ue8m0(256, N1),
+                                    sfa, sfb, 1);
+            }
         }
         tc_commit_2sm_mcast(&bar, 0x1);
         if (!mbar_wait_bounded(&bar, 0, &abort_flag, 8000000000LL)) atomicAdd(err, 1);
@@ -162,13 +176,17 @@ bmlp_status run_probe(bmlp_ctx* ctx, int kind, int iters, double* rate) {
     cudaError_t ce = cudaSuccess;
     if (kind == 0) ce = cudaFuncSetAttribute(mma_rate_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
     if (kind == 1) ce = cudaFuncSetAttribute(mma_rate_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
-    if (kind == 2) ce = cudaFuncSetAttribute(mma_rate_2sm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
+    if (kind == 2)
+        ce = cudaFuncSetAttribute(mma_rate_2sm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
+    if (kind == 4)
+        ce = cudaFuncSetAttribute(mma_rate_2sm_kernel<224>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
     if (ce != cudaSuccess) return cuda_err(ctx, ce, "probe attribute");
     const int pairs = ctx->sm_count / 2;
     auto launch = [&](int it) {
         if (kind == 0) mma_rate_kernel<0><<<ctx->sm_count, 128, PROBE_SMEM>>>(it, err);
         if (kind == 1) mma_rate_kernel<1><<<ctx->sm_count, 128, PROBE_SMEM>>>(it, err);
-        if (kind == 2) mma_rate_2sm_kernel<<<2 * pairs, 128, PROBE_SMEM>>>(it, err);
+        if (kind == 2) mma_rate_2sm_kernel<0><<<2 * pairs, 128, PROBE_SMEM>>>(it, err);
+        if (kind == 4) mma_rate_2sm_kernel<224><<<2 * pairs, 128, PROBE_SMEM>>>(it, err);
         if (kind == 3) or_rate_kernel<<<4 * ctx->sm_count, 256>>>(it, 0x243F6A8885A308D3ull,
                                                                    reinterpret_cast<uint64_t*>(err + 2));
     };
@@ -195,6 +213,7 @@ bmlp_status run_probe(bmlp_ctx* ctx, int kind, int iters, double* rate) {
     if (kind == 1) work = static_cast<double>(ctx->sm_count) * iters * 4.0 * 2.0 * 128.0 * 256.0 * 64.0;
     if (kind == 2) work = static_cast<double>(pairs) * iters * 4.0 * 2.0 * 256.0 * 256.0 * 64.0;
     if (kind == 3) work = 4.0 * ctx->sm_count * 256.0 * static_cast<double>(iters) * 16.0 * 8.0;
+    if (kind == 4) work = static_cast<double>(pairs) * iters * 4.0 * 2.0 * 256.0 * 480.0 * 64.0;
     *rate = work / (static_cast<double>(ms) * 1e-3) / 1e12;
     return BMLP_OK;
 }
@@ -203,7 +222,7 @@ bmlp_status run_probe(bmlp_ctx* ctx, int kind, int iters, double* rate) {
 }  // namespace bmlp
 
 extern "C" bmlp_status bmlp_mma_issue_rate(bmlp_ctx* ctx, int32_t kind, int32_t iters, double* tflops) {
-    if (!ctx || !tflops || iters <= 0 || kind < 0 || kind > 3) return BMLP_ERR_INVALID_ARG;
+    if (!ctx || !tflops || iters <= 0 || kind < 0 || kind > 4) return BMLP_ERR_INVALID_ARG;
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);

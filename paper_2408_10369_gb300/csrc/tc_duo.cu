@@ -145,19 +145,38 @@ constexpr int ERR_D_PRODUCER = 0x211;
 constexpr int ERR_D_MMA = 0x212;
 constexpr int ERR_D_EPILOGUE = 0x213;
 
+// 32 accumulator counts (FP32, exact integers 0 .. 2^24) -> bit j = (count j > 0).
+// The top byte of a count is 0 for 0 and 0x3F .. 0x4B for 1 .. 2^24, so adding
+// 0x41 sets its bit 7 exactly for the nonzero counts, without a carry into the
+// next byte. Word k gathers the top bytes of columns k, 8 + k, 16 + k and
+// 24 + k with byte permutes, so that its flags (bits 7, 15, 23, 31) shifted
+// right by 7 - k land on bits k, 8 + k, 16 + k, 24 + k: six integer operations
+// per four counts instead of a compare and a select for each.
+__device__ __forceinline__ uint32_t f4_threshold32(const uint32_t (&v)[32]) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t lo = __byte_perm(v[k], v[8 + k], 0x0073);        // top bytes in bytes 0, 1
+        const uint32_t hi = __byte_perm(v[16 + k], v[24 + k], 0x7300);  // and in bytes 2, 3
+        const uint32_t w = __byte_perm(lo, hi, 0x7610) + 0x41414141u;
+        bits |= (w >> (7 - k)) & (0x80808080u >> (7 - k));
+    }
+    return bits;
+}
+
 // Epilogue, part 1: C > 0 for the accumulator columns of this thread's TMEM
-// lane, as CHUNKS x 32 bits.
+// lane, as CHUNKS x 32 bits. The load of chunk c + 1 is in flight while chunk
+// c is thresholded.
 template <int CHUNKS>
 __device__ __forceinline__ void f4_drain(uint32_t taddr, uint32_t (&cb)[CHUNKS]) {
+    uint32_t va[32], vb[32];
+    tmem_ld_32x32b_x32(taddr, va);
 #pragma unroll
     for (int c = 0; c < CHUNKS; ++c) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c * 32), v);
-        tmem_ld_wait();
-        uint32_t bits = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) bits |= (v[j] != 0u ? 1u : 0u) << j;
-        cb[c] = bits;
+        uint32_t(&cur)[32] = (c & 1) ? vb : va;
+        tmem_ld_wait_regs(cur);
+        if (c + 1 < CHUNKS) tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>((c + 1) * 32), (c & 1) ? va : vb);
+        cb[c] = f4_threshold32(cur);
     }
 }
 

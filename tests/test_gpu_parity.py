@@ -280,13 +280,15 @@ def test_mma_issue_rate(ctx):
     """The issue-rate probes run and report positive rates; the 4-bit kind
     carries twice the K per instruction, so it is never slower than E4M3, and
     the 2-SM form does the work of two 1-SM MMAs per instruction pair; the
-    word-OR probe reports a rate too. Unknown kinds are refused."""
+    word-OR probe reports a rate too, and so does the squaring kernel's
+    N = 256 + 224 mix. Unknown kinds are refused."""
     r8 = ctx.mma_issue_rate(0, iters=2000)
     r4 = ctx.mma_issue_rate(1, iters=2000)
     r4x2 = ctx.mma_issue_rate(2, iters=2000)
     ors = ctx.mma_issue_rate(3, iters=2000)
-    assert r8 > 0 and r4 >= r8 and r4x2 > 0.5 * r4 and ors > 0
-    for bad in (-1, 4):
+    r480 = ctx.mma_issue_rate(4, iters=2000)
+    assert r8 > 0 and r4 >= r8 and r4x2 > 0.5 * r4 and ors > 0 and r480 > 0.5 * r4x2
+    for bad in (-1, 5):
         with pytest.raises(pkg.BmlpError):
             ctx.mma_issue_rate(bad)
 
