@@ -125,6 +125,85 @@ __global__ void encode_e2m1_tile(Src src, int64_t rows, uint8_t* __restrict__ R,
     *reinterpret_cast<uint2*>(RT + (col0 + r) * ld4 + (row0 + cseg) / 2) = make_uint2(nib_spread8(t), nib_spread8(t >> 8));
 }
 
+// The 32 x 32 bit block held by a warp, one 32-bit row per lane (bit j =
+// column j), transposed: lane j receives column j (bit i = row i). Five
+// exchange stages, each swapping the off-diagonal s x s sub-blocks of every
+// 2s x 2s block between lanes L and L ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int sh = 16 >> st;
+        const uint32_t m = masks[st];  // the columns j with (j & sh) == 0
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y >> sh) & m)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint4 nib_spread32(uint32_t b) {
+    return make_uint4(nib_spread8(b), nib_spread8(b >> 8), nib_spread8(b >> 16), nib_spread8(b >> 24));
+}
+
+// Packed bit rows (ldw words per row, n x n) -> packed E2M1 R and R^T (n_pad x
+// n_pad, row stride ld4 = n_pad / 2 bytes, padding zero): one 256 x 256 tile
+// per block of 256 threads. Thread t reads row row0 + t (four 64-bit words);
+// each warp turns its 32 rows into R^T bits as eight 32 x 32 bit blocks
+// transposed in registers. Both bit tiles go through shared memory (rows of 8
+// words padded to 9), so that every global store is 8 lanes x 16 bytes = one
+// 128-byte line of a row of R or R^T, 4 lines per warp instruction.
+__global__ void __launch_bounds__(256) packed_to_e2m1_kernel(const uint64_t* __restrict__ p, int64_t ldw, int64_t n,
+                                                             uint8_t* __restrict__ R, uint8_t* __restrict__ RT,
+                                                             int64_t ld4, bool vec) {
+    __shared__ uint32_t sR[256][9];   // row t of the tile: bits of columns 32 w .. 32 w + 31 in word w
+    __shared__ uint32_t sT[256][9];   // row c of the transposed tile: bits of rows 32 w .. 32 w + 31
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row0 = static_cast<int64_t>(blockIdx.y) * 256, col0 = static_cast<int64_t>(blockIdx.x) * 256;
+    const int64_t r = row0 + threadIdx.x;
+    uint64_t w[4] = {0, 0, 0, 0};
+    if (r < n) {
+        const uint64_t* src = p + r * ldw + col0 / 64;
+        const int64_t words = (n - col0 + 63) / 64;  // words of this row inside the tile that hold columns < n
+        if (vec && words >= 4) {
+            const uint4 a = reinterpret_cast<const uint4*>(src)[0], b = reinterpret_cast<const uint4*>(src)[1];
+            w[0] = (static_cast<uint64_t>(a.y) << 32) | a.x;
+            w[1] = (static_cast<uint64_t>(a.w) << 32) | a.z;
+            w[2] = (static_cast<uint64_t>(b.y) << 32) | b.x;
+            w[3] = (static_cast<uint64_t>(b.w) << 32) | b.z;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < words) w[q] = src[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t valid = n - (col0 + 64 * q);
+            if (valid <= 0) w[q] = 0;
+            else if (valid < 64) w[q] &= (1ull << valid) - 1ull;
+        }
+    }
+    uint32_t x[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        x[2 * q] = static_cast<uint32_t>(w[q]);
+        x[2 * q + 1] = static_cast<uint32_t>(w[q] >> 32);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        sR[threadIdx.x][k] = x[k];
+        sT[32 * k + lane][warp] = warp_transpose32(x[k], lane);  // column 32 k + lane, rows 32 warp + i
+    }
+    __syncthreads();
+    // lanes 8 q .. 8 q + 7 write the 8 pieces (16 bytes = 32 elements each) of one row
+    const int piece = lane & 7;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int t = warp * 32 + i * 4 + (lane >> 3);
+        *reinterpret_cast<uint4*>(R + (row0 + t) * ld4 + col0 / 2 + piece * 16) = nib_spread32(sR[t][piece]);
+        *reinterpret_cast<uint4*>(RT + (col0 + t) * ld4 + row0 / 2 + piece * 16) = nib_spread32(sT[t][piece]);
+    }
+}
+
 // Packed E2M1 rows -> u8 0/1 rows (n x n, + I if reflexive); 16 outputs per thread.
 __global__ void e2m1_to_u8_kernel(const uint8_t* __restrict__ Q, int64_t ld4, int64_t n, uint8_t* __restrict__ out,
                                   int reflexive, bool vec_out) {
@@ -394,9 +473,10 @@ void launch_u8_to_e2m1(const uint8_t* in, int64_t n, uint8_t* R, uint8_t* RT, in
 
 void launch_packed_to_e2m1(const uint64_t* in, int64_t ldw_in, int64_t n, uint8_t* R, uint8_t* RT, int64_t n_pad,
                            cudaStream_t s) {
-    SrcPacked src{in, ldw_in, n};
-    dim3 grid(static_cast<unsigned>(n_pad / T), static_cast<unsigned>(n_pad / T));
-    encode_e2m1_tile<SrcPacked><<<grid, 256, 0, s>>>(src, n, R, RT, n_pad / 2);
+    // n_pad is a multiple of 256 (TC_PAD); 16-byte row loads when every tile's first word is 16-byte aligned
+    const bool vec = (ldw_in % 2 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+    dim3 grid(static_cast<unsigned>(n_pad / 256), static_cast<unsigned>(n_pad / 256));
+    packed_to_e2m1_kernel<<<grid, 256, 0, s>>>(in, ldw_in, n, R, RT, n_pad / 2, vec);
 }
 
 void launch_e2m1_to_u8(const uint8_t* Q, int64_t ld4, int64_t n, uint8_t* out, int reflexive, cudaStream_t s) {
