@@ -335,10 +335,12 @@ bool tc_skip_enabled() {
 // (M[0], T[0]). On return *res points at the buffer holding R1+ (and *res_t at
 // its transpose). With res_f4 set, the caller has instead encoded R / R^T as
 // packed E2M1 into the halves of M[1] / T[1]; every squaring then runs on
-// 4-bit operands and *res_f4 receives the E2M1 result (row stride n_pad / 2).
+// 4-bit operands and *res_f4 receives the E2M1 result (row stride n_pad / 2);
+// the squarings also keep R as bit rows, and *res_bits receives them (n_pad
+// rows of n_pad / 64 words), or null if no squaring ran.
 bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], uint8_t* T[2], int max_iters,
                         const bmlp_options& o, cudaStream_t s, int* iters, uint8_t** res, uint8_t** res_t,
-                        const uint8_t** res_f4 = nullptr) {
+                        const uint8_t** res_f4 = nullptr, const uint64_t** res_bits = nullptr) {
     NvtxRange nvtx_("tensor-core squarings");
     CUtensorMap mapA[2], mapB[2], mapBh[2];
     for (int b = 0; b < 2; ++b) {
@@ -420,14 +422,23 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
     const int64_t ldw_t = n_pad / 64;
     const bool thin_on = !o.tc_only && thin_enabled() && thin_fixed_s(n_pad) < tc4_product_s(n_pad);
     bool thin_try = false;  // the last 4-bit squaring left R dense enough (sampled) to size the next one
+    // bit rows of R and R^T (n_pad rows each): written by every 4-bit squaring's epilogue when the caller takes the
+    // result from them (res_bits), kept by the restricted squarings; bits_current once a squaring has written them
+    uint64_t* P = nullptr;
+    uint64_t* PT = nullptr;
+    bool bits_current = false;
+    if (thin_on || res_bits != nullptr) {
+        void* pp = nullptr;
+        ST(ws_get(ctx, WS_THIN_P, static_cast<size_t>(2 * n_pad * ldw_t * 8), &pp));
+        P = static_cast<uint64_t*>(pp);
+        PT = P + n_pad * ldw_t;
+    }
+    if (res_bits != nullptr) *res_bits = nullptr;
     auto thin_step = [&](bool* ran, int* changed) -> bmlp_status {
         *ran = false;
-        void *pp = nullptr, *aux = nullptr;
-        ST(ws_get(ctx, WS_THIN_P, static_cast<size_t>(2 * n * ldw_t * 8), &pp));
+        void* aux = nullptr;
         const size_t aux_bytes = static_cast<size_t>(2 * n * 8 + (ldw_t + 1) * 8 + 2 * n * 4);
         ST(ws_get(ctx, WS_THIN_AUX, aux_bytes, &aux));
-        uint64_t* P = static_cast<uint64_t*>(pp);
-        uint64_t* PT = P + n * ldw_t;
         int64_t* rowcnt = static_cast<int64_t*>(aux);
         int64_t* colcnt = rowcnt + n;
         uint64_t* Bmask = reinterpret_cast<uint64_t*>(colcnt + n);
@@ -435,8 +446,9 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
         int32_t* rlist = blist + n;
         auto* stat = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_THIN);
         CK(launch_thin_stats(Q[qcur], QT[qcur], ld4, n, P, PT, ldw_t, rowcnt, colcnt, Bmask, blist, rlist, stat,
-                             ctx->sm_count, s),
+                             bits_current, ctx->sm_count, s),
            "thin squaring statistics");
+        bits_current = true;  // P, PT hold R, R^T from here on (converted, or already there)
         ctx->stats.launches += 4;
         ST(read_ctl(ctx, s, nullptr));
         unsigned long long st[6];
@@ -508,6 +520,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
                 if (!changed) {  // R is its closure; Q[qcur], QT[qcur] hold it
                     if (res_f4 != nullptr) {
                         *res_f4 = Q[qcur];
+                        if (res_bits != nullptr && bits_current) *res_bits = P;
                         *res = *res_t = nullptr;
                         return BMLP_OK;
                     }
@@ -525,6 +538,14 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
             p4.old_r = Q[qcur];
             p4.out_r = Q[qcur ^ 1];
             p4.out_rt = QT[qcur ^ 1];
+            // the epilogue writes the bit rows too when the result leaves from them, or a restricted squaring may
+            // follow (which then needs no conversion from E2M1)
+            const bool bits_out = P != nullptr && (res_bits != nullptr || thin_on);
+            if (bits_out) {
+                p4.out_bits = reinterpret_cast<uint32_t*>(P);
+                p4.out_bits_t = reinterpret_cast<uint32_t*>(PT);
+                p4.ldb = 2 * ldw_t;
+            }
             ST(tm.begin());
             CK(launch_tc4_product_duo(mapA4[qcur], mapB4[qcur], mapB4x[qcur], p4, ctx->sm_count, s),
                "tensor-core product launch");
@@ -532,6 +553,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
             ctx->stats.product_launches++;
             ctx->stats.e2m1_products++;
             ctx->stats.launches += 2;
+            bits_current = bits_out;
             auto* sample = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_THIN) + 6;
             if (thin_on) {
                 // whether the rows of the new R that reach most constants are saturated (a sample of 256 rows),
@@ -551,6 +573,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
             if (!changed) {
                 if (res_f4 != nullptr) {
                     *res_f4 = Q[qcur];
+                    if (res_bits != nullptr && bits_current) *res_bits = P;
                     *res = *res_t = nullptr;
                     return BMLP_OK;
                 }
@@ -610,6 +633,7 @@ bmlp_status rms_tc_loop(bmlp_ctx* ctx, int64_t n, int64_t n_pad, uint8_t* M[2], 
     }
     if (on_f4 && res_f4 != nullptr) {
         *res_f4 = Q[qcur];
+        if (res_bits != nullptr && bits_current) *res_bits = P;
         *res = *res_t = nullptr;
     } else if (on_f4) {
         ST(finish_f4(res, res_t));
@@ -1295,8 +1319,12 @@ static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt
             CK(cudaGetLastError(), "E2M1 encode");
             ctx->stats.launches++;
             const uint8_t* q = nullptr;
-            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q);
-            if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) {
+            const uint64_t* qb = nullptr;
+            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q, &qb);
+            if ((st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) && qb != nullptr) {
+                // the squarings kept R as bit rows: the result leaves from them
+                ST(packed_out(ctx, qb, n_pad / 64, n, fmt, ov.dev, o.reflexive, s));
+            } else if (st == BMLP_OK || st == BMLP_ERR_NOT_CONVERGED) {
                 if (fmt == BMLP_FMT_U8)
                     launch_e2m1_to_u8(q, ld4, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
                 else

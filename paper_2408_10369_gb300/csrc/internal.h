@@ -53,6 +53,11 @@ struct TcParams {
     unsigned long long* issued; // multiply-adds issued in units of 128 x 32 x 128 (rows x columns x K), or null
     const int* guard;           // 4-bit squaring kernel: if not null and *guard == 0 the launch does nothing (a step
                                 // of a device-side loop that a decision kernel switched off)
+    // squaring kernels on packed operands: if not null, the epilogue also writes R' and R'^T as bit rows of ldb
+    // 32-bit words (bit j of word u = column 32 u + j), n_pad rows each
+    uint32_t* out_bits;
+    uint32_t* out_bits_t;
+    int64_t ldb;
 };
 
 // One problem of a grouped batch (device copy; built on the host).
@@ -316,21 +321,22 @@ cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const
                                int reflexive, int* levels, int max_levels, int sms, cudaStream_t s, Deadline dl);
 // ---- a squaring restricted to the rows and columns of R that still hold zeros (thin.cu)
 // launch_thin_stats: bit rows P, PT (n rows of ldw = n_pad / 64 words) of the E2M1 R, R^T (ld4 = n_pad / 2 bytes per
-// row) with their ones (rowcnt, colcnt); B = the columns with fewer than n / 2 ones (Bmask, blist) and Rb = the rows
-// with a zero outside B (rlist); stat[0..5] = |B|, |Rb|, ones in B's columns, ones in Rb's rows, the most ones of a
-// column of B and of a row of Rb.
+// row) with their ones (rowcnt, colcnt); with bits_current, P and PT already hold R and R^T (written by the squaring
+// kernel's epilogue and kept by launch_thin_squaring) and only their ones are counted; B = the columns with fewer
+// than n / 2 ones (Bmask, blist) and Rb = the rows with a zero outside B (rlist); stat[0..5] = |B|, |Rb|, ones in B's
+// columns, ones in Rb's rows, the most ones of a column of B and of a row of Rb.
 // launch_thin_sample: of `rows` rows of Q spread over its n rows, those with at least n / 2 ones: stat[0] = the most
 // ones of one, stat[1] = the most zeros of one (stat[0..1] zero beforehand).
-// launch_thin_squaring: R' = R + R R on those columns and rows, the new ones ORed into Q (R) and QT (R^T) in place,
-// *changed raised when there are any; T1, T2: nb x ldw and nr x ldw words of scratch.
+// launch_thin_squaring: R' = R + R R on those columns and rows, the new ones ORed into Q (R) and QT (R^T) and into
+// the bit rows P, PT in place, *changed raised when there are any; T1, T2: nb x ldw and nr x ldw words of scratch.
 cudaError_t launch_thin_stats(const uint8_t* Q, const uint8_t* QT, int64_t ld4, int64_t n, uint64_t* P, uint64_t* PT,
                               int64_t ldw, int64_t* rowcnt, int64_t* colcnt, uint64_t* Bmask, int32_t* blist,
-                              int32_t* rlist, unsigned long long* stat, int sms, cudaStream_t s);
+                              int32_t* rlist, unsigned long long* stat, bool bits_current, int sms, cudaStream_t s);
 cudaError_t launch_thin_sample(const uint8_t* Q, int64_t ld4, int64_t n, int rows, unsigned long long* stat,
                                cudaStream_t s);
-cudaError_t launch_thin_squaring(const uint64_t* P, const uint64_t* PT, int64_t ldw, const int32_t* blist,
-                                 int64_t nb, const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2,
-                                 uint8_t* Q, uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);
+cudaError_t launch_thin_squaring(uint64_t* P, uint64_t* PT, int64_t ldw, const int32_t* blist, int64_t nb,
+                                 const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2, uint8_t* Q,
+                                 uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);
 // nonzero words of R + R R (out[0] += their total) and the word ORs of that squaring (out[1] += their total), from
 // the word index of R (ldw words per row, at most 49,152), without forming R + R R
 cudaError_t launch_square_growth(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,

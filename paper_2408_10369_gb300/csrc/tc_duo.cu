@@ -242,6 +242,7 @@ __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int64_t
         const uint32_t nbits = obits | f4_pick(cb, c);
         any |= nbits ^ obits;
         store_bits32<KIND>(p.out_r + off, nbits);
+        if (p.out_bits != nullptr) p.out_bits[row * p.ldb + col0 / 32] = nbits;
         // column col0 + j of these 32 rows is row col0 + j of R'^T: lane j gathers it
         uint32_t mine = 0;
 #pragma unroll
@@ -250,6 +251,7 @@ __device__ __forceinline__ uint32_t f4_update(const TcParams& p, int mb, int64_t
             mine = (lane == j) ? b : mine;
         }
         store_bits32<KIND>(p.out_rt + (col0 + lane) * p.ld + rt_col, mine);
+        if (p.out_bits_t != nullptr) p.out_bits_t[(col0 + lane) * p.ldb + rt_col / CB] = mine;
     }
     return any;
 }

@@ -62,6 +62,21 @@ __global__ void __launch_bounds__(256) e2m1_to_bits_kernel(const uint8_t* __rest
     }
 }
 
+// The ones of each of the n_rows bit rows of P (ldw words each) into cnt (warp per row).
+__global__ void __launch_bounds__(256) bits_count_kernel(const uint64_t* __restrict__ P, int64_t ldw, int64_t n_rows,
+                                                         int64_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_rows;
+         i += warps) {
+        const uint64_t* row = P + i * ldw;
+        int64_t c = 0;
+        for (int64_t w = lane; w < ldw; w += 32) c += __popcll(row[w]);
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+        if (lane == 0) cnt[i] = c;
+    }
+}
+
 // Columns of B: colcnt[j] < n / 2 (j < n). Bmask gets their bits, blist the columns (in no particular order);
 // stat[0] += |B|, stat[2] += the ones in those columns, stat[4] = the most ones of one of them.
 __global__ void thin_columns_kernel(const int64_t* __restrict__ colcnt, int64_t n, uint64_t* __restrict__ Bmask,
@@ -179,28 +194,35 @@ __device__ __forceinline__ void set_nibble(uint8_t* Q, int64_t ld4, int64_t row,
     atomicOr(reinterpret_cast<unsigned int*>(Q + (byte & ~int64_t(3))), 1u << bit);
 }
 
-// New ones of a thin squaring into R (Q) and R^T (QT): for list entry l with index x = list[l] and computed row
-// T[l], the bits of T[l] not in Cur[x] are entry (x, j) of Cur's matrix; transposed says whether Cur is R^T (then
-// (x, j) is R[j][x]). Raises *changed when anything is new.
-__global__ void __launch_bounds__(256) thin_apply_kernel(const uint64_t* __restrict__ Cur, const uint64_t* __restrict__ T,
+// New ones of a thin squaring into R (Q and the bit rows P) and R^T (QT and PT): for list entry l with index
+// x = list[l] and computed row T[l], the bits of T[l] not in row x of Cur (P, or PT when transposed) are entry
+// (x, j) of Cur's matrix (R[j][x] when transposed). Word w of row x is read and written by one thread only (list
+// entries are distinct), and the other matrix's bits go in with atomic ORs; a one that the column pass already set
+// is not new to the row pass. Raises *changed when anything is new.
+__global__ void __launch_bounds__(256) thin_apply_kernel(uint64_t* P, uint64_t* PT, const uint64_t* __restrict__ T,
                                                          int64_t ldw, const int32_t* __restrict__ list, int64_t count,
                                                          int transposed, uint8_t* __restrict__ Q,
                                                          uint8_t* __restrict__ QT, int64_t ld4,
                                                          int* __restrict__ changed) {
+    uint64_t* Cur = transposed ? PT : P;
+    uint64_t* Other = transposed ? P : PT;
     const int64_t total = count * ldw;
     bool any = false;
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t l = t / ldw, w = t % ldw;
         const int64_t x = list[l];
-        uint64_t nb = T[t] & ~Cur[x * ldw + w];
+        const uint64_t old = Cur[x * ldw + w];
+        uint64_t nb = T[t] & ~old;
         any |= nb != 0ull;
+        if (nb) Cur[x * ldw + w] = old | nb;
         while (nb) {
             const int64_t j = w * 64 + (__ffsll(static_cast<long long>(nb)) - 1);
             nb &= nb - 1ull;
             const int64_t r = transposed ? j : x, c = transposed ? x : j;  // the new entry is R[r][c]
             set_nibble(Q, ld4, r, c);
             set_nibble(QT, ld4, c, r);
+            atomicOr(reinterpret_cast<unsigned long long*>(Other + j * ldw + (x >> 6)), 1ull << (x & 63));
         }
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(changed, 1);
@@ -225,26 +247,31 @@ cudaError_t launch_thin_sample(const uint8_t* Q, int64_t ld4, int64_t n, int row
 
 cudaError_t launch_thin_stats(const uint8_t* Q, const uint8_t* QT, int64_t ld4, int64_t n, uint64_t* P, uint64_t* PT,
                               int64_t ldw, int64_t* rowcnt, int64_t* colcnt, uint64_t* Bmask, int32_t* blist,
-                              int32_t* rlist, unsigned long long* stat, int sms, cudaStream_t s) {
+                              int32_t* rlist, unsigned long long* stat, bool bits_current, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(stat, 0, 6 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(Q, ld4, n, P, ldw, rowcnt);
-    e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(QT, ld4, n, PT, ldw, colcnt);
+    if (bits_current) {
+        bits_count_kernel<<<rows_grid(n, sms), 256, 0, s>>>(P, ldw, n, rowcnt);
+        bits_count_kernel<<<rows_grid(n, sms), 256, 0, s>>>(PT, ldw, n, colcnt);
+    } else {
+        e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(Q, ld4, n, P, ldw, rowcnt);
+        e2m1_to_bits_kernel<<<rows_grid(n, sms), 256, 0, s>>>(QT, ld4, n, PT, ldw, colcnt);
+    }
     const int64_t wpr = (n + 63) / 64;
     thin_columns_kernel<<<static_cast<int>((wpr + 255) / 256), 256, 0, s>>>(colcnt, n, Bmask, blist, stat);
     thin_rows_kernel<<<rows_grid(n, sms), 256, 0, s>>>(P, ldw, n, rowcnt, Bmask, rlist, stat);
     return cudaGetLastError();
 }
 
-cudaError_t launch_thin_squaring(const uint64_t* P, const uint64_t* PT, int64_t ldw, const int32_t* blist,
-                                 int64_t nb, const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2,
-                                 uint8_t* Q, uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s) {
+cudaError_t launch_thin_squaring(uint64_t* P, uint64_t* PT, int64_t ldw, const int32_t* blist, int64_t nb,
+                                 const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2, uint8_t* Q,
+                                 uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s) {
     if (nb > 0) thin_row_or_kernel<<<rows_grid(nb, sms), 256, 0, s>>>(PT, ldw, blist, nb, T1);
     if (nr > 0) thin_row_or_kernel<<<rows_grid(nr, sms), 256, 0, s>>>(P, ldw, rlist, nr, T2);
     // every new one is found from the old R before any is written
     const int apply_grid = sms * 8;
-    if (nb > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(PT, T1, ldw, blist, nb, 1, Q, QT, ld4, changed);
-    if (nr > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, T2, ldw, rlist, nr, 0, Q, QT, ld4, changed);
+    if (nb > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T1, ldw, blist, nb, 1, Q, QT, ld4, changed);
+    if (nr > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T2, ldw, rlist, nr, 0, Q, QT, ld4, changed);
     return cudaGetLastError();
 }
 
