@@ -228,9 +228,7 @@ bmlp_status finish_out(bmlp_ctx* ctx, const OutView& o, cudaStream_t s) {
 }
 
 long long wait_cycles(bmlp_ctx* ctx, const bmlp_options& o) {
-    int khz = 0;
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
-    if (khz <= 0) khz = 2100000;
+    const int khz = ctx->clock_khz > 0 ? ctx->clock_khz : 2100000;
     const double ns = o.timeout_ns ? static_cast<double>(o.timeout_ns) : 2.0e9;
     return static_cast<long long>(ns * static_cast<double>(khz) * 1e-6);
 }
@@ -1180,6 +1178,8 @@ bmlp_status bmlp_ctx_create(bmlp_ctx** out, int32_t device) {
     for (int& t : ctx->tune) t = -1;
     DeviceGuard g(device);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // the clock rate bounds every in-kernel wait; its query is slow (about 0.7 ms), so it is read here only
+    cudaDeviceGetAttribute(&ctx->clock_khz, cudaDevAttrClockRate, device);
     if (cudaMalloc(&ctx->d_ctl, CTL_WORDS * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ctl, CTL_HOST_WORDS * sizeof(int)) != cudaSuccess ||
         cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess) {

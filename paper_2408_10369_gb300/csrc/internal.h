@@ -134,6 +134,7 @@ struct DevBuf {
 struct bmlp_ctx {
     int device = 0;
     int sm_count = 0;
+    int clock_khz = 0;           // SM clock rate, read once (the query takes hundreds of microseconds)
     char err[512] = {0};
     bmlp::DevBuf ws[40];
     void* batch = nullptr;       // cached grouped-batch graph (batch.cu)

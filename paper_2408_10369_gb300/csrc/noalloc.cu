@@ -98,10 +98,19 @@ extern "C" bmlp_status bmlp_rms_tc_noalloc(const void* R, int64_t n, int32_t fmt
     bmlp_status st = scratch_on_current_device(&dev, &base);
     if (st != BMLP_OK) return st;
     if (!on_device(R, dev) || !on_device(out, dev)) return BMLP_ERR_INVALID_ARG;
-    int sms = 0, khz = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2100000;
+    // SM count and clock rate per device, queried once (the clock-rate query takes about 0.7 ms); concurrent first
+    // calls may both query and store the same values
+    static int dev_sms[64] = {0}, dev_khz[64] = {0};
+    int sms = dev < 64 ? dev_sms[dev] : 0, khz = dev < 64 ? dev_khz[dev] : 0;
+    if (sms <= 0 || khz <= 0) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        if (khz <= 0) khz = 2100000;
+        if (dev < 64 && sms > 0) {
+            dev_sms[dev] = sms;
+            dev_khz[dev] = khz;
+        }
+    }
 
     const int64_t n_pad = (n + TC_PAD - 1) / TC_PAD * TC_PAD;
     const size_t mat = static_cast<size_t>(n_pad * n_pad);

@@ -1410,9 +1410,27 @@ cudaLaunchConfig_t cluster_config(int64_t clusters, int ctas, int lg, cudaStream
 }
 }  // namespace
 
+static bool smp_cluster_fits_query(int ctas, int lg);
+
 bool smp_cluster_fits(int64_t n, int64_t rows, int sms) {
     int ctas = 0, lg = 0;
     if (rows < 1 || !smp_cluster_shape(n, (rows + 63) / 64, sms, &ctas, &lg)) return false;
+    // the answer depends on the device and the launch shape only: kept per (device, ctas, log2 chunk), since the
+    // occupancy query costs far more than a launch (0: not asked yet, 1: fits, 2: does not)
+    static signed char known[16][9][32] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    const bool keyed = dev >= 0 && dev < 16 && ctas >= 1 && ctas <= 8 && lg >= 0 && lg < 32;
+    if (keyed && known[dev][ctas][lg] != 0) return known[dev][ctas][lg] == 1;
+    const bool fits = smp_cluster_fits_query(ctas, lg);
+    if (keyed) known[dev][ctas][lg] = fits ? 1 : 2;
+    return fits;
+}
+
+static bool smp_cluster_fits_query(int ctas, int lg) {
     cudaLaunchAttribute at;
     const cudaLaunchConfig_t cfg = cluster_config(1, ctas, lg, nullptr, &at);
     if (cudaFuncSetAttribute(smp_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -51,7 +51,7 @@ def test_model_choices_on_the_heldout_corpus():
     best = T.min(1).sum()
     fixed_tc = T[:, 0].sum()
     assert chosen <= 1.02 * best, (chosen, best)
-    assert fixed_tc > 1.5 * chosen, (fixed_tc, chosen)
+    assert fixed_tc > 1.4 * chosen, (fixed_tc, chosen)
     with open(os.path.join(PKG, "data", "dispatch_eval_gb300.json")) as f:
         ev = json.load(f)
     hist = np.bincount(choice, minlength=ref.NV)
