@@ -719,6 +719,14 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
 }
 
+// The caller's rows themselves when they are packed bit rows on the device with ldw words per row (words_of(n) even)
+// and 16-byte aligned, so that a read-only pass can use them without a copy; else null.
+const uint64_t* in_place_packed(const Operand& in, int32_t fmt, int64_t n, int64_t ldw) {
+    if (fmt != BMLP_FMT_PACKED64 || in.host || words_of(n) != ldw) return nullptr;
+    if ((reinterpret_cast<uintptr_t>(in.dev) & 15) != 0) return nullptr;
+    return static_cast<const uint64_t*>(in.dev);
+}
+
 // Packed copy of a caller matrix (any format) into n x ldw words.
 bmlp_status to_packed(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int64_t n, uint64_t* P, int64_t ldw,
                       cudaStream_t s) {
@@ -821,13 +829,19 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
     ST(ws_get(ctx, WS_SQIDX, static_cast<size_t>(n * ldw * 4), &widx));
     ST(ws_get(ctx, WS_SQVAL, static_cast<size_t>(n * ldw * 8), &wval));
     uint64_t* P[2] = {static_cast<uint64_t*>(pa), static_cast<uint64_t*>(pb)};
-    ST(to_packed(ctx, in, fmt, n, P[0], ldw, s));
+    // the first pass reads the caller's rows in place when they already have this layout (never written)
+    const uint64_t* R0 = in_place_packed(in, fmt, n, ldw);
+    if (R0 == nullptr) {
+        ST(to_packed(ctx, in, fmt, n, P[0], ldw, s));
+        R0 = P[0];
+    }
     auto* cost = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
     const double limit = tc_product_s(n_pad);
     ProductTimer tm{ctx, o.profile != 0, s, &ctx->stats.sparse_ms};
     int cur = 0;
     for (;;) {
-        CK(launch_wcsr_build(P[cur], n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+        const uint64_t* Rc = out->iters == 0 ? R0 : P[cur];
+        CK(launch_wcsr_build(Rc, n, ldw, static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
                              static_cast<uint64_t*>(wval), s, scan_scratch(ctx)),
            "word index build");
         CK(cudaMemsetAsync(cost, 0, 2 * sizeof(unsigned long long), s), "reset cost");
@@ -851,7 +865,7 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
         CK(cudaMemsetAsync(ctx->d_ctl + CTL_CHANGED, 0, sizeof(int), s), "reset flag");
         ST(tm.begin());
         CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx), static_cast<uint64_t*>(wval),
-                              P[cur], n, ldw, P[cur ^ 1], ctx->sm_count, s, ctx->d_ctl + CTL_CHANGED),
+                              Rc, n, ldw, P[cur ^ 1], ctx->sm_count, s, ctx->d_ctl + CTL_CHANGED),
            "squaring launch");
         ST(tm.end());
         ctx->stats.launches++;
@@ -1239,11 +1253,15 @@ static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt
     if (o.variant == BMLP_AUTO && dispatch_trained(ctx)) {
         // learned choice: features on the GPU, MLP prediction, argmin
         const int64_t ldw = round_up(words_of(n), 2);
-        void* P = nullptr;
-        ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
-        ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+        const uint64_t* Pin = in_place_packed(in, fmt, n, ldw);
+        if (Pin == nullptr) {
+            void* P = nullptr;
+            ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
+            ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+            Pin = static_cast<const uint64_t*>(P);
+        }
         int32_t choice = BMLP_RMS_TC;
-        ST(dispatch_choose_packed(ctx, static_cast<uint64_t*>(P), n, ldw, &choice, s));
+        ST(dispatch_choose_packed(ctx, Pin, n, ldw, &choice, s));
         variant = choice;
         ctx->stats.variant = variant;
     }
@@ -1898,10 +1916,14 @@ static bmlp_status core_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t 
     Operand in;
     ST(stage_in(ctx, R, fmt_bytes(fmt, n, n), WS_IN0, s, &in));
     const int64_t ldw = round_up(words_of(n), 2);
-    void* P = nullptr;
-    ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
-    ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
-    return dispatch_features_packed(ctx, static_cast<uint64_t*>(P), n, ldw, feats, s);
+    const uint64_t* Pin = in_place_packed(in, fmt, n, ldw);
+    if (Pin == nullptr) {
+        void* P = nullptr;
+        ST(ws_get(ctx, WS_FEAT, static_cast<size_t>(n * ldw * 8), &P));
+        ST(to_packed(ctx, in, fmt, n, static_cast<uint64_t*>(P), ldw, s));
+        Pin = static_cast<const uint64_t*>(P);
+    }
+    return dispatch_features_packed(ctx, Pin, n, ldw, feats, s);
 }
 
 bmlp_status bmlp_dispatch_train(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,
