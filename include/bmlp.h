@@ -458,6 +458,20 @@ bmlp_status bmlp_dispatch_train(bmlp_ctx* ctx, const float* feats, const float* 
  * null) for m host feature rows. */
 bmlp_status bmlp_dispatch_predict(bmlp_ctx* ctx, const float* feats, int64_t m, float* pred, int32_t* choice);
 
+/* The batched form of bmlp_dispatch_features + bmlp_dispatch_predict: for m
+ * matrices R[i] (n[i] x n[i], all in format fmt, each in device or host
+ * memory), choice (m host ints) receives the predicted fastest bmlp_variant
+ * and feats (m x 16 host floats, may be null) the features. The features of
+ * every matrix and one prediction over all of them run on the GPU in stream
+ * order, and the host waits once (bmlp_dispatch_features waits per matrix).
+ * Packed device rows with an even word count and 16-byte alignment are read
+ * in place; other matrices are converted into one workspace. Needs an active
+ * model (trained, loaded or set): else BMLP_ERR_UNSUPPORTED. Errors:
+ * BMLP_ERR_INVALID_ARG for m < 0, a null array with m > 0, a null R[i] or
+ * n[i] <= 0, or a bad format. */
+bmlp_status bmlp_dispatch_choose_many(bmlp_ctx* ctx, const void* const* R, const int64_t* n, int64_t m, int32_t fmt,
+                                      int32_t* choice, float* feats, cudaStream_t stream);
+
 /* Loss and gradient (BMLP_MLP_PARAMS floats) over m samples at the current
  * weights, computed by the training kernels' forward and backward code. */
 bmlp_status bmlp_dispatch_loss_grad(bmlp_ctx* ctx, const float* feats, const float* log2_ms, const uint8_t* censored,

@@ -138,6 +138,8 @@ def lib():
             L.bmlp_dispatch_features.argtypes = [vp, vp, i64, i32, fp, vp]
             L.bmlp_dispatch_train.argtypes = [vp, fp, fp, u8p, i64, ctypes.POINTER(bmlp_train_cfg), fp]
             L.bmlp_dispatch_predict.argtypes = [vp, fp, i64, fp, ctypes.POINTER(i32)]
+            L.bmlp_dispatch_choose_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i32,
+                                                    ctypes.POINTER(i32), fp, vp]
             L.bmlp_dispatch_loss_grad.argtypes = [vp, fp, fp, u8p, i64, fp, fp]
             L.bmlp_dispatch_set_params.argtypes = [vp, fp, fp, fp]
             L.bmlp_dispatch_get_params.argtypes = [vp, fp, fp, fp]
@@ -145,7 +147,8 @@ def lib():
             L.bmlp_dispatch_load.argtypes = [vp, ctypes.c_char_p]
             for name in ("bmlp_ctx_create", "bmlp_ctx_destroy", "bmlp_get_stats", "bmlp_rms", "bmlp_smp",
                          "bmlp_compose", "bmlp_batch_run", "bmlp_batch_autotune", "bmlp_dispatch_features",
-                         "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_loss_grad",
+                         "bmlp_dispatch_train", "bmlp_dispatch_predict", "bmlp_dispatch_choose_many",
+                         "bmlp_dispatch_loss_grad",
                          "bmlp_dispatch_set_params", "bmlp_dispatch_get_params", "bmlp_dispatch_save",
                          "bmlp_dispatch_load", "bmlp_transpose", "bmlp_union", "bmlp_negate", "bmlp_is_foreign",
                          "bmlp_mma_issue_rate", "bmlp_insert"):
@@ -316,6 +319,21 @@ class Context:
         self._check(self._L.bmlp_dispatch_features(self.handle, _ptr(R), int(n), int(fmt), _fptr(f),
                                                    _stream(stream, self.device)))
         return f
+
+    def dispatch_choose_many(self, mats, ns, fmt=BMLP_FMT_U8, stream=None, features=False):
+        """bmlp_dispatch_choose_many: the chosen bmlp_variant of each matrix (numpy int32, m), and with
+        features=True also their features (m x 16 float32); one host wait for all of them."""
+        import numpy as np
+        m = len(mats)
+        ptrs = (ctypes.c_void_p * max(m, 1))(*[_ptr(a).value for a in mats])
+        nn = (ctypes.c_int64 * max(m, 1))(*[int(x) for x in ns])
+        choice = np.zeros(max(m, 1), np.int32)
+        f = np.zeros((max(m, 1), BMLP_NFEAT), np.float32) if features else None
+        self._check(self._L.bmlp_dispatch_choose_many(self.handle, ptrs, nn, m, int(fmt),
+                                                      choice.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                      _fptr(f) if features else None,
+                                                      _stream(stream, self.device)))
+        return (choice[:m], f[:m]) if features else choice[:m]
 
     def dispatch_train(self, feats, log2_ms, censored, epochs=200, batch=256, lr=1e-3, weight_decay=1e-4, seed=0):
         """bmlp_dispatch_train on host arrays; returns the last epoch's loss."""

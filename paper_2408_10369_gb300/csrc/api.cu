@@ -2129,6 +2129,54 @@ bmlp_status bmlp_is_foreign(bmlp_ctx* ctx, const void* contains, const void* adj
     return e4m3_out_done(ctx, t, out, n, s);
 }
 
+bmlp_status bmlp_dispatch_choose_many(bmlp_ctx* ctx, const void* const* R, const int64_t* n, int64_t m, int32_t fmt,
+                                      int32_t* choice, float* feats, cudaStream_t s) {
+    if (!ctx) return BMLP_ERR_INVALID_ARG;
+    if (m < 0 || (m > 0 && (!R || !n || !choice))) return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad matrix list");
+    const bool e4m3 = fmt == BMLP_FMT_E4M3;
+    FMT_WRAP_CHECK(fmt);
+    if (!e4m3 && fmt != BMLP_FMT_U8 && fmt != BMLP_FMT_PACKED64)
+        return set_err(ctx, BMLP_ERR_INVALID_ARG, "bad format %d", fmt);
+    for (int64_t i = 0; i < m; ++i)
+        if (!R[i] || n[i] <= 0) return set_err(ctx, BMLP_ERR_INVALID_ARG, "matrix %lld: null or n <= 0", (long long)i);
+    DeviceGuard g(ctx->device);
+    if (!dispatch_trained(ctx)) return set_err(ctx, BMLP_ERR_UNSUPPORTED, "no dispatcher model (train, load or set one)");
+    if (m == 0) return BMLP_OK;
+    std::vector<const uint64_t*> P(static_cast<size_t>(m), nullptr);
+    std::vector<int64_t> ldw(static_cast<size_t>(m));
+    size_t need = 0;  // 64-bit words of the matrices that are converted
+    for (int64_t i = 0; i < m; ++i) {
+        ldw[i] = round_up(words_of(n[i]), 2);
+        if (!e4m3 && is_device_ptr(R[i])) P[i] = in_place_packed(Operand{R[i], false}, fmt, n[i], ldw[i]);
+        if (P[i] == nullptr) need += static_cast<size_t>(n[i] * ldw[i]);
+    }
+    uint64_t* buf = nullptr;
+    if (need > 0) {
+        void* b = nullptr;
+        ST(ws_get(ctx, WS_FEAT, need * 8, &b));
+        buf = static_cast<uint64_t*>(b);
+    }
+    // converted one after another in stream order, so the staging slots may be reused from one matrix to the next
+    size_t off = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (P[i] != nullptr) continue;
+        Operand in;
+        int32_t f = fmt;
+        if (e4m3) {
+            const void* r = nullptr;
+            ST(e4m3_in(ctx, R[i], n[i], WS_E8_IN0, s, &r));
+            in.dev = r;
+            f = BMLP_FMT_U8;
+        } else {
+            ST(stage_in(ctx, R[i], fmt_bytes(fmt, n[i], n[i]), WS_IN0, s, &in));
+        }
+        ST(to_packed(ctx, in, f, n[i], buf + off, ldw[i], s));
+        P[i] = buf + off;
+        off += static_cast<size_t>(n[i] * ldw[i]);
+    }
+    return dispatch_choose_many_packed(ctx, P.data(), n, ldw.data(), m, feats, choice, s);
+}
+
 bmlp_status bmlp_dispatch_features(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt, float* feats, cudaStream_t s) {
     FMT_WRAP_CHECK(fmt);
     if (fmt != BMLP_FMT_E4M3 || !ctx || n <= 0 || !R) return core_dispatch_features(ctx, R, n, fmt == BMLP_FMT_E4M3 ? BMLP_FMT_U8 : fmt, feats, s);

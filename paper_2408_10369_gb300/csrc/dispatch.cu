@@ -508,8 +508,10 @@ bmlp_status to_device(bmlp_ctx* ctx, const T* h, size_t count, T** out) {
 
 }  // namespace
 
-// The feature kernels of a device matrix in packed rows (n x ldw words): the 16 features land in d->d_feat.
-static bmlp_status launch_features(bmlp_ctx* ctx, Dispatch* d, const uint64_t* P, int64_t n, int64_t ldw, cudaStream_t s) {
+// The feature kernels of a device matrix in packed rows (n x ldw words): the 16 features land in dst (default
+// d->d_feat).
+static bmlp_status launch_features(bmlp_ctx* ctx, Dispatch* d, const uint64_t* P, int64_t n, int64_t ldw, cudaStream_t s,
+                                   float* dst = nullptr) {
     if (d->indeg_cap < n) {
         if (d->d_indeg) cudaFree(d->d_indeg);
         d->d_indeg = nullptr;
@@ -527,7 +529,7 @@ static bmlp_status launch_features(bmlp_ctx* ctx, Dispatch* d, const uint64_t* P
     int64_t b3 = (n + 255) / 256;
     if (b3 > ctx->sm_count * 8) b3 = ctx->sm_count * 8;
     feat_indeg_kernel<<<static_cast<int>(b3 < 1 ? 1 : b3), 256, 0, s>>>(d->d_indeg, n, d->d_acc);
-    feat_final_kernel<<<1, 1, 0, s>>>(d->d_acc, n, ns, d->d_feat);
+    feat_final_kernel<<<1, 1, 0, s>>>(d->d_acc, n, ns, dst != nullptr ? dst : d->d_feat);
     DCK(cudaGetLastError(), "feature kernels");
     ctx->stats.launches += 4;
     return BMLP_OK;
@@ -580,6 +582,35 @@ bmlp_status dispatch_choose_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, 
     DCK(cudaMemcpyAsync(&c, d->d_pc, sizeof(int), cudaMemcpyDeviceToHost, s), "read choice");
     DCK(host_sync(ctx, s), "synchronise choice");
     *choice = c + 1;  // bmlp_variant numbering
+    return BMLP_OK;
+}
+
+// Features and predictions for m device matrices in packed rows (P[i]: n[i] x ldw[i] words) with one host wait:
+// the features of matrix i land in row i of the prediction input, one predict launch covers all m rows, and the
+// choices (bmlp_variant numbering) and, if feat_host is not null, the features (m x 16) are read back together.
+bmlp_status dispatch_choose_many_packed(bmlp_ctx* ctx, const uint64_t* const* P, const int64_t* n, const int64_t* ldw,
+                                        int64_t m, float* feat_host, int32_t* choice, cudaStream_t s) {
+    Dispatch* d = nullptr;
+    bmlp_status st = dispatch_state(ctx, &d);
+    if (st != BMLP_OK) return st;
+    if (m <= 0) return BMLP_OK;
+    st = pred_buffers(ctx, d, m);
+    if (st != BMLP_OK) return st;
+    for (int64_t i = 0; i < m; ++i) {
+        st = launch_features(ctx, d, P[i], n[i], ldw[i], s, d->d_px + i * NF);
+        if (st != BMLP_OK) return st;
+    }
+    const int blocks = static_cast<int>((m + MLP_THREADS - 1) / MLP_THREADS);
+    mlp_predict_kernel<<<blocks, MLP_THREADS, 0, s>>>(d->d_w, d->d_norm, d->d_norm + NF, d->d_px, static_cast<int>(m),
+                                                      d->d_py, d->d_pc);
+    DCK(cudaGetLastError(), "predict kernel");
+    ctx->stats.launches++;
+    std::vector<int> c(m);
+    DCK(cudaMemcpyAsync(c.data(), d->d_pc, m * sizeof(int), cudaMemcpyDeviceToHost, s), "read choices");
+    if (feat_host)
+        DCK(cudaMemcpyAsync(feat_host, d->d_px, m * NF * sizeof(float), cudaMemcpyDeviceToHost, s), "read features");
+    DCK(host_sync(ctx, s), "synchronise choices");
+    for (int64_t i = 0; i < m; ++i) choice[i] = c[i] + 1;
     return BMLP_OK;
 }
 

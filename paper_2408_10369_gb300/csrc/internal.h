@@ -184,6 +184,8 @@ void batch_cache_free(bmlp_ctx* ctx);
 bmlp_status dispatch_features_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, float* feat_host,
                                      cudaStream_t s);
 // features and prediction on the device, one host wait: *choice = the predicted fastest bmlp_variant
+bmlp_status dispatch_choose_many_packed(bmlp_ctx* ctx, const uint64_t* const* P, const int64_t* n, const int64_t* ldw,
+                                        int64_t m, float* feat_host, int32_t* choice, cudaStream_t s);
 bmlp_status dispatch_choose_packed(bmlp_ctx* ctx, const uint64_t* P, int64_t n, int64_t ldw, int32_t* choice,
                                    cudaStream_t s);
 bool dispatch_trained(const bmlp_ctx* ctx);

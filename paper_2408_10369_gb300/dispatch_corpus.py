@@ -297,8 +297,8 @@ def live_pipeline(ctx, rows, n_max, return_outputs=False):
         o.zero_()
 
     def dispatched():
-        feats = np.stack([ctx.dispatch_features(P, g["n"], fmt=F) for g, P in graphs])
-        _, choice = ctx.dispatch_predict(feats)
+        # features and prediction for every graph with one host wait
+        choice = ctx.dispatch_choose_many([P for _, P in graphs], [g["n"] for g, _ in graphs], fmt=F)
         group = []
         for (g, P), o, c in zip(graphs, outs_b, choice):
             if c in (bmlp.BMLP_RMS_TC, bmlp.BMLP_RMS_PACKED, bmlp.BMLP_SMP_PACKED) and g["n"] <= GROUP_MAX_N:

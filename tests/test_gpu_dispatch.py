@@ -122,3 +122,50 @@ def test_dispatched_heldout_corpus_matches_oracle(ctx):
         got = o.cpu().numpy().view(np.uint64)
         for r0, blk in oracle.closure_bits_chunks(n, g["indptr"], g["indices"], 4096):
             np.testing.assert_array_equal(got[r0:r0 + blk.shape[0], :blk.shape[1]], blk)
+
+
+def test_choose_many_matches_single_calls(ctx):
+    """bmlp_dispatch_choose_many on 24 corpus graphs of mixed sizes and
+    formats (packed rows read in place, misaligned rows that are copied, u8
+    and host-memory inputs converted) gives the features and the choices of
+    bmlp_dispatch_features + bmlp_dispatch_predict, one matrix at a time; with
+    no model it refuses, and an empty list is a no-op."""
+    import os
+
+    from paper_2408_10369_gb300 import dispatch_corpus as dc
+    fresh = pkg.Context(0)
+    try:
+        with pytest.raises(bmlp.BmlpError) as e:
+            fresh.dispatch_choose_many([torch.zeros((64, 2), dtype=torch.int64, device="cuda")], [64],
+                                       fmt=bmlp.BMLP_FMT_PACKED64)
+        assert e.value.status == bmlp.BMLP_ERR_UNSUPPORTED
+    finally:
+        fresh.close()
+    ctx.dispatch_load(os.path.join(os.path.dirname(pkg.__file__), "dispatch_model.bin"))
+    assert len(ctx.dispatch_choose_many([], [], fmt=bmlp.BMLP_FMT_PACKED64)) == 0
+    graphs = [dc.graph_on_device(i, 8192) for i in range(9040, 9064)]
+    mats, ns = [], []
+    for k, (g, P) in enumerate(graphs):
+        n = g["n"]
+        if k % 4 == 1:      # the rows at an 8-byte but not 16-byte aligned address: converted, not read in place
+            w = P.shape[1]
+            flat = torch.zeros(n * w + 1, dtype=torch.int64, device="cuda")
+            Q = flat[1:].view(n, w)
+            Q.copy_(P)
+            mats.append(Q)
+        elif k % 4 == 2:    # host memory
+            mats.append(P.cpu())
+        else:
+            mats.append(P)
+        ns.append(n)
+    choice, feats = ctx.dispatch_choose_many(mats, ns, fmt=bmlp.BMLP_FMT_PACKED64, features=True)
+    single = np.stack([ctx.dispatch_features(P, g["n"], fmt=bmlp.BMLP_FMT_PACKED64) for g, P in graphs])
+    _, single_choice = ctx.dispatch_predict(single)
+    np.testing.assert_allclose(feats, single, rtol=1e-6, atol=1e-6)
+    np.testing.assert_array_equal(choice, single_choice)
+    # the same matrices as 0/1 bytes
+    u8 = [torch.from_numpy(wl.unpack_rows(P.cpu().numpy().view(np.uint64), g["n"]).astype(np.uint8)).cuda()
+          for g, P in graphs[:6]]
+    c8, f8 = ctx.dispatch_choose_many(u8, ns[:6], fmt=bmlp.BMLP_FMT_U8, features=True)
+    np.testing.assert_allclose(f8, single[:6], rtol=1e-6, atol=1e-6)
+    np.testing.assert_array_equal(c8, single_choice[:6])
