@@ -949,21 +949,26 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
        "word index build");
     ctx->stats.launches += 3;
     // nonzero words of R (W) and of R + R R (W2, counted from the word index of R without forming R + R R)
+    int64_t ones = -1;  // ones of the current R (with its word index), when a growth test has counted them
     auto growth = [&](int64_t* W, int64_t* W2) -> bmlp_status {
         auto* cnt = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_COST);
+        auto* bits = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_BITS);
         CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset counts");
+        CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s), "reset ones");
         CK(launch_square_growth(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
-                                static_cast<uint64_t*>(wval), n, ldw, cnt, ctx->sm_count, s),
+                                static_cast<uint64_t*>(wval), n, ldw, cnt, ctx->sm_count, s, bits),
            "squaring growth launch");
         CK(cudaMemcpyAsync(ctx->h_ctl + CTL_HOST_I64, static_cast<const int64_t*>(wptr) + n, sizeof(int64_t),
                            cudaMemcpyDeviceToHost, s),
            "read word count");
         ST(read_ctl(ctx, s, nullptr));
         ctx->stats.launches++;
-        unsigned long long w2 = 0;
+        unsigned long long w2 = 0, b = 0;
         memcpy(&w2, ctx->h_ctl + CTL_COST, sizeof(w2));
+        memcpy(&b, ctx->h_ctl + CTL_BITS, sizeof(b));
         memcpy(W, ctx->h_ctl + CTL_HOST_I64, sizeof(int64_t));
         *W2 = static_cast<int64_t>(w2);
+        ones = static_cast<int64_t>(b);
         return BMLP_OK;
     };
     bool dense_reach = false;
@@ -997,6 +1002,7 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
             std::swap(wptr, wptr2);
             std::swap(widx, widx2);
             std::swap(wval, wval2);
+            ones = -1;  // counted for the R before this squaring
             ctx->stats.frontier_squarings++;
         }
     }
@@ -1013,7 +1019,16 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     ST(ws_get(ctx, WS_WPTRT, static_cast<size_t>((n + 2) * 8), &wptrT));
     ST(ws_get(ctx, WS_WIDXT, static_cast<size_t>(n * ldw * 4), &widxT));
     ST(ws_get(ctx, WS_WVALT, static_cast<size_t>(n * ldw * 8), &wvalT));
-    CK(launch_bit_transpose(static_cast<uint64_t*>(P), static_cast<uint64_t*>(PT), n, ldw, s), "bit transpose");
+    if (ones >= 0 && ones * 16 <= n * ldw) {
+        // few ones: R^T scattered from R's word index (clearing n x ldw words and one atomic OR per one) instead
+        // of reading and writing every word
+        CK(launch_scatter_transpose(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
+                                    static_cast<uint64_t*>(wval), n, ldw, static_cast<uint64_t*>(PT), ctx->sm_count,
+                                    s),
+           "scatter transpose");
+    } else {
+        CK(launch_bit_transpose(static_cast<uint64_t*>(P), static_cast<uint64_t*>(PT), n, ldw, s), "bit transpose");
+    }
     CK(launch_wcsr_build(static_cast<uint64_t*>(PT), n, ldw, static_cast<int64_t*>(wptrT),
                          static_cast<int32_t*>(widxT), static_cast<uint64_t*>(wvalT), s, scan_scratch(ctx)),
        "transposed word index build");

@@ -151,11 +151,11 @@ struct bmlp_ctx {
 
 namespace bmlp {
 
-// CTL_QCOUNT, CTL_T0 and CTL_ISSUED are 64-bit words, CTL_COST two of them and CTL_THIN eight (two ints each,
-// 8-byte aligned).
+// CTL_QCOUNT, CTL_T0, CTL_ISSUED and CTL_BITS are 64-bit words, CTL_COST two of them and CTL_THIN eight (two ints
+// each, 8-byte aligned).
 enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
-    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_WORDS = 32
+    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_BITS = 32, CTL_WORDS = 34
 };
 // The pinned host mirror has two more ints: CTL_HOST_I64 is a 64-bit slot for values read from elsewhere.
 constexpr int CTL_HOST_I64 = CTL_WORDS;
@@ -341,9 +341,16 @@ cudaError_t launch_thin_squaring(uint64_t* P, uint64_t* PT, int64_t ldw, const i
                                  const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2, uint8_t* Q,
                                  uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);
 // nonzero words of R + R R (out[0] += their total) and the word ORs of that squaring (out[1] += their total), from
-// the word index of R (ldw words per row, at most 49,152), without forming R + R R
+// the word index of R (ldw words per row, at most 49,152), without forming R + R R; bits_out (if not null) += the
+// ones of R
 cudaError_t launch_square_growth(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
-                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s);
+                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s,
+                                 unsigned long long* bits_out = nullptr);
+// R^T's bit rows (n x ldw words) from R's word index: cleared, then every set bit (i, j) of R sets bit i of row j
+// by a 64-bit atomic OR. Work in proportion to the ones of R, against n x ldw words read and written by
+// launch_bit_transpose.
+cudaError_t launch_scatter_transpose(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                                     int64_t ldw, uint64_t* out, int sms, cudaStream_t s);
 // word ORs of the next squaring step (sum over the set bits k of a row of the nonzero words of row k):
 // cost[0] += their total over all rows, cost[1] = max(cost[1], the largest row's)
 cudaError_t launch_square_cost(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,

@@ -932,13 +932,14 @@ __global__ void __launch_bounds__(256) square_cost_kernel(const int64_t* __restr
 __global__ void __launch_bounds__(256) square_growth_kernel(const int64_t* __restrict__ wptr,
                                                             const int32_t* __restrict__ widx,
                                                             const uint64_t* __restrict__ wval, int64_t n, int64_t ldw,
-                                                            unsigned long long* __restrict__ out) {
+                                                            unsigned long long* __restrict__ out,
+                                                            unsigned long long* __restrict__ bits_out) {
     extern __shared__ uint32_t growth_bm[];
     const int lane = threadIdx.x & 31;
     const int bw = static_cast<int>((ldw + 31) / 32);  // bitmap words per warp
     uint32_t* bm = growth_bm + (threadIdx.x >> 5) * bw;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-    unsigned long long words = 0, ors = 0;
+    unsigned long long words = 0, ors = 0, ones = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         for (int j = lane; j < bw; j += 32) bm[j] = 0u;
         __syncwarp();
@@ -947,6 +948,7 @@ __global__ void __launch_bounds__(256) square_growth_kernel(const int64_t* __res
             const int x = widx[e];
             atomicOr(&bm[x >> 5], 1u << (x & 31));
             uint64_t d = wval[e];
+            ones += static_cast<unsigned long long>(__popcll(d));
             const int64_t base = static_cast<int64_t>(x) << 6;
             while (d) {
                 const int64_t k = base + (__ffsll(static_cast<long long>(d)) - 1);
@@ -966,10 +968,37 @@ __global__ void __launch_bounds__(256) square_growth_kernel(const int64_t* __res
     for (int off = 16; off > 0; off >>= 1) {
         words += __shfl_xor_sync(FULL, words, off);
         ors += __shfl_xor_sync(FULL, ors, off);
+        ones += __shfl_xor_sync(FULL, ones, off);
     }
     if (lane == 0 && (words | ors) != 0ull) {
         atomicAdd(out, words);
         atomicAdd(out + 1, ors);
+    }
+    if (lane == 0 && bits_out != nullptr && ones != 0ull) atomicAdd(bits_out, ones);
+}
+
+// Bit rows of R^T from the word index of R (out cleared beforehand): warp per row i of R, a lane per nonzero word;
+// each set bit (i, j) ORs bit i into word i / 64 of row j. Rows i of one 64-row group hit the same words of R^T,
+// on different bits.
+__global__ void __launch_bounds__(256) scatter_transpose_kernel(const int64_t* __restrict__ wptr,
+                                                                const int32_t* __restrict__ widx,
+                                                                const uint64_t* __restrict__ wval, int64_t n,
+                                                                int64_t ldw, unsigned long long* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const unsigned long long bit = 1ull << (i & 63);
+        const int64_t wi = i >> 6;
+        const int64_t e1 = wptr[i + 1];
+        for (int64_t e = wptr[i] + lane; e < e1; e += 32) {
+            uint64_t d = wval[e];
+            const int64_t base = static_cast<int64_t>(widx[e]) << 6;
+            while (d) {
+                const int64_t j = base + (__ffsll(static_cast<long long>(d)) - 1);
+                d &= d - 1ull;
+                if (j < n) atomicOr(out + j * ldw + wi, bit);  // a caller's bits beyond column n are not columns
+            }
+        }
     }
 }
 
@@ -1463,10 +1492,21 @@ cudaError_t launch_smp_cluster(const int64_t* wptrT, const int32_t* widxT, const
 }
 
 cudaError_t launch_square_growth(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
-                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s) {
+                                 int64_t ldw, unsigned long long* out, int sms, cudaStream_t s,
+                                 unsigned long long* bits_out) {
     const size_t smem = static_cast<size_t>(8) * ((ldw + 31) / 32) * 4;
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
-    square_growth_kernel<<<warps_grid(n, sms), 256, smem, s>>>(wptr, widx, wval, n, ldw, out);
+    square_growth_kernel<<<warps_grid(n, sms), 256, smem, s>>>(wptr, widx, wval, n, ldw, out, bits_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_transpose(const int64_t* wptr, const int32_t* widx, const uint64_t* wval, int64_t n,
+                                     int64_t ldw, uint64_t* out, int sms, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(n) * static_cast<size_t>(ldw) * 8, s);
+    if (e != cudaSuccess) return e;
+    scatter_transpose_kernel<<<warps_grid(n, sms), 256, 0, s>>>(wptr, widx, wval, n, ldw,
+                                                                reinterpret_cast<unsigned long long*>(out));
     return cudaGetLastError();
 }
 
