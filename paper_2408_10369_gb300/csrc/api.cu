@@ -719,10 +719,11 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
 }
 
-// The caller's rows themselves when they are packed bit rows on the device with ldw words per row (words_of(n) even)
+// The caller's rows themselves when they are packed bit rows on the device with ldw words per row (words_of(n) even),
+// no padding bits (n a multiple of 64: a caller's bits at columns >= n are to be ignored, and the copy clears them)
 // and 16-byte aligned, so that a read-only pass can use them without a copy; else null.
 const uint64_t* in_place_packed(const Operand& in, int32_t fmt, int64_t n, int64_t ldw) {
-    if (fmt != BMLP_FMT_PACKED64 || in.host || words_of(n) != ldw) return nullptr;
+    if (fmt != BMLP_FMT_PACKED64 || in.host || words_of(n) != ldw || n % 64 != 0) return nullptr;
     if ((reinterpret_cast<uintptr_t>(in.dev) & 15) != 0) return nullptr;
     return static_cast<const uint64_t*>(in.dev);
 }
@@ -937,8 +938,9 @@ bmlp_status smp_packed_run(bmlp_ctx* ctx, const Operand& R, int32_t fmt, int64_t
     ST(ws_get(ctx, WS_WPTR, static_cast<size_t>((n + 2) * 8), &wptr));
     ST(ws_get(ctx, WS_WIDX, static_cast<size_t>(n * ldw * 4), &widx));
     ST(ws_get(ctx, WS_WVAL, static_cast<size_t>(n * ldw * 8), &wval));
-    if (!square_first && fmt == BMLP_FMT_PACKED64 && words_of(n) == ldw) {
-        // query rows: R is only read, so packed rows of the working width are used where they are
+    if (!square_first && fmt == BMLP_FMT_PACKED64 && words_of(n) == ldw && n % 64 == 0) {
+        // query rows: R is only read, so packed rows of the working width without padding bits are used where
+        // they are
         P = const_cast<void*>(R.dev);
     } else {
         ST(ws_get(ctx, WS_M0, static_cast<size_t>(n * ldw * 8), &P));

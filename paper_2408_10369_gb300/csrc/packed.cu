@@ -126,6 +126,15 @@ __global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __r
 }
 
 // ---- word-CSR of packed rows
+// Word x of a row of an n x n matrix with its bits at columns >= n cleared (a caller's padding bits are not
+// columns; words past ceil(n / 64) are padding too).
+__device__ __forceinline__ uint64_t wcsr_columns(uint64_t w, int64_t x, int64_t n) {
+    const int64_t nw = (n + 63) >> 6;
+    if (x < nw - 1) return w;
+    if (x > nw - 1) return 0ull;
+    return (n & 63) ? (w & ((1ull << (n & 63)) - 1ull)) : w;
+}
+
 // Rows warp_id, warp_id + nwarps, ... of P: their counts of nonzero words into wptr[i + 1].
 __device__ __forceinline__ void wcsr_count_rows(const uint64_t* __restrict__ P, int64_t n, int64_t ldw,
                                                 int64_t* __restrict__ wptr, int64_t warp_id, int64_t nwarps,
@@ -139,10 +148,11 @@ __device__ __forceinline__ void wcsr_count_rows(const uint64_t* __restrict__ P, 
 #pragma unroll
             for (int k = 0; k < 4; ++k) w[k] = row[wb + 32 * k + lane];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) c += __popc(__ballot_sync(FULL, w[k] != 0ull));
+            for (int k = 0; k < 4; ++k)
+                c += __popc(__ballot_sync(FULL, wcsr_columns(w[k], wb + 32 * k + lane, n) != 0ull));
         }
         for (; wb < ldw; wb += 32) {
-            const uint64_t w = (wb + lane < ldw) ? row[wb + lane] : 0ull;
+            const uint64_t w = (wb + lane < ldw) ? wcsr_columns(row[wb + lane], wb + lane, n) : 0ull;
             c += __popc(__ballot_sync(FULL, w != 0ull));
         }
         if (lane == 0) wptr[i + 1] = c;
@@ -312,6 +322,8 @@ __device__ __forceinline__ void wcsr_fill_rows(const uint64_t* __restrict__ P, i
 #pragma unroll
             for (int k = 0; k < 4; ++k) w[k] = row[wb + 32 * k + lane];
 #pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = wcsr_columns(w[k], wb + 32 * k + lane, n);
+#pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const unsigned m = __ballot_sync(FULL, w[k] != 0ull);
                 if (w[k]) {
@@ -323,7 +335,7 @@ __device__ __forceinline__ void wcsr_fill_rows(const uint64_t* __restrict__ P, i
             }
         }
         for (; wb < ldw; wb += 32) {
-            const uint64_t w = (wb + lane < ldw) ? row[wb + lane] : 0ull;
+            const uint64_t w = (wb + lane < ldw) ? wcsr_columns(row[wb + lane], wb + lane, n) : 0ull;
             const unsigned m = __ballot_sync(FULL, w != 0ull);
             if (w) {
                 const int64_t at = o + __popc(m & below);
