@@ -818,7 +818,6 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
     const int64_t np_max = round_up(nmax, TC_PAD);
     const size_t pk = static_cast<size_t>(nmax * ldw_max * 8);
     const size_t q = static_cast<size_t>(np_max * np_max / 2);
-    const size_t e8 = static_cast<size_t>(np_max * np_max);
     size_t total = 0;
     auto take = [&](size_t bytes) {
         size_t o = total;
@@ -832,13 +831,8 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
         oQ[k] = take(q);
         oQT[k] = take(q);
     }
-    size_t oM0 = 0, oM1 = 0, oT1 = 0, oX = 0;
-    if (any_compose) {
-        oM0 = take(e8);
-        oM1 = take(e8);
-        oT1 = take(e8);
-        oX = take(e8);
-    }
+    size_t oM0 = 0;
+    if (any_compose) oM0 = take(q);  // a composition's final product: scratch for the transposed output
     void* base = nullptr;
     BST(ws_get(ctx, WS_SOLO, total, &base));
     uint8_t* b8 = static_cast<uint8_t*>(base);
@@ -850,9 +844,6 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
     uint8_t* Q[2] = {b8 + oQ[0], b8 + oQ[1]};
     uint8_t* QT[2] = {b8 + oQT[0], b8 + oQT[1]};
     uint8_t* M0 = b8 + oM0;
-    uint8_t* M1 = b8 + oM1;
-    uint8_t* T1 = b8 + oT1;
-    uint8_t* X = b8 + oX;
     BCK(cudaMalloc(&c->d_solo, sizeof(int) * SW_WORDS * ns), "cudaMalloc(large-problem state)");
     BCK(cudaMemset(c->d_solo, 0, sizeof(int) * SW_WORDS * ns), "clear large-problem state");
     c->h_solo.assign(static_cast<size_t>(SW_WORDS * ns), 0);
@@ -982,33 +973,36 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
             else
                 launch_e2m1_to_packed(Q[0], ld4, n, static_cast<uint64_t*>(p.out), (n + 63) / 64, p.reflexive, cs);
         } else {
-            // out = (I + R2+) R1 on E4M3 operands: A = I + R2+, B^T = R1^T
-            launch_e2m1_to_e4m3(Q[0], M0, n_pad * n_pad, cs);
-            launch_set_diag_e4m3(M0, n_pad, n, cs);
+            // out = (I + R2+) R1 on 4-bit operands, on the squaring kernel: A = I + R2+ (Q[0], diagonal set),
+            // B^T = R1^T (encoded with R1 into the free pair Q[1], QT[1]), and a zero "old R" (QT[0]), so that the
+            // kernel's R' is C > 0; R' goes to Q[1] (R1 is no longer needed), R'^T to the scratch
+            launch_set_diag_e2m1(Q[0], ld4, n, cs);
             if (p.fmt == BMLP_FMT_U8)
-                launch_u8_to_e4m3(static_cast<const uint8_t*>(p.R1), n, M1, T1, n_pad, cs);
+                launch_u8_to_e2m1(static_cast<const uint8_t*>(p.R1), n, Q[1], QT[1], n_pad, cs);
             else
-                launch_packed_to_e4m3(static_cast<const uint64_t*>(p.R1), (n + 63) / 64, n, n, M1, T1, n_pad, n_pad,
-                                      cs);
-            CUtensorMap fa, fb;
-            SST(make_tmap(ctx, &fa, M0, n_pad, n_pad, n_pad, TC_BM));
-            SST(make_tmap(ctx, &fb, T1, n_pad, n_pad, n_pad, TC_BN));
+                launch_packed_to_e2m1(static_cast<const uint64_t*>(p.R1), (n + 63) / 64, n, Q[1], QT[1], n_pad, cs);
+            SCK(cudaMemsetAsync(QT[0], 0, static_cast<size_t>(n_pad) * static_cast<size_t>(ld4), cs), "clear old R");
+            CUtensorMap fa, fb0, fb1;
+            SST(make_tmap(ctx, &fa, Q[0], n_pad, ld4, ld4, TC_BM));
+            SST(make_tmap(ctx, &fb0, QT[1], n_pad, ld4, ld4, TC_BN / 2));
+            SST(make_tmap(ctx, &fb1, QT[1], n_pad, ld4, ld4, tc4_b1_rows()));
             TcParams pp{};
             pp.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
-            pp.n_tiles = static_cast<int32_t>(n_pad / TC_BN);
-            pp.k_blocks = static_cast<int32_t>(n_pad / TC_BK);
-            pp.mode = TC_MODE_PLAIN;
-            pp.ld = n_pad;
-            pp.out_r = X;
+            pp.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
+            pp.k_blocks = static_cast<int32_t>(n_pad / 256);
+            pp.mode = TC_MODE_RMS;
+            pp.ld = ld4;
+            pp.old_r = QT[0];
+            pp.out_r = Q[1];
+            pp.out_rt = M0;
             pp.changed = w + SW_CHANGED;
             pp.error = ctx->d_ctl + CTL_ERROR;
             pp.wait_cycles = wait_cycles;
-            const int tiles = pp.m_tiles * pp.n_tiles;
-            SCK(launch_tc_product(fa, fb, pp, tiles < sms ? tiles : sms, cs), "final product");
+            SCK(launch_tc4_product_duo(fa, fb0, fb1, pp, sms, cs), "final product");
             if (p.fmt == BMLP_FMT_U8)
-                launch_bytes_to_u8(X, n_pad, n, static_cast<uint8_t*>(p.out), 0, cs);
+                launch_e2m1_to_u8(Q[1], ld4, n, static_cast<uint8_t*>(p.out), 0, cs);
             else
-                launch_bytes_to_packed(X, n_pad, n, n, static_cast<uint64_t*>(p.out), (n + 63) / 64, 0, cs);
+                launch_e2m1_to_packed(Q[1], ld4, n, static_cast<uint64_t*>(p.out), (n + 63) / 64, 0, cs);
         }
         SCK(cudaGetLastError(), "large-problem launches");
     }

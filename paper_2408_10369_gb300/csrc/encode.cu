@@ -421,6 +421,13 @@ __global__ void negate_restrict_kernel(const uint64_t* __restrict__ in, int64_t 
     }
 }
 
+// Entry (i, i) of a packed E2M1 matrix (ld bytes per row) set to one for i < n: nibble i & 1 of byte i / 2 of row i
+// (each row's byte is written by one thread).
+__global__ void set_diag_e2m1_kernel(uint8_t* Q, int64_t ld, int64_t n) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) Q[i * ld + (i >> 1)] |= static_cast<uint8_t>((i & 1) ? 0x20 : 0x02);
+}
+
 __global__ void set_diag_kernel(uint8_t* R, int64_t ld, int64_t n) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -542,6 +549,10 @@ void launch_packed_negate(const uint64_t* in, int64_t ldw_in, int64_t n, const u
 
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s) {
     set_diag_kernel<<<grid_for(n, 256), 256, 0, s>>>(R, ld, n);
+}
+
+void launch_set_diag_e2m1(uint8_t* Q, int64_t ld4, int64_t n, cudaStream_t s) {
+    set_diag_e2m1_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(Q, ld4, n);
 }
 
 void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t n_pad, uint8_t* flags,

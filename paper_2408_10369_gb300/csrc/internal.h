@@ -249,6 +249,7 @@ void launch_e4m3_bytes_to_01(uint8_t* p, int64_t bytes, cudaStream_t s);
 void launch_01_to_e4m3_bytes(uint8_t* p, int64_t bytes, cudaStream_t s);
 // set the diagonal of an n x n byte matrix (ld) to E4M3 one
 void launch_set_diag_e4m3(uint8_t* R, int64_t ld, int64_t n, cudaStream_t s);
+void launch_set_diag_e2m1(uint8_t* Q, int64_t ld4, int64_t n, cudaStream_t s);
 // per (M block, K block) nonzero flags of a byte matrix rows_pad x n_pad
 // (row stride of flags: flags_ld, default n_pad / 128)
 void launch_block_flags(const uint8_t* A, int64_t ld, int64_t rows_pad, int64_t n_pad, uint8_t* flags,
