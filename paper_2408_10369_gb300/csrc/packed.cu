@@ -1061,26 +1061,59 @@ __global__ void __launch_bounds__(kSlicedThreads) smp_sliced_kernel(const int64_
             if (tid == 0 && dl.budget_ns) stop = dl.past() ? 1 : 0;
             if (__syncthreads_or(stop)) break;
             uint64_t grown = 0ull;
-            for (int64_t w = tid; w < n; w += blockDim.x) {
-                const uint64_t vw = V[w];
-                const uint64_t need = act & ~vw;  // active sources that have not reached w
-                uint64_t acc = 0ull;
-                if (need) {
-                    const int64_t e1 = wptrT[w + 1];
-                    for (int64_t e = wptrT[w]; e < e1 && (acc & need) != need; ++e) {
-                        uint64_t bits = wvalT[e];
-                        const int64_t base = static_cast<int64_t>(widxT[e]) << 6;
-                        while (bits) {
-                            const int64_t v = base + (__ffsll(static_cast<long long>(bits)) - 1);
-                            bits &= bits - 1ull;
-                            acc |= D[v];
+            // two constants per thread at a time, w and w + blockDim.x, whose in-lists are walked in lockstep so
+            // that their chains of dependent loads (row range, in-word, frontier words) overlap
+            const int64_t stride = blockDim.x;
+            for (int64_t wa = tid; wa < n; wa += 2 * stride) {
+                const int64_t wb = wa + stride;
+                const bool hb = wb < n;
+                const uint64_t va = V[wa];
+                const uint64_t vb = hb ? V[wb] : ~0ull;
+                const uint64_t needa = act & ~va;  // active sources that have not reached the constant
+                const uint64_t needb = act & ~vb;
+                uint64_t acca = 0ull, accb = 0ull;
+                int64_t ea = 0, ea1 = 0, eb = 0, eb1 = 0;
+                if (needa) {
+                    ea = wptrT[wa];
+                    ea1 = wptrT[wa + 1];
+                }
+                if (needb) {
+                    eb = wptrT[wb];
+                    eb1 = wptrT[wb + 1];
+                }
+                while (true) {
+                    const bool ta = ea < ea1 && (acca & needa) != needa;
+                    const bool tb = eb < eb1 && (accb & needb) != needb;
+                    if (!ta && !tb) break;
+                    uint64_t ba = ta ? wvalT[ea] : 0ull;
+                    uint64_t bb = tb ? wvalT[eb] : 0ull;
+                    const int64_t basea = ta ? static_cast<int64_t>(widxT[ea]) << 6 : 0;
+                    const int64_t baseb = tb ? static_cast<int64_t>(widxT[eb]) << 6 : 0;
+                    while (ba | bb) {
+                        if (ba) {
+                            const int64_t v = basea + (__ffsll(static_cast<long long>(ba)) - 1);
+                            ba &= ba - 1ull;
+                            acca |= D[v];
+                        }
+                        if (bb) {
+                            const int64_t v = baseb + (__ffsll(static_cast<long long>(bb)) - 1);
+                            bb &= bb - 1ull;
+                            accb |= D[v];
                         }
                     }
+                    ea += ta ? 1 : 0;
+                    eb += tb ? 1 : 0;
                 }
-                const uint64_t nn = acc & need;
-                Dn[w] = nn;
-                if (nn) V[w] = vw | nn;
-                grown |= nn;
+                const uint64_t nna = acca & needa;
+                Dn[wa] = nna;
+                if (nna) V[wa] = va | nna;
+                grown |= nna;
+                if (hb) {
+                    const uint64_t nnb = accb & needb;
+                    Dn[wb] = nnb;
+                    if (nnb) V[wb] = vb | nnb;
+                    grown |= nnb;
+                }
             }
             const unsigned glo = __reduce_or_sync(FULL, static_cast<unsigned>(grown));
             const unsigned ghi = __reduce_or_sync(FULL, static_cast<unsigned>(grown >> 32));
