@@ -398,8 +398,12 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
     t, kern = packed_step(dense8k, 8192)
     bits = int(np.unpackbits(dense8k.cpu().numpy().view(np.uint8)).sum())
     ors = float(bits) * (8192 // 64)
+    # each one of R reads one row of R (8,192 bits) through L2 while the rows are ORed: that read rate, not the ALU,
+    # bounds this dense product
+    l2_bytes = float(bits) * (8192 // 8)
     pk["n8192_dense"] = {"ms": t * 1e3, "ones": bits, "kernel": kern, "word_or_tera_per_s": ors / t / 1e12,
-                         "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"]}
+                         "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"],
+                         "l2_row_bytes": l2_bytes, "l2_row_read_tbs": l2_bytes / t / 1e12}
     del dense8k
     ex["packed_product"] = pk
 
