@@ -2211,4 +2211,9 @@ double bitrow_s_per_word() { return sparse_s_per_word(); }
 double bitrow_row_s_per_word() { return sparse_row_s_per_word(); }
 double bitrow_step_s() { return kSparseStepS; }
 double tc4_product_s(int64_t n_pad) { return tc_product_s(n_pad); }
+// The restricted squaring's fixed cost, switch, sampled rows and row-count spread, for the device-driven pipelines.
+double thin_fixed_seconds(int64_t n_pad) { return thin_fixed_s(n_pad); }
+bool thin_is_enabled() { return thin_enabled(); }
+int thin_sample_rows() { return kThinSampleRows; }
+double thin_row_spread() { return kThinRowSpread; }
 }  // namespace bmlp

@@ -324,16 +324,22 @@ __global__ void __launch_bounds__(256) batch_decode_kernel(const GroupProblem* p
 }
 
 // ------------------------------------------- device-driven large problems --
-// Control words of one large problem (ints; the two 64-bit cost words at SW_COST).
+// Control words of one large problem (ints; 64-bit words at SW_COST, SW_SMP and SW_TSTAT, 8-byte aligned).
 enum SoloWord : int {
-    SW_ITERS = 0,    // squarings issued so far
-    SW_NOTDONE = 1,  // 1 while the closure is not finished on bit rows
-    SW_NOTCONV = 2,  // stopped at the cap while still changing
-    SW_CHANGED = 3,  // set by the squaring kernels
-    SW_GC = 4,       // guard of the first tensor-core product of a loop iteration
-    SW_G1 = 5,       // guard of the second
-    SW_COST = 8,     // word ORs of the next bit-row squaring: total, largest row (2 x u64)
-    SW_WORDS = 16
+    SW_ITERS = 0,     // squarings issued so far
+    SW_NOTDONE = 1,   // 1 while the closure is not finished on bit rows
+    SW_NOTCONV = 2,   // stopped at the cap while still changing
+    SW_CHANGED = 3,   // set by the squaring kernels
+    SW_GC = 4,        // guard of the first tensor-core product of a loop iteration
+    SW_G1 = 5,        // guard of the second
+    SW_TCHANGED = 6,  // set by a restricted squaring that found new ones
+    SW_RES = 7,       // 1: a restricted squaring left the closure in Q1 (else Q0 holds it)
+    SW_COST = 8,      // word ORs of the next bit-row squaring: total, largest row (2 x u64)
+    SW_THIN_GO = 12,  // the restricted squaring is cheaper than a product (set inside its statistics' IF)
+    SW_STOP = 13,     // a restricted squaring ended the loop
+    SW_SMP = 16,      // the row sample after a product (2 x u64, thin.cu)
+    SW_TSTAT = 20,    // the restricted squaring's statistics (6 x u64, thin.cu)
+    SW_WORDS = 32
 };
 
 // dst = src, 16 bytes per thread and step (sizes are multiples of 16 bytes).
@@ -403,6 +409,69 @@ __global__ void solo_tc_decide_kernel(int* w, int cap, int half, cudaGraphCondit
         if (!go) w[SW_GC] = 0;
         cudaGraphSetConditional(h, go ? 1u : 0u);
     }
+}
+
+// After tensor-core product `half` (its R in Q[half ^ 1]): whether the next squaring may run only on the rows and
+// columns of R that still hold zeros. Only while the loop goes on (the next product's guard is set) and when the
+// sampled rows that reach at least n / 2 constants agree in count within spread x n; the sample is cleared for the
+// next product. The statistics' IF reads hT; the squaring's IF stays off until they say it is cheaper.
+__global__ void solo_thin_gate_kernel(int* w, int half, int64_t n, double spread, cudaGraphConditionalHandle hT) {
+    unsigned long long* sm = reinterpret_cast<unsigned long long*>(w + SW_SMP);
+    const int next = half == 0 ? w[SW_G1] : w[SW_GC];
+    const double sp = static_cast<double>(sm[0]) - (static_cast<double>(n) - static_cast<double>(sm[1]));
+    const bool go = next != 0 && sm[0] > 0 && sp <= spread * static_cast<double>(n);
+    sm[0] = 0;
+    sm[1] = 0;
+    w[SW_THIN_GO] = 0;
+    cudaGraphSetConditional(hT, go ? 1u : 0u);
+}
+
+// Inside the statistics' IF: the restricted squaring's cost by the bit-row model (the word ORs over the GPU, or one
+// warp's heaviest list entry) against a tensor-core product, as on the host loop.
+__global__ void solo_thin_decide_kernel(int* w, int64_t ldw, double fixed_s, double s_word, double s_row, double limit) {
+    const unsigned long long* st = reinterpret_cast<const unsigned long long*>(w + SW_TSTAT);
+    const double words = static_cast<double>(st[2] + st[3]) * static_cast<double>(ldw);
+    const double row_words = static_cast<double>(st[4] > st[5] ? st[4] : st[5]) * static_cast<double>(ldw);
+    const double t = fixed_s + fmax(words * s_word, row_words * s_row);
+    w[SW_THIN_GO] = t < limit ? 1 : 0;
+    w[SW_TCHANGED] = 0;
+}
+
+__global__ void solo_thin_arm_kernel(const int* w, cudaGraphConditionalHandle hT2) {
+    cudaGraphSetConditional(hT2, w[SW_THIN_GO] ? 1u : 0u);
+}
+
+// After a restricted squaring that followed product `half` (R in Q[half ^ 1], updated in place): one more squaring
+// counted; if it changed nothing that buffer holds the closure, and at the cap while changing the loop stops
+// unconverged; either way the guards go off and the loop-control kernel ends the loop.
+__global__ void solo_thin_post_kernel(int* w, int half, int cap) {
+    w[SW_ITERS] += 1;
+    bool stop = false;
+    if (!w[SW_TCHANGED]) {
+        stop = true;
+    } else if (w[SW_ITERS] >= cap) {
+        w[SW_NOTCONV] = 1;
+        stop = true;
+    }
+    if (stop) {
+        w[SW_RES] = half ^ 1;
+        w[SW_GC] = 0;
+        w[SW_G1] = 0;
+        w[SW_STOP] = 1;
+    }
+    w[SW_THIN_GO] = 0;
+}
+
+__global__ void solo_loop_ctl_kernel(const int* w, cudaGraphConditionalHandle hC) {
+    if (w[SW_STOP]) cudaGraphSetConditional(hC, 0u);
+}
+
+// After the tensor-core loop: the closure into Q0 when a restricted squaring left it in Q1 (16 bytes per thread).
+__global__ void solo_result_copy_kernel(const int* w, uint4* __restrict__ q0, const uint4* __restrict__ q1, int64_t n16) {
+    if (w[SW_RES] != 1) return;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n16;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        q0[i] = q1[i];
 }
 
 // --------------------------------------------------------------- host --
@@ -784,7 +853,8 @@ bmlp_status build_batch(bmlp_ctx* ctx, const bmlp_problem* probs, int64_t count,
 
 // Adds a conditional WHILE node after the current capture dependencies of `cs` and returns its body graph; the
 // capture of `cs` continues after the node.
-bmlp_status add_while(bmlp_ctx* ctx, cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+bmlp_status add_conditional(bmlp_ctx* ctx, cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            cudaGraph_t* body) {
     cudaStreamCaptureStatus st;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -793,14 +863,18 @@ bmlp_status add_while(bmlp_ctx* ctx, cudaStream_t cs, cudaGraphConditionalHandle
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.type = type;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    BCK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp), "while node");
+    BCK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp), "conditional node");
     BCK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
         "capture dependencies");
     *body = cp.conditional.phGraph_out[0];
     return BMLP_OK;
+}
+
+bmlp_status add_while(bmlp_ctx* ctx, cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    return add_conditional(ctx, cs, h, cudaGraphCondTypeWhile, body);
 }
 
 // The large problems as device-driven single-problem pipelines, one after another (they share one scratch sized
@@ -833,6 +907,18 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
     }
     size_t oM0 = 0;
     if (any_compose) oM0 = take(q);  // a composition's final product: scratch for the transposed output
+    // the squaring restricted to the rows and columns holding zeros: bit rows of R and R^T (written by the 4-bit
+    // squarings' epilogue), its computed rows, and its counts and lists
+    const bool thin_any = thin_is_enabled();
+    const int64_t ldwt_max = np_max / 64;
+    size_t oTP = 0, oTPT = 0, oTT = 0, oTAux = 0;
+    if (thin_any) {
+        const size_t bits = static_cast<size_t>(np_max * ldwt_max * 8);
+        oTP = take(bits);
+        oTPT = take(bits);
+        oTT = take(2 * bits);
+        oTAux = take(static_cast<size_t>(2 * nmax * 8 + (ldwt_max + 1) * 8 + 2 * nmax * 4));
+    }
     void* base = nullptr;
     BST(ws_get(ctx, WS_SOLO, total, &base));
     uint8_t* b8 = static_cast<uint8_t*>(base);
@@ -844,24 +930,35 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
     uint8_t* Q[2] = {b8 + oQ[0], b8 + oQ[1]};
     uint8_t* QT[2] = {b8 + oQT[0], b8 + oQT[1]};
     uint8_t* M0 = b8 + oM0;
+    uint64_t* TP = reinterpret_cast<uint64_t*>(b8 + oTP);
+    uint64_t* TPT = reinterpret_cast<uint64_t*>(b8 + oTPT);
+    uint64_t* TT = reinterpret_cast<uint64_t*>(b8 + oTT);
+    int64_t* t_rowcnt = reinterpret_cast<int64_t*>(b8 + oTAux);
+    int64_t* t_colcnt = t_rowcnt + nmax;
+    uint64_t* t_bmask = reinterpret_cast<uint64_t*>(t_colcnt + nmax);
+    int32_t* t_blist = reinterpret_cast<int32_t*>(t_bmask + ldwt_max + 1);
+    int32_t* t_rlist = t_blist + nmax;
     BCK(cudaMalloc(&c->d_solo, sizeof(int) * SW_WORDS * ns), "cudaMalloc(large-problem state)");
     BCK(cudaMemset(c->d_solo, 0, sizeof(int) * SW_WORDS * ns), "clear large-problem state");
     c->h_solo.assign(static_cast<size_t>(SW_WORDS * ns), 0);
 
-    cudaStream_t cs = nullptr, cb = nullptr;
+    cudaStream_t cs = nullptr, cb = nullptr, cc = nullptr;
     BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
     cudaError_t ce = cudaStreamCreateWithFlags(&cb, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cc, cudaStreamNonBlocking);
     if (ce != cudaSuccess) {
         cudaStreamDestroy(cs);
+        if (cb) cudaStreamDestroy(cb);
         return cuda_err(ctx, ce, "capture stream");
     }
     struct Streams {
-        cudaStream_t a, b;
+        cudaStream_t a, b, c;
         ~Streams() {
             cudaStreamDestroy(a);
             cudaStreamDestroy(b);
+            cudaStreamDestroy(c);
         }
-    } guard_streams{cs, cb};
+    } guard_streams{cs, cb, cc};
     BCK(cudaStreamBeginCaptureToGraph(cs, c->graph, after, nullptr, nafter, cudaStreamCaptureModeRelaxed),
         "begin capture of the large problems");
     bmlp_status status = BMLP_OK;
@@ -937,6 +1034,30 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
             SST(make_tmap(ctx, &mB1[b], QT[b], n_pad, ld4, ld4, tc4_b1_rows()));
         }
         SST(add_while(ctx, cs, hC, &body));
+        // after each product, when R is close to its closure, the next squaring may run only on the rows and columns
+        // that still hold zeros: IF nodes inside the loop's body, one for its statistics and one for the squaring
+        const int64_t ldw_t = n_pad / 64;
+        const bool thin_p = thin_any && thin_fixed_seconds(n_pad) < limit;
+        cudaGraphConditionalHandle hT[2], hT2[2];
+        if (thin_p) {
+            for (int h = 0; h < 2; ++h) {
+                SCK(cudaGraphConditionalHandleCreate(&hT[h], body, 0, cudaGraphCondAssignDefault), "conditional handle");
+                SCK(cudaGraphConditionalHandleCreate(&hT2[h], body, 0, cudaGraphCondAssignDefault), "conditional handle");
+            }
+        }
+        auto* t_smp = reinterpret_cast<unsigned long long*>(w + SW_SMP);
+        auto* t_stat = reinterpret_cast<unsigned long long*>(w + SW_TSTAT);
+        // captures one IF body on stream cc: fn() issues its launches
+        auto capture_if = [&](cudaGraphConditionalHandle hh, auto fn) -> cudaError_t {
+            cudaGraph_t ifb = nullptr;
+            if (add_conditional(ctx, cb, hh, cudaGraphCondTypeIf, &ifb) != BMLP_OK) return cudaErrorUnknown;
+            cudaError_t e1 = cudaStreamBeginCaptureToGraph(cc, ifb, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e1 != cudaSuccess) return e1;
+            e1 = fn();
+            cudaGraph_t tmp = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cc, &tmp);
+            return e1 != cudaSuccess ? e1 : e2;
+        };
         SCK(cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
             "begin capture of the tensor-core loop");
         {
@@ -955,16 +1076,60 @@ bmlp_status build_solo(bmlp_ctx* ctx, BatchCache* c, const bmlp_problem* probs, 
                 p4.error = ctx->d_ctl + CTL_ERROR;
                 p4.wait_cycles = wait_cycles;
                 p4.guard = w + (half == 0 ? SW_GC : SW_G1);
+                if (thin_p) {  // the epilogue keeps R and R^T as bit rows for the restricted squaring
+                    p4.out_bits = reinterpret_cast<uint32_t*>(TP);
+                    p4.out_bits_t = reinterpret_cast<uint32_t*>(TPT);
+                    p4.ldb = 2 * ldw_t;
+                }
                 e = launch_tc4_product_duo(mA[half], mB0[half], mB1[half], p4, sms, cb);
                 if (e == cudaSuccess) {
                     solo_tc_decide_kernel<<<1, 1, 0, cb>>>(w, cap, half, hC);
                     e = cudaGetLastError();
+                }
+                if (thin_p && e == cudaSuccess) {
+                    uint8_t* Qn = Q[half ^ 1];
+                    uint8_t* QTn = QT[half ^ 1];
+                    e = launch_thin_sample(Qn, ld4, n, thin_sample_rows(), t_smp, cb);
+                    if (e == cudaSuccess) {
+                        solo_thin_gate_kernel<<<1, 1, 0, cb>>>(w, half, n, thin_row_spread(), hT[half]);
+                        e = cudaGetLastError();
+                    }
+                    if (e == cudaSuccess)
+                        e = capture_if(hT[half], [&]() -> cudaError_t {
+                            cudaError_t e3 = launch_thin_stats(Qn, QTn, ld4, n, TP, TPT, ldw_t, t_rowcnt, t_colcnt,
+                                                               t_bmask, t_blist, t_rlist, t_stat, true, sms, cc);
+                            if (e3 != cudaSuccess) return e3;
+                            solo_thin_decide_kernel<<<1, 1, 0, cc>>>(w, ldw_t, thin_fixed_seconds(n_pad), s_word, s_row,
+                                                                     limit);
+                            return cudaGetLastError();
+                        });
+                    if (e == cudaSuccess) {
+                        solo_thin_arm_kernel<<<1, 1, 0, cb>>>(w, hT2[half]);
+                        e = cudaGetLastError();
+                    }
+                    if (e == cudaSuccess)
+                        e = capture_if(hT2[half], [&]() -> cudaError_t {
+                            cudaError_t e3 = launch_thin_squaring_dev(TP, TPT, ldw_t, n, t_blist, t_rlist, t_stat, TT,
+                                                                      Qn, QTn, ld4, w + SW_TCHANGED, sms, cc);
+                            if (e3 != cudaSuccess) return e3;
+                            solo_thin_post_kernel<<<1, 1, 0, cc>>>(w, half, cap);
+                            return cudaGetLastError();
+                        });
+                    if (e == cudaSuccess) {
+                        solo_loop_ctl_kernel<<<1, 1, 0, cb>>>(w, hC);
+                        e = cudaGetLastError();
+                    }
                 }
             }
             cudaGraph_t tmp = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cb, &tmp);
             if (e != cudaSuccess || e2 != cudaSuccess)
                 return fail(cuda_err(ctx, e != cudaSuccess ? e : e2, "tensor-core loop"));
+        }
+        if (thin_p) {  // a restricted squaring that ended the loop after the first product left the closure in Q1
+            solo_result_copy_kernel<<<sms * 4, 256, 0, cs>>>(w, reinterpret_cast<uint4*>(Q[0]),
+                                                             reinterpret_cast<const uint4*>(Q[1]), n_pad * ld4 / 16);
+            SCK(cudaGetLastError(), "result copy");
         }
         // ---- results: Q[0] holds the closure (a product that changed nothing left both buffers equal)
         if (p.kind == BMLP_PROBLEM_CLOSURE) {

@@ -341,6 +341,15 @@ cudaError_t launch_thin_sample(const uint8_t* Q, int64_t ld4, int64_t n, int row
 cudaError_t launch_thin_squaring(uint64_t* P, uint64_t* PT, int64_t ldw, const int32_t* blist, int64_t nb,
                                  const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2, uint8_t* Q,
                                  uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);
+// The same with |B| = stat[0] and |Rb| = stat[1] read on the device (T1: 2 n x ldw words; Rb's rows after B's),
+// for device-driven pipelines whose host never sees the counts.
+cudaError_t launch_thin_squaring_dev(uint64_t* P, uint64_t* PT, int64_t ldw, int64_t n, const int32_t* blist,
+                                     const int32_t* rlist, const unsigned long long* stat, uint64_t* T1, uint8_t* Q,
+                                     uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s);
+double thin_fixed_seconds(int64_t n_pad);
+bool thin_is_enabled();
+int thin_sample_rows();
+double thin_row_spread();
 // nonzero words of R + R R (out[0] += their total) and the word ORs of that squaring (out[1] += their total), from
 // the word index of R (ldw words per row, at most 49,152), without forming R + R R; bits_out (if not null) += the
 // ones of R

@@ -156,10 +156,15 @@ __global__ void __launch_bounds__(256) e2m1_sample_kernel(const uint8_t* __restr
 }
 
 // T[l] = OR of Src[k] over the set bits k of Src[list[l]] (bit rows of ldw words; warp per list entry, each lane
-// ORing its own words of T[l], so one entry's work runs on one warp).
+// ORing its own words of T[l], so one entry's work runs on one warp). With count_dev, the count is *count_dev, and
+// with toff_dev, T starts *toff_dev rows further (counts known only on the device).
 __global__ void __launch_bounds__(256) thin_row_or_kernel(const uint64_t* __restrict__ Src, int64_t ldw,
                                                           const int32_t* __restrict__ list, int64_t count,
-                                                          uint64_t* __restrict__ T) {
+                                                          uint64_t* __restrict__ T,
+                                                          const unsigned long long* __restrict__ count_dev,
+                                                          const unsigned long long* __restrict__ toff_dev) {
+    if (count_dev != nullptr) count = static_cast<int64_t>(*count_dev);
+    if (toff_dev != nullptr) T += static_cast<int64_t>(*toff_dev) * ldw;
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     for (int64_t l = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); l < count;
@@ -203,7 +208,11 @@ __global__ void __launch_bounds__(256) thin_apply_kernel(uint64_t* P, uint64_t* 
                                                          int64_t ldw, const int32_t* __restrict__ list, int64_t count,
                                                          int transposed, uint8_t* __restrict__ Q,
                                                          uint8_t* __restrict__ QT, int64_t ld4,
-                                                         int* __restrict__ changed) {
+                                                         int* __restrict__ changed,
+                                                         const unsigned long long* __restrict__ count_dev,
+                                                         const unsigned long long* __restrict__ toff_dev) {
+    if (count_dev != nullptr) count = static_cast<int64_t>(*count_dev);
+    if (toff_dev != nullptr) T += static_cast<int64_t>(*toff_dev) * ldw;
     uint64_t* Cur = transposed ? PT : P;
     uint64_t* Other = transposed ? P : PT;
     const int64_t total = count * ldw;
@@ -266,12 +275,29 @@ cudaError_t launch_thin_stats(const uint8_t* Q, const uint8_t* QT, int64_t ld4, 
 cudaError_t launch_thin_squaring(uint64_t* P, uint64_t* PT, int64_t ldw, const int32_t* blist, int64_t nb,
                                  const int32_t* rlist, int64_t nr, uint64_t* T1, uint64_t* T2, uint8_t* Q,
                                  uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s) {
-    if (nb > 0) thin_row_or_kernel<<<rows_grid(nb, sms), 256, 0, s>>>(PT, ldw, blist, nb, T1);
-    if (nr > 0) thin_row_or_kernel<<<rows_grid(nr, sms), 256, 0, s>>>(P, ldw, rlist, nr, T2);
+    if (nb > 0) thin_row_or_kernel<<<rows_grid(nb, sms), 256, 0, s>>>(PT, ldw, blist, nb, T1, nullptr, nullptr);
+    if (nr > 0) thin_row_or_kernel<<<rows_grid(nr, sms), 256, 0, s>>>(P, ldw, rlist, nr, T2, nullptr, nullptr);
     // every new one is found from the old R before any is written
     const int apply_grid = sms * 8;
-    if (nb > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T1, ldw, blist, nb, 1, Q, QT, ld4, changed);
-    if (nr > 0) thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T2, ldw, rlist, nr, 0, Q, QT, ld4, changed);
+    if (nb > 0)
+        thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T1, ldw, blist, nb, 1, Q, QT, ld4, changed, nullptr,
+                                                     nullptr);
+    if (nr > 0)
+        thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T2, ldw, rlist, nr, 0, Q, QT, ld4, changed, nullptr,
+                                                     nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thin_squaring_dev(uint64_t* P, uint64_t* PT, int64_t ldw, int64_t n, const int32_t* blist,
+                                     const int32_t* rlist, const unsigned long long* stat, uint64_t* T1, uint8_t* Q,
+                                     uint8_t* QT, int64_t ld4, int* changed, int sms, cudaStream_t s) {
+    // |B| = stat[0] and |Rb| = stat[1] are read by the kernels; the grids cover up to n entries each
+    const int g = rows_grid(n, sms);
+    thin_row_or_kernel<<<g, 256, 0, s>>>(PT, ldw, blist, 0, T1, stat, nullptr);
+    thin_row_or_kernel<<<g, 256, 0, s>>>(P, ldw, rlist, 0, T1, stat + 1, stat);
+    const int apply_grid = sms * 8;
+    thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T1, ldw, blist, 0, 1, Q, QT, ld4, changed, stat, nullptr);
+    thin_apply_kernel<<<apply_grid, 256, 0, s>>>(P, PT, T1, ldw, rlist, 0, 0, Q, QT, ld4, changed, stat + 1, stat);
     return cudaGetLastError();
 }
 
