@@ -272,3 +272,58 @@ def test_batch_frontier_engine(ctx, fmt):
     ctx.batch_run(items, variant="smp_packed")
     torch.cuda.synchronize()
     check(items, expect)
+
+
+def chain_tail_graph(n0=9000, tail=60, seed=33):
+    """A dense random part with a chain of `tail` nodes hanging off it: the chain's columns are reached by most
+    rows only after several squarings, so the squarings restricted to the rows and columns holding zeros find new
+    ones before the closure is reached."""
+    n = n0 + tail
+    ip0, ix0 = wl.er_graph(n0, 5.0, seed)
+    src = np.concatenate([np.repeat(np.arange(n0), np.diff(ip0)), [0], n0 + np.arange(tail - 1)])
+    dst = np.concatenate([ix0, [n0], n0 + 1 + np.arange(tail - 1)])
+    ip, ix = wl.csr_from_pairs(n, src, dst)
+    return n, ip, ix
+
+
+@pytest.mark.parametrize("fmt", [bmlp.BMLP_FMT_U8, bmlp.BMLP_FMT_PACKED64])
+def test_device_pipeline_restricted_squaring(ctx, fmt):
+    """Large closures whose last squarings run only on the rows and columns holding zeros, inside the batch graph
+    (IF nodes in the tensor-core loop of the device-driven pipeline): a dense ER closure (only the confirming
+    squaring is restricted), the chain-tail graph (restricted squarings that find new ones), a composition whose
+    R2 is that graph, and a small closure beside them; every bit against the oracle, and each closure's count of
+    squarings is Algorithm 1's."""
+    specs = []
+    n, ip, ix = 12000, *wl.er_graph(12000, 4.0, 31)
+    specs.append(("closure", n, ip, ix))
+    specs.append(("closure", *chain_tail_graph()))
+    n2, ip2, ix2 = chain_tail_graph()
+    ip1, ix1 = wl.er_graph(n2, 2.0, 35)
+    specs.append(("compose", n2, (ip1, ix1), (ip2, ix2)))
+    specs.append(("closure", 700, *wl.er_graph(700, 2.0, 36)))
+    items, expect, keep = [], [], []
+    for sp in specs:
+        if sp[0] == "closure":
+            _, n, ip, ix = sp
+            m = wl.dense_u8(n, ip, ix)
+            R = dev(m if fmt == bmlp.BMLP_FMT_U8 else wl.pack_rows(m).view(np.int64))
+            out = torch.zeros_like(R)
+            keep += [R, out]
+            items.append(dict(kind=bmlp.BMLP_PROBLEM_CLOSURE, n=n, R1=R, out=out, fmt=fmt))
+            expect.append(("closure", n, ip, ix))
+        else:
+            _, n, c1, c2 = sp
+            m1, m2 = wl.dense_u8(n, *c1), wl.dense_u8(n, *c2)
+            if fmt != bmlp.BMLP_FMT_U8:
+                m1, m2 = wl.pack_rows(m1).view(np.int64), wl.pack_rows(m2).view(np.int64)
+            R1, R2 = dev(m1), dev(m2)
+            out = torch.zeros_like(R1)
+            keep += [R1, R2, out]
+            items.append(dict(kind=bmlp.BMLP_PROBLEM_COMPOSE, n=n, R1=R1, R2=R2, out=out, fmt=fmt))
+            expect.append(("compose", n, c1, c2))
+    iters = ctx.batch_run(items, variant="rms_tc")
+    torch.cuda.synchronize()
+    check(items, expect)
+    for it, ex in zip(iters, expect):
+        if ex[0] == "closure":
+            assert it == oracle.rms_iterations(oracle.longest_shortest_path(ex[1], ex[2], ex[3]))
