@@ -719,6 +719,27 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
     return set_err(ctx, BMLP_ERR_NOT_CONVERGED, "no fixpoint within %d products", max_iters);
 }
 
+// Whether R (format fmt; packed rows of ldw words) is dense by its 128 x 128 block map: then a closure starts on
+// 4-bit operands and leaves from them, else on E4M3 with empty K blocks skipped.
+bmlp_status dense_by_blocks(bmlp_ctx* ctx, const Operand& src, int32_t fmt, int64_t ldw, int64_t n, int64_t n_pad,
+                            cudaStream_t s, bool* dense) {
+    const int64_t kb = n_pad / 128;
+    *dense = !tc_skip_enabled() || kb > 256;
+    if (*dense) return BMLP_OK;
+    void* f = nullptr;
+    ST(ws_get(ctx, WS_F0, static_cast<size_t>(kb * kb), &f));
+    launch_input_block_flags(src.dev, fmt, ldw, n, n_pad, static_cast<uint8_t*>(f), kb, s);
+    CK(cudaGetLastError(), "input block map");
+    ctx->stats.launches++;
+    std::vector<uint8_t> h(static_cast<size_t>(kb * kb));
+    CK(cudaMemcpyAsync(h.data(), f, h.size(), cudaMemcpyDeviceToHost, s), "read input block map");
+    CK(host_sync(ctx, s), "read input block map");
+    size_t nz = 0;
+    for (uint8_t x : h) nz += x != 0;
+    *dense = static_cast<double>(nz) >= kSkipMaxDensity * static_cast<double>(kb * kb);
+    return BMLP_OK;
+}
+
 // The caller's rows themselves when they are packed bit rows on the device with ldw words per row (words_of(n) even),
 // no padding bits (n a multiple of 64: a caller's bits at columns >= n are to be ignored, and the copy clears them)
 // and 16-byte aligned, so that a read-only pass can use them without a copy; else null.
@@ -1327,24 +1348,7 @@ static bmlp_status core_rms(bmlp_ctx* ctx, const void* R, int64_t n, int32_t fmt
             sldw = sp.ldw;
         }
         bool direct = false;
-        if (o.e4m3_only == 0) {
-            // a dense input (by its 128 x 128 block map) starts on 4-bit operands and leaves from them
-            const int64_t kb = n_pad / 128;
-            direct = !tc_skip_enabled() || kb > 256;
-            if (!direct) {
-                void* f = nullptr;
-                ST(ws_get(ctx, WS_F0, static_cast<size_t>(kb * kb), &f));
-                launch_input_block_flags(src.dev, sfmt, sldw, n, n_pad, static_cast<uint8_t*>(f), kb, s);
-                CK(cudaGetLastError(), "input block map");
-                ctx->stats.launches++;
-                std::vector<uint8_t> h(static_cast<size_t>(kb * kb));
-                CK(cudaMemcpyAsync(h.data(), f, h.size(), cudaMemcpyDeviceToHost, s), "read input block map");
-                CK(host_sync(ctx, s), "read input block map");
-                size_t nz = 0;
-                for (uint8_t x : h) nz += x != 0;
-                direct = static_cast<double>(nz) >= kSkipMaxDensity * static_cast<double>(kb * kb);
-            }
-        }
+        if (o.e4m3_only == 0) ST(dense_by_blocks(ctx, src, sfmt, sldw, n, n_pad, s, &direct));
         if (direct) {
             const int64_t ld4 = n_pad / 2;
             if (sfmt == BMLP_FMT_U8)
@@ -1551,31 +1555,101 @@ static bmlp_status core_compose(bmlp_ctx* ctx, const void* R1, const void* R2, i
         // R2+ as in bmlp_rms: squarings on bit rows while R2 is sparse, then on the tensor cores
         SparseStart sp;
         if (!o.tc_only) ST(sparse_squarings(ctx, b, fmt, n, n_pad, max_iters, o, s, &sp));
+        Operand src = b;
+        int32_t sfmt = fmt;
+        int64_t sldw = words_of(n);
         if (sp.P) {
-            Operand pk;
-            pk.dev = sp.P;
-            ST(to_e4m3(ctx, pk, BMLP_FMT_PACKED64, n, M[0], T[0], n_pad, s, sp.ldw));
-        } else {
-            ST(to_e4m3(ctx, b, fmt, n, M[0], T[0], n_pad, s));
+            src.dev = sp.P;
+            src.host = false;
+            sfmt = BMLP_FMT_PACKED64;
+            sldw = sp.ldw;
         }
-        uint8_t *res = nullptr, *res_t = nullptr;
-        if (sp.done) {
-            res = M[0];
-            res_t = T[0];
+        bool direct = false;
+        if (o.e4m3_only == 0) ST(dense_by_blocks(ctx, src, sfmt, sldw, n, n_pad, s, &direct));
+        if (direct) {
+            // dense R2: its closure on packed E2M1 operands in the halves of M[1], T[1] (as bmlp_rms), then
+            // (I + R2+) R1 on the same 4-bit squaring kernel: A = I + R2+ (diagonal set in place), B^T = R1^T
+            // (R1 and R1^T encoded into the first halves of M[0], T[0]) and a zero old R (M[0]'s second half), so
+            // that the kernel's R' is C > 0 (into X; R'^T into T[0]'s second half)
+            const int64_t ld4 = n_pad / 2;
+            const size_t half = static_cast<size_t>(n_pad) * static_cast<size_t>(ld4);
+            if (sfmt == BMLP_FMT_U8)
+                launch_u8_to_e2m1(static_cast<const uint8_t*>(src.dev), n, M[1], T[1], n_pad, s);
+            else
+                launch_packed_to_e2m1(static_cast<const uint64_t*>(src.dev), sldw, n, M[1], T[1], n_pad, s);
+            CK(cudaGetLastError(), "E2M1 encode");
+            ctx->stats.launches++;
+            const uint8_t* q = M[1];  // the closure already, when the bit-row squarings reached it
             st = BMLP_OK;
+            if (!sp.done) {
+                uint8_t *res = nullptr, *res_t = nullptr;
+                st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t, &q);
+            }
+            iters += sp.iters;
+            if (st != BMLP_OK) return st;
+            uint8_t* A = const_cast<uint8_t*>(q);  // a half of M[1], this call's workspace
+            launch_set_diag_e2m1(A, ld4, n, s);
+            if (fmt == BMLP_FMT_U8)
+                launch_u8_to_e2m1(static_cast<const uint8_t*>(a.dev), n, M[0], T[0], n_pad, s);
+            else
+                launch_packed_to_e2m1(static_cast<const uint64_t*>(a.dev), words_of(n), n, M[0], T[0], n_pad, s);
+            CK(cudaGetLastError(), "E2M1 encode of R1");
+            CK(cudaMemsetAsync(M[0] + half, 0, half, s), "clear old R");
+            ctx->stats.launches += 2;
+            CUtensorMap fa, fb0, fb1;
+            ST(make_tmap(ctx, &fa, A, n_pad, ld4, ld4, TC_BM));
+            ST(make_tmap(ctx, &fb0, T[0], n_pad, ld4, ld4, TC_BN / 2));
+            ST(make_tmap(ctx, &fb1, T[0], n_pad, ld4, ld4, tc4_b1_rows()));
+            TcParams pp{};
+            pp.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+            pp.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
+            pp.k_blocks = static_cast<int32_t>(n_pad / 256);
+            pp.mode = TC_MODE_RMS;
+            pp.ld = ld4;
+            pp.old_r = M[0] + half;
+            pp.out_r = X;
+            pp.out_rt = T[0] + half;
+            pp.changed = ctx->d_ctl + CTL_CHANGED;
+            pp.error = ctx->d_ctl + CTL_ERROR;
+            pp.wait_cycles = wait_cycles(ctx, o);
+            CK(launch_tc4_product_duo(fa, fb0, fb1, pp, ctx->sm_count, s), "final product launch");
+            ctx->stats.product_launches++;
+            ctx->stats.e2m1_products++;
+            ctx->stats.launches += 2;
+            ST(read_ctl(ctx, s, nullptr));
+            if (fmt == BMLP_FMT_U8)
+                launch_e2m1_to_u8(X, ld4, n, static_cast<uint8_t*>(ov.dev), 0, s);
+            else
+                launch_e2m1_to_packed(X, ld4, n, static_cast<uint64_t*>(ov.dev), words_of(n), 0, s);
+            CK(cudaGetLastError(), "E2M1 decode");
+            ctx->stats.launches++;
         } else {
-            st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
+            if (sp.P) {
+                Operand pk;
+                pk.dev = sp.P;
+                ST(to_e4m3(ctx, pk, BMLP_FMT_PACKED64, n, M[0], T[0], n_pad, s, sp.ldw));
+            } else {
+                ST(to_e4m3(ctx, b, fmt, n, M[0], T[0], n_pad, s));
+            }
+            uint8_t *res = nullptr, *res_t = nullptr;
+            if (sp.done) {
+                res = M[0];
+                res_t = T[0];
+                st = BMLP_OK;
+            } else {
+                st = rms_tc_loop(ctx, n, n_pad, M, T, max_iters - sp.iters, o, s, &iters, &res, &res_t);
+            }
+            iters += sp.iters;
+            if (st != BMLP_OK) return st;
+            // A = I + R2+ (row-major, in res); B^T = R1^T (written into the other R^T buffer)
+            launch_set_diag_e4m3(res, n_pad, n, s);
+            ctx->stats.launches++;
+            uint8_t* r1t = (res_t == T[0]) ? T[1] : T[0];
+            uint8_t* r1 = (res == M[0]) ? M[1] : M[0];
+            ST(to_e4m3(ctx, a, fmt, n, r1, r1t, n_pad, s));
+            ST(tc_plain_product(ctx, res, r1t, n_pad, X, o, s));
+            ST(bytes_out(ctx, X, n_pad, n, fmt, ov.dev, 0, s));
         }
-        iters += sp.iters;
-        if (st != BMLP_OK) return st;
-        // A = I + R2+ (row-major, in res); B^T = R1^T (written into the other R^T buffer)
-        launch_set_diag_e4m3(res, n_pad, n, s);
-        ctx->stats.launches++;
-        uint8_t* r1t = (res_t == T[0]) ? T[1] : T[0];
-        uint8_t* r1 = (res == M[0]) ? M[1] : M[0];
-        ST(to_e4m3(ctx, a, fmt, n, r1, r1t, n_pad, s));
-        ST(tc_plain_product(ctx, res, r1t, n_pad, X, o, s));
-        ST(bytes_out(ctx, X, n_pad, n, fmt, ov.dev, 0, s));
     } else {
         const int64_t ldw = round_up(words_of(n), 2);
         ctx->stats.n_pad = ldw * 64;
