@@ -903,6 +903,36 @@ bmlp_status sparse_squarings(bmlp_ctx* ctx, const Operand& in, int32_t fmt, int6
     return BMLP_OK;
 }
 
+// X = A B thresholded to 0/1 for packed E2M1 operands (A row-major, B given as B^T, both n_pad x n_pad / 2 bytes), on
+// the 4-bit squaring kernel with a zero old R (Z, cleared here), so that its R' is the product; its R'^T goes to XT
+// (scratch). Raises the call's error on an in-kernel timeout.
+bmlp_status e2m1_product(bmlp_ctx* ctx, const uint8_t* A, const uint8_t* BT, int64_t n_pad, uint8_t* Z, uint8_t* X,
+                         uint8_t* XT, const bmlp_options& o, cudaStream_t s) {
+    const int64_t ld4 = n_pad / 2;
+    CK(cudaMemsetAsync(Z, 0, static_cast<size_t>(n_pad) * static_cast<size_t>(ld4), s), "clear old R");
+    CUtensorMap fa, fb0, fb1;
+    ST(make_tmap(ctx, &fa, A, n_pad, ld4, ld4, TC_BM));
+    ST(make_tmap(ctx, &fb0, BT, n_pad, ld4, ld4, TC_BN / 2));
+    ST(make_tmap(ctx, &fb1, BT, n_pad, ld4, ld4, tc4_b1_rows()));
+    TcParams pp{};
+    pp.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
+    pp.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
+    pp.k_blocks = static_cast<int32_t>(n_pad / 256);
+    pp.mode = TC_MODE_RMS;
+    pp.ld = ld4;
+    pp.old_r = Z;
+    pp.out_r = X;
+    pp.out_rt = XT;
+    pp.changed = ctx->d_ctl + CTL_CHANGED;
+    pp.error = ctx->d_ctl + CTL_ERROR;
+    pp.wait_cycles = wait_cycles(ctx, o);
+    CK(launch_tc4_product_duo(fa, fb0, fb1, pp, ctx->sm_count, s), "4-bit product launch");
+    ctx->stats.product_launches++;
+    ctx->stats.e2m1_products++;
+    ctx->stats.launches += 2;
+    return read_ctl(ctx, s, nullptr);
+}
+
 // X = A B for E4M3 0/1 operands on the tensor cores: A row-major, B given as B^T (both n_pad x n_pad); one plain
 // product (no OR with an old R) with exact FP32 counts thresholded to 0/1.
 bmlp_status tc_plain_product(bmlp_ctx* ctx, const uint8_t* A, const uint8_t* BT, int64_t n_pad, uint8_t* X,
@@ -1594,29 +1624,8 @@ static bmlp_status core_compose(bmlp_ctx* ctx, const void* R1, const void* R2, i
             else
                 launch_packed_to_e2m1(static_cast<const uint64_t*>(a.dev), words_of(n), n, M[0], T[0], n_pad, s);
             CK(cudaGetLastError(), "E2M1 encode of R1");
-            CK(cudaMemsetAsync(M[0] + half, 0, half, s), "clear old R");
             ctx->stats.launches += 2;
-            CUtensorMap fa, fb0, fb1;
-            ST(make_tmap(ctx, &fa, A, n_pad, ld4, ld4, TC_BM));
-            ST(make_tmap(ctx, &fb0, T[0], n_pad, ld4, ld4, TC_BN / 2));
-            ST(make_tmap(ctx, &fb1, T[0], n_pad, ld4, ld4, tc4_b1_rows()));
-            TcParams pp{};
-            pp.m_tiles = static_cast<int32_t>(n_pad / TC_BM);
-            pp.n_tiles = static_cast<int32_t>((n_pad + tc4_tile_n() - 1) / tc4_tile_n());
-            pp.k_blocks = static_cast<int32_t>(n_pad / 256);
-            pp.mode = TC_MODE_RMS;
-            pp.ld = ld4;
-            pp.old_r = M[0] + half;
-            pp.out_r = X;
-            pp.out_rt = T[0] + half;
-            pp.changed = ctx->d_ctl + CTL_CHANGED;
-            pp.error = ctx->d_ctl + CTL_ERROR;
-            pp.wait_cycles = wait_cycles(ctx, o);
-            CK(launch_tc4_product_duo(fa, fb0, fb1, pp, ctx->sm_count, s), "final product launch");
-            ctx->stats.product_launches++;
-            ctx->stats.e2m1_products++;
-            ctx->stats.launches += 2;
-            ST(read_ctl(ctx, s, nullptr));
+            ST(e2m1_product(ctx, A, T[0], n_pad, M[0] + half, X, T[0] + half, o, s));
             if (fmt == BMLP_FMT_U8)
                 launch_e2m1_to_u8(X, ld4, n, static_cast<uint8_t*>(ov.dev), 0, s);
             else
@@ -1732,14 +1741,34 @@ static bmlp_status core_rms_alg1(bmlp_ctx* ctx, const void* R, int64_t n, int32_
     ST(ws_get(ctx, WS_T0, bytes, &bb[2]));
     ST(ws_get(ctx, WS_T1, bytes, &bb[3]));
     ST(ws_get(ctx, WS_M2, bytes, &bb[4]));
-    Operand qs;
-    qs.dev = q;
-    ST(to_e4m3(ctx, qs, BMLP_FMT_PACKED64, n, static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[2]), n_pad, s,
-               ldw));
-    ST(to_e4m3(ctx, a, fmt, n, static_cast<uint8_t*>(bb[1]), static_cast<uint8_t*>(bb[3]), n_pad, s));
-    ST(tc_plain_product(ctx, static_cast<uint8_t*>(bb[0]), static_cast<uint8_t*>(bb[3]), n_pad,
-                        static_cast<uint8_t*>(bb[4]), o, s));
-    ST(bytes_out(ctx, static_cast<uint8_t*>(bb[4]), n_pad, n, fmt, ov.dev, o.reflexive, s));
+    uint8_t* B8[5];
+    for (int k = 0; k < 5; ++k) B8[k] = static_cast<uint8_t*>(bb[k]);
+    if (o.e4m3_only == 0) {
+        // on 4-bit operands: A = I + R1+ and R1 (with R1^T) as packed E2M1 in the first halves of the buffers
+        const int64_t ld4 = n_pad / 2;
+        const size_t half = static_cast<size_t>(n_pad) * static_cast<size_t>(ld4);
+        launch_packed_to_e2m1(static_cast<const uint64_t*>(q), ldw, n, B8[0], B8[2], n_pad, s);
+        if (fmt == BMLP_FMT_U8)
+            launch_u8_to_e2m1(static_cast<const uint8_t*>(a.dev), n, B8[1], B8[3], n_pad, s);
+        else
+            launch_packed_to_e2m1(static_cast<const uint64_t*>(a.dev), ldw, n, B8[1], B8[3], n_pad, s);
+        CK(cudaGetLastError(), "E2M1 encode");
+        ctx->stats.launches += 2;
+        ST(e2m1_product(ctx, B8[0], B8[3], n_pad, B8[0] + half, B8[4], B8[2] + half, o, s));
+        if (fmt == BMLP_FMT_U8)
+            launch_e2m1_to_u8(B8[4], ld4, n, static_cast<uint8_t*>(ov.dev), o.reflexive, s);
+        else
+            launch_e2m1_to_packed(B8[4], ld4, n, static_cast<uint64_t*>(ov.dev), words_of(n), o.reflexive, s);
+        CK(cudaGetLastError(), "E2M1 decode");
+        ctx->stats.launches++;
+    } else {
+        Operand qs;
+        qs.dev = q;
+        ST(to_e4m3(ctx, qs, BMLP_FMT_PACKED64, n, B8[0], B8[2], n_pad, s, ldw));
+        ST(to_e4m3(ctx, a, fmt, n, B8[1], B8[3], n_pad, s));
+        ST(tc_plain_product(ctx, B8[0], B8[3], n_pad, B8[4], o, s));
+        ST(bytes_out(ctx, B8[4], n_pad, n, fmt, ov.dev, o.reflexive, s));
+    }
     ctx->stats.iterations = squarings + 1;
     if (iters_out) *iters_out = squarings + 1;
     return finish_out(ctx, ov, s);
