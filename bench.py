@@ -362,8 +362,8 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
     del o2
 
     # -- one bit-row squaring R <- R + R R (rms_packed) on the sparse input (ER mean out-degree 4; through the word
-    # index, square_rows_kernel) and on a dense one (the closure of the n = 8,192 graph; whole rows,
-    # product_packed_kernel)
+    # index, square_rows_kernel) and on a dense one (the closure of the n = 8,192 graph; whole rows, Four Russians
+    # tables, product_m4rm_kernel)
     pk = {}
 
     def packed_step(Pn, nn):
@@ -376,7 +376,7 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
                 if e.status != bmlp.BMLP_ERR_NOT_CONVERGED:
                     raise
             tms.append(ctx.stats()["product_ms"])
-        kern = "square_rows_kernel" if ctx.stats()["sparse_squarings"] else "product_packed_kernel"
+        kern = "square_rows_kernel" if ctx.stats()["sparse_squarings"] else "product_m4rm_kernel"
         return statistics.median(tms[1:]) / 1e3, kern
 
     dense8k = None
@@ -394,16 +394,16 @@ def run_extras(args, ctx, stream, n, ip, ix, R, FMT, out_main, bf16, hbm, check)
         if nn == 8192:
             dense8k = torch.zeros_like(Pn)
             ctx.rms(Pn, nn, dense8k, fmt=PK, variant="rms_tc", stream=stream)
-    # dense rows: the word ORs (nnz(R) x n / 64) against the integer-ALU rate
+    # dense rows: the word ORs of the definition (nnz(R) x n / 64: one row of R per one of R) per second, against
+    # the integer-ALU rate; the kernel reads, instead of a row per one, one 16-byte table entry per nibble of R for
+    # every pair of output words (n x n / 128 x n / 4 entries), from shared memory
     t, kern = packed_step(dense8k, 8192)
     bits = int(np.unpackbits(dense8k.cpu().numpy().view(np.uint8)).sum())
     ors = float(bits) * (8192 // 64)
-    # each one of R reads one row of R (8,192 bits) through L2 while the rows are ORed: that read rate, not the ALU,
-    # bounds this dense product
-    l2_bytes = float(bits) * (8192 // 8)
+    table_bytes = 8192.0 * (8192 // 128) * (8192 // 4) * 16
     pk["n8192_dense"] = {"ms": t * 1e3, "ones": bits, "kernel": kern, "word_or_tera_per_s": ors / t / 1e12,
                          "word_or_frac": ors / t / 1e12 / probes["word_or_tera_per_s"],
-                         "l2_row_bytes": l2_bytes, "l2_row_read_tbs": l2_bytes / t / 1e12}
+                         "table_read_bytes": table_bytes, "table_read_tbs": table_bytes / t / 1e12}
     del dense8k
     ex["packed_product"] = pk
 

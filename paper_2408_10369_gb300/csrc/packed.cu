@@ -1,12 +1,12 @@
 // Bit-packed kernels: rows of R are uint64 bit codes (paper Sec. 3.2, bit j
 // of row i = R_ij, least significant bit first).
 //
-//  * product_packed  one Boolean product on bitsets, C_i = OR_{k : A_ik = 1} B_k,
+//  * product_m4rm  one Boolean product on bitsets, C_i = OR_{k : A_ik = 1} B_k,
 //                 optionally OR-ed with A_i; with A = B = R that is one
 //                 squaring step of Eq. 4: C_i = R_i | OR_{k : R_ik = 1} R_k.
-//                 One warp per row i; the set bits k of A_i are enumerated
-//                 with warp ballots and find-first-set, and row k is OR-ed in
-//                 with coalesced 128-bit loads into per-lane registers.
+//                 Tiles of 256 rows x 1,024 columns; per word of A, 16
+//                 shared-memory tables of the ORs of 4 rows of B (Four
+//                 Russians), one lookup per nonzero nibble of A_i.
 //  * wcsr_build   the nonzero words of every row (word index + value), so
 //                 that frontier expansion touches only words that hold bits.
 //  * smp_packed   the selective product of Eq. 5 / Algorithm 2 per query row:
@@ -32,13 +32,6 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-__device__ __forceinline__ void or4(uint4& a, const uint4& b) {
-    a.x |= b.x;
-    a.y |= b.y;
-    a.z |= b.z;
-    a.w |= b.w;
-}
-
 // 64 x 64 bit transpose across a warp: lane l holds rows l (a0) and l + 32 (a1) and receives columns l (c0) and
 // l + 32 (c1), where bit r of column c is bit c of row r.
 __device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int lane, uint64_t& c0, uint64_t& c1) {
@@ -54,75 +47,121 @@ __device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int l
     }
 }
 
-template <int VEC>
-__global__ void __launch_bounds__(256) product_packed_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
-                                                             uint64_t* __restrict__ dst, int64_t n, int64_t ldw, int or_a,
-                                                             int* changed, Deadline dl) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    const int64_t chunk_words = 64 * VEC;  // 32 lanes x VEC x 2 words
-    uint32_t any = 0;
-    for (int64_t i = warp_id; i < n; i += nwarps) {
-        if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
-        const uint64_t* arow = A + i * ldw;
-        for (int64_t c0 = 0; c0 < ldw; c0 += chunk_words) {
-            uint4 acc[VEC];
+// ---- one Boolean product on bit rows by the method of Four Russians (Arlazarov, Dinic, Kronrod, Faradzev 1970)
+// C_i = (A_i if or_a) OR (OR over the set bits k of A_i of B_k). A CTA owns a tile of kM4Rows rows and kM4Cols
+// words (64 kM4Cols columns) of C and walks k one word of A (64 values of k) at a time. For each nibble h of that
+// word it tabulates, in shared memory, the 16 ORs of the four B rows 64 kw + 4 h .. 64 kw + 4 h + 3 over the tile's
+// columns; a row then ORs in one table entry per nonzero nibble of its A word instead of one B row per set bit.
+// So an output word costs at most n / 4 shared-memory reads however dense A is, where gathering the named rows
+// costs nnz(A_i) reads of B through L2. The tables are double buffered (one barrier per word of A), and the B
+// words of the next table are loaded while the current one is read.
+// Thread layouts: a table is built by thread (h = tid / 16, column word c = tid % 16), entry x at T[h][x][c]; a
+// lookup thread owns row slot r = tid / 8 (rows r, r + 32, ..., r + 224 of the tile) and the column words
+// 2 (tid % 8), 2 (tid % 8) + 1, so each row slot reads one whole 128-byte entry per lookup (no bank conflicts).
+constexpr int kM4Threads = 256;
+constexpr int kM4Cols = 16;
+constexpr int kM4Rows = 256;
+constexpr int kM4RowsPerThread = kM4Rows / (kM4Threads / 8);
+constexpr int kM4TableWords = 16 * 16 * kM4Cols;  // one buffer: 16 nibbles x 16 values x kM4Cols words (32 KiB)
+constexpr size_t kM4Smem = 2 * kM4TableWords * sizeof(uint64_t);
+
+__global__ void __launch_bounds__(kM4Threads, 2) product_m4rm_kernel(const uint64_t* __restrict__ A,
+                                                                     const uint64_t* __restrict__ B,
+                                                                     uint64_t* __restrict__ dst, int64_t n,
+                                                                     int64_t ldw, int or_a, int* changed, Deadline dl) {
+    extern __shared__ __align__(16) uint64_t m4t[];
+    const int tid = threadIdx.x;
+    const int64_t nch = (ldw + kM4Cols - 1) / kM4Cols;
+    const int64_t row0 = (static_cast<int64_t>(blockIdx.x) / nch) * kM4Rows;
+    const int64_t c0 = (static_cast<int64_t>(blockIdx.x) % nch) * kM4Cols;
+    const int64_t kwn = (n + 63) >> 6;  // words of A that hold columns < n
+    // table building: B words of column c0 + bc for rows 64 kw + 4 bh + q
+    const int bh = tid >> 4, bc = tid & 15;
+    const bool bcol = c0 + bc < ldw;
+    auto load_b = [&](int64_t kw, uint64_t (&b)[4]) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const int64_t w = c0 + 2 * (lane + 32 * v);
-                acc[v] = (or_a && w < ldw) ? *reinterpret_cast<const uint4*>(arow + w) : make_uint4(0, 0, 0, 0);
-            }
-            for (int64_t wb = 0; wb < ldw; wb += 32) {
-                const uint64_t aw = (wb + lane < ldw) ? arow[wb + lane] : 0ull;
-                unsigned m = __ballot_sync(FULL, aw != 0ull);
-                while (m) {
-                    const int sl = __ffs(m) - 1;
-                    m &= m - 1;
-                    uint64_t bits = __shfl_sync(FULL, aw, sl);
-                    const int64_t kbase = (wb + sl) * 64;
-                    while (bits) {
-                        const int b0 = __ffsll(static_cast<long long>(bits)) - 1;
-                        bits &= bits - 1;
-                        int b1 = -1;
-                        if (bits) {
-                            b1 = __ffsll(static_cast<long long>(bits)) - 1;
-                            bits &= bits - 1;
-                        }
-                        const uint64_t* r0 = B + (kbase + b0) * ldw + c0;
-                        const uint64_t* r1 = B + (kbase + (b1 < 0 ? b0 : b1)) * ldw + c0;
-                        uint4 x0[VEC], x1[VEC];
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = kw * 64 + bh * 4 + q;
+            b[q] = (bcol && k < n) ? B[k * ldw + c0 + bc] : 0ull;
+        }
+    };
+    auto build = [&](int buf, const uint64_t (&b)[4]) {
+        uint64_t* t = m4t + buf * kM4TableWords + bh * 16 * kM4Cols + bc;
+        const uint64_t e3 = b[0] | b[1], e5 = b[2] | b[0], e6 = b[2] | b[1], e7 = b[2] | e3;
+        t[0 * kM4Cols] = 0ull;
+        t[1 * kM4Cols] = b[0];
+        t[2 * kM4Cols] = b[1];
+        t[3 * kM4Cols] = e3;
+        t[4 * kM4Cols] = b[2];
+        t[5 * kM4Cols] = e5;
+        t[6 * kM4Cols] = e6;
+        t[7 * kM4Cols] = e7;
+        t[8 * kM4Cols] = b[3];
+        t[9 * kM4Cols] = b[3] | b[0];
+        t[10 * kM4Cols] = b[3] | b[1];
+        t[11 * kM4Cols] = b[3] | e3;
+        t[12 * kM4Cols] = b[3] | b[2];
+        t[13 * kM4Cols] = b[3] | e5;
+        t[14 * kM4Cols] = b[3] | e6;
+        t[15 * kM4Cols] = b[3] | e7;
+    };
+    // lookups: rows row0 + lr + 32 j, words c0 + 2 lc, c0 + 2 lc + 1
+    const int lr = tid >> 3, lc = tid & 7;
+    const int64_t wcol = c0 + 2 * lc;  // ldw is even, so wcol < ldw covers both words
+    uint4 acc[kM4RowsPerThread];
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            const int64_t w = 2 * (lane + 32 * v);
-                            if (c0 + w < ldw) {
-                                x0[v] = __ldg(reinterpret_cast<const uint4*>(r0 + w));
-                                x1[v] = __ldg(reinterpret_cast<const uint4*>(r1 + w));
-                            } else {
-                                x0[v] = make_uint4(0, 0, 0, 0);
-                                x1[v] = x0[v];
-                            }
-                        }
+    for (int j = 0; j < kM4RowsPerThread; ++j) {
+        const int64_t i = row0 + lr + 32 * j;
+        acc[j] = (or_a && i < n && wcol < ldw) ? *reinterpret_cast<const uint4*>(A + i * ldw + wcol)
+                                               : make_uint4(0, 0, 0, 0);
+    }
+    uint64_t bq[4];
+    if (kwn > 0) {
+        load_b(0, bq);
+        build(0, bq);
+    }
+    for (int64_t kw = 0; kw < kwn; ++kw) {
+        int stop = 0;
+        if (tid == 0 && dl.budget_ns && (kw & 63) == 0) stop = dl.past() ? 1 : 0;
+        // table kw is complete, and every thread is done with table kw - 1, whose buffer the next build reuses
+        if (__syncthreads_or(stop)) return;
+        if (kw + 1 < kwn) load_b(kw + 1, bq);
+        uint64_t aw[kM4RowsPerThread];
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            or4(acc[v], x0[v]);
-                            or4(acc[v], x1[v]);
-                        }
-                    }
-                }
-            }
+        for (int j = 0; j < kM4RowsPerThread; ++j) {
+            const int64_t i = row0 + lr + 32 * j;
+            aw[j] = i < n ? A[i * ldw + kw] : 0ull;
+        }
+        const char* tb = reinterpret_cast<const char*>(m4t + (kw & 1) * kM4TableWords) + lc * 16;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const int64_t w = c0 + 2 * (lane + 32 * v);
-                if (w < ldw) {
-                    const uint4 o = *reinterpret_cast<const uint4*>(arow + w);  // A_i: the squaring's old row
-                    any |= (o.x ^ acc[v].x) | (o.y ^ acc[v].y) | (o.z ^ acc[v].z) | (o.w ^ acc[v].w);
-                    *reinterpret_cast<uint4*>(dst + i * ldw + w) = acc[v];
+        for (int j = 0; j < kM4RowsPerThread; ++j) {
+            if (aw[j] == 0ull) continue;
+#pragma unroll
+            for (int h = 0; h < 16; ++h) {
+                const uint32_t half = h < 8 ? static_cast<uint32_t>(aw[j]) : static_cast<uint32_t>(aw[j] >> 32);
+                const uint32_t x = (half >> (4 * (h & 7))) & 15u;
+                if (x) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(tb + (h * 16 + x) * (kM4Cols * 8));
+                    acc[j].x |= v.x;
+                    acc[j].y |= v.y;
+                    acc[j].z |= v.z;
+                    acc[j].w |= v.w;
                 }
             }
         }
+        if (kw + 1 < kwn) build(static_cast<int>((kw + 1) & 1), bq);
     }
-    if (__any_sync(FULL, any != 0) && lane == 0) atomicOr(changed, 1);
+    uint32_t any = 0;
+#pragma unroll
+    for (int j = 0; j < kM4RowsPerThread; ++j) {
+        const int64_t i = row0 + lr + 32 * j;
+        if (i < n && wcol < ldw) {
+            const uint4 o = *reinterpret_cast<const uint4*>(A + i * ldw + wcol);  // A_i: the squaring's old row
+            any |= (o.x ^ acc[j].x) | (o.y ^ acc[j].y) | (o.z ^ acc[j].z) | (o.w ^ acc[j].w);
+            *reinterpret_cast<uint4*>(dst + i * ldw + wcol) = acc[j];
+        }
+    }
+    if (__any_sync(FULL, any != 0) && (tid & 31) == 0) atomicOr(changed, 1);
 }
 
 // ---- word-CSR of packed rows
@@ -1383,13 +1422,14 @@ inline int warps_grid(int64_t rows, int sms) {
 
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
                                   int or_a, int* changed, int sms, cudaStream_t s, Deadline dl) {
-    const int grid = warps_grid(n, sms);
-    if (ldw <= 128)
-        product_packed_kernel<2><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
-    else if (ldw <= 256)
-        product_packed_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
-    else
-        product_packed_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl);
+    (void)sms;
+    if (n <= 0) return cudaSuccess;
+    const int64_t grid = ((n + kM4Rows - 1) / kM4Rows) * ((ldw + kM4Cols - 1) / kM4Cols);
+    cudaError_t e = cudaFuncSetAttribute(product_m4rm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kM4Smem));
+    if (e != cudaSuccess) return e;
+    product_m4rm_kernel<<<static_cast<unsigned>(grid), kM4Threads, kM4Smem, s>>>(A, B, dst, n, ldw, or_a, changed,
+                                                                                   dl);
     return cudaGetLastError();
 }
 

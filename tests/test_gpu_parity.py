@@ -248,7 +248,7 @@ def test_smp_wide_rows_long_paths(ctx):
 
 # ------------------------------------------------------------ compose --
 @pytest.mark.parametrize("variant", ["rms_tc", "rms_packed"])
-@pytest.mark.parametrize("n,seed", [(1, 0), (77, 1), (256, 2), (513, 3)])
+@pytest.mark.parametrize("n,seed", [(1, 0), (77, 1), (256, 2), (513, 3), (1100, 4), (2100, 5)])
 def test_compose(ctx, variant, n, seed):
     ip1, ix1, m1 = er_case(n, 1.0, seed)
     ip2, ix2, m2 = er_case(n, 1.4, seed + 50)
