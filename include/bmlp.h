@@ -163,7 +163,11 @@ typedef struct bmlp_stats {
                                   (few, and holding few ones: R close to its
                                   closure); counted in iterations, not in
                                   product_launches                              */
-    int32_t reserved2;         /* 0                                             */
+    int32_t table_squarings;   /* BMLP_RMS_PACKED: whole-row squarings run on
+                                  shared-memory tables of 4-row ORs (Four
+                                  Russians; once R's nonzero words hold >= 10
+                                  bits on average, and the first whole-row
+                                  step); the others gathered the named rows   */
 } bmlp_stats;
 
 typedef struct bmlp_ctx bmlp_ctx;

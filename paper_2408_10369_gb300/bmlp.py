@@ -63,7 +63,7 @@ class bmlp_stats(ctypes.Structure):
                 ("issued_ops", ctypes.c_double), ("e2m1_products", ctypes.c_int32), ("frontier_squarings", ctypes.c_int32),
                 ("sparse_squarings", ctypes.c_int32), ("sliced_closures", ctypes.c_int32), ("sparse_ms", ctypes.c_double),
                 ("sparse_words", ctypes.c_double), ("host_syncs", ctypes.c_int32), ("cluster_frontiers", ctypes.c_int32),
-                ("thin_squarings", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("thin_squarings", ctypes.c_int32), ("table_squarings", ctypes.c_int32)]
 
 
 class bmlp_problem(ctypes.Structure):

@@ -105,6 +105,9 @@ constexpr int WS_SCAN = 34;
 // squaring restricted to the rows and columns that still hold zeros.
 constexpr int WS_THIN_P = 35, WS_THIN_AUX = 36, WS_THIN_T = 37;
 constexpr int64_t kSquareMinN = 4096;
+// Bits per nonzero word of R from which a whole-row bit-row squaring uses the Four Russians tables instead of
+// gathering the named rows (measured at n = 8,192 and 16,384: equal times at 9.5 and 11.5 bits).
+constexpr double kM4MinBitsPerWord = 10.0;
 constexpr int kSquareMaxSteps = 3;  // measured: chains with 1 % shortcuts are fastest after 3 (band of 8)
 // A squaring is kept while it grows the rows' nonzero words by at most this factor (path-like relations).
 constexpr double kSquareMaxGrowth = 1.5;
@@ -685,9 +688,14 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
         CK(host_sync(ctx, s), "read word count");
         sparse = !half_full();
     }
+    // ones and nonzero words of the current R, counted by the whole-row step that wrote it (-1: not counted, as
+    // after a word-indexed step)
+    auto* pstat = reinterpret_cast<unsigned long long*>(ctx->d_ctl + CTL_PSTAT);
+    int64_t ones = -1, words = -1;
     for (int it = 0; it < max_iters; ++it) {
         const int nxt = cur ^ 1;
         CK(cudaMemsetAsync(ctx->d_ctl, 0, 2 * sizeof(int), s), "reset flags");
+        CK(cudaMemsetAsync(pstat, 0, 2 * sizeof(unsigned long long), s), "reset counts");
         ST(tm.begin());
         if (sparse) {
             CK(launch_square_rows(static_cast<int64_t*>(wptr), static_cast<int32_t*>(widx),
@@ -696,9 +704,13 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
                "word-indexed squaring launch");
             ctx->stats.sparse_squarings++;
         } else {
+            // whole rows: the Four Russians tables once the nonzero words of R carry many bits (their cost does not
+            // depend on the bits; gathering the named rows costs one row of R per one)
+            const bool tables = ones < 0 || static_cast<double>(ones) >= kM4MinBitsPerWord * static_cast<double>(words);
             CK(launch_product_packed(P[cur], P[cur], P[nxt], n, ldw, 1, ctx->d_ctl + CTL_CHANGED, ctx->sm_count, s,
-                                     deadline_of(ctx)),
+                                     deadline_of(ctx), pstat, tables),
                "packed product launch");
+            if (tables) ctx->stats.table_squarings++;
         }
         ST(tm.end());
         ctx->stats.product_launches++;
@@ -707,6 +719,14 @@ bmlp_status rms_packed_loop(bmlp_ctx* ctx, int64_t n, int64_t ldw, uint64_t* P[2
         int changed = 0;
         ST(read_ctl(ctx, s, &changed));
         ST(tm.collect());
+        if (sparse) {
+            ones = words = -1;
+        } else {
+            unsigned long long cnt[2];
+            memcpy(cnt, ctx->h_ctl + CTL_PSTAT, sizeof(cnt));
+            ones = static_cast<int64_t>(cnt[0]);
+            words = static_cast<int64_t>(cnt[1]);
+        }
         *iters = it + 1;
         cur = nxt;
         if (!changed) {

@@ -151,11 +151,11 @@ struct bmlp_ctx {
 
 namespace bmlp {
 
-// CTL_QCOUNT, CTL_T0, CTL_ISSUED and CTL_BITS are 64-bit words, CTL_COST two of them and CTL_THIN eight (two ints
-// each, 8-byte aligned).
+// CTL_QCOUNT, CTL_T0, CTL_ISSUED and CTL_BITS are 64-bit words, CTL_COST and CTL_PSTAT (the ones and nonzero words
+// a bit-row squaring wrote) two of them and CTL_THIN eight (two ints each, 8-byte aligned).
 enum CtlWord : int {
     CTL_CHANGED = 0, CTL_ERROR = 1, CTL_ITERS = 2, CTL_LEVELS = 3, CTL_QCOUNT = 4, CTL_T0 = 6, CTL_BUDGET = 8,
-    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_BITS = 32, CTL_WORDS = 34
+    CTL_ISSUED = 10, CTL_COST = 12, CTL_THIN = 16, CTL_BITS = 32, CTL_PSTAT = 34, CTL_WORDS = 38
 };
 // The pinned host mirror has two more ints: CTL_HOST_I64 is a 64-bit slot for values read from elsewhere.
 constexpr int CTL_HOST_I64 = CTL_WORDS;
@@ -288,9 +288,15 @@ cudaError_t prepare_tc_group();
 // ---- packed kernels (packed.cu)
 // dst_i = (or_a ? A_i : 0) | OR_{k : A_ik = 1} B_k over n packed rows of ldw
 // words; raises *changed when dst_i != A_i. With A = B and or_a = 1 this is
-// one squaring step R <- R + R R.
+// one squaring step R <- R + R R. tables: the Four Russians form (shared-memory
+// tables of 4-row ORs; its time does not depend on the bits per word), else one
+// warp per row gathering the named rows of B (time in proportion to the ones
+// of A). pstat (or nullptr): the ones and the nonzero words of dst are added
+// into pstat[0] and pstat[1].
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
-                                  int or_a, int* changed, int sms, cudaStream_t s, Deadline dl = Deadline{0, nullptr, nullptr});
+                                  int or_a, int* changed, int sms, cudaStream_t s,
+                                  Deadline dl = Deadline{0, nullptr, nullptr}, unsigned long long* pstat = nullptr,
+                                  bool tables = true);
 // word-CSR of packed rows: counts -> (exclusive scan by caller kernel) -> fill
 // (widx / wval must hold n * ldw entries: the dense worst case; wptr holds n + 2 entries, wptr[n + 1] receives
 // the largest row's count)

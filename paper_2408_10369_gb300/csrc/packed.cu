@@ -1,12 +1,14 @@
 // Bit-packed kernels: rows of R are uint64 bit codes (paper Sec. 3.2, bit j
 // of row i = R_ij, least significant bit first).
 //
-//  * product_m4rm  one Boolean product on bitsets, C_i = OR_{k : A_ik = 1} B_k,
-//                 optionally OR-ed with A_i; with A = B = R that is one
-//                 squaring step of Eq. 4: C_i = R_i | OR_{k : R_ik = 1} R_k.
-//                 Tiles of 256 rows x 1,024 columns; per word of A, 16
-//                 shared-memory tables of the ORs of 4 rows of B (Four
-//                 Russians), one lookup per nonzero nibble of A_i.
+//  * product_m4rm / product_gather  one Boolean product on bitsets,
+//                 C_i = OR_{k : A_ik = 1} B_k, optionally OR-ed with A_i; with
+//                 A = B = R that is one squaring step of Eq. 4:
+//                 C_i = R_i | OR_{k : R_ik = 1} R_k. Dense words: tiles of 256
+//                 rows x 1,024 columns, per word of A 16 shared-memory tables
+//                 of the ORs of 4 rows of B (Four Russians), one lookup per
+//                 nibble; few bits per word: one warp per row gathers the
+//                 named rows of B.
 //  * wcsr_build   the nonzero words of every row (word index + value), so
 //                 that frontier expansion touches only words that hold bits.
 //  * smp_packed   the selective product of Eq. 5 / Algorithm 2 per query row:
@@ -47,14 +49,137 @@ __device__ __forceinline__ void warp_transpose64(uint64_t a0, uint64_t a1, int l
     }
 }
 
+__device__ __forceinline__ void or4(uint4& a, const uint4& b) {
+    a.x |= b.x;
+    a.y |= b.y;
+    a.z |= b.z;
+    a.w |= b.w;
+}
+
+// Ones and nonzero words of two output words (a uint4), and a block's totals added into pstat[0] / pstat[1]
+// (called by every thread of the block: one pair of atomics per block, since all blocks add to the same two words).
+__device__ __forceinline__ void count_words(const uint4& v, unsigned long long& ones, unsigned long long& words) {
+    ones += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    words += ((v.x | v.y) != 0u ? 1u : 0u) + ((v.z | v.w) != 0u ? 1u : 0u);
+}
+__device__ __forceinline__ void block_add_counts(unsigned long long* pstat, unsigned long long ones,
+                                                 unsigned long long words) {
+    __shared__ unsigned long long part[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ones += __shfl_xor_sync(FULL, ones, off);
+        words += __shfl_xor_sync(FULL, words, off);
+    }
+    if (lane == 0) {
+        part[0][warp] = ones;
+        part[1][warp] = words;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = static_cast<int>(blockDim.x >> 5);
+        ones = lane < nw ? part[0][lane] : 0ull;
+        words = lane < nw ? part[1][lane] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ones += __shfl_xor_sync(FULL, ones, off);
+            words += __shfl_xor_sync(FULL, words, off);
+        }
+        if (lane == 0 && (ones | words) != 0ull) {
+            atomicAdd(pstat, ones);
+            atomicAdd(pstat + 1, words);
+        }
+    }
+}
+
+// ---- one Boolean product on bit rows by gathering the named rows
+// C_i = (A_i if or_a) OR (OR over the set bits k of A_i of B_k): one warp per row i; the set bits of A_i are found
+// with warp ballots and find-first-set, and row k is ORed in with coalesced 128-bit loads (two rows in flight).
+// Its work is nnz(A_i) rows of B per row: the form for rows with few bits per nonzero word.
+template <int VEC>
+__global__ void __launch_bounds__(256) product_gather_kernel(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                                                             uint64_t* __restrict__ dst, int64_t n, int64_t ldw, int or_a,
+                                                             int* changed, Deadline dl,
+                                                             unsigned long long* __restrict__ pstat) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t chunk_words = 64 * VEC;  // 32 lanes x VEC x 2 words
+    uint32_t any = 0;
+    unsigned long long ones = 0, words = 0;  // of the rows written
+    for (int64_t i = warp_id; i < n; i += nwarps) {
+        if (dl.budget_ns && __shfl_sync(FULL, lane == 0 ? static_cast<int>(dl.past()) : 0, 0)) break;
+        const uint64_t* arow = A + i * ldw;
+        for (int64_t c0 = 0; c0 < ldw; c0 += chunk_words) {
+            uint4 acc[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t w = c0 + 2 * (lane + 32 * v);
+                acc[v] = (or_a && w < ldw) ? *reinterpret_cast<const uint4*>(arow + w) : make_uint4(0, 0, 0, 0);
+            }
+            for (int64_t wb = 0; wb < ldw; wb += 32) {
+                const uint64_t aw = (wb + lane < ldw) ? arow[wb + lane] : 0ull;
+                unsigned m = __ballot_sync(FULL, aw != 0ull);
+                while (m) {
+                    const int sl = __ffs(m) - 1;
+                    m &= m - 1;
+                    uint64_t bits = __shfl_sync(FULL, aw, sl);
+                    const int64_t kbase = (wb + sl) * 64;
+                    while (bits) {
+                        const int b0 = __ffsll(static_cast<long long>(bits)) - 1;
+                        bits &= bits - 1;
+                        int b1 = -1;
+                        if (bits) {
+                            b1 = __ffsll(static_cast<long long>(bits)) - 1;
+                            bits &= bits - 1;
+                        }
+                        const uint64_t* r0 = B + (kbase + b0) * ldw + c0;
+                        const uint64_t* r1 = B + (kbase + (b1 < 0 ? b0 : b1)) * ldw + c0;
+                        uint4 x0[VEC], x1[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const int64_t w = 2 * (lane + 32 * v);
+                            if (c0 + w < ldw) {
+                                x0[v] = __ldg(reinterpret_cast<const uint4*>(r0 + w));
+                                x1[v] = __ldg(reinterpret_cast<const uint4*>(r1 + w));
+                            } else {
+                                x0[v] = make_uint4(0, 0, 0, 0);
+                                x1[v] = x0[v];
+                            }
+                        }
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            or4(acc[v], x0[v]);
+                            or4(acc[v], x1[v]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t w = c0 + 2 * (lane + 32 * v);
+                if (w < ldw) {
+                    const uint4 o = *reinterpret_cast<const uint4*>(arow + w);  // A_i: the squaring's old row
+                    any |= (o.x ^ acc[v].x) | (o.y ^ acc[v].y) | (o.z ^ acc[v].z) | (o.w ^ acc[v].w);
+                    *reinterpret_cast<uint4*>(dst + i * ldw + w) = acc[v];
+                    if (pstat != nullptr) count_words(acc[v], ones, words);
+                }
+            }
+        }
+    }
+    if (__any_sync(FULL, any != 0) && lane == 0) atomicOr(changed, 1);
+    if (pstat != nullptr) block_add_counts(pstat, ones, words);
+}
+
 // ---- one Boolean product on bit rows by the method of Four Russians (Arlazarov, Dinic, Kronrod, Faradzev 1970)
 // C_i = (A_i if or_a) OR (OR over the set bits k of A_i of B_k). A CTA owns a tile of kM4Rows rows and kM4Cols
 // words (64 kM4Cols columns) of C and walks k one word of A (64 values of k) at a time. For each nibble h of that
 // word it tabulates, in shared memory, the 16 ORs of the four B rows 64 kw + 4 h .. 64 kw + 4 h + 3 over the tile's
-// columns; a row then ORs in one table entry per nonzero nibble of its A word instead of one B row per set bit.
-// So an output word costs at most n / 4 shared-memory reads however dense A is, where gathering the named rows
-// costs nnz(A_i) reads of B through L2. The tables are double buffered (one barrier per word of A), and the B
-// words of the next table are loaded while the current one is read.
+// columns; a row then ORs in one table entry per nibble of each nonzero word of A_i instead of one B row per set
+// bit. So an output word costs at most n / 4 shared-memory reads however dense A is, where gathering the named
+// rows costs nnz(A_i) reads of B through L2. Every nibble of a nonzero word is looked up, zero or not (measured
+// faster than testing each: the loads issue back to back). The tables are double buffered (one barrier per word
+// of A), and the B words of the next table are loaded while the current one is read.
 // Thread layouts: a table is built by thread (h = tid / 16, column word c = tid % 16), entry x at T[h][x][c]; a
 // lookup thread owns row slot r = tid / 8 (rows r, r + 32, ..., r + 224 of the tile) and the column words
 // 2 (tid % 8), 2 (tid % 8) + 1, so each row slot reads one whole 128-byte entry per lookup (no bank conflicts).
@@ -68,7 +193,8 @@ constexpr size_t kM4Smem = 2 * kM4TableWords * sizeof(uint64_t);
 __global__ void __launch_bounds__(kM4Threads, 2) product_m4rm_kernel(const uint64_t* __restrict__ A,
                                                                      const uint64_t* __restrict__ B,
                                                                      uint64_t* __restrict__ dst, int64_t n,
-                                                                     int64_t ldw, int or_a, int* changed, Deadline dl) {
+                                                                     int64_t ldw, int or_a, int* changed, Deadline dl,
+                                                                     unsigned long long* __restrict__ pstat) {
     extern __shared__ __align__(16) uint64_t m4t[];
     const int tid = threadIdx.x;
     const int64_t nch = (ldw + kM4Cols - 1) / kM4Cols;
@@ -139,19 +265,18 @@ __global__ void __launch_bounds__(kM4Threads, 2) product_m4rm_kernel(const uint6
 #pragma unroll
             for (int h = 0; h < 16; ++h) {
                 const uint32_t half = h < 8 ? static_cast<uint32_t>(aw[j]) : static_cast<uint32_t>(aw[j] >> 32);
-                const uint32_t x = (half >> (4 * (h & 7))) & 15u;
-                if (x) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(tb + (h * 16 + x) * (kM4Cols * 8));
-                    acc[j].x |= v.x;
-                    acc[j].y |= v.y;
-                    acc[j].z |= v.z;
-                    acc[j].w |= v.w;
-                }
+                const uint32_t x = (half >> (4 * (h & 7))) & 15u;  // entry 0 is zero: no test needed
+                const uint4 v = *reinterpret_cast<const uint4*>(tb + (h * 16 + x) * (kM4Cols * 8));
+                acc[j].x |= v.x;
+                acc[j].y |= v.y;
+                acc[j].z |= v.z;
+                acc[j].w |= v.w;
             }
         }
         if (kw + 1 < kwn) build(static_cast<int>((kw + 1) & 1), bq);
     }
     uint32_t any = 0;
+    unsigned long long ones = 0, words = 0;
 #pragma unroll
     for (int j = 0; j < kM4RowsPerThread; ++j) {
         const int64_t i = row0 + lr + 32 * j;
@@ -159,9 +284,11 @@ __global__ void __launch_bounds__(kM4Threads, 2) product_m4rm_kernel(const uint6
             const uint4 o = *reinterpret_cast<const uint4*>(A + i * ldw + wcol);  // A_i: the squaring's old row
             any |= (o.x ^ acc[j].x) | (o.y ^ acc[j].y) | (o.z ^ acc[j].z) | (o.w ^ acc[j].w);
             *reinterpret_cast<uint4*>(dst + i * ldw + wcol) = acc[j];
+            if (pstat != nullptr) count_words(acc[j], ones, words);
         }
     }
     if (__any_sync(FULL, any != 0) && (tid & 31) == 0) atomicOr(changed, 1);
+    if (pstat != nullptr) block_add_counts(pstat, ones, words);
 }
 
 // ---- word-CSR of packed rows
@@ -1421,15 +1548,25 @@ inline int warps_grid(int64_t rows, int sms) {
 }  // namespace
 
 cudaError_t launch_product_packed(const uint64_t* A, const uint64_t* B, uint64_t* dst, int64_t n, int64_t ldw,
-                                  int or_a, int* changed, int sms, cudaStream_t s, Deadline dl) {
-    (void)sms;
+                                  int or_a, int* changed, int sms, cudaStream_t s, Deadline dl,
+                                  unsigned long long* pstat, bool tables) {
     if (n <= 0) return cudaSuccess;
+    if (!tables) {
+        const int grid = warps_grid(n, sms);
+        if (ldw <= 128)
+            product_gather_kernel<2><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl, pstat);
+        else if (ldw <= 256)
+            product_gather_kernel<4><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl, pstat);
+        else
+            product_gather_kernel<8><<<grid, 256, 0, s>>>(A, B, dst, n, ldw, or_a, changed, dl, pstat);
+        return cudaGetLastError();
+    }
     const int64_t grid = ((n + kM4Rows - 1) / kM4Rows) * ((ldw + kM4Cols - 1) / kM4Cols);
     cudaError_t e = cudaFuncSetAttribute(product_m4rm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kM4Smem));
     if (e != cudaSuccess) return e;
     product_m4rm_kernel<<<static_cast<unsigned>(grid), kM4Threads, kM4Smem, s>>>(A, B, dst, n, ldw, or_a, changed,
-                                                                                   dl);
+                                                                                   dl, pstat);
     return cudaGetLastError();
 }
 

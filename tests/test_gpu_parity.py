@@ -194,6 +194,27 @@ def test_closure_long_paths(ctx, variant, n, shape, seed):
         assert ctx.stats()["frontier_squarings"] >= 1
 
 
+@pytest.mark.parametrize("n,seed", [(2560, 1), (2597, 2)])
+def test_packed_squaring_forms(ctx, n, seed):
+    """Whole-row bit-row squarings in both forms: edges only into the columns
+    64 w keep one bit per nonzero word through every squaring, while more than
+    half the words are nonzero from the start. The first whole-row step runs
+    on the Four Russians tables (its input's bits per word are not counted
+    yet), the later ones gather the named rows."""
+    rng = np.random.default_rng(seed)
+    cols = np.arange(0, n, 64)
+    keep = rng.random((n, len(cols))) < 0.6
+    src = np.repeat(np.arange(n), keep.sum(1))
+    dst = np.concatenate([cols[k] for k in keep])
+    ip, ix = wl.csr_from_pairs(n, src, dst)
+    want = oracle.closure(n, ip, ix)
+    got, it = run_rms(ctx, wl.dense_u8(n, ip, ix), "rms_packed", fmt="packed")
+    np.testing.assert_array_equal(got, want)
+    st = ctx.stats()
+    assert st["sparse_squarings"] == 0 and it >= 2
+    assert st["table_squarings"] == 1
+
+
 def test_squaring_operand_forms(ctx):
     """Dense R: every squaring on packed E2M1 operands. Block-sparse R (a
     chain with shortcuts): E4M3 squarings with skipped K blocks first, E2M1
