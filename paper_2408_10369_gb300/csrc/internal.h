@@ -287,7 +287,8 @@ cudaError_t prepare_tc_group();
 
 // ---- packed kernels (packed.cu)
 // dst_i = (or_a ? A_i : 0) | OR_{k : A_ik = 1} B_k over n packed rows of ldw
-// words; raises *changed when dst_i != A_i. With A = B and or_a = 1 this is
+// words (ldw even, matrices 16-byte aligned: rows move as 128-bit words; bits
+// of A at columns >= n zero); raises *changed when dst_i != A_i. With A = B and or_a = 1 this is
 // one squaring step R <- R + R R. tables: the Four Russians form (shared-memory
 // tables of 4-row ORs; its time does not depend on the bits per word), else one
 // warp per row gathering the named rows of B (time in proportion to the ones
