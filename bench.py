@@ -728,7 +728,7 @@ def main():
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    prod_ms, prod_n, launches, issued, e2m1_n, sparse_n, thin_n = 0.0, 0, 0, 0.0, 0, 0, 0
+    prod_ms, prod_n, launches, issued, e2m1_n, sparse_n, thin_n, table_n = 0.0, 0, 0, 0.0, 0, 0, 0, 0
     for _ in range(args.steps):
         iters = step(True)
         st = ctx.stats()
@@ -739,6 +739,7 @@ def main():
         e2m1_n += st["e2m1_products"]
         sparse_n += st["sparse_squarings"]
         thin_n += st["thin_squarings"]
+        table_n += st["table_squarings"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -819,7 +820,7 @@ def main():
     kname = "tc_duo_kernel" if fp4 else "tc_duo_kernel_e4m3"
     # what this GPU issues for the kernel's operand kind and form (back-to-back MMAs, no operand traffic):
     # one M256 N256 K64 MMA per CTA pair for the 4-bit kernel, M128 N256 K32 per CTA for the E4M3 one
-    issue = ctx.mma_issue_rate(2 if fp4 else 0)
+    issue = ctx.mma_issue_rate(2 if fp4 else 0) if args.variant == "rms_tc" else None
     roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(kname, n),
             "peak_source": "%s bf16 burst x %g (%s nominal); the product runs unthrottled at max SM clock"
@@ -828,6 +829,25 @@ def main():
             "issue_rate_kind": "tcgen05 kind::mxf4 M256 N256 K64 .cta_group::2" if fp4
                                else "tcgen05 kind::f8f6f4 M128 N256 K32",
             "issue_rate_peak": issue, "issue_rate_frac": (achieved / issue) if achieved and issue else None}
+    if args.variant != "rms_tc":
+        # the tensor-core roofline above describes the rms_tc path; the other variants' kernels are measured by the
+        # secondary workloads (bit-row product, frontier batches) of the default run
+        roof = {"bound": None, "kernel": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "note": "reported for the default variant (rms_tc)"}
+    steps_div = max(args.steps, 1)
+    if args.variant == "rms_tc":
+        dtype = ("e2m1 0/1 operands (UE8M0 block scales of 1), fp32 accumulate" if fp4
+                 else "e4m3 0/1 operands, fp32 accumulate")
+        counts = {"bit_row_squarings": sparse_n // steps_div, "tensor_core_squarings": prod_n // steps_div,
+                  "zero_row_column_squarings": thin_n // steps_div}
+    elif args.variant == "rms_packed":
+        dtype = "u64 bit rows (64-bit word OR)"
+        counts = {"word_indexed_squarings": sparse_n // steps_div,
+                  "whole_row_squarings": (prod_n - sparse_n) // steps_div,
+                  "table_squarings": table_n // steps_div}
+    else:
+        dtype = "u64 bit rows (64-bit word OR)" if args.variant == "smp_packed" else "e4m3 0/1 operands, fp32 accumulate"
+        counts = {"frontier_levels": iters}
     if rank != 0:
         ctx.close()
         if world > 1:
@@ -857,13 +877,9 @@ def main():
                "closure_s": t_full, "closure_s_1_thread": t1_full}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": ("e2m1 0/1 operands (UE8M0 block scales of 1), fp32 accumulate" if fp4
-                                           else "e4m3 0/1 operands, fp32 accumulate"), "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": "er_n%d_deg%g" % (n, args.degree), "n": n, "mean_out_degree": args.degree,
-                       "seed": "rank", "variant": args.variant, "iterations": iters,
-                       "bit_row_squarings": sparse_n // max(args.steps, 1),
-                       "tensor_core_squarings": prod_n // max(args.steps, 1),
-                       "zero_row_column_squarings": thin_n // max(args.steps, 1), "nnz": int(len(ix)),
+                       "seed": "rank", "variant": args.variant, "iterations": iters, **counts, "nnz": int(len(ix)),
                        "graphs_per_s": args.steps * world / t,
                        "fmt": args.fmt,
                        "l2": ("operands larger than L2 (%.2f GiB per E2M1 matrix, %.0f MiB input)"
